@@ -1,0 +1,297 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics
+(closed forms, brute force, invariants, published test vectors).  None of
+these checks re-types an oracle formula; each would fail for a dropped term,
+a wrong sign or index, or a transposed operand in the oracle."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------- generator pins
+def test_philox_known_answers():
+    """Philox4x32-10 against the published known-answer vectors."""
+    rows = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            w = [int(v, 16) for v in line.split()]
+            out = oracle.philox4x32_10(w[0:4], w[4:6])
+            assert [int(v) for v in out] == w[6:10]
+            rows += 1
+    assert rows == 3
+
+
+@pytest.mark.parametrize("n,p", [(1, 1), (2, 1), (17, 4), (1000, 7), (4096, 16), (65, 64)])
+def test_random_partition_is_even_bijection(n, p):
+    """Alg. DC-KRR lines 1-5: a shuffle (a bijection) cut into p even parts,
+    the larger parts first."""
+    perm, offsets, assign = oracle.partition_random(n, p, 99)
+    assert np.array_equal(np.sort(perm), np.arange(n))
+    sizes = np.diff(offsets)
+    assert sizes.sum() == n and sizes.max() - sizes.min() <= 1
+    assert np.all(np.diff(sizes) <= 0)
+    for j in range(p):
+        assert np.all(assign[perm[offsets[j]:offsets[j + 1]]] == j)
+
+
+def test_random_partition_depends_on_seed():
+    a, _, _ = oracle.partition_random(500, 4, 1)
+    b, _, _ = oracle.partition_random(500, 4, 2)
+    assert not np.array_equal(a, b)
+    c, _, _ = oracle.partition_random(500, 4, 1)
+    assert np.array_equal(a, c)
+
+
+# ----------------------------------------------------------- kernel pins
+def test_gaussian_kernel_hand_values():
+    """Table 1 Gaussian kernel against hand-computed values."""
+    with open(os.path.join(GOLDEN, "gaussian_kernel_hand.txt")) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            s, a, b, v = [f.strip() for f in line.split("|")]
+            A = np.array([[float(x) for x in a.split(",")]])
+            B = np.array([[float(x) for x in b.split(",")]])
+            K = oracle.kernel_matrix(A, B, float(s))
+            assert abs(K[0, 0] - float(v)) <= 2e-16 * max(1.0, float(v))
+
+
+def test_linear_kernel_hand_value():
+    A = np.array([[1.0, 2.0, 3.0]])
+    B = np.array([[4.0, -5.0, 6.0]])
+    assert oracle.kernel_matrix(A, B, 1.0, oracle.KIND_LINEAR)[0, 0] == 12.0
+
+
+def test_kernel_matrix_structure():
+    """K symmetric, unit diagonal, entries in (0, 1]."""
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((40, 7))
+    K = oracle.kernel_matrix(X, X, 1.7)
+    assert np.array_equal(K, K.T)
+    assert np.all(np.diag(K) == 1.0)
+    assert np.all(K > 0) and np.all(K <= 1.0)
+    # direct-difference brute force in exact rational arithmetic of the squared distance
+    i, j = 3, 17
+    dd = math.fsum((float(a) - float(b)) ** 2 for a, b in zip(X[i], X[j]))
+    assert abs(K[i, j] - math.exp(-dd / (2 * 1.7 ** 2))) <= 1e-15
+
+
+# ----------------------------------------------------------- solve pins
+def _data(m, d, seed=0):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((m, d))
+    y = np.sin(X[:, 0]) + 0.1 * rng.standard_normal(m)
+    return X, y
+
+
+@pytest.mark.parametrize("m,sigma,lam", [(8, 1.0, 1e-3), (33, 2.0, 1e-4), (64, 3.0, 1e-2)])
+def test_solve_matches_high_precision_inverse(m, sigma, lam):
+    """Eq. 6 against an explicit inverse in 40-digit arithmetic (m <= 64)."""
+    mpmath = pytest.importorskip("mpmath")
+    X, y = _data(m, 5, m)
+    alpha, info, rc = oracle.fit(X, y, sigma, lam)
+    assert rc == 0
+    K = oracle.kernel_matrix(X, X, sigma)
+    mpmath.mp.dps = 40
+    A = mpmath.matrix(K.tolist())
+    for i in range(m):
+        A[i, i] += mpmath.mpf(lam) * m
+    exact = (A ** -1) * mpmath.matrix(y.tolist())
+    exact = np.array([float(v) for v in exact])
+    assert np.max(np.abs(alpha - exact)) <= 1e-13 * np.max(np.abs(exact))
+
+
+def test_sigma_to_zero_closed_form():
+    """sigma -> 0: off-diagonal kernel entries underflow to 0, so K = I and
+    alpha = y / (1 + lambda m); predictions of unseen points vanish."""
+    X, y = _data(50, 5, 3)
+    lam = 1e-3
+    alpha, _, rc = oracle.fit(X, y, 1e-3, lam)
+    assert rc == 0
+    np.testing.assert_allclose(alpha, y / (1 + lam * 50), rtol=1e-15, atol=0)
+    Xt = np.random.default_rng(9).standard_normal((5, 5))
+    assert np.all(oracle.predict(X, alpha, Xt, 1e-3) == 0.0)
+
+
+def test_sigma_to_infinity_sherman_morrison():
+    """sigma -> inf: K -> 1 1^T and (1 1^T + c I) alpha = y has the
+    Sherman-Morrison solution alpha = (y - 1 (1^T y) / (c + m)) / c, c = lambda m."""
+    m, lam = 40, 0.05
+    X, y = _data(m, 4, 5)
+    alpha, _, rc = oracle.fit(X, y, 1e6, lam)
+    assert rc == 0
+    c = lam * m
+    sm = (y - np.sum(y) / (c + m)) / c
+    np.testing.assert_allclose(alpha, sm, rtol=0, atol=1e-8 * np.abs(sm).max())
+
+
+def test_linear_kernel_equals_primal_ridge():
+    """Linear kernel (Table 1) KRR predictions equal the ridge regression
+    (Eq. 2) closed form xhat^T (X^T X + lambda m I_d)^{-1} X^T y."""
+    m, d, lam = 120, 6, 1e-2
+    X, y = _data(m, d, 11)
+    Xt = np.random.default_rng(12).standard_normal((9, d))
+    alpha, _, rc = oracle.fit(X, y, 1.0, lam, oracle.KIND_LINEAR)
+    assert rc == 0
+    yh = oracle.predict(X, alpha, Xt, 1.0, oracle.KIND_LINEAR)
+    w = np.linalg.solve(X.T @ X + lam * m * np.eye(d), X.T @ y)
+    np.testing.assert_allclose(yh, Xt @ w, rtol=1e-10, atol=1e-12)
+
+
+def test_residual_and_library_cross_check():
+    """Backward error <= 1e-12 and agreement with scipy's Cholesky solve."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    X, y = _data(300, 8, 21)
+    sigma, lam = 2.5, 1e-5
+    alpha, info, rc = oracle.fit(X, y, sigma, lam)
+    assert rc == 0
+    A = oracle.kernel_matrix(X, X, sigma) + lam * 300 * np.eye(300)
+    r = A @ alpha - y
+    assert np.abs(r).max() <= 1e-12 * (np.abs(A).sum(1).max() * np.abs(alpha).max() + np.abs(y).max())
+    ref = scipy_linalg.cho_solve(scipy_linalg.cho_factor(A, lower=True), y)
+    kappa = np.linalg.cond(A)
+    assert np.abs(alpha - ref).max() <= 1e-15 * kappa * np.abs(ref).max() * 10
+    assert info[0] >= kappa * 0.999  # Gershgorin estimate bounds kappa from above
+
+
+def test_not_spd_reported():
+    """A negative shift makes K + lambda m I indefinite: the solve reports it."""
+    X, y = _data(20, 3, 2)
+    _, _, rc = oracle.fit(X, y, 1e-3, -2.0 / 20)
+    assert rc == 1
+
+
+def test_single_row_partition():
+    X = np.array([[0.3, -0.2]])
+    y = np.array([2.0])
+    alpha, _, rc = oracle.fit(X, y, 1.0, 0.5)
+    assert rc == 0 and abs(alpha[0] - 2.0 / 1.5) < 1e-16
+
+
+# ----------------------------------------------------------- predict / MSE pins
+def test_mse_hand_value():
+    assert oracle.mse(np.array([1.0, 2.0, 3.0]), np.array([1.0, 1.0, 1.0])) == 5.0 / 3.0
+
+
+def test_predict_on_training_rows_reproduces_fit():
+    """Eq. 7 at the training rows gives K alpha = y - lambda m alpha."""
+    X, y = _data(60, 4, 8)
+    lam = 1e-3
+    alpha, _, _ = oracle.fit(X, y, 1.5, lam)
+    yh = oracle.predict(X, alpha, X, 1.5)
+    np.testing.assert_allclose(yh, y - lam * 60 * alpha, rtol=0, atol=1e-12)
+
+
+# ----------------------------------------------------------- K-means pins
+def test_assign_brute_force_and_ties():
+    """Alg. 2 step 4: the nearest centre; exact ties go to the lower index."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((500, 6))
+    C = rng.standard_normal((9, 6))
+    got = oracle.assign(X, C)
+    dist = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+    assert np.array_equal(got, np.argmin(dist, axis=1))
+    # exact ties: centres at (+-1, 0), points on the perpendicular bisector
+    C2 = np.array([[1.0, 0.0], [-1.0, 0.0], [1.0, 0.0]])
+    P = np.array([[0.0, 0.5], [0.0, -3.0], [2.0, 0.0]])
+    assert list(oracle.assign(P, C2)) == [0, 0, 0]
+    C3 = np.array([[5.0, 5.0], [-1.0, 0.0], [1.0, 0.0]])
+    assert list(oracle.assign(P, C3)) == [1, 1, 2]
+
+
+def test_kmeans_objective_non_increasing_and_fixed_point():
+    rng = np.random.default_rng(5)
+    X = np.concatenate([rng.standard_normal((300, 3)) + 6 * rng.standard_normal(3) for _ in range(5)])
+    init = rng.choice(len(X), 5, replace=False)
+    prev = np.inf
+    for r in range(1, 8):
+        C, c, delta = oracle.kmeans(X, 5, init, r)
+        obj = ((X - C[c]) ** 2).sum()
+        assert obj <= prev * (1 + 1e-12)
+        prev = obj
+        dist = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+        assert np.array_equal(c, np.argmin(dist, axis=1))
+    assert delta[0] == len(X)  # first round: every point is new
+
+
+def test_kmeans_single_cluster_is_mean():
+    rng = np.random.default_rng(6)
+    X = rng.standard_normal((3000, 4)) * 10
+    C, c, delta = oracle.kmeans(X, 1, [17], 3)
+    exact = np.array([math.fsum(X[:, f]) / 3000 for f in range(4)])
+    np.testing.assert_allclose(C[0], exact, rtol=1e-14, atol=1e-14)
+    assert np.all(c == 0) and list(delta) == [3000, 0]
+
+
+def test_kmeans_empty_cluster_keeps_centre():
+    X = np.array([[0.0], [0.1], [0.2], [10.0]])
+    C0 = np.array([[0.0], [10.0], [100.0]])
+    C = oracle.update_centres(X, np.array([0, 0, 0, 1], np.int32), C0)
+    assert C[2, 0] == 100.0 and C[1, 0] == 10.0
+    assert abs(C[0, 0] - 0.1) < 1e-16
+
+
+def test_gather_stable():
+    rng = np.random.default_rng(7)
+    a = rng.integers(0, 6, 777).astype(np.int32)
+    perm, offsets = oracle.gather_stable(a, 6)
+    assert np.array_equal(perm, np.argsort(a, kind="stable"))
+    assert np.array_equal(np.diff(offsets), np.bincount(a, minlength=6))
+
+
+# ----------------------------------------------------------- selection pins
+def test_select_hand_values_and_ties():
+    yt = np.array([0.0, 0.0])
+    yhat = np.array([[1.0, 1.0], [0.0, 1.0], [1.0, 0.0], [2.0, 0.0]])
+    mses, best = oracle.select(yhat, yt, oracle.SEL_PER_MODEL)
+    assert list(mses) == [1.0, 0.5, 0.5, 2.0] and best == 1
+
+
+def test_single_partition_modes_agree_with_dkrr():
+    """p = 1: random, K-means, routed, per-model and averaged selection all
+    reduce to Alg. 1 (DKRR)."""
+    rng = np.random.default_rng(8)
+    X = rng.standard_normal((80, 3))
+    y = np.cos(X[:, 0])
+    Xt = rng.standard_normal((20, 3))
+    yt = np.cos(Xt[:, 0])
+    sig, lams = [1.0, 2.0], [1e-3]
+    a_dkrr = [oracle.fit(X, y, s, lams[0])[0] for s in sig]
+    ref = [oracle.mse(oracle.predict(X, a, Xt, s), yt) for a, s in zip(a_dkrr, sig)]
+    perm, off, _ = oracle.partition_random(80, 1, 5)
+    al, _, _ = oracle.fit_batch(X, y, np.sort(perm), off, sig, lams)
+    yh = oracle.predict_all(X, np.sort(perm), off, al, sig, lams, Xt)
+    for mode in (oracle.SEL_PER_MODEL, oracle.SEL_AVERAGE, oracle.SEL_ORACLE):
+        mses, best = oracle.select(yh, yt, mode, 1, 2)
+        np.testing.assert_allclose(mses, ref, rtol=1e-12)
+    yr = oracle.predict_all(X, np.sort(perm), off, al, sig, lams, Xt, route=np.zeros(20, np.int32))
+    mses, _ = oracle.select(yr, yt, oracle.SEL_ROUTED)
+    np.testing.assert_allclose(mses, ref, rtol=1e-12)
+
+
+def test_bkrr3_lower_bound():
+    """The per-point best model (BKRR3) never scores worse than routing or
+    than any single partition's model."""
+    rng = np.random.default_rng(10)
+    X = rng.standard_normal((240, 3)) * 2
+    y = np.sin(X.sum(1))
+    Xt = rng.standard_normal((50, 3)) * 2
+    yt = np.sin(Xt.sum(1))
+    C, c, _ = oracle.kmeans(X, 4, [0, 1, 2, 3], 10)
+    perm, off = oracle.gather_stable(c, 4)
+    route = oracle.assign(Xt, C)
+    sig, lams = [1.0], [1e-3]
+    al, _, _ = oracle.fit_batch(X, y, perm, off, sig, lams)
+    yall = oracle.predict_all(X, perm, off, al, sig, lams, Xt)
+    yr = oracle.predict_all(X, perm, off, al, sig, lams, Xt, route=route)
+    m3, _ = oracle.select(yall, yt, oracle.SEL_ORACLE, 4, 1)
+    m2, _ = oracle.select(yr, yt, oracle.SEL_ROUTED)
+    mp, _ = oracle.select(yall, yt, oracle.SEL_PER_MODEL)
+    assert m3[0] <= m2[0] and m3[0] <= mp.min()
