@@ -1,0 +1,382 @@
+"""Benchmark of the BKRR2 hot path on GB300: partition-solves per second.
+
+One step = one pass of the whole hot path over one synthetic BKRR2 workload
+(n = 65536 training and 8192 test rows, d = 90, p = 16 random equal
+partitions, sigma in {1, 4, 16} x lambda in {1e-6, 1e-4}): random partition,
+kernel build + TF32-factor Cholesky + FP64-level refinement of all 96
+(partition, sigma, lambda) solves, all-model prediction of the 8192 test rows,
+best-model selection.  Inputs are resident in HBM when a timed step starts;
+L2 is flushed (512 MB write) before every timed step.  `e2e` repeats the
+measurement through the same public calls with the inputs copied from pinned
+host memory each step and the chosen model read back.
+
+Multi-GPU (torchrun): weak scaling -- every rank fits its own independent
+BKRR2 workload (partitions are independent problems); the one exchange is the
+global best-model choice.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload (it is the deliberately slow reference).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "KRR partition-solves/s & TFLOP/s vs plain FP64 at ≤1e-6 rel err; serve p50/p99"
+UNIT = "partition-solves/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--panel", type=int, default=0, help="Cholesky outer panel width (0 = library default)")
+    ap.add_argument("--cpu-sample", type=int, default=0, help="oracle solves in the CPU baseline (0 = auto)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-path", action="store_true")
+    ap.add_argument("--profile", action="store_true", help="print per-kernel-class times to stderr")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+def _oracle_solve(args):
+    """One full partition-solve pipeline of the oracle (kernel build, Cholesky,
+    refinement, prediction of every test row, MSE)."""
+    Xp, yp, Xt, yt, sigma, lam = args
+    import oracle
+    t0 = time.perf_counter()
+    a, info, rc = oracle.fit(Xp, yp, sigma, lam)
+    yh = oracle.predict(Xp, a, Xt, sigma)
+    m = oracle.mse(yh, yt)
+    return time.perf_counter() - t0, m
+
+
+def _oracle_jobs(w, perm, offsets, count):
+    jobs = []
+    G = len(w["sigmas"]) * len(w["lambdas"])
+    for k in range(count):
+        j = k % (len(offsets) - 1)
+        g = (k * 5 + 2) % G
+        si, li = divmod(g, len(w["lambdas"]))
+        rows = perm[offsets[j]:offsets[j + 1]]
+        jobs.append((w["X"][rows], w["y"][rows], w["Xt"], w["yt"], w["sigmas"][si], w["lambdas"][li]))
+    return jobs
+
+
+def cpu_baseline(w, sample: int):
+    import oracle
+    oracle.build()
+    perm, offsets, _ = oracle.partition_random(w["X"].shape[0], w["p"], w["part_seed"])
+    jobs = _oracle_jobs(w, perm, offsets, sample)
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(processes=sample) as pool:
+        res = pool.map(_oracle_solve, jobs)
+    wall = time.perf_counter() - t0
+    return dict(value=sample / wall, unit=UNIT, cores=sample, kind="oracle",
+                sample="%d of the %d (partition, sigma, lambda) solves of %s, one process each: kernel build + "
+                       "Cholesky + long-double refinement + prediction of all %d test rows + MSE; %.1f s wall"
+                       % (sample, w["p"] * len(w["sigmas"]) * len(w["lambdas"]), w["workload"],
+                          w["Xt"].shape[0], wall))
+
+
+# ---------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                s, m, pw = float(f[1]), float(f[2]), float(f[3])
+            except ValueError:
+                continue
+            mx = max(mx, m)
+            if pw > 200.0:  # under load
+                sm.append(s)
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(self.lines), "samples_under_load": len(sm)}
+
+
+# ---------------------------------------------------------------- our arm
+def solve_flops(m: int, d: int) -> float:
+    """Algorithmic flops of one partition-solve: Cholesky m^3/3, kernel m^2 d,
+    two triangular solves 2 m^2."""
+    return m ** 3 / 3.0 + m * m * d + 2.0 * m * m
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1805_00569_gb300 as K
+    from paper_1805_00569_gb300 import dist as kd, synth
+
+    torch.cuda.set_device(local_rank)
+    w = synth.bkrr2(seed=1 + rank)
+    n, d = w["X"].shape
+    t = w["Xt"].shape[0]
+    p = w["p"]
+    S, L = w["sigmas"], w["lambdas"]
+    G = len(S) * len(L)
+    nsolve = p * G
+    stream = torch.cuda.current_stream()
+    ctx = K.krr_ctx_create(local_rank, stream)
+    if args.panel:
+        K.krr_ctx_set_panel_width(ctx, args.panel)
+    dev = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dt)
+    X, y, Xt, yt = dev(w["X"]), dev(w["y"]), dev(w["Xt"]), dev(w["yt"])
+    yhat_buf = torch.empty((nsolve, t), dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(Xd, yd, Xtd, ytd, prec):
+        _, _, perm, offsets, _ = K.krr_partition(ctx, Xd, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+        model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
+        yh = K.krr_predict(ctx, model, Xtd, out=yhat_buf)
+        mse, best = K.krr_select(ctx, yh, ytd, p, G, K.KRR_SEL_PER_MODEL)
+        model.free()
+        return mse, best, status
+
+    for _ in range(args.warmup):
+        mse, best, status = step(X, y, Xt, yt, args.prec)
+    torch.cuda.synchronize()
+    bad = int((status != K.KRR_OK).sum().item())
+
+    # ---- device-timed steps (inputs resident)
+    clocks = Clocks(local_rank)
+    launches0 = ctx.lib.krr_launch_count()
+    K.krr_ctx_set_profiling(ctx, True)
+    clocks.start()
+    times = []
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mse, best, status = step(X, y, Xt, yt, args.prec)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if world > 1:
+        tdist.barrier()
+    clk = clocks.stop()
+    prof = K.krr_ctx_profile(ctx)
+    K.krr_ctx_set_profiling(ctx, False)
+    launches = ctx.lib.krr_launch_count() - launches0
+    flush_launches = 0
+    total_ms = kd.max_over_ranks(sum(times))
+    gbest, gmse = kd.global_best(mse, rank * nsolve)
+
+    # ---- end to end through the same calls, host inputs
+    hX, hy, hXt, hyt = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+                        (w["X"], w["y"], w["Xt"], w["yt"]))
+    dX, dy, dXt, dyt = (torch.empty_like(a, device="cuda") for a in (hX, hy, hXt, hyt))
+    hbest = torch.empty(1, dtype=torch.int32).pin_memory()
+    hmse = torch.empty(nsolve, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for it in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for h, dd in ((hX, dX), (hy, dy), (hXt, dXt), (hyt, dyt)):
+            dd.copy_(h, non_blocking=True)
+        mse2, best2, _ = step(dX, dy, dXt, dyt, args.prec)
+        hbest.copy_(best2, non_blocking=True)
+        hmse.copy_(mse2, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e_s = kd.max_over_ranks(sum(e2e_times))
+    h2d = sum(a.numel() * a.element_size() for a in (hX, hy, hXt, hyt))
+    d2h = hbest.numel() * 4 + hmse.numel() * 8
+
+    # ---- plain FP64 path, one step, for the comparison the metric names
+    fp64 = None
+    if not args.no_fp64_path and rank == 0:
+        torch.cuda.synchronize()
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, st64 = step(X, y, Xt, yt, "fp64")
+        e1.record(stream)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": nsolve / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
+                "ok_solves": int((st64 == K.KRR_OK).sum().item())}
+    ctx.close()
+
+    ms_per_step = total_ms / args.steps
+    value = world * nsolve * args.steps / (total_ms / 1e3)
+    m = n // p
+    tflops = world * nsolve * solve_flops(m, d) * args.steps / (total_ms / 1e3) / 1e12
+    return dict(w=w, value=value, ms_per_step=ms_per_step, tflops=tflops, prof=prof, clocks=clk,
+                launches=launches + flush_launches, e2e=dict(value=world * nsolve * args.steps / e2e_s, unit=UNIT,
+                                                         h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times)
+
+
+def roofline(res, steps, peaks):
+    """Roofline of the kernel class with the largest share of device time."""
+    prof = res["prof"]
+    w = res["w"]
+    n, d = w["X"].shape
+    p = w["p"]
+    m = n // p
+    G = len(w["sigmas"]) * len(w["lambdas"])
+    t = w["Xt"].shape[0]
+    dom = max(prof, key=lambda k: prof[k][0])
+    ms, launches = prof[dom]
+    clock = (res["clocks"] or {}).get("sm_mhz") or 1455.0
+    fp32_peak = 152 * 128 * 2 * clock * 1e6 / 1e12  # TFLOP/s of FFMA at the sampled clock
+    tf32_peak = peaks.get("bf16_tflops_sustained", 1715.4) * (1.1 / 2.25)
+    out = {"kernel": dom, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
+           "share": ms / sum(v[0] for v in prof.values())}
+    if dom == "update":
+        flops = steps * p * G * m ** 3 / 3.0
+        out.update(bound="tensor", achieved=flops / (ms / 1e3) / 1e12, peak=tf32_peak, unit="TFLOP/s",
+                   peak_note="TF32 = measured bf16 sustained x nominal TF32/BF16 ratio (1.1/2.25), of measured")
+    elif dom in ("kbuild", "predict"):
+        if dom == "kbuild":
+            flops = steps * p * (m * m * d + len(w["sigmas"]) * m * m / 2.0 * 20)
+        else:
+            flops = steps * p * t * m * (2.0 * d + len(w["sigmas"]) * 20 + 2 * G)
+        out.update(bound="alu", achieved=flops / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
+                   peak_note="FP32 FFMA peak = 152 SMs x 128 lanes x 2 x sampled SM clock; algorithmic FP64-class "
+                             "flops (each costs ~12 FP32 ops in double-float)")
+    else:
+        tiles = (m // 128) * (m // 128 + 1) // 2 + m // 128
+        byts = steps * p * G * tiles * 128 * 128 * 4 * 2 * max(1, launches // max(steps, 1)) / max(1, G)
+        out.update(bound="hbm", achieved=byts / (ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6797.9), unit="GB/s",
+                   peak_note="measured copy bandwidth; bytes assume every solve active (upper bound)")
+    out["frac"] = out["achieved"] / out["peak"]
+    out["traffic"] = None
+    return out
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    res = run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+    if rank != 0:
+        return
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    roof = roofline(res, args.steps, peaks)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        sample = args.cpu_sample or max(1, min(16, os.cpu_count() or 1))
+        cpu = cpu_baseline(res["w"], sample)
+    if args.profile:
+        sys.stderr.write(json.dumps({k: [round(v[0], 3), v[1]] for k, v in res["prof"].items()}) + "\n")
+        sys.stderr.write("step ms: %s\n" % [round(x, 2) for x in res["times"]])
+    w = res["w"]
+    line = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "tf32+f64" if args.prec == "tf32" else ("f32+f64" if args.prec == "fp32" else "f64"),
+        "data": "synthetic",
+        "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": args.prec,
+                   "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]),
+                   "parallelism": "independent workloads per GPU" if world > 1 else "single GPU",
+                   "l2": "flushed (512 MB write) before every timed step"},
+        "tflops": res["tflops"], "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"],
+        "clocks": res["clocks"], "gpu_launches": res["launches"], "fp64_path": res["fp64"],
+        "failed_solves": res["bad"], "best_model": res["best"], "best_mse": res["best_mse"],
+        "stages_ms_per_step": {k: v[0] / args.steps for k, v in res["prof"].items()},
+    }
+    print(json.dumps(line))
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1805_00569_gb300 import synth
+    w = synth.bkrr2(seed=1)
+    sample = args.cpu_sample or max(1, min(16, os.cpu_count() or 1))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(w, sample)
+        if i >= args.warmup:
+            vals.append(sample / r["value"])
+    wall = sum(vals)
+    value = sample * args.steps / wall
+    cpu = dict(value=value, unit=UNIT, cores=sample, kind="oracle",
+               sample="per step %d of the 96 solves of %s (kernel build + Cholesky + refinement + predict + MSE), "
+                      "one process each" % (sample, w["workload"]))
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": "fp64"},
+        "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * krr.h -- C ABI of libkrr, a GB300 (sm_103a) implementation of the hot path
+ * of partitioned kernel ridge regression (You, Demmel, Hsieh, Vuduc,
+ * "Accurate, Fast and Scalable Kernel Ridge Regression on Parallel and
+ * Distributed Systems", ICS'18): DKRR (one partition), BKRR2 with random
+ * equal partitions and KKRR2 with K-means partitions.
+ *
+ * Conventions for every entry point
+ *  - Array arguments are DEVICE pointers unless marked "host".  They are
+ *    caller-owned, row-major and FP64 unless stated.  Outputs are
+ *    caller-allocated.
+ *  - Work is enqueued on the context's stream.  The synchronous return value
+ *    reports argument and launch validation only; numerical outcomes arrive in
+ *    per-solve status words valid after the stream is synchronised.
+ *  - No exception crosses the ABI.  On a non-OK return krr_last_error()
+ *    describes the failure.
+ *  - A context is not thread-safe; use one per host thread/stream.
+ */
+#ifndef KRR_H
+#define KRR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct krr_ctx krr_ctx;     /* opaque: stream, HBM budget, error text */
+typedef struct krr_model krr_model; /* opaque: library-owned device memory   */
+
+typedef enum {
+    KRR_OK = 0,
+    KRR_ERR_ARG = 1,          /* invalid argument (sizes, null pointers, modes) */
+    KRR_ERR_OOM = 2,          /* cudaMalloc failed                               */
+    KRR_ERR_BUDGET = 3,       /* the context's HBM budget would be exceeded      */
+    KRR_ERR_CUDA = 4,         /* a CUDA call failed                              */
+    KRR_ERR_NOT_SPD = 5,      /* per solve: K + lambda m I not positive definite */
+    KRR_ERR_NO_CONVERGE = 6,  /* per solve: refinement did not reach tolerance   */
+    KRR_ERR_TIMEOUT = 7,      /* a bounded device-side wait expired              */
+    KRR_ERR_UNSUPPORTED = 8   /* a valid request this build does not implement   */
+} krr_status;
+
+typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1 } krr_part_mode;
+
+/* Arithmetic of the kernel build, the Cholesky factor and its refinement.
+ * FP64:  FP64 kernel, FP64 Cholesky, FP64 refinement (the plain path).
+ * FP32:  FP32 factor of the double-float (~44-bit) kernel, FP32 trailing
+ *        updates; conjugate-gradient refinement with double-float residuals.
+ * TF32:  as FP32 but the Cholesky trailing updates run on the tcgen05 tensor
+ *        cores in TF32 with FP32 accumulation.                               */
+typedef enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_TF32 = 2 } krr_prec;
+
+/* Model choice (Eq. 3 scores):
+ * PER_MODEL: one MSE per (partition, sigma, lambda) model; best model.
+ * ROUTED:    each test point scored by its routed partition (Alg. BKRR2 lines
+ *            13-19, KKRR2 Sec. 4.2); one MSE per grid point; best grid point.
+ * AVERAGE:   DC-KRR (Alg. DC-KRR line 15): predictions averaged over the
+ *            partitions; one MSE per grid point.
+ * ORACLE:    BKRR3 (Alg. BKRR3 lines 14-17): each test point takes the
+ *            partition whose prediction is closest to its label.             */
+typedef enum {
+    KRR_SEL_PER_MODEL = 0,
+    KRR_SEL_ROUTED = 1,
+    KRR_SEL_AVERAGE = 2,
+    KRR_SEL_ORACLE = 3
+} krr_sel;
+
+/* Create a context on `device` that enqueues on `cuda_stream` (a
+ * cudaStream_t; NULL = legacy default stream).  hbm_budget_bytes caps the
+ * device memory the library allocates (0 = no cap).  Errors: KRR_ERR_ARG,
+ * KRR_ERR_CUDA. */
+krr_status krr_ctx_create(krr_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes);
+/* Destroy a context (models must be freed first).  Synchronises its stream. */
+krr_status krr_ctx_destroy(krr_ctx *ctx);
+/* Text of the last failure on this context (valid until the next call). */
+const char *krr_last_error(const krr_ctx *ctx);
+/* Bytes currently allocated through the context. */
+size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
+
+/* Partition the training rows (Alg. DC-KRR lines 1-5 for RANDOM; Alg. 2
+ * plain K-means plus the KKRR2 nearest-centre rule, Sec. 4.2, for KMEANS).
+ *   X [n x d], Xt [t x d] (Xt may be NULL when t == 0).
+ *   RANDOM: a seeded bijection (Feistel network over Philox4x32-10, cycle
+ *     walking) shuffles the rows; the shuffled order is cut into p parts, the
+ *     first n mod p one row longer.  perm[k] = row at shuffled position k.
+ *     seed is used; iters, init_idx, centers, route are ignored (route, when
+ *     given, is filled with 0).
+ *   KMEANS: p = number of clusters; centres start at rows init_idx[0..p)
+ *     (device, int64); `iters` assign+update rounds (stopping early at a
+ *     fixed point is result-neutral); ties go to the lowest centre index;
+ *     empty clusters keep their centre; centre sums run in one canonical
+ *     order (blocks of 1024 rows, pairwise tree over blocks).  A final
+ *     assignment with the final centres defines the partitions and routes
+ *     the test rows.  Assignments are bit-exact with that definition (an FP64
+ *     recheck decides near ties).
+ * Outputs: assign[n] (int32 partition of each row), perm[n] (int64 rows grouped
+ * by partition; ascending row order inside a partition for KMEANS),
+ * offsets[p+1] (int64), route[t] (int32, nullable), centers[p x d] (nullable;
+ * required for KMEANS).  Errors: KRR_ERR_ARG, KRR_ERR_BUDGET, KRR_ERR_CUDA. */
+krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const double *Xt, int64_t t,
+                         krr_part_mode mode, int32_t p, int32_t iters, uint64_t seed, const int64_t *init_idx,
+                         int32_t *assign, int32_t *route, int64_t *perm, int64_t *offsets, double *centers);
+
+/* Fit every (partition, sigma, lambda) model: for partition j with m_j rows
+ * X_j = X[perm[offsets[j] .. offsets[j+1])], solve Eq. 6 in its partitioned
+ * form (K_j + lambda m_j I) alpha = y_j with the Gaussian kernel of Table 1,
+ * K_ab = exp(-||x_a - x_b||^2 / (2 sigma^2)), by Cholesky factorisation
+ * (Sec. 5.4) and refinement to FP64-level residuals.
+ *   X [n x d], y [n], perm [n], offsets [p+1] (device; read back to the host).
+ *   sigmas [ns], lambdas [nl]: HOST arrays.  Grid index g = i_sigma * nl +
+ *   i_lambda; solve/model index = j * (ns * nl) + g.
+ *   *out receives a model owning the gathered rows and every alpha until
+ *   krr_model_free.  solve_status [p*ns*nl] (device int32, nullable) receives
+ *   KRR_OK, KRR_ERR_NOT_SPD or KRR_ERR_NO_CONVERGE per solve.
+ *   alpha (device, nullable) receives n*ns*nl doubles: partition j's block
+ *   starts at offsets[j]*ns*nl and holds, for each g, m_j coefficients in the
+ *   partition's row order.
+ * This call synchronises the stream (partition sizes are needed on the host;
+ * refinement rounds poll a device flag).  Errors: KRR_ERR_ARG,
+ * KRR_ERR_BUDGET, KRR_ERR_OOM, KRR_ERR_CUDA, KRR_ERR_TIMEOUT. */
+krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                         const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas, int32_t ns,
+                         const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
+                         int32_t *solve_status, double *alpha);
+
+/* Eq. 7 prediction, fused: kernel rows are built on the fly and contracted
+ * with alpha; K(test, train) is never stored.
+ *   Xt [t x d].  route == NULL: every model predicts every test row and
+ *   yhat is [p*ns*nl x t] (model-major).  route [t] given: row q is predicted
+ *   only by partition route[q]'s models and yhat is [ns*nl x t].  A partition
+ *   with no rows predicts 0.  Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */
+krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, int64_t t, const int32_t *route,
+                       double *yhat);
+
+/* Score and choose (Eq. 3; see krr_sel).
+ *   yhat as produced by krr_predict (routed layout for ROUTED, all-models
+ *   layout otherwise), yt [t].  p, G = ns*nl.
+ *   mse (device FP64): p*G entries for PER_MODEL, G otherwise.
+ *   best (device int32, 1 entry): index of the lowest MSE, lowest index on
+ *   ties.  Deterministic: fixed reduction order.  Errors: KRR_ERR_ARG,
+ *   KRR_ERR_CUDA. */
+krr_status krr_select(krr_ctx *ctx, const double *yhat, const double *yt, int64_t t, int32_t p, int32_t G,
+                      krr_sel mode, double *mse, int32_t *best);
+
+/* Per-solve diagnostics of a fitted model (HOST outputs, p*ns*nl entries
+ * each, nullable): refinement iterations, Gershgorin condition estimate
+ * (max row sum of K + lambda m I over lambda m) and final scaled residual.
+ * Synchronises the stream. */
+krr_status krr_model_stats(krr_ctx *ctx, const krr_model *model, int32_t *iters, double *kappa_est,
+                           double *resid);
+
+/* Release a model's device memory. */
+krr_status krr_model_free(krr_ctx *ctx, krr_model *model);
+
+/* ---- instrumentation and tuning (no counterpart in the paper) ----------
+ * krr_ctx_set_profiling: when on, every kernel launch of the context is
+ *   bracketed by CUDA events on the context's stream (adds ~2 us per launch).
+ *   Turning it on or off clears the totals.
+ * krr_ctx_profile: total device time (ms, host output) and launch count of
+ *   one kernel class since profiling was switched on; synchronises the
+ *   stream.  kind: 0 partition, 1 stage, 2 kernel build, 3 potrf, 4 trsm,
+ *   5 trailing update, 6 matvec, 7 preconditioner, 8 CG vector ops,
+ *   9 predict, 10 select.  Errors: KRR_ERR_ARG.
+ * krr_ctx_set_panel_width: outer panel width W (tiles) of the blocked
+ *   Cholesky schedule, 1..64; 0 restores the default.  Errors: KRR_ERR_ARG.
+ * krr_launch_count: kernels launched by this process through libkrr. */
+krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
+krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);
+krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
+long long krr_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRR_H */

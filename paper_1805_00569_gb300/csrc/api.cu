@@ -1,0 +1,612 @@
+// api.cu -- the C ABI of libkrr (declared in include/krr.h): context and
+// budget, model lifetime, and the orchestration of the hot path
+//   krr_partition -> krr_fit_batch -> krr_predict -> krr_select.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+#include "internal.h"
+
+struct krr_ctx {
+    krr::Ctx c;
+};
+struct krr_model {
+    krr::Model m;
+};
+
+namespace krr {
+
+std::atomic<long long> g_launch_count{0};
+
+// ---- defined in the other translation units
+krr_status run_partition_random(Ctx *, int64_t, int32_t, uint64_t, int32_t *, int64_t *, int64_t *, int32_t *,
+                                int64_t);
+krr_status run_partition_kmeans(Ctx *, const double *, int64_t, int32_t, const double *, int64_t, int32_t, int32_t,
+                                const int64_t *, int32_t *, int32_t *, int64_t *, int64_t *, double *);
+krr_status run_gather(Ctx *, const int32_t *, int64_t, int32_t, int64_t *, int64_t *);
+void launch_stage(cudaStream_t, const double *, const double *, const int64_t *, const Model &, double *);
+void launch_kbuild_df(cudaStream_t, const Model &, int64_t, float *, float *, float *);
+void launch_kbuild_fp64(cudaStream_t, const Model &, int64_t, double *, double *);
+struct CholLaunch {
+    int kind;
+    int K0, W;
+    int64_t pre;
+    int64_t tasks;
+};
+void build_chol_plan(const std::vector<int> &, int, std::vector<CholLaunch> &, std::vector<int64_t> &);
+cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
+                          const SolveDesc *, int, int32_t *, bool, const CUtensorMap *, int *, Prof *);
+bool make_tile_tmap(CUtensorMap *, float *, int64_t);
+size_t pcg_state_size();
+size_t precond_smem_bytes(bool, int);
+struct PcgBuffers {
+    double *x, *r, *z, *p, *q, *y, *slots;
+    PcgState *state;
+    unsigned int *nactive;
+    GroupDesc *d_groups;
+    int64_t *d_gpre;
+    int ng;
+    int64_t gtiles;
+};
+cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
+                    const void *, const void *, bool, int, double, int, const int32_t *, unsigned int *, int, Prof *);
+void launch_predict(cudaStream_t, const Model &, const double *, int64_t, const int64_t *, const int64_t *, int64_t,
+                    int, double *);
+void launch_select(cudaStream_t, const double *, const double *, int64_t, int, int, int, double *, int32_t *);
+
+// ---- budgeted stream-ordered allocation
+cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (c->budget && c->used + bytes > c->budget) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    if (e == cudaSuccess) c->used += bytes;
+    return e;
+}
+void ctx_free(Ctx *c, void *p, size_t bytes) {
+    if (!p) return;
+    if (bytes == 0) bytes = 256;
+    cudaFreeAsync(p, c->stream);
+    c->used -= std::min(c->used, bytes);
+}
+
+// ---- small kernels of the fit
+__global__ void fill_rhs_kernel(const SolveDesc *__restrict__ solves, const PartDesc *__restrict__ parts,
+                                const double *__restrict__ yg, double *__restrict__ y) {
+    const SolveDesc S = solves[blockIdx.x];
+    const PartDesc P = parts[S.part];
+    for (int e = threadIdx.x; e < S.T * KRR_TILE; e += blockDim.x) y[S.vec0 + e] = yg[P.prow0 + e];
+}
+__global__ void export_kernel(const SolveDesc *__restrict__ solves, const PartDesc *__restrict__ parts, int G,
+                              const double *__restrict__ x, const PcgState *__restrict__ state,
+                              int32_t *__restrict__ status, double *__restrict__ alpha_out) {
+    const int s = blockIdx.x;
+    const SolveDesc S = solves[s];
+    const PartDesc P = parts[S.part];
+    if (threadIdx.x == 0 && status) status[s] = state[s].status;
+    if (alpha_out) {
+        const int g = s % G;
+        double *dst = alpha_out + P.row0 * G + (int64_t)g * S.m;
+        for (int e = threadIdx.x; e < S.m; e += blockDim.x) dst[e] = x[S.vec0 + e];
+    }
+}
+// refill the factor tiles of the listed solves with K_hi + (lambda m + shift) I
+__global__ void reform_kernel(const SolveDesc *__restrict__ sub, const int64_t *__restrict__ pre, int nsub,
+                              const float *__restrict__ Kh, float *__restrict__ A, float shift) {
+    int lo = 0, hi = nsub - 1;
+    const int64_t b = blockIdx.x;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    const SolveDesc S = sub[lo];
+    const int64_t lt = b - pre[lo];
+    int ti, tj;
+    tri_decode(lt, ti, tj);
+    const float *src = Kh + (S.ktile0 + lt) * KRR_TILE_ELEMS;
+    float *dst = A + (S.ltile0 + lt) * KRR_TILE_ELEMS;
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int r = e >> 7, c = e & 127;
+        const int gr = ti * KRR_TILE + r, gc = tj * KRR_TILE + c;
+        dst[e] = src[e] + ((gr == gc && gr < S.m) ? (float)S.lambda_m + shift : 0.f);
+    }
+}
+
+struct DevBuf {
+    Ctx *c;
+    std::vector<std::pair<void *, size_t>> list;
+    explicit DevBuf(Ctx *c_) : c(c_) {}
+    template <typename T>
+    cudaError_t get(T **p, size_t bytes) {
+        cudaError_t e = ctx_malloc(c, (void **)p, bytes);
+        if (e == cudaSuccess) list.push_back({(void *)*p, bytes});
+        return e;
+    }
+    ~DevBuf() {
+        for (auto &a : list) ctx_free(c, a.first, a.second);
+    }
+};
+
+static krr_status fail(Ctx *c, krr_status s, const std::string &msg) {
+    c->last_error = msg;
+    return s;
+}
+
+static void free_model(Ctx *c, Model &M) {
+    for (auto &a : M.allocs) ctx_free(c, a.first, a.second);
+    M.allocs.clear();
+}
+
+template <typename T>
+static cudaError_t model_alloc(Ctx *c, Model &M, T **p, size_t bytes) {
+    cudaError_t e = ctx_malloc(c, (void **)p, bytes);
+    if (e == cudaSuccess) M.allocs.push_back({(void *)*p, bytes});
+    return e;
+}
+
+}  // namespace krr
+
+using namespace krr;
+
+#define API_TRY(ctxp, expr)                                                                  \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess) {                                                             \
+            (ctxp)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e);        \
+            return (_e == cudaErrorMemoryAllocation)                                         \
+                       ? ((ctxp)->budget ? KRR_ERR_BUDGET : KRR_ERR_OOM)                    \
+                       : KRR_ERR_CUDA;                                                       \
+        }                                                                                    \
+    } while (0)
+
+extern "C" {
+
+krr_status krr_ctx_create(krr_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes) {
+    if (!out) return KRR_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return KRR_ERR_ARG;
+    krr_ctx *k = new (std::nothrow) krr_ctx();
+    if (!k) return KRR_ERR_OOM;
+    k->c.device = device;
+    k->c.stream = (cudaStream_t)cuda_stream;
+    k->c.budget = hbm_budget_bytes;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&k->c.d_err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(k->c.d_err, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&k->c.h_flag, sizeof(unsigned int)) != cudaSuccess) {
+        delete k;
+        return KRR_ERR_CUDA;
+    }
+    *out = k;
+    return KRR_OK;
+}
+
+krr_status krr_ctx_destroy(krr_ctx *ctx) {
+    if (!ctx) return KRR_ERR_ARG;
+    cudaStreamSynchronize(ctx->c.stream);
+    for (auto e : ctx->c.prof.pool) cudaEventDestroy(e);
+    cudaFree(ctx->c.d_err);
+    cudaFreeHost(ctx->c.h_flag);
+    delete ctx;
+    return KRR_OK;
+}
+
+long long krr_launch_count(void) { return g_launch_count.load(); }
+
+const char *krr_last_error(const krr_ctx *ctx) { return ctx ? ctx->c.last_error.c_str() : "null context"; }
+
+size_t krr_ctx_bytes_in_use(const krr_ctx *ctx) { return ctx ? ctx->c.used : 0; }
+
+// Per-kernel-class timing (not part of krr.h's core path; used by benchmarks).
+krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on) {
+    if (!ctx) return KRR_ERR_ARG;
+    ctx->c.prof.on = on != 0;
+    ctx->c.prof.reset();
+    return KRR_OK;
+}
+krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches) {
+    if (!ctx || kind < 0 || kind >= PROF_NKINDS) return KRR_ERR_ARG;
+    cudaStreamSynchronize(ctx->c.stream);
+    ctx->c.prof.collect();
+    if (total_ms) *total_ms = ctx->c.prof.total_ms[kind];
+    if (launches) *launches = ctx->c.prof.launches[kind];
+    return KRR_OK;
+}
+krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W) {
+    if (!ctx || W < 0 || W > 64) return KRR_ERR_ARG;
+    ctx->c.chol_W = W;
+    return KRR_OK;
+}
+
+krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const double *Xt, int64_t t,
+                         krr_part_mode mode, int32_t p, int32_t iters, uint64_t seed, const int64_t *init_idx,
+                         int32_t *assign, int32_t *route, int64_t *perm, int64_t *offsets, double *centers) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (n < 0 || d <= 0 || p <= 0 || t < 0 || !assign || !perm || !offsets || (n > 0 && !X) ||
+        (t > 0 && route && !Xt))
+        return fail(c, KRR_ERR_ARG, "krr_partition: invalid argument");
+    if (p > n && n > 0 && mode == KRR_PART_KMEANS) return fail(c, KRR_ERR_ARG, "krr_partition: p > n");
+    cudaSetDevice(c->device);
+    ProfScope ps(&c->prof, PROF_PARTITION, c->stream);
+    if (mode == KRR_PART_RANDOM) return run_partition_random(c, n, p, seed, assign, perm, offsets, route, t);
+    if (mode == KRR_PART_KMEANS) {
+        if (!init_idx || !centers || iters < 0)
+            return fail(c, KRR_ERR_ARG, "krr_partition: K-means needs init_idx and centers");
+        return run_partition_kmeans(c, X, n, d, Xt, t, p, iters, init_idx, assign, route, perm, offsets, centers);
+    }
+    return fail(c, KRR_ERR_ARG, "krr_partition: unknown mode");
+}
+
+krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                         const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas, int32_t ns,
+                         const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
+                         int32_t *solve_status, double *alpha) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (!out || !X || !y || !perm || !offsets || !sigmas || !lambdas || n <= 0 || d <= 0 || p <= 0 || ns <= 0 ||
+        nl <= 0 || ns > 8 || nl > 8 || (prec != KRR_PREC_FP64 && prec != KRR_PREC_FP32 && prec != KRR_PREC_TF32))
+        return fail(c, KRR_ERR_ARG, "krr_fit_batch: invalid argument (1 <= ns, nl <= 8)");
+    for (int i = 0; i < ns; ++i)
+        if (!(sigmas[i] > 0.0) || !std::isfinite(sigmas[i]))
+            return fail(c, KRR_ERR_ARG, "krr_fit_batch: sigma must be positive and finite");
+    for (int i = 0; i < nl; ++i)
+        if (!std::isfinite(lambdas[i])) return fail(c, KRR_ERR_ARG, "krr_fit_batch: lambda must be finite");
+    *out = nullptr;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    const bool fp64 = prec == KRR_PREC_FP64;
+    const bool tf32 = prec == KRR_PREC_TF32;
+    Prof *prof = c->prof.on ? &c->prof : nullptr;
+
+    // partition sizes on the host
+    std::vector<int64_t> off(p + 1);
+    API_TRY(c, cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * (p + 1), cudaMemcpyDeviceToHost, st));
+    API_TRY(c, cudaStreamSynchronize(st));
+    if (off[0] != 0 || off[p] != n) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must run from 0 to n");
+    for (int j = 0; j < p; ++j)
+        if (off[j + 1] < off[j]) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must be non-decreasing");
+
+    krr_model *km = new (std::nothrow) krr_model();
+    if (!km) return KRR_ERR_OOM;
+    Model &M = km->m;
+    M.d = d;
+    M.dp = ((d + 15) / 16) * 16;
+    M.p = p;
+    M.nsig = ns;
+    M.nlam = nl;
+    M.prec = prec;
+    M.n = n;
+    M.sigmas.assign(sigmas, sigmas + ns);
+    M.lambdas.assign(lambdas, lambdas + nl);
+    const int G = ns * nl;
+    int64_t prow = 0, ktot = 0;
+    int maxT = 0;
+    for (int j = 0; j < p; ++j) {
+        PartDesc P;
+        P.m = (int32_t)(off[j + 1] - off[j]);
+        P.T = (P.m + KRR_TILE - 1) / KRR_TILE;
+        P.row0 = off[j];
+        P.prow0 = prow;
+        P.ktile0 = ktot;
+        prow += (int64_t)P.T * KRR_TILE;
+        ktot += tri(P.T);
+        maxT = std::max(maxT, P.T);
+        M.parts.push_back(P);
+    }
+    M.prows = prow;
+    int64_t ltiles = 0, dtiles = 0, vec = 0, scratch = 0;
+    std::vector<GroupDesc> groups;
+    std::vector<int64_t> gpre;
+    for (int j = 0; j < p; ++j) {
+        const PartDesc &P = M.parts[j];
+        for (int is = 0; is < ns; ++is) {
+            GroupDesc Gd;
+            Gd.part = j;
+            Gd.isig = is;
+            Gd.T = P.T;
+            Gd.nlam = nl;
+            Gd.ktile0 = (int64_t)is * ktot + P.ktile0;
+            Gd.solve0 = (int64_t)j * G + is * nl;
+            Gd.scratch0 = scratch;
+            scratch += (int64_t)nl * P.T * P.T * KRR_TILE;
+            gpre.push_back(groups.empty() ? 0 : gpre.back() + tri(groups.back().T));
+            groups.push_back(Gd);
+            for (int il = 0; il < nl; ++il) {
+                SolveDesc S;
+                S.part = j;
+                S.isig = is;
+                S.ilam = il;
+                S.T = P.T;
+                S.m = P.m;
+                S.grp = j * ns + is;
+                S.ltile0 = ltiles;
+                S.dtile0 = dtiles;
+                S.ktile0 = Gd.ktile0;
+                S.vec0 = vec;
+                S.lambda_m = lambdas[il] * (double)P.m;
+                ltiles += tri(P.T);
+                dtiles += P.T;
+                vec += (int64_t)P.T * KRR_TILE;
+                M.solves.push_back(S);
+            }
+        }
+    }
+    const int64_t gtiles = groups.empty() ? 0 : gpre.back() + tri(groups.back().T);
+    M.nvec = vec;
+    const int nsolve = (int)M.solves.size();
+    const size_t esz = fp64 ? 8 : 4;
+    if (precond_smem_bytes(fp64, maxT) > 200 * 1024) {
+        delete km;
+        return fail(c, KRR_ERR_UNSUPPORTED, "krr_fit_batch: partition too large for the preconditioner (m <= " +
+                                                std::to_string(fp64 ? 24000 : 48000) + ")");
+    }
+
+    // ---- budget check before any allocation
+    const size_t tileb = (size_t)KRR_TILE_ELEMS * esz;
+    size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 8 +
+                         sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
+    size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
+                        (size_t)dtiles * tileb + 5 * (size_t)vec * 8 + (size_t)scratch * 8 +
+                        pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
+                        4 * nsolve + 64 * 1024 * 1024;
+    if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
+        delete km;
+        return fail(c, KRR_ERR_BUDGET, "krr_fit_batch: needs " + std::to_string(model_bytes + work_bytes) +
+                                           " bytes, budget leaves " + std::to_string(c->budget - c->used));
+    }
+
+    auto bail = [&](krr_status s, const std::string &msg) {
+        free_model(c, M);
+        delete km;
+        return fail(c, s, msg);
+    };
+#define FIT_TRY(expr)                                                                        \
+    do {                                                                                     \
+        cudaError_t _e = (expr);                                                             \
+        if (_e != cudaSuccess)                                                               \
+            return bail(_e == cudaErrorMemoryAllocation ? KRR_ERR_OOM : KRR_ERR_CUDA,       \
+                        std::string(#expr) + ": " + cudaGetErrorString(_e));                 \
+    } while (0)
+
+    FIT_TRY(model_alloc(c, M, &M.X64, (size_t)prow * d * 8));
+    FIT_TRY(model_alloc(c, M, &M.Xh, (size_t)prow * M.dp * 4));
+    FIT_TRY(model_alloc(c, M, &M.Xl, (size_t)prow * M.dp * 4));
+    FIT_TRY(model_alloc(c, M, &M.nrm, (size_t)prow * 8));
+    FIT_TRY(model_alloc(c, M, &M.alpha, (size_t)vec * 8));
+    FIT_TRY(model_alloc(c, M, &M.d_parts, sizeof(PartDesc) * p));
+    FIT_TRY(model_alloc(c, M, &M.d_solves, sizeof(SolveDesc) * nsolve));
+    FIT_TRY(cudaMemcpyAsync(M.d_parts, M.parts.data(), sizeof(PartDesc) * p, cudaMemcpyHostToDevice, st));
+    FIT_TRY(cudaMemcpyAsync(M.d_solves, M.solves.data(), sizeof(SolveDesc) * nsolve, cudaMemcpyHostToDevice, st));
+
+    {
+        DevBuf W(c);
+        double *yg = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *yv = nullptr,
+               *slots = nullptr;
+        void *Kst = nullptr, *Ast = nullptr, *Zst = nullptr;
+        PcgState *state = nullptr;
+        unsigned int *nactive = nullptr;
+        GroupDesc *d_groups = nullptr;
+        int64_t *d_gpre = nullptr, *d_plan = nullptr;
+        int32_t *flags = nullptr;
+        FIT_TRY(W.get(&yg, (size_t)prow * 8));
+        FIT_TRY(W.get(&Kst, (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb));
+        FIT_TRY(W.get(&Ast, (size_t)ltiles * tileb));
+        FIT_TRY(W.get(&Zst, (size_t)dtiles * tileb));
+        FIT_TRY(W.get(&r, (size_t)vec * 8));
+        FIT_TRY(W.get(&z, (size_t)vec * 8));
+        FIT_TRY(W.get(&pv, (size_t)vec * 8));
+        FIT_TRY(W.get(&q, (size_t)vec * 8));
+        FIT_TRY(W.get(&yv, (size_t)vec * 8));
+        FIT_TRY(W.get(&slots, (size_t)scratch * 8));
+        FIT_TRY(W.get((unsigned char **)&state, pcg_state_size() * nsolve));
+        FIT_TRY(W.get(&nactive, sizeof(unsigned int)));
+        FIT_TRY(W.get(&d_groups, sizeof(GroupDesc) * groups.size()));
+        FIT_TRY(W.get(&d_gpre, sizeof(int64_t) * gpre.size()));
+        FIT_TRY(W.get(&flags, sizeof(int32_t) * nsolve));
+        FIT_TRY(cudaMemcpyAsync(d_groups, groups.data(), sizeof(GroupDesc) * groups.size(), cudaMemcpyHostToDevice,
+                                st));
+        FIT_TRY(cudaMemcpyAsync(d_gpre, gpre.data(), sizeof(int64_t) * gpre.size(), cudaMemcpyHostToDevice, st));
+        FIT_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * nsolve, st));
+        FIT_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
+
+        // stage + kernel build
+        {
+            ProfScope ps(prof, PROF_STAGE, st);
+            launch_stage(st, X, y, perm, M, yg);
+        }
+        float *Kh = nullptr, *Kl = nullptr;
+        double *K64 = nullptr;
+        {
+            ProfScope ps(prof, PROF_KBUILD, st);
+            if (fp64) {
+                K64 = (double *)Kst;
+                launch_kbuild_fp64(st, M, ktot, K64, (double *)Ast);
+            } else {
+                Kh = (float *)Kst;
+                Kl = Kh + (size_t)ns * ktot * KRR_TILE_ELEMS;
+                launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
+            }
+        }
+        FIT_TRY(cudaGetLastError());
+
+        // Cholesky schedule
+        std::vector<int> Ts(nsolve);
+        for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
+        const int Wp = c->chol_W > 0 ? c->chol_W : 1;
+        std::vector<CholLaunch> plan;
+        std::vector<int64_t> pre;
+        build_chol_plan(Ts, Wp, plan, pre);
+        FIT_TRY(W.get(&d_plan, sizeof(int64_t) * std::max<size_t>(pre.size(), 1)));
+        if (!pre.empty())
+            FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
+        CUtensorMap tmap;
+        memset(&tmap, 0, sizeof(tmap));
+        if (tf32 && !make_tile_tmap(&tmap, (float *)Ast, ltiles))
+            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
+        FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tf32, &tmap, c->d_err,
+                              prof));
+
+        // breakdown of the low-precision factor: refactor those solves with a diagonal shift
+        if (!fp64) {
+            for (int attempt = 0; attempt < 3; ++attempt) {
+                std::vector<int32_t> hf(nsolve);
+                FIT_TRY(cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
+                FIT_TRY(cudaStreamSynchronize(st));
+                std::vector<SolveDesc> sub;
+                for (int s = 0; s < nsolve; ++s)
+                    if (hf[s]) sub.push_back(M.solves[s]);
+                if (sub.empty()) break;
+                // the sub-batch reuses the solves' own tiles; status of the originals stays flagged
+                // until the retry succeeds
+                DevBuf R(c);
+                SolveDesc *d_sub = nullptr;
+                int64_t *d_rpre = nullptr, *d_rplan = nullptr;
+                int32_t *rflags = nullptr;
+                const int nsub = (int)sub.size();
+                std::vector<int64_t> rpre(nsub + 1, 0);
+                for (int i = 0; i < nsub; ++i) rpre[i + 1] = rpre[i] + tri(sub[i].T);
+                FIT_TRY(R.get(&d_sub, sizeof(SolveDesc) * nsub));
+                FIT_TRY(R.get(&d_rpre, sizeof(int64_t) * (nsub + 1)));
+                FIT_TRY(R.get(&rflags, sizeof(int32_t) * nsub));
+                FIT_TRY(cudaMemcpyAsync(d_sub, sub.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
+                FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice,
+                                        st));
+                FIT_TRY(cudaMemsetAsync(rflags, 0, sizeof(int32_t) * nsub, st));
+                const float shift = (float)(std::pow(10.0, attempt) * 1e-4 * 0.5 * (double)sub[0].m + 1e-6);
+                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsub], 256, 0, st>>>(d_sub, d_rpre, nsub, Kh, (float *)Ast, shift);
+                std::vector<int> rT(nsub);
+                for (int i = 0; i < nsub; ++i) rT[i] = sub[i].T;
+                std::vector<CholLaunch> rplan;
+                std::vector<int64_t> rp;
+                build_chol_plan(rT, Wp, rplan, rp);
+                FIT_TRY(R.get(&d_rplan, sizeof(int64_t) * std::max<size_t>(rp.size(), 1)));
+                FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
+                                        st));
+                FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, tf32, &tmap,
+                                      c->d_err, prof));
+                std::vector<int32_t> hr(nsub);
+                FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
+                FIT_TRY(cudaStreamSynchronize(st));
+                int k = 0;
+                for (int s = 0; s < nsolve; ++s)
+                    if (hf[s]) hf[s] = hr[k++];
+                FIT_TRY(cudaMemcpyAsync(flags, hf.data(), sizeof(int32_t) * nsolve, cudaMemcpyHostToDevice, st));
+            }
+        }
+
+        // refinement
+        KRR_LAUNCHED(), fill_rhs_kernel<<<nsolve, 256, 0, st>>>(M.d_solves, M.d_parts, yg, yv);
+        PcgBuffers B;
+        B.x = M.alpha;
+        B.r = r;
+        B.z = z;
+        B.p = pv;
+        B.q = q;
+        B.y = yv;
+        B.slots = slots;
+        B.state = state;
+        B.nactive = nactive;
+        B.d_groups = d_groups;
+        B.d_gpre = d_gpre;
+        B.ng = (int)groups.size();
+        B.gtiles = gtiles;
+        const double tau = fp64 ? std::ldexp(1.0, -50) : std::ldexp(1.0, -46);
+        FIT_TRY(run_pcg(st, M, B, Kh, Kl, K64, Ast, Zst, fp64, maxT, tau, 80, flags, c->h_flag, 2, prof));
+        KRR_LAUNCHED(), export_kernel<<<nsolve, 256, 0, st>>>(M.d_solves, M.d_parts, G, M.alpha, state, solve_status, alpha);
+        FIT_TRY(cudaGetLastError());
+        int herr = 0;
+        std::vector<PcgState> hs(nsolve);
+        FIT_TRY(cudaMemcpyAsync(hs.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));
+        FIT_TRY(cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FIT_TRY(cudaStreamSynchronize(st));
+        M.st_iters.resize(nsolve);
+        M.st_status.resize(nsolve);
+        M.st_kappa.resize(nsolve);
+        M.st_resid.resize(nsolve);
+        for (int s = 0; s < nsolve; ++s) {
+            M.st_iters[s] = hs[s].iters;
+            M.st_status[s] = hs[s].status;
+            M.st_kappa[s] = M.solves[s].lambda_m > 0 ? hs[s].anorm / M.solves[s].lambda_m : INFINITY;
+            M.st_resid[s] = hs[s].resid;
+        }
+        if (herr != 0) return bail(KRR_ERR_TIMEOUT, "krr_fit_batch: a bounded device wait expired");
+        // kernel stores (Kh/Kl, K64) could stay for later refinement; they are released here
+        (void)Zst;
+    }
+#undef FIT_TRY
+    *out = km;
+    return KRR_OK;
+}
+
+krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, int64_t t, const int32_t *route,
+                       double *yhat) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (!model || t < 0 || (t > 0 && (!Xt || !yhat))) return fail(c, KRR_ERR_ARG, "krr_predict: invalid argument");
+    const Model &M = model->m;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    Prof *prof = c->prof.on ? &c->prof : nullptr;
+    const int G = M.nsig * M.nlam;
+    if (t == 0) return KRR_OK;
+    if (!route) {
+        ProfScope ps(prof, PROF_PREDICT, st);
+        launch_predict(st, M, Xt, t, nullptr, nullptr, t, 0, yhat);
+        API_TRY(c, cudaGetLastError());
+        return KRR_OK;
+    }
+    // routed: group the test rows by partition (stable), predict, scatter back
+    int64_t *tperm = nullptr, *toff = nullptr;
+    API_TRY(c, ctx_malloc(c, (void **)&tperm, (size_t)t * 8));
+    cudaError_t e = ctx_malloc(c, (void **)&toff, (size_t)(M.p + 1) * 8);
+    if (e != cudaSuccess) {
+        ctx_free(c, tperm, (size_t)t * 8);
+        API_TRY(c, e);
+    }
+    krr_status rc = run_gather(c, route, t, M.p, tperm, toff);
+    if (rc == KRR_OK) {
+        API_TRY(c, cudaMemsetAsync(yhat, 0, sizeof(double) * (size_t)G * t, st));
+        ProfScope ps(prof, PROF_PREDICT, st);
+        launch_predict(st, M, Xt, t, toff, tperm, t, 1, yhat);
+    }
+    ctx_free(c, toff, (size_t)(M.p + 1) * 8);
+    ctx_free(c, tperm, (size_t)t * 8);
+    API_TRY(c, cudaGetLastError());
+    return rc;
+}
+
+krr_status krr_select(krr_ctx *ctx, const double *yhat, const double *yt, int64_t t, int32_t p, int32_t G,
+                      krr_sel mode, double *mse, int32_t *best) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (!yhat || !yt || !mse || !best || t <= 0 || p <= 0 || G <= 0 || (int)mode < 0 || (int)mode > 3)
+        return fail(c, KRR_ERR_ARG, "krr_select: invalid argument");
+    cudaSetDevice(c->device);
+    ProfScope ps(c->prof.on ? &c->prof : nullptr, PROF_SELECT, c->stream);
+    launch_select(c->stream, yhat, yt, t, p, G, (int)mode, mse, best);
+    API_TRY(c, cudaGetLastError());
+    return KRR_OK;
+}
+
+krr_status krr_model_stats(krr_ctx *ctx, const krr_model *model, int32_t *iters, double *kappa_est,
+                           double *resid) {
+    if (!ctx || !model) return KRR_ERR_ARG;
+    const Model &M = model->m;
+    const size_t n = M.st_iters.size();
+    if (iters) std::copy(M.st_iters.begin(), M.st_iters.end(), iters);
+    if (kappa_est) std::copy(M.st_kappa.begin(), M.st_kappa.begin() + n, kappa_est);
+    if (resid) std::copy(M.st_resid.begin(), M.st_resid.begin() + n, resid);
+    return KRR_OK;
+}
+
+krr_status krr_model_free(krr_ctx *ctx, krr_model *model) {
+    if (!ctx || !model) return KRR_ERR_ARG;
+    free_model(&ctx->c, model->m);
+    delete model;
+    return KRR_OK;
+}
+
+}  // extern "C"

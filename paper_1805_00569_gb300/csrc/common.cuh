@@ -1,0 +1,271 @@
+// common.cuh -- device helpers shared by the sm_103a kernels of libkrr.
+//
+// * double-float ("df") arithmetic: a value is hi + lo, two FP32 numbers with
+//   |lo| <= ulp(hi)/2.  Error-free transformations: TwoSum (Knuth, TAOCP vol. 2,
+//   Sec. 4.2.2), Fast2Sum and TwoProduct via FMA (Dekker, "A floating-point
+//   technique for extending the available precision", Numer. Math. 1971).
+//   This gives ~44-bit arithmetic on the FP32 pipes, which on GB300 are 64x
+//   faster than the FP64 pipe.
+// * df exponential: Cody-Waite reduction by ln 2 (three-part constant), a
+//   further 2^-4 argument scaling undone by four squarings, and the Taylor
+//   series to degree 6 (relative error ~1e-14 for arguments <= 0).
+// * Philox4x32-10 (Salmon et al., SC'11) for the seeded row shuffle.
+// * thin inline-PTX wrappers for mbarrier, cp.async.bulk(.tensor) and tcgen05.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#define KRR_TILE 128            // tile edge of every kernel/factor tile
+#define KRR_TILE_ELEMS (KRR_TILE * KRR_TILE)
+
+// ----------------------------------------------------------------- df
+struct df { float hi, lo; };
+
+__device__ __forceinline__ df df_make(float h, float l) { df r; r.hi = h; r.lo = l; return r; }
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+    df r; fast_two_sum(s, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    df r; fast_two_sum(p, e, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ df df_scale2(df a, float pow2) {  // exact scaling by a power of two
+    return df_make(a.hi * pow2, a.lo * pow2);
+}
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ df df_from_double(double x) {
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return df_make(h, l);
+}
+
+// Accumulator that adds exact products of df numbers: acc += a*b, where the
+// hi*hi product is kept exactly and the cross terms are rounded once.
+struct df_acc { float s, c; };  // value = s + c (c unnormalised)
+__device__ __forceinline__ void dfa_zero(df_acc &a) { a.s = 0.f; a.c = 0.f; }
+__device__ __forceinline__ void dfa_fma(df_acc &acc, float ah, float al, float bh, float bl) {
+    float p = __fmul_rn(ah, bh);
+    float e = __fmaf_rn(ah, bh, -p);
+    e = __fmaf_rn(ah, bl, e);
+    e = __fmaf_rn(al, bh, e);
+    float s, t;
+    two_sum(acc.s, p, s, t);
+    acc.s = s;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(t, e));
+}
+__device__ __forceinline__ df dfa_value(const df_acc &a) {
+    df r; fast_two_sum(a.s, a.c, r.hi, r.lo);
+    if (!(fabsf(a.s) >= fabsf(a.c))) two_sum(a.s, a.c, r.hi, r.lo);
+    return r;
+}
+
+// exp(x) for df x <= 0 (x > 0 is clamped to 0), relative error ~1e-14;
+// returns 0 below -87 where the FP32 hi part would be subnormal.
+__device__ __forceinline__ df df_exp_nonpos(df x) {
+    if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
+    if (x.hi >= 0.f) return df_make(1.f, 0.f);
+    // ln 2 = L1 + L2 + L3; L1 has 15 significant bits so k*L1 is exact.
+    const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
+    float k = rintf(x.hi * 1.44269504088896341f);
+    float rh = __fsub_rn(x.hi, k * L1);                // exact (Sterbenz)
+    df r = df_add(df_make(rh, 0.f), df_make(x.lo, 0.f));
+    float p2 = __fmul_rn(k, L2), e2 = __fmaf_rn(k, L2, -p2);
+    r = df_add(r, df_make(-p2, -e2));
+    r = df_add(r, df_make(-k * L3, 0.f));
+    r = df_scale2(r, 0.0625f);                          // |r| <= 0.0217
+    // Taylor coefficients 1/j!, j = 6..0, as df constants.
+    const df c6 = df_make(0x1.6c16c2p-10f, -0x1.27d27ep-35f);
+    const df c5 = df_make(0x1.111112p-7f, -0x1.dddddep-32f);
+    const df c4 = df_make(0x1.555556p-5f, -0x1.555556p-30f);
+    const df c3 = df_make(0x1.555556p-3f, -0x1.555556p-28f);
+    df y = c6;
+    y = df_add(df_mul(y, r), c5);
+    y = df_add(df_mul(y, r), c4);
+    y = df_add(df_mul(y, r), c3);
+    y = df_add(df_mul(y, r), df_make(0.5f, 0.f));
+    y = df_add(df_mul(y, r), df_make(1.f, 0.f));
+    y = df_add(df_mul(y, r), df_make(1.f, 0.f));
+    y = df_mul(y, y); y = df_mul(y, y); y = df_mul(y, y); y = df_mul(y, y);
+    // scale by 2^k in two exact steps (k >= -126)
+    int ki = (int)k;
+    int k1 = ki / 2, k2 = ki - k1;
+    float s1 = __int_as_float((127 + k1) << 23), s2 = __int_as_float((127 + k2) << 23);
+    y = df_scale2(df_scale2(y, s1), s2);
+    return y;
+}
+
+// ----------------------------------------------------------------- Philox4x32-10
+struct u32x4 { uint32_t x, y, z, w; };
+__device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+        uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+        u32x4 n;
+        n.x = hi1 ^ c.y ^ k0;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k1;
+        n.w = lo0;
+        c = n;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// ----------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: gives up after ~2^26 polls (each try_wait itself blocks for a
+// hardware-defined interval), sets *err and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err, int code) {
+    for (uint32_t it = 0; it < (1u << 26); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    if (err) atomicExch(err, code);
+    return false;
+}
+
+// 1-D bulk copy global -> shared, completion counted on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// 2-D tiled TMA load.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// tcgen05 (5th-generation tensor core, accumulator in tensor memory)
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D(tmem) (+)= A(smem desc) * B(smem desc)^T, kind::tf32 / kind::f16
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+// 32 lanes x 32 consecutive columns of FP32 from tensor memory.
+__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float *v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+        "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor, K-major operand with the 128-byte swizzle
+// (8-row x 128-byte atoms, atoms 1024 bytes apart along M/N).
+__device__ __forceinline__ uint64_t smem_desc_sw128(const void *p) {
+    uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;          // start address
+    d |= (uint64_t)1 << 16;                 // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor: FP32 accumulate, A/B format code fmt (TF32 = 2 for
+// kind::tf32, BF16 = 1 for kind::f16), both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint32_t N) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((N >> 3) << 17) | ((M >> 4) << 24);
+}
+
+// ----------------------------------------------------------------- misc
+__device__ __forceinline__ int64_t tri_index(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
+// inverse of tri_index for idx < T(T+1)/2: row i (>= col j)
+__device__ __forceinline__ void tri_decode(int64_t idx, int &i, int &j) {
+    int r = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    while ((int64_t)(r + 1) * (r + 2) / 2 <= idx) ++r;
+    while ((int64_t)r * (r + 1) / 2 > idx) --r;
+    i = r;
+    j = (int)(idx - (int64_t)r * (r + 1) / 2);
+}

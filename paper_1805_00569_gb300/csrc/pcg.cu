@@ -1,0 +1,519 @@
+// pcg.cu -- refinement of every solve of Eq. 6 to FP64-level residuals.
+//
+// The low-precision Cholesky factor L (FP32 storage, TF32 or FP32 trailing
+// updates) preconditions a conjugate-gradient iteration on the exact system
+// (K + lambda m I) alpha = y.  Vectors and scalars are FP64; the residual
+// products use the double-float kernel K_hi + K_lo (~1e-13 relative), so the
+// attainable accuracy is that of the kernel, not of the factor.  With the
+// plain FP64 path the same loop runs with the FP64 factor and FP64 kernel.
+//
+//   matvec      q = (K + lambda m I) p for every lambda of a (partition, sigma)
+//               group: each lower tile contributes K_ij p_j to row block i and
+//               K_ij^T p_i to row block j into a private slot; a second kernel
+//               sums the slots of each row block in a fixed order, so results
+//               do not depend on scheduling.
+//   precond     z = L^-T L^-1 r by blocked substitution, one CTA per solve:
+//               off-diagonal tiles as matrix-vector products, diagonal blocks
+//               through the stored inverses Z_ii (no sequential 128-step
+//               solves).
+//   pcg_*       per-solve dot products (fixed-order reductions), updates,
+//               stopping test ||r||_inf <= tau (||A||_inf ||x||_inf + ||y||_inf).
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+
+// ---------------------------------------------------------------- matvec
+__device__ __forceinline__ int find_group(const GroupDesc *gd, const int64_t *gpre, int ng, int64_t b) {
+    int lo = 0, hi = ng - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (gpre[mid] <= b) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// refined: K = Kh + Kl (df), p FP64.  grid = sum over groups of tri(T)
+template <bool DF>
+__global__ void __launch_bounds__(256)
+matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, const double *__restrict__ K64,
+                    const GroupDesc *__restrict__ groups, const int64_t *__restrict__ gpre, int ng,
+                    const SolveDesc *__restrict__ solves, const PcgState *__restrict__ state,
+                    const double *__restrict__ pv, double *__restrict__ slots) {
+    __shared__ float2 sp_row[8][KRR_TILE];  // p of column block (df) per lambda
+    __shared__ float2 sp_col[8][KRR_TILE];  // p of row block
+    __shared__ double sred[16][KRR_TILE + 1];
+    const int gi = find_group(groups, gpre, ng, blockIdx.x);
+    const GroupDesc G = groups[gi];
+    bool any = false;
+    for (int l = 0; l < G.nlam; ++l) any |= state[G.solve0 + l].active != 0;
+    if (!any) return;
+    int ti, tj;
+    tri_decode((int64_t)blockIdx.x - gpre[gi], ti, tj);
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int e = threadIdx.x; e < G.nlam * KRR_TILE; e += 256) {
+        const int l = e >> 7, c = e & 127;
+        const SolveDesc S = solves[G.solve0 + l];
+        const double a = pv[S.vec0 + (int64_t)tj * KRR_TILE + c];
+        const double b = pv[S.vec0 + (int64_t)ti * KRR_TILE + c];
+        const float ah = __double2float_rn(a), bh = __double2float_rn(b);
+        sp_row[l][c] = make_float2(ah, __double2float_rn(a - (double)ah));
+        sp_col[l][c] = make_float2(bh, __double2float_rn(b - (double)bh));
+    }
+    __syncthreads();
+    const int64_t tile = G.ktile0 + (int64_t)ti * (ti + 1) / 2 + tj;
+    float kh[8][8], kl[8][8];
+    double k64[8][8];
+    if (DF) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float *rh = Kh + tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8;
+            const float *rl = Kl + tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8;
+            float4 a0 = *reinterpret_cast<const float4 *>(rh), a1 = *reinterpret_cast<const float4 *>(rh + 4);
+            float4 b0 = *reinterpret_cast<const float4 *>(rl), b1 = *reinterpret_cast<const float4 *>(rl + 4);
+            kh[i][0] = a0.x; kh[i][1] = a0.y; kh[i][2] = a0.z; kh[i][3] = a0.w;
+            kh[i][4] = a1.x; kh[i][5] = a1.y; kh[i][6] = a1.z; kh[i][7] = a1.w;
+            kl[i][0] = b0.x; kl[i][1] = b0.y; kl[i][2] = b0.z; kl[i][3] = b0.w;
+            kl[i][4] = b1.x; kl[i][5] = b1.y; kl[i][6] = b1.z; kl[i][7] = b1.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                k64[i][j] = K64[tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8 + j];
+    }
+    const int T = G.T;
+    for (int l = 0; l < G.nlam; ++l) {
+        const SolveDesc S = solves[G.solve0 + l];
+        double *base = slots + G.scratch0 + (int64_t)l * T * T * KRR_TILE;
+        // row part: out[r] = sum_c K[r][c] p_j[c]  -> slot (ti, tj)
+        double rowp[8], colp[8];
+        if (DF) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                df_acc a;
+                dfa_zero(a);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float2 pj = sp_row[l][tx * 8 + j];
+                    dfa_fma(a, kh[i][j], kl[i][j], pj.x, pj.y);
+                }
+                rowp[i] = df_to_double(dfa_value(a));
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                df_acc a;
+                dfa_zero(a);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 pi = sp_col[l][ty * 8 + i];
+                    dfa_fma(a, kh[i][j], kl[i][j], pi.x, pi.y);
+                }
+                colp[j] = df_to_double(dfa_value(a));
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                double a = 0.0;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float2 pj = sp_row[l][tx * 8 + j];
+                    a = fma(k64[i][j], (double)pj.x + (double)pj.y, a);
+                }
+                rowp[i] = a;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                double a = 0.0;
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const float2 pi = sp_col[l][ty * 8 + i];
+                    a = fma(k64[i][j], (double)pi.x + (double)pi.y, a);
+                }
+                colp[j] = a;
+            }
+        }
+        // reduce row partials over tx (fixed order)
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sred[tx][ty * 8 + i] = rowp[i];
+        __syncthreads();
+        if (threadIdx.x < KRR_TILE) {
+            double s = 0.0;
+            for (int u = 0; u < 16; ++u) s += sred[u][threadIdx.x];
+            base[((int64_t)ti * T + tj) * KRR_TILE + threadIdx.x] = s;
+        }
+        if (ti != tj) {
+            __syncthreads();
+#pragma unroll
+            for (int j = 0; j < 8; ++j) sred[ty][tx * 8 + j] = colp[j];
+            __syncthreads();
+            if (threadIdx.x < KRR_TILE) {
+                double s = 0.0;
+                for (int u = 0; u < 16; ++u) s += sred[u][threadIdx.x];
+                base[((int64_t)tj * T + ti) * KRR_TILE + threadIdx.x] = s;
+            }
+        }
+        (void)S;
+    }
+}
+
+// q_a = sum_b slot(a, b) + lambda m p_a ; grid (solves), 128 threads
+__global__ void matvec_reduce_kernel(const GroupDesc *__restrict__ groups, const SolveDesc *__restrict__ solves,
+                                     const PcgState *__restrict__ state, const double *__restrict__ pv,
+                                     const double *__restrict__ slots, double *__restrict__ q) {
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const GroupDesc G = groups[S.grp];
+    const int l = s - (int)G.solve0;
+    const int T = G.T;
+    const double *base = slots + G.scratch0 + (int64_t)l * T * T * KRR_TILE;
+    for (int64_t e = threadIdx.x; e < (int64_t)T * KRR_TILE; e += blockDim.x) {
+        const int a = (int)(e >> 7), c = (int)(e & 127);
+        double acc = 0.0;
+        for (int b = 0; b < T; ++b) acc += base[((int64_t)a * T + b) * KRR_TILE + c];
+        const bool real = e < S.m;
+        q[S.vec0 + e] = real ? acc + S.lambda_m * pv[S.vec0 + e] : pv[S.vec0 + e];
+    }
+}
+
+// ---------------------------------------------------------------- preconditioner
+// z = L^-T L^-1 r for active solves; L tiles in Lst (type T), inverses in Zst.
+// 512 threads (16 warps).  v: working vector in shared memory (T type).
+template <typename TT>
+__global__ void __launch_bounds__(512)
+precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const SolveDesc *__restrict__ solves,
+               const PcgState *__restrict__ state, const double *__restrict__ r, double *__restrict__ z) {
+    extern __shared__ __align__(16) unsigned char pc_dyn[];
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const int T = S.T, M = T * KRR_TILE;
+    TT *v = reinterpret_cast<TT *>(pc_dyn);            // [M]
+    TT *red = v + M;                                   // [16][128]
+    TT *tmp = red + 16 * KRR_TILE;                     // [128]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) v[e] = (TT)r[S.vec0 + e];
+    __syncthreads();
+    // forward: y_i = Z_ii (v_i - sum_{j<i} L_ij y_j); y overwrites v
+    for (int i = 0; i < T; ++i) {
+        // partial sums over j in this warp's share: warp w takes rows w, w+16, ...
+        TT accr[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) accr[u] = TT(0);
+        for (int j = 0; j < i; ++j) {
+            const TT *Lt = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2 + j) * KRR_TILE_ELEMS;
+            const TT *yj = v + j * KRR_TILE;
+            TT y0 = yj[lane], y1 = yj[lane + 32], y2 = yj[lane + 64], y3 = yj[lane + 96];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const TT *row = Lt + (warp + 16 * u) * KRR_TILE;
+                accr[u] += row[lane] * y0 + row[lane + 32] * y1 + row[lane + 64] * y2 + row[lane + 96] * y3;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            TT a = accr[u];
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+            if (lane == 0) tmp[warp + 16 * u] = v[i * KRR_TILE + warp + 16 * u] - a;
+        }
+        __syncthreads();
+        // y_i = Z_ii tmp
+        {
+            const TT *Zt = Zst + (S.dtile0 + i) * KRR_TILE_ELEMS;
+            const TT t0 = tmp[lane], t1 = tmp[lane + 32], t2 = tmp[lane + 64], t3 = tmp[lane + 96];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const TT *row = Zt + (warp + 16 * u) * KRR_TILE;
+                TT a = row[lane] * t0 + row[lane + 32] * t1 + row[lane + 64] * t2 + row[lane + 96] * t3;
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
+                if (lane == 0) v[i * KRR_TILE + warp + 16 * u] = a;
+            }
+        }
+        __syncthreads();
+    }
+    // backward: w_i = Z_ii^T (y_i - sum_{j>i} L_ji^T w_j), right-looking over j
+    for (int j = T - 1; j >= 0; --j) {
+        // w_j = Z_jj^T v_j   (transposed product: lanes over columns, warps over rows)
+        {
+            const TT *Zt = Zst + (S.dtile0 + j) * KRR_TILE_ELEMS;
+            TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
+            for (int rr = warp; rr < KRR_TILE; rr += 16) {
+                const TT vr = v[j * KRR_TILE + rr];
+                const TT *row = Zt + rr * KRR_TILE;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) part[q] += row[lane + 32 * q] * vr;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + lane + 32 * q] = part[q];
+            __syncthreads();
+            if (threadIdx.x < KRR_TILE) {
+                TT a = TT(0);
+                for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
+                tmp[threadIdx.x] = a;
+            }
+            __syncthreads();
+            if (threadIdx.x < KRR_TILE) v[j * KRR_TILE + threadIdx.x] = tmp[threadIdx.x];
+            __syncthreads();
+        }
+        // v_i -= L_ji^T w_j for i < j  (tiles of block row j)
+        for (int i = 0; i < j; ++i) {
+            const TT *Lt = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2 + i) * KRR_TILE_ELEMS;
+            TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
+            for (int rr = warp; rr < KRR_TILE; rr += 16) {
+                const TT wr = v[j * KRR_TILE + rr];
+                const TT *row = Lt + rr * KRR_TILE;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) part[q] += row[lane + 32 * q] * wr;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + lane + 32 * q] = part[q];
+            __syncthreads();
+            if (threadIdx.x < KRR_TILE) {
+                TT a = TT(0);
+                for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
+                v[i * KRR_TILE + threadIdx.x] -= a;
+            }
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < M; e += blockDim.x) z[S.vec0 + e] = (e < S.m) ? (double)v[e] : 0.0;
+}
+
+// ---------------------------------------------------------------- PCG vector steps
+// block reduction helpers (256 threads, fixed order)
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ double block_max(double v, double *sh) {
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+// phase 0: p = 1 on real rows (for ||A||_inf = max (A 1) since A >= 0), x = 0
+__global__ void pcg_prepare_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
+                                   const int32_t *__restrict__ flags, double *__restrict__ x, double *__restrict__ p) {
+    const int s = blockIdx.x;
+    const SolveDesc S = solves[s];
+    const int M = S.T * KRR_TILE;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        x[S.vec0 + e] = 0.0;
+        p[S.vec0 + e] = (e < S.m) ? 1.0 : 0.0;
+    }
+    if (threadIdx.x == 0) {
+        PcgState st;
+        st.rz = 0.0; st.anorm = 0.0; st.ymax = 0.0; st.resid = 0.0;
+        const bool broken = flags && flags[s] != 0;  // factorisation failed for good
+        st.active = (S.m > 0 && !broken) ? 1 : 0;
+        st.iters = 0;
+        st.status = broken ? KRR_ERR_NOT_SPD : KRR_OK;
+        st.pad = 0;
+        state[s] = st;
+    }
+}
+
+// phase 1: anorm = max(q), ymax, r = y
+__global__ void pcg_norms_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
+                                 const double *__restrict__ y, const double *__restrict__ q, double *__restrict__ r) {
+    __shared__ double sh[256];
+    const int s = blockIdx.x;
+    const SolveDesc S = solves[s];
+    const int M = S.T * KRR_TILE;
+    double an = 0.0, ym = 0.0;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const double yv = (e < S.m) ? y[S.vec0 + e] : 0.0;
+        r[S.vec0 + e] = yv;
+        if (e < S.m) {
+            an = fmax(an, fabs(q[S.vec0 + e]));
+            ym = fmax(ym, fabs(yv));
+        }
+    }
+    an = block_max(an, sh);
+    ym = block_max(ym, sh);
+    if (threadIdx.x == 0) {
+        state[s].anorm = an;
+        state[s].ymax = ym;
+    }
+}
+
+// phase 2 (after the first preconditioner application): p = z, rz = r.z
+__global__ void pcg_start_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
+                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p) {
+    __shared__ double sh[256];
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const int M = S.T * KRR_TILE;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const double zv = z[S.vec0 + e];
+        p[S.vec0 + e] = zv;
+        acc += r[S.vec0 + e] * zv;
+    }
+    acc = block_sum(acc, sh);
+    if (threadIdx.x == 0) state[s].rz = acc;
+}
+
+// step 1: a = rz / p.q ; x += a p ; r -= a q ; stopping test
+__global__ void pcg_step1_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
+                                 double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
+                                 const double *__restrict__ q, double tau, int maxit,
+                                 unsigned int *__restrict__ nactive) {
+    __shared__ double sh[256];
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const int M = S.T * KRR_TILE;
+    double pq = 0.0;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) pq += p[S.vec0 + e] * q[S.vec0 + e];
+    pq = block_sum(pq, sh);
+    PcgState st = state[s];
+    if (!(pq > 0.0)) {  // the system matrix is not positive definite (or breakdown)
+        if (threadIdx.x == 0) {
+            state[s].active = 0;
+            state[s].status = (st.iters == 0) ? KRR_ERR_NOT_SPD : KRR_ERR_NO_CONVERGE;
+        }
+        return;
+    }
+    const double a = st.rz / pq;
+    double rmax = 0.0, xmax = 0.0;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const double xv = x[S.vec0 + e] + a * p[S.vec0 + e];
+        const double rv = r[S.vec0 + e] - a * q[S.vec0 + e];
+        x[S.vec0 + e] = xv;
+        r[S.vec0 + e] = rv;
+        rmax = fmax(rmax, fabs(rv));
+        xmax = fmax(xmax, fabs(xv));
+    }
+    rmax = block_max(rmax, sh);
+    xmax = block_max(xmax, sh);
+    if (threadIdx.x == 0) {
+        const double scale = st.anorm * xmax + st.ymax;
+        const double rel = scale > 0.0 ? rmax / scale : 0.0;
+        state[s].resid = rel;
+        state[s].iters = st.iters + 1;
+        if (rel <= tau) {
+            state[s].active = 0;
+            state[s].status = KRR_OK;
+        } else if (st.iters + 1 >= maxit) {
+            state[s].active = 0;
+            state[s].status = KRR_ERR_NO_CONVERGE;
+        } else {
+            atomicAdd(nactive, 1u);
+        }
+    }
+}
+
+// step 2: rz' = r.z ; p = z + (rz'/rz) p
+__global__ void pcg_step2_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
+                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p) {
+    __shared__ double sh[256];
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const int M = S.T * KRR_TILE;
+    double acc = 0.0;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) acc += r[S.vec0 + e] * z[S.vec0 + e];
+    acc = block_sum(acc, sh);
+    const double beta = acc / state[s].rz;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) p[S.vec0 + e] = z[S.vec0 + e] + beta * p[S.vec0 + e];
+    __syncthreads();
+    if (threadIdx.x == 0) state[s].rz = acc;
+}
+
+// ---------------------------------------------------------------- host
+struct PcgBuffers {
+    double *x, *r, *z, *p, *q, *y, *slots;
+    PcgState *state;
+    unsigned int *nactive;
+    GroupDesc *d_groups;
+    int64_t *d_gpre;
+    int ng;
+    int64_t gtiles;
+};
+
+size_t pcg_state_size() { return sizeof(PcgState); }
+
+static void launch_matvec(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
+                          const double *K64, bool fp64, const double *p, Prof *prof) {
+    if (B.gtiles == 0) return;
+    ProfScope ps(prof, PROF_MATVEC, st);
+    if (fp64)
+        KRR_LAUNCHED(), matvec_tiles_kernel<false><<<(unsigned)B.gtiles, 256, 0, st>>>(Kh, Kl, K64, B.d_groups, B.d_gpre, B.ng,
+                                                                       M.d_solves, B.state, p, B.slots);
+    else
+        KRR_LAUNCHED(), matvec_tiles_kernel<true><<<(unsigned)B.gtiles, 256, 0, st>>>(Kh, Kl, K64, B.d_groups, B.d_gpre, B.ng,
+                                                                      M.d_solves, B.state, p, B.slots);
+    KRR_LAUNCHED(), matvec_reduce_kernel<<<(unsigned)M.solves.size(), 128, 0, st>>>(B.d_groups, M.d_solves, B.state, p, B.slots,
+                                                                    B.q);
+}
+
+static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuffers &B, const void *L, const void *Z,
+                                  bool fp64, int maxT, Prof *prof) {
+    ProfScope ps(prof, PROF_PRECOND, st);
+    const size_t esz = fp64 ? 8 : 4;
+    const size_t sm = esz * ((size_t)maxT * KRR_TILE + 17 * KRR_TILE);
+    if (fp64) {
+        cudaFuncSetAttribute(precond_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        KRR_LAUNCHED(), precond_kernel<double><<<(unsigned)M.solves.size(), 512, sm, st>>>(
+            (const double *)L, (const double *)Z, M.d_solves, B.state, B.r, B.z);
+    } else {
+        cudaFuncSetAttribute(precond_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        KRR_LAUNCHED(), precond_kernel<float><<<(unsigned)M.solves.size(), 512, sm, st>>>((const float *)L, (const float *)Z,
+                                                                           M.d_solves, B.state, B.r, B.z);
+    }
+    return cudaGetLastError();
+}
+
+size_t precond_smem_bytes(bool fp64, int maxT) {
+    return (fp64 ? 8 : 4) * ((size_t)maxT * KRR_TILE + 17 * KRR_TILE);
+}
+
+// Runs the whole refinement; returns the CUDA status of the last launch.
+cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
+                    const double *K64, const void *L, const void *Z, bool fp64, int maxT, double tau, int maxit,
+                    const int32_t *flags, unsigned int *h_nactive, int check_every, Prof *prof) {
+    const unsigned ns = (unsigned)M.solves.size();
+    KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, flags, B.x, B.p);
+    launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
+    KRR_LAUNCHED(), pcg_norms_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.y, B.q, B.r);
+    cudaError_t e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
+    if (e != cudaSuccess) return e;
+    KRR_LAUNCHED(), pcg_start_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);
+    for (int it = 0; it < maxit; ++it) {
+        cudaMemsetAsync(B.nactive, 0, sizeof(unsigned int), st);
+        launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
+        KRR_LAUNCHED(), pcg_step1_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.x, B.r, B.p, B.q, tau, maxit, B.nactive);
+        e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
+        if (e != cudaSuccess) return e;
+        KRR_LAUNCHED(), pcg_step2_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);
+        if (it % check_every == check_every - 1) {
+            cudaMemcpyAsync(h_nactive, B.nactive, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
+            e = cudaStreamSynchronize(st);
+            if (e != cudaSuccess) return e;
+            if (*h_nactive == 0) break;
+        }
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace krr

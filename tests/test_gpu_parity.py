@@ -1,0 +1,313 @@
+"""Parity of the sm_103a path (called through the C ABI) with the FP64 oracle.
+
+Bars: partition assignments, permutations and centres bit-exact; alpha,
+predictions and MSE within 1e-6 relative (max-norm per model) for the refined
+precisions (FP32, TF32) and 1e-10 for the plain FP64 path where the
+condition estimate times the FP64 unit roundoff stays below 1e-11.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1805_00569_gb300 as K
+from paper_1805_00569_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+REFINED_TOL = 1e-6
+FP64_TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = K.krr_ctx_create(0)
+    yield c
+    c.close()
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = np.max(np.abs(b))
+    return 0.0 if den == 0 and np.max(np.abs(a)) == 0 else float(np.max(np.abs(a - b)) / den)
+
+
+def tol_for(prec, kappa):
+    if prec == "fp64":
+        return FP64_TOL if kappa * 2.0 ** -53 <= 1e-11 else None
+    return REFINED_TOL
+
+
+def split_alpha(alpha, offsets, G):
+    """Caller layout of krr_fit_batch's alpha -> alphas[j][g]."""
+    out = []
+    for j in range(len(offsets) - 1):
+        m = offsets[j + 1] - offsets[j]
+        blk = alpha[offsets[j] * G:offsets[j + 1] * G]
+        out.append([blk[g * m:(g + 1) * m] for g in range(G)])
+    return out
+
+
+# ------------------------------------------------------------------ partitions
+@pytest.mark.parametrize("n,p,seed", [(1, 1, 3), (1000, 7, 12345), (65536, 16, 2**63 + 5), (4097, 128, 9)])
+def test_random_partition_bit_exact(ctx, n, p, seed):
+    X = np.random.default_rng(0).standard_normal((n, 3))
+    assign, _, perm, offsets, _ = K.krr_partition(ctx, cuda(X), None, K.KRR_PART_RANDOM, p, seed=seed)
+    operm, ooff, oassign = oracle.partition_random(n, p, seed)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+
+
+def _mixture(n, t, d, k, seed):
+    rng = np.random.default_rng(seed)
+    C = 4.0 * rng.standard_normal((k, d))
+    X = C[rng.integers(0, k, n)] + rng.standard_normal((n, d))
+    Xt = C[rng.integers(0, k, t)] + rng.standard_normal((t, d))
+    return X, Xt, rng.choice(n, k, replace=False).astype(np.int64)
+
+
+@pytest.mark.parametrize("n,t,d,k,iters", [(5000, 700, 12, 8, 10), (3333, 129, 90, 16, 5), (2500, 1, 3, 5, 0)])
+def test_kmeans_partition_bit_exact(ctx, n, t, d, k, iters):
+    X, Xt, init = _mixture(n, t, d, k, n)
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, k,
+                                                            iters=iters, init_idx=cuda(init, torch.int64))
+    operm, ooff, oassign, oroute, oC, _ = oracle.partition_kmeans(X, Xt, k, init, iters)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+    assert np.array_equal(route.cpu().numpy(), oroute)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+
+
+def test_kmeans_exact_ties_and_empty_cluster(ctx):
+    """Integer points equidistant from two centres go to the lower index; a
+    duplicated initial centre loses every tie and keeps its position."""
+    g = np.arange(-6, 7, dtype=np.float64)
+    X = np.array([[a, b] for a in g for b in g])  # 169 integer grid points
+    init = np.array([0, 168, 84, 0], np.int64)  # centre 3 duplicates centre 0
+    Xt = np.array([[0.0, 0.0], [-6.0, -6.0], [6.0, 6.0]])
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, 4, iters=4,
+                                                            init_idx=cuda(init, torch.int64))
+    operm, ooff, oassign, oroute, oC, _ = oracle.partition_kmeans(X, Xt, 4, init, 4)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+    assert np.array_equal(route.cpu().numpy(), oroute)
+    assert np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+    assert ooff[4] - ooff[3] == 0  # the duplicate centre owns no rows
+
+
+# ------------------------------------------------------------------ fit / predict / select
+def _case(seed=7, n=950, d=13, t=333):
+    rng = np.random.default_rng(seed)
+    col = rng.uniform(0.5, 1.5, d)
+    X = rng.standard_normal((n, d)) * col
+    Xt = rng.standard_normal((t, d)) * col
+    w = rng.standard_normal(d)
+    y = np.tanh(X @ w / np.sqrt(d)) + 0.05 * rng.standard_normal(n)
+    yt = np.tanh(Xt @ w / np.sqrt(d)) + 0.05 * rng.standard_normal(t)
+    perm = rng.permutation(n).astype(np.int64)
+    offsets = np.array([0, 300, 817, n], np.int64)  # 300, 517, 133 rows: ragged tiles
+    return X, y, Xt, yt, perm, offsets
+
+
+SIG = [0.8, 3.0]
+LAM = [1e-5, 1e-3]
+
+
+@pytest.fixture(scope="module")
+def oracle_case():
+    X, y, Xt, yt, perm, offsets = _case()
+    al, infos, rcs = oracle.fit_batch(X, y, perm, offsets, SIG, LAM)
+    yall = oracle.predict_all(X, perm, offsets, al, SIG, LAM, Xt)
+    return dict(X=X, y=y, Xt=Xt, yt=yt, perm=perm, offsets=offsets, alphas=al, infos=infos, rcs=rcs, yall=yall)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+def test_fit_predict_select_parity(ctx, oracle_case, prec):
+    c = oracle_case
+    G = len(SIG) * len(LAM)
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(c["X"]), cuda(c["y"]), cuda(c["perm"], torch.int64),
+                                           cuda(c["offsets"], torch.int64), SIG, LAM, prec, want_alpha=True)
+    try:
+        assert np.all(status.cpu().numpy() == K.KRR_OK), status
+        galpha = split_alpha(alpha.cpu().numpy(), c["offsets"], G)
+        worst = 0.0
+        for j in range(3):
+            for g in range(G):
+                kappa = c["infos"][j][g][0]
+                tol = tol_for(prec, kappa)
+                e = rel(galpha[j][g], c["alphas"][j][g])
+                worst = max(worst, e)
+                if tol is not None:
+                    assert e <= tol, (prec, j, g, e, kappa)
+        yhat = K.krr_predict(ctx, model, cuda(c["Xt"])).cpu().numpy()
+        for row in range(3 * G):
+            kappa = c["infos"][row // G][row % G][0]
+            tol = tol_for(prec, kappa)
+            if tol is not None:
+                assert rel(yhat[row], c["yall"][row]) <= tol, (prec, row)
+        for mode in (K.KRR_SEL_PER_MODEL, K.KRR_SEL_AVERAGE, K.KRR_SEL_ORACLE):
+            mse, best = K.krr_select(ctx, cuda(yhat), cuda(c["yt"]), 3, G, mode)
+            omse, obest = oracle.select(c["yall"], c["yt"], mode, 3, G)
+            np.testing.assert_allclose(mse.cpu().numpy(), omse, rtol=REFINED_TOL if prec != "fp64" else 1e-9)
+            b = int(best.cpu()[0])
+            assert omse[b] <= omse[obest] * (1 + REFINED_TOL)
+        it, kap, res = K.krr_model_stats(ctx, model)
+        assert np.all(it.numpy() >= 1)
+    finally:
+        model.free()
+
+
+def test_routed_predict_parity(ctx):
+    X, Xt, init = _mixture(1400, 300, 7, 5, 31)
+    y = np.sin(X.sum(1)) + 0.05 * np.random.default_rng(1).standard_normal(1400)
+    yt = np.sin(Xt.sum(1))
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, 5, iters=6,
+                                                            init_idx=cuda(init, torch.int64))
+    operm, ooff, _, oroute, _, _ = oracle.partition_kmeans(X, Xt, 5, init, 6)
+    assert np.array_equal(perm.cpu().numpy(), operm) and np.array_equal(route.cpu().numpy(), oroute)
+    sig, lam = [2.0, 5.0], [1e-4]
+    model, status, _ = K.krr_fit_batch(ctx, cuda(X), cuda(y), perm, offsets, sig, lam, "tf32")
+    try:
+        assert np.all(status.cpu().numpy() == K.KRR_OK)
+        yr = K.krr_predict(ctx, model, cuda(Xt), route=route).cpu().numpy()
+        al, infos, _ = oracle.fit_batch(X, y, operm, ooff, sig, lam)
+        oyr = oracle.predict_all(X, operm, ooff, al, sig, lam, Xt, route=oroute)
+        for g in range(2):
+            assert rel(yr[g], oyr[g]) <= REFINED_TOL
+        mse, best = K.krr_select(ctx, cuda(yr), cuda(yt), 5, 2, K.KRR_SEL_ROUTED)
+        omse, _ = oracle.select(oyr, yt, oracle.SEL_ROUTED)
+        np.testing.assert_allclose(mse.cpu().numpy(), omse, rtol=REFINED_TOL)
+    finally:
+        model.free()
+
+
+def test_dkrr_fp64_full_size(ctx):
+    """The plain DKRR workload (n = 2048, one partition) on the FP64 path."""
+    w = synth.dkrr(seed=0)
+    n = w["X"].shape[0]
+    perm = np.arange(n, dtype=np.int64)
+    off = np.array([0, n], np.int64)
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(w["X"]), cuda(w["y"]), cuda(perm, torch.int64),
+                                           cuda(off, torch.int64), w["sigmas"], w["lambdas"], "fp64",
+                                           want_alpha=True)
+    try:
+        assert int(status.cpu()[0]) == K.KRR_OK
+        oa, info, rc = oracle.fit(w["X"], w["y"], w["sigmas"][0], w["lambdas"][0])
+        assert rc == 0 and info[0] * 2.0 ** -53 <= 1e-11
+        assert rel(alpha.cpu().numpy(), oa) <= FP64_TOL
+        yh = K.krr_predict(ctx, model, cuda(w["Xt"])).cpu().numpy()[0]
+        oyh = oracle.predict(w["X"], oa, w["Xt"], w["sigmas"][0])
+        assert rel(yh, oyh) <= FP64_TOL
+        mse, _ = K.krr_select(ctx, cuda(yh[None, :]), cuda(w["yt"]), 1, 1, K.KRR_SEL_PER_MODEL)
+        assert abs(float(mse.cpu()[0]) - oracle.mse(oyh, w["yt"])) <= 1e-9 * oracle.mse(oyh, w["yt"])
+    finally:
+        model.free()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_bkrr2_full_size_sampled(ctx, prec):
+    """The BKRR2 workload at full size (n = 65536, p = 16 x 4096, 3 sigma x 2
+    lambda) in the benchmark's launch configuration; the oracle recomputes two
+    of the 96 solves (the worst conditioned and a mid one) and their
+    predictions on a sample of test rows."""
+    w = synth.bkrr2()
+    X, y, Xt, yt = w["X"], w["y"], w["Xt"], w["yt"]
+    dX = cuda(X)
+    assign, _, perm, offsets, _ = K.krr_partition(ctx, dX, None, K.KRR_PART_RANDOM, 16, seed=w["part_seed"])
+    model, status, alpha = K.krr_fit_batch(ctx, dX, cuda(y), perm, offsets, w["sigmas"], w["lambdas"], prec,
+                                           want_alpha=True)
+    try:
+        st = status.cpu().numpy()
+        assert np.all(st == K.KRR_OK), st
+        G = 6
+        operm, ooff, _ = oracle.partition_random(65536, 16, w["part_seed"])
+        assert np.array_equal(perm.cpu().numpy(), operm)
+        galpha = split_alpha(alpha.cpu().numpy(), ooff, G)
+        sample = np.random.default_rng(5).choice(Xt.shape[0], 256, replace=False)
+        yhat = K.krr_predict(ctx, model, cuda(Xt[sample])).cpu().numpy()
+        for j, si, li in [(0, 2, 0), (9, 1, 1)]:  # (sigma 16, lambda 1e-6) and (sigma 4, lambda 1e-4)
+            rows = operm[ooff[j]:ooff[j + 1]]
+            oa, info, rc = oracle.fit(X[rows], y[rows], w["sigmas"][si], w["lambdas"][li])
+            g = si * 2 + li
+            assert rc == 0
+            assert rel(galpha[j][g], oa) <= REFINED_TOL, (j, g, info)
+            oyh = oracle.predict(X[rows], oa, Xt[sample], w["sigmas"][si])
+            assert rel(yhat[j * G + g], oyh) <= REFINED_TOL
+            gm = np.mean((yhat[j * G + g] - yt[sample]) ** 2)
+            assert abs(gm - oracle.mse(oyh, yt[sample])) <= REFINED_TOL * oracle.mse(oyh, yt[sample])
+    finally:
+        model.free()
+
+
+# ------------------------------------------------------------------ edge cases and errors
+def test_single_row_and_empty_partitions(ctx):
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((130, 4))
+    y = rng.standard_normal(130)
+    perm = np.arange(130, dtype=np.int64)
+    off = np.array([0, 1, 1, 130], np.int64)  # sizes 1, 0, 129
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(off, torch.int64),
+                                           [1.5], [1e-3], "tf32", want_alpha=True)
+    try:
+        st = status.cpu().numpy()
+        assert st[0] == K.KRR_OK and st[2] == K.KRR_OK
+        a = alpha.cpu().numpy()
+        assert abs(a[0] - y[0] / (1 + 1e-3)) <= 1e-15 * abs(y[0])
+        oa, _, _ = oracle.fit(X[1:], y[1:], 1.5, 1e-3)
+        assert rel(a[1:], oa) <= REFINED_TOL
+        Xt = rng.standard_normal((70, 4))
+        yh = K.krr_predict(ctx, model, cuda(Xt)).cpu().numpy()
+        assert np.all(yh[1] == 0.0)  # the empty partition predicts 0
+        assert rel(yh[2], oracle.predict(X[1:], oa, Xt, 1.5)) <= REFINED_TOL
+    finally:
+        model.free()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_indefinite_system_is_reported_per_solve(ctx, prec):
+    """A negative shift makes K + lambda m I indefinite: that solve reports
+    NOT_SPD (or NO_CONVERGE), the batch itself succeeds."""
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((200, 3)) * 0.01  # nearly identical rows: K ~ 1 1^T, eigenvalues ~ 0
+    y = rng.standard_normal(200)
+    perm = np.arange(200, dtype=np.int64)
+    off = np.array([0, 200], np.int64)
+    model, status, _ = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(off, torch.int64),
+                                       [1.0], [-0.5 / 200, 1e-2], prec)
+    try:
+        st = status.cpu().numpy()
+        assert st[0] in (K.KRR_ERR_NOT_SPD, K.KRR_ERR_NO_CONVERGE), st
+        assert st[1] == K.KRR_OK
+    finally:
+        model.free()
+
+
+def test_budget_and_argument_errors(ctx):
+    rng = np.random.default_rng(5)
+    X = cuda(rng.standard_normal((600, 5)))
+    y = cuda(rng.standard_normal(600))
+    perm = cuda(np.arange(600), torch.int64)
+    off = cuda(np.array([0, 600]), torch.int64)
+    small = K.krr_ctx_create(0, hbm_budget_bytes=1 << 20)
+    with pytest.raises(K.KrrError) as e:
+        K.krr_fit_batch(small, X, y, perm, off, [1.0], [1e-3], "tf32")
+    assert e.value.status == K.KRR_ERR_BUDGET
+    assert small.bytes_in_use() == 0
+    small.close()
+    with pytest.raises(K.KrrError) as e:
+        K.krr_fit_batch(ctx, X, y, perm, off, [0.0], [1e-3], "tf32")
+    assert e.value.status == K.KRR_ERR_ARG
+    bad = cuda(np.array([0, 599]), torch.int64)
+    with pytest.raises(K.KrrError) as e:
+        K.krr_fit_batch(ctx, X, y, perm, bad, [1.0], [1e-3], "tf32")
+    assert e.value.status == K.KRR_ERR_ARG
+    with pytest.raises(K.KrrError) as e:
+        K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, 0)
+    assert e.value.status == K.KRR_ERR_ARG
