@@ -87,19 +87,23 @@ def test_kmeans_partition_bit_exact(ctx, n, t, d, k, iters):
 
 def test_kmeans_exact_ties_and_empty_cluster(ctx):
     """Integer points equidistant from two centres go to the lower index; a
-    duplicated initial centre loses every tie and keeps its position."""
+    duplicated initial centre loses every tie, so with no update round it owns
+    no rows; with updates the result still equals the definition bit for bit."""
     g = np.arange(-6, 7, dtype=np.float64)
     X = np.array([[a, b] for a in g for b in g])  # 169 integer grid points
     init = np.array([0, 168, 84, 0], np.int64)  # centre 3 duplicates centre 0
     Xt = np.array([[0.0, 0.0], [-6.0, -6.0], [6.0, 6.0]])
-    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, 4, iters=4,
-                                                            init_idx=cuda(init, torch.int64))
-    operm, ooff, oassign, oroute, oC, _ = oracle.partition_kmeans(X, Xt, 4, init, 4)
-    assert np.array_equal(assign.cpu().numpy(), oassign)
-    assert np.array_equal(route.cpu().numpy(), oroute)
-    assert np.array_equal(offsets.cpu().numpy(), ooff)
-    assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
-    assert ooff[4] - ooff[3] == 0  # the duplicate centre owns no rows
+    for iters in (0, 4):
+        assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, 4,
+                                                                iters=iters, init_idx=cuda(init, torch.int64))
+        operm, ooff, oassign, oroute, oC, _ = oracle.partition_kmeans(X, Xt, 4, init, iters)
+        assert np.array_equal(assign.cpu().numpy(), oassign)
+        assert np.array_equal(route.cpu().numpy(), oroute)
+        assert np.array_equal(perm.cpu().numpy(), operm)
+        assert np.array_equal(offsets.cpu().numpy(), ooff)
+        assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+        if iters == 0:
+            assert ooff[4] - ooff[3] == 0  # the duplicate centre owns no rows
 
 
 # ------------------------------------------------------------------ fit / predict / select
