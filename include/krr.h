@@ -153,6 +153,29 @@ krr_status krr_model_stats(krr_ctx *ctx, const krr_model *model, int32_t *iters,
 /* Release a model's device memory. */
 krr_status krr_model_free(krr_ctx *ctx, krr_model *model);
 
+/* Group rows by partition without allocating any device memory -- the same
+ * grouping krr_partition performs after its assignment (rows of partition 0
+ * first, ascending row order inside a partition).  The paper has no
+ * counterpart: this variant exists for callers that cannot call cudaMalloc,
+ * e.g. code whose GPU memory is entirely owned by another allocator, or a
+ * request loop that must not allocate because cudaMalloc/cudaFree can
+ * synchronise the device and take unbounded time.
+ *   cuda_stream: the stream to enqueue on (a cudaStream_t; NULL = legacy
+ *   default stream).  assign [n] (device int32, every value in [0, p)),
+ *   perm [n] (device int64, output), offsets [p+1] (device int64, output);
+ *   all caller-owned.  No context is needed and nothing is allocated: the
+ *   per-block counts live in a fixed 4 MiB device array inside the library
+ *   (held on every GPU that loads it until the process exits), so
+ *   ceil(n / 1024) * p must not exceed 524288 and p must not exceed 12288;
+ *   larger requests return KRR_ERR_ARG before anything is enqueued.
+ *   The first call on a device looks up that array's device address (once
+ *   per device); make that first call before any stream capture.  Calls share
+ *   the array and keep the last call's contents (every entry read is written
+ *   first); calls that overlap on the GPU race on it and must be serialised.
+ * Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */
+krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t n, int32_t p, int64_t *perm,
+                              int64_t *offsets);
+
 /* ---- instrumentation and tuning (no counterpart in the paper) ----------
  * krr_ctx_set_profiling: when on, every kernel launch of the context is
  *   bracketed by CUDA events on the context's stream (adds ~2 us per launch).
