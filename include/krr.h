@@ -186,11 +186,16 @@ krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t 
  *   5 trailing update, 6 matvec, 7 preconditioner, 8 CG vector ops,
  *   9 predict, 10 select.  Errors: KRR_ERR_ARG.
  * krr_ctx_set_panel_width: outer panel width W (tiles) of the blocked
- *   Cholesky schedule, 1..64; 0 restores the default.  Errors: KRR_ERR_ARG.
+ *   Cholesky schedule, 1..64; 0 (the default) lets the library tune it: the
+ *   first fit of a context for a given (precision, largest tile count) times
+ *   W in {1, 2, 4, 8} on its own matrices and keeps the fastest.
+ * krr_ctx_get_panel_width: the width in force for (precision, largest tile
+ *   count): the explicit one, the tuned one, or 0 if not tuned yet.
  * krr_launch_count: kernels launched by this process through libkrr. */
 krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
 krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
+krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);
 long long krr_launch_count(void);
 
 #ifdef __cplusplus

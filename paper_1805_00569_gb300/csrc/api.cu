@@ -214,6 +214,13 @@ krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *
     if (launches) *launches = ctx->c.prof.launches[kind];
     return KRR_OK;
 }
+krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W) {
+    if (!ctx || !W) return KRR_ERR_ARG;
+    auto it = ctx->c.tuned_W.find(std::make_pair(prec, max_tiles));
+    *W = ctx->c.chol_W > 0 ? ctx->c.chol_W : (it == ctx->c.tuned_W.end() ? 0 : it->second);
+    return KRR_OK;
+}
+
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W) {
     if (!ctx || W < 0 || W > 64) return KRR_ERR_ARG;
     ctx->c.chol_W = W;
@@ -435,17 +442,69 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         // Cholesky schedule
         std::vector<int> Ts(nsolve);
         for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
-        const int Wp = c->chol_W > 0 ? c->chol_W : 1;
+        CUtensorMap tmap;
+        memset(&tmap, 0, sizeof(tmap));
+        if (tf32 && !make_tile_tmap(&tmap, (float *)Ast, ltiles))
+            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
+        // outer panel width: explicit, cached per (precision, max tiles), or tuned now by timing
+        // each candidate schedule on these matrices (restored from K_hi between trials)
+        int Wp = c->chol_W;
+        const std::pair<int, int> key((int)prec, maxT);
+        if (Wp <= 0 && c->tuned_W.count(key)) Wp = c->tuned_W[key];
+        if (Wp <= 0 && (fp64 || maxT < 4)) Wp = 1;
+        if (Wp <= 0) {
+            DevBuf TW(c);
+            SolveDesc *dummy = nullptr;
+            (void)dummy;
+            int64_t *d_rpre = nullptr, *d_tplan = nullptr;
+            std::vector<int64_t> rpre(nsolve + 1, 0);
+            for (int s = 0; s < nsolve; ++s) rpre[s + 1] = rpre[s] + tri(M.solves[s].T);
+            FIT_TRY(TW.get(&d_rpre, sizeof(int64_t) * (nsolve + 1)));
+            FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsolve + 1), cudaMemcpyHostToDevice, st));
+            cudaEvent_t e0, e1;
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            float best_ms = 1e30f;
+            int best_W = 1;
+            const int cands[4] = {1, 2, 4, 8};
+            for (int ci = 0; ci < 4; ++ci) {
+                const int Wc = cands[ci];
+                if (Wc > maxT) break;
+                std::vector<CholLaunch> tplan;
+                std::vector<int64_t> tpre;
+                build_chol_plan(Ts, Wc, tplan, tpre);
+                if (d_tplan) ctx_free(c, d_tplan, 0), TW.list.pop_back();
+                FIT_TRY(TW.get(&d_tplan, sizeof(int64_t) * std::max<size_t>(tpre.size(), 1)));
+                FIT_TRY(cudaMemcpyAsync(d_tplan, tpre.data(), sizeof(int64_t) * tpre.size(), cudaMemcpyHostToDevice,
+                                        st));
+                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
+                                                                                     (float *)Ast, 0.f);
+                cudaEventRecord(e0, st);
+                FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tf32, &tmap,
+                                      c->d_err, nullptr));
+                cudaEventRecord(e1, st);
+                FIT_TRY(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best_W = Wc;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            Wp = best_W;
+            c->tuned_W[key] = best_W;
+            KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
+                                                                                 (float *)Ast, 0.f);
+            FIT_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * nsolve, st));
+        }
         std::vector<CholLaunch> plan;
         std::vector<int64_t> pre;
         build_chol_plan(Ts, Wp, plan, pre);
         FIT_TRY(W.get(&d_plan, sizeof(int64_t) * std::max<size_t>(pre.size(), 1)));
         if (!pre.empty())
             FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
-        CUtensorMap tmap;
-        memset(&tmap, 0, sizeof(tmap));
-        if (tf32 && !make_tile_tmap(&tmap, (float *)Ast, ltiles))
-            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
         FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tf32, &tmap, c->d_err,
                               prof));
 

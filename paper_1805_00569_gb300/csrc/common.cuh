@@ -6,9 +6,9 @@
 //   technique for extending the available precision", Numer. Math. 1971).
 //   This gives ~44-bit arithmetic on the FP32 pipes, which on GB300 are 64x
 //   faster than the FP64 pipe.
-// * df exponential: Cody-Waite reduction by ln 2 (three-part constant), a
-//   further 2^-4 argument scaling undone by four squarings, and the Taylor
-//   series to degree 6 (relative error ~1e-14 for arguments <= 0).
+// * df exponential: table-driven reduction by ln2/256 (three-part constant,
+//   256-entry df table of 2^(j/256)) and a short series (relative error ~2e-13
+//   for arguments <= 0).
 // * Philox4x32-10 (Salmon et al., SC'11) for the seeded row shuffle.
 // * thin inline-PTX wrappers for mbarrier, cp.async.bulk(.tensor) and tcgen05.
 #pragma once
@@ -77,39 +77,45 @@ __device__ __forceinline__ df dfa_value(const df_acc &a) {
     return r;
 }
 
-// exp(x) for df x <= 0 (x > 0 is clamped to 0), relative error ~1e-14;
-// returns 0 below -87 where the FP32 hi part would be subnormal.
-__device__ __forceinline__ df df_exp_nonpos(df x) {
+// exp(x) for df x <= 0 (x > 0 is clamped to 1); 0 below -87 where the FP32
+// hi part would be subnormal.  Method (table-driven, Tang-style): with
+// n = round(x * 256 / ln 2), x = n ln2/256 + r, |r| <= ln2/512, so
+// exp(x) = 2^(n >> 8) * 2^((n & 255)/256) * exp(r).  ln2/256 is split in three
+// parts (the first with 8 significant bits, so n * C1 is exact for |n| < 2^15
+// and x.hi - n C1 is exact by Sterbenz); exp(r) = 1 + r + q with
+// q = r^2/2 + r^3/6 + r^4/24 taken in FP32 from r.hi (|q| < 1e-6, so its
+// rounding is below 1e-13 absolute); the 256 table values 2^(j/256) are df
+// numbers in shared memory.  Relative error ~2e-13.
+__device__ __forceinline__ void exp_table_init(float2 *tab) {
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) {
+        const double v = exp2((double)j / 256.0);
+        const float h = __double2float_rn(v);
+        tab[j] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+}
+__device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab) {
     if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
     if (x.hi >= 0.f) return df_make(1.f, 0.f);
-    // ln 2 = L1 + L2 + L3; L1 has 15 significant bits so k*L1 is exact.
-    const float L1 = 0x1.62e4p-1f, L2 = 0x1.7f7d1cp-20f, L3 = 0x1.ef357ap-45f;
-    float k = rintf(x.hi * 1.44269504088896341f);
-    float rh = __fsub_rn(x.hi, k * L1);                // exact (Sterbenz)
-    df r = df_add(df_make(rh, 0.f), df_make(x.lo, 0.f));
-    float p2 = __fmul_rn(k, L2), e2 = __fmaf_rn(k, L2, -p2);
+    const float C1 = 0x1.62p-9f, C2 = 0x1.c85fep-18f, C3 = -0x1.718432p-43f;
+    const float nf = rintf(x.hi * 369.329930467574632284140718f);  // 256 / ln 2
+    const int n = (int)nf;
+    df r = df_add(df_make(__fsub_rn(x.hi, nf * C1), 0.f), df_make(x.lo, 0.f));
+    const float p2 = __fmul_rn(nf, C2), e2 = __fmaf_rn(nf, C2, -p2);
     r = df_add(r, df_make(-p2, -e2));
-    r = df_add(r, df_make(-k * L3, 0.f));
-    r = df_scale2(r, 0.0625f);                          // |r| <= 0.0217
-    // Taylor coefficients 1/j!, j = 6..0, as df constants.
-    const df c6 = df_make(0x1.6c16c2p-10f, -0x1.27d27ep-35f);
-    const df c5 = df_make(0x1.111112p-7f, -0x1.dddddep-32f);
-    const df c4 = df_make(0x1.555556p-5f, -0x1.555556p-30f);
-    const df c3 = df_make(0x1.555556p-3f, -0x1.555556p-28f);
-    df y = c6;
-    y = df_add(df_mul(y, r), c5);
-    y = df_add(df_mul(y, r), c4);
-    y = df_add(df_mul(y, r), c3);
-    y = df_add(df_mul(y, r), df_make(0.5f, 0.f));
-    y = df_add(df_mul(y, r), df_make(1.f, 0.f));
-    y = df_add(df_mul(y, r), df_make(1.f, 0.f));
-    y = df_mul(y, y); y = df_mul(y, y); y = df_mul(y, y); y = df_mul(y, y);
-    // scale by 2^k in two exact steps (k >= -126)
-    int ki = (int)k;
-    int k1 = ki / 2, k2 = ki - k1;
-    float s1 = __int_as_float((127 + k1) << 23), s2 = __int_as_float((127 + k2) << 23);
-    y = df_scale2(df_scale2(y, s1), s2);
-    return y;
+    r = df_add(r, df_make(-nf * C3, 0.f));
+    const float h = r.hi;
+    const float q = h * h * __fmaf_rn(h, __fmaf_rn(h, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
+    float s, t;
+    fast_two_sum(1.0f, h, s, t);
+    t = __fadd_rn(t, __fadd_rn(r.lo, q));
+    df e;
+    fast_two_sum(s, t, e.hi, e.lo);
+    const float2 tv = tab[n & 255];
+    df y = df_mul(df_make(tv.x, tv.y), e);
+    const int k = n >> 8;  // floor division, k in [-126, 0]
+    const int k1 = k / 2, k2 = k - k1;
+    const float s1 = __int_as_float((127 + k1) << 23), s2 = __int_as_float((127 + k2) << 23);
+    return df_scale2(df_scale2(y, s1), s2);
 }
 
 // ----------------------------------------------------------------- Philox4x32-10

@@ -6,6 +6,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <atomic>
+#include <map>
 
 #include "../../include/krr.h"
 
@@ -123,6 +124,7 @@ struct Ctx {
     unsigned int *h_flag = nullptr;  // pinned host word for polling
     Prof prof;
     int chol_W = 0;            // outer panel width (0 = tuned on first use)
+    std::map<std::pair<int, int>, int> tuned_W;  // (precision, max tiles) -> tuned panel width
 };
 
 struct Model {

@@ -92,6 +92,8 @@ kbuild_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, con
     __shared__ __align__(16) float sAl[KC][KRR_TILE];
     __shared__ __align__(16) float sBh[KC][KRR_TILE];
     __shared__ __align__(16) float sBl[KC][KRR_TILE];
+    __shared__ float2 sExp[256];
+    exp_table_init(sExp);
     const int64_t tile = blockIdx.x;
     const int pj = find_part(parts, np, tile);
     const PartDesc P = parts[pj];
@@ -169,7 +171,7 @@ kbuild_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, con
             df k;
             if (gr >= P.m || gc >= P.m) k = df_make(gr == gc ? 1.f : 0.f, 0.f);
             else if (gr == gc) k = df_make(1.f, 0.f);
-            else k = df_exp_nonpos(df_mul(D, df_make(-kp.inv2s2_hi[is], -kp.inv2s2_lo[is])));
+            else k = df_exp_nonpos(df_mul(D, df_make(-kp.inv2s2_hi[is], -kp.inv2s2_lo[is])), sExp);
             const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
             Kh[kt * KRR_TILE_ELEMS + e] = k.hi;
             Kl[kt * KRR_TILE_ELEMS + e] = k.lo;

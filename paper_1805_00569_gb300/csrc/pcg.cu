@@ -180,10 +180,97 @@ __global__ void matvec_reduce_kernel(const GroupDesc *__restrict__ groups, const
 }
 
 // ---------------------------------------------------------------- preconditioner
-// z = L^-T L^-1 r for active solves; L tiles in Lst (type T), inverses in Zst.
-// 512 threads (16 warps).  v: working vector in shared memory (T type).
+// z = L^-T L^-1 r for active solves; L tiles in Lst (type TT), inverses in Zst.
+// 512 threads (16 warps).  v: working vector in shared memory (TT type).
+// Off-diagonal tiles are processed two at a time with every load of both
+// tiles issued before the arithmetic (streaming hint, no L1 allocation): one
+// CTA per solve must keep ~100 KB in flight to approach its share of HBM.
+// four consecutive elements, loaded with one (float) or two (double) 16-byte
+// streaming loads
+struct V4f { float a, b, c, d; };
+struct V4d { double a, b, c, d; };
+__device__ __forceinline__ V4f ld4(const float *p) {
+    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
+    return V4f{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ V4d ld4(const double *p) {
+    const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
+    const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
+    return V4d{v0.x, v0.y, v1.x, v1.y};
+}
+template <typename TT> struct V4 { using type = V4f; };
+template <> struct V4<double> { using type = V4d; };
+
+// acc[u] += sum over this lane's columns 4 lane .. 4 lane + 3 of row (warp + 16u)
 template <typename TT>
-__global__ void __launch_bounds__(512)
+__device__ __forceinline__ void rows_dot(const TT *__restrict__ t, const TT *__restrict__ y, int warp, int lane,
+                                         TT (&acc)[8]) {
+    const TT y0 = y[4 * lane], y1 = y[4 * lane + 1], y2 = y[4 * lane + 2], y3 = y[4 * lane + 3];
+    typename V4<TT>::type l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] += l[u].a * y0 + l[u].b * y1 + l[u].c * y2 + l[u].d * y3;
+}
+// the same for two tiles at once (all 16 wide loads issued before any use)
+template <typename TT>
+__device__ __forceinline__ void rows_dot2(const TT *__restrict__ t0, const TT *__restrict__ y0p,
+                                          const TT *__restrict__ t1, const TT *__restrict__ y1p, int warp, int lane,
+                                          TT (&acc)[8]) {
+    typename V4<TT>::type l[16];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
+        l[8 + u] = ld4(t1 + (warp + 16 * u) * KRR_TILE + 4 * lane);
+    }
+    const TT a0 = y0p[4 * lane], a1 = y0p[4 * lane + 1], a2 = y0p[4 * lane + 2], a3 = y0p[4 * lane + 3];
+    const TT b0 = y1p[4 * lane], b1 = y1p[4 * lane + 1], b2 = y1p[4 * lane + 2], b3 = y1p[4 * lane + 3];
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+        acc[u] += (l[u].a * a0 + l[u].b * a1 + l[u].c * a2 + l[u].d * a3) +
+                  (l[8 + u].a * b0 + l[8 + u].b * b1 + l[8 + u].c * b2 + l[8 + u].d * b3);
+}
+template <typename TT>
+__device__ __forceinline__ void cols_dot2(const TT *__restrict__ t0, const TT *__restrict__ t1,
+                                          const TT *__restrict__ w, int warp, int lane, TT (&p0)[4], TT (&p1)[4]) {
+    typename V4<TT>::type l[16];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
+        l[8 + u] = ld4(t1 + (warp + 16 * u) * KRR_TILE + 4 * lane);
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const TT wr = w[warp + 16 * u];
+        p0[0] += l[u].a * wr;
+        p0[1] += l[u].b * wr;
+        p0[2] += l[u].c * wr;
+        p0[3] += l[u].d * wr;
+        p1[0] += l[8 + u].a * wr;
+        p1[1] += l[8 + u].b * wr;
+        p1[2] += l[8 + u].c * wr;
+        p1[3] += l[8 + u].d * wr;
+    }
+}
+// part[q] += sum over this warp's rows rr of t[rr][4 lane + q] * w[rr]
+template <typename TT>
+__device__ __forceinline__ void cols_dot(const TT *__restrict__ t, const TT *__restrict__ w, int warp, int lane,
+                                         TT (&part)[4]) {
+    typename V4<TT>::type l[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        const TT wr = w[warp + 16 * u];
+        part[0] += l[u].a * wr;
+        part[1] += l[u].b * wr;
+        part[2] += l[u].c * wr;
+        part[3] += l[u].d * wr;
+    }
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(512, 1)
 precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const SolveDesc *__restrict__ solves,
                const PcgState *__restrict__ state, const double *__restrict__ r, double *__restrict__ z) {
     extern __shared__ __align__(16) unsigned char pc_dyn[];
@@ -192,43 +279,38 @@ precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const Sol
     const SolveDesc S = solves[s];
     const int T = S.T, M = T * KRR_TILE;
     TT *v = reinterpret_cast<TT *>(pc_dyn);            // [M]
-    TT *red = v + M;                                   // [16][128]
-    TT *tmp = red + 16 * KRR_TILE;                     // [128]
+    TT *red = v + M;                                   // [2][16][128]
+    TT *tmp = red + 32 * KRR_TILE;                     // [128]
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int e = threadIdx.x; e < M; e += blockDim.x) v[e] = (TT)r[S.vec0 + e];
     __syncthreads();
     // forward: y_i = Z_ii (v_i - sum_{j<i} L_ij y_j); y overwrites v
     for (int i = 0; i < T; ++i) {
-        // partial sums over j in this warp's share: warp w takes rows w, w+16, ...
-        TT accr[8];
+        TT acc[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) accr[u] = TT(0);
-        for (int j = 0; j < i; ++j) {
-            const TT *Lt = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2 + j) * KRR_TILE_ELEMS;
-            const TT *yj = v + j * KRR_TILE;
-            TT y0 = yj[lane], y1 = yj[lane + 32], y2 = yj[lane + 64], y3 = yj[lane + 96];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const TT *row = Lt + (warp + 16 * u) * KRR_TILE;
-                accr[u] += row[lane] * y0 + row[lane + 32] * y1 + row[lane + 64] * y2 + row[lane + 96] * y3;
-            }
-        }
+        for (int u = 0; u < 8; ++u) acc[u] = TT(0);
+        const TT *row0 = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2) * KRR_TILE_ELEMS;
+        int j = 0;
+        for (; j + 1 < i; j += 2)
+            rows_dot2(row0 + (int64_t)j * KRR_TILE_ELEMS, v + j * KRR_TILE, row0 + (int64_t)(j + 1) * KRR_TILE_ELEMS,
+                      v + (j + 1) * KRR_TILE, warp, lane, acc);
+        if (j < i) rows_dot(row0 + (int64_t)j * KRR_TILE_ELEMS, v + j * KRR_TILE, warp, lane, acc);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-            TT a = accr[u];
+            TT a = acc[u];
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
             if (lane == 0) tmp[warp + 16 * u] = v[i * KRR_TILE + warp + 16 * u] - a;
         }
         __syncthreads();
-        // y_i = Z_ii tmp
         {
-            const TT *Zt = Zst + (S.dtile0 + i) * KRR_TILE_ELEMS;
-            const TT t0 = tmp[lane], t1 = tmp[lane + 32], t2 = tmp[lane + 64], t3 = tmp[lane + 96];
+            TT zr[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) zr[u] = TT(0);
+            rows_dot(Zst + (S.dtile0 + i) * KRR_TILE_ELEMS, tmp, warp, lane, zr);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const TT *row = Zt + (warp + 16 * u) * KRR_TILE;
-                TT a = row[lane] * t0 + row[lane + 32] * t1 + row[lane + 64] * t2 + row[lane + 96] * t3;
+                TT a = zr[u];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) a += __shfl_xor_sync(0xffffffffu, a, off);
                 if (lane == 0) v[i * KRR_TILE + warp + 16 * u] = a;
@@ -236,20 +318,13 @@ precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const Sol
         }
         __syncthreads();
     }
-    // backward: w_i = Z_ii^T (y_i - sum_{j>i} L_ji^T w_j), right-looking over j
+    // backward: w_j = Z_jj^T (y_j - sum_{i>j} L_ij^T w_i), right-looking over j
     for (int j = T - 1; j >= 0; --j) {
-        // w_j = Z_jj^T v_j   (transposed product: lanes over columns, warps over rows)
         {
-            const TT *Zt = Zst + (S.dtile0 + j) * KRR_TILE_ELEMS;
             TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
-            for (int rr = warp; rr < KRR_TILE; rr += 16) {
-                const TT vr = v[j * KRR_TILE + rr];
-                const TT *row = Zt + rr * KRR_TILE;
+            cols_dot(Zst + (S.dtile0 + j) * KRR_TILE_ELEMS, v + j * KRR_TILE, warp, lane, part);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) part[q] += row[lane + 32 * q] * vr;
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + lane + 32 * q] = part[q];
+            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + 4 * lane + q] = part[q];
             __syncthreads();
             if (threadIdx.x < KRR_TILE) {
                 TT a = TT(0);
@@ -260,23 +335,30 @@ precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const Sol
             if (threadIdx.x < KRR_TILE) v[j * KRR_TILE + threadIdx.x] = tmp[threadIdx.x];
             __syncthreads();
         }
-        // v_i -= L_ji^T w_j for i < j  (tiles of block row j)
-        for (int i = 0; i < j; ++i) {
-            const TT *Lt = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2 + i) * KRR_TILE_ELEMS;
-            TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
-            for (int rr = warp; rr < KRR_TILE; rr += 16) {
-                const TT wr = v[j * KRR_TILE + rr];
-                const TT *row = Lt + rr * KRR_TILE;
+        // v_i -= L_ji^T w_j for i < j  (tiles of block row j), two tiles per pass
+        const TT *row0 = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2) * KRR_TILE_ELEMS;
+        const TT *wj = v + j * KRR_TILE;
+        for (int i = 0; i < j; i += 2) {
+            const bool two = i + 1 < j;
+            TT p0[4] = {TT(0), TT(0), TT(0), TT(0)}, p1[4] = {TT(0), TT(0), TT(0), TT(0)};
+            if (two)
+                cols_dot2(row0 + (int64_t)i * KRR_TILE_ELEMS, row0 + (int64_t)(i + 1) * KRR_TILE_ELEMS, wj, warp, lane,
+                          p0, p1);
+            else
+                cols_dot(row0 + (int64_t)i * KRR_TILE_ELEMS, wj, warp, lane, p0);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) part[q] += row[lane + 32 * q] * wr;
+            for (int q = 0; q < 4; ++q) {
+                red[warp * KRR_TILE + 4 * lane + q] = p0[q];
+                red[16 * KRR_TILE + warp * KRR_TILE + 4 * lane + q] = p1[q];
             }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + lane + 32 * q] = part[q];
             __syncthreads();
-            if (threadIdx.x < KRR_TILE) {
-                TT a = TT(0);
-                for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
-                v[i * KRR_TILE + threadIdx.x] -= a;
+            if (threadIdx.x < 2 * KRR_TILE) {
+                const int h = threadIdx.x >> 7, c = threadIdx.x & 127;
+                if (h == 0 || two) {
+                    TT a = TT(0);
+                    for (int w = 0; w < 16; ++w) a += red[h * 16 * KRR_TILE + w * KRR_TILE + c];
+                    v[(i + h) * KRR_TILE + c] -= a;
+                }
             }
             __syncthreads();
         }
@@ -471,7 +553,7 @@ static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuff
                                   bool fp64, int maxT, Prof *prof) {
     ProfScope ps(prof, PROF_PRECOND, st);
     const size_t esz = fp64 ? 8 : 4;
-    const size_t sm = esz * ((size_t)maxT * KRR_TILE + 17 * KRR_TILE);
+    const size_t sm = esz * ((size_t)maxT * KRR_TILE + 33 * KRR_TILE);
     if (fp64) {
         cudaFuncSetAttribute(precond_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         KRR_LAUNCHED(), precond_kernel<double><<<(unsigned)M.solves.size(), 512, sm, st>>>(
@@ -485,7 +567,7 @@ static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuff
 }
 
 size_t precond_smem_bytes(bool fp64, int maxT) {
-    return (fp64 ? 8 : 4) * ((size_t)maxT * KRR_TILE + 17 * KRR_TILE);
+    return (fp64 ? 8 : 4) * ((size_t)maxT * KRR_TILE + 33 * KRR_TILE);
 }
 
 // Runs the whole refinement; returns the CUDA status of the last launch.

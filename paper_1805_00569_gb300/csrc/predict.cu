@@ -50,6 +50,8 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
     float2 *sTn = reinterpret_cast<float2 *>(sXl + PKC * KRR_TILE);  // [PT] test norms
     int64_t *sRow = reinterpret_cast<int64_t *>(sTn + PT);           // [PT] test row ids
     float2 *sY = reinterpret_cast<float2 *>(sRow + PT);               // [PG][256] df accumulators
+    float2 *sExp = sY + PG * 256;                                     // [256] 2^(j/256) table
+    exp_table_init(sExp);
 
     const int j = blockIdx.x;
     const PartDesc P = parts[j];
@@ -155,7 +157,7 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
             const df D = df_make(dv.x, dv.y);
 #pragma unroll 1
             for (int is = 0; is < pp.nsig; ++is) {
-                const df k = df_exp_nonpos(df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is])));
+                const df k = df_exp_nonpos(df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is])), sExp);
 #pragma unroll 1
                 for (int il = 0; il < pp.nlam; ++il) {
                     const int g = is * pp.nlam + il;
@@ -303,7 +305,7 @@ __global__ void argmin_kernel(const double *__restrict__ v, int n, int32_t *__re
 static size_t predict_df_smem() {
     return (size_t)KRR_TILE * PT * sizeof(float2) + PG * KRR_TILE * sizeof(float2) + 2 * PKC * PT * sizeof(float) +
            2 * PKC * KRR_TILE * sizeof(float) + PT * sizeof(float2) + PT * sizeof(int64_t) +
-           (size_t)PG * 256 * sizeof(float2);
+           (size_t)PG * 256 * sizeof(float2) + 256 * sizeof(float2);
 }
 
 void launch_predict(cudaStream_t st, const Model &M, const double *Xt, int64_t t, const int64_t *toff,
