@@ -55,6 +55,13 @@ cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float
 void launch_predict(cudaStream_t, const Model &, const double *, int64_t, const int64_t *, const int64_t *, int64_t,
                     int, double *);
 void launch_select(cudaStream_t, const double *, const double *, int64_t, int, int, int, double *, int32_t *);
+int oz_dpz(int d);
+bool oz_supported(int d);
+void launch_oz_slice(cudaStream_t, const double *, int, const int64_t *, int64_t, int64_t, void *, int32_t *, float2 *);
+bool make_slice_tmap(CUtensorMap *, void *, int64_t, int, int);
+cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
+                              const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
+                              int *);
 
 // ---- budgeted stream-ordered allocation
 cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes) {
@@ -354,6 +361,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     // ---- budget check before any allocation
     const size_t tileb = (size_t)KRR_TILE_ELEMS * esz;
     size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 8 +
+                         (size_t)prow * (10 * (size_t)((d + 31) / 32 * 32) + 4) +
                          sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
                         (size_t)dtiles * tileb + 5 * (size_t)vec * 8 + (size_t)scratch * 8 +
@@ -423,6 +431,14 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         {
             ProfScope ps(prof, PROF_STAGE, st);
             launch_stage(st, X, y, perm, M, yg);
+            if (!fp64 && oz_supported(d)) {
+                M.dpz = oz_dpz(d);
+                FIT_TRY(model_alloc(c, M, (unsigned char **)&M.ozS, (size_t)5 * prow * M.dpz * 2));
+                FIT_TRY(model_alloc(c, M, &M.ozex, (size_t)prow * 4));
+                launch_oz_slice(st, M.X64, d, nullptr, prow, prow, M.ozS, M.ozex, nullptr);
+                if (!make_slice_tmap(&M.oz_tmB, M.ozS, (int64_t)5 * prow, M.dpz, 64))
+                    return bail(KRR_ERR_CUDA, "krr_fit_batch: slice tensor map encoding failed");
+            }
         }
         float *Kh = nullptr, *Kl = nullptr;
         double *K64 = nullptr;
@@ -611,30 +627,51 @@ krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, i
     Prof *prof = c->prof.on ? &c->prof : nullptr;
     const int G = M.nsig * M.nlam;
     if (t == 0) return KRR_OK;
-    if (!route) {
-        ProfScope ps(prof, PROF_PREDICT, st);
-        launch_predict(st, M, Xt, t, nullptr, nullptr, t, 0, yhat);
-        API_TRY(c, cudaGetLastError());
-        return KRR_OK;
-    }
-    // routed: group the test rows by partition (stable), predict, scatter back
+    const bool oz = M.ozS != nullptr;
+    // routed: group the test rows by partition (stable) first
     int64_t *tperm = nullptr, *toff = nullptr;
-    API_TRY(c, ctx_malloc(c, (void **)&tperm, (size_t)t * 8));
-    cudaError_t e = ctx_malloc(c, (void **)&toff, (size_t)(M.p + 1) * 8);
-    if (e != cudaSuccess) {
-        ctx_free(c, tperm, (size_t)t * 8);
-        API_TRY(c, e);
-    }
-    krr_status rc = run_gather(c, route, t, M.p, tperm, toff);
-    if (rc == KRR_OK) {
+    if (route) {
+        API_TRY(c, ctx_malloc(c, (void **)&tperm, (size_t)t * 8));
+        cudaError_t e = ctx_malloc(c, (void **)&toff, (size_t)(M.p + 1) * 8);
+        if (e != cudaSuccess) {
+            ctx_free(c, tperm, (size_t)t * 8);
+            API_TRY(c, e);
+        }
+        krr_status rc = run_gather(c, route, t, M.p, tperm, toff);
+        if (rc != KRR_OK) {
+            ctx_free(c, toff, (size_t)(M.p + 1) * 8);
+            ctx_free(c, tperm, (size_t)t * 8);
+            return rc;
+        }
         API_TRY(c, cudaMemsetAsync(yhat, 0, sizeof(double) * (size_t)G * t, st));
-        ProfScope ps(prof, PROF_PREDICT, st);
-        launch_predict(st, M, Xt, t, toff, tperm, t, 1, yhat);
     }
-    ctx_free(c, toff, (size_t)(M.p + 1) * 8);
-    ctx_free(c, tperm, (size_t)t * 8);
-    API_TRY(c, cudaGetLastError());
-    return rc;
+    cudaError_t err = cudaSuccess;
+    if (oz) {
+        const int64_t t_rows = (t + 127) / 128 * 128 + 128;
+        const size_t b_sl = (size_t)5 * t_rows * M.dpz * 2, b_ex = (size_t)t_rows * 4, b_nr = (size_t)t_rows * 8;
+        void *sl = nullptr;
+        int32_t *tex = nullptr;
+        float2 *tnr = nullptr;
+        err = ctx_malloc(c, &sl, b_sl);
+        if (err == cudaSuccess) err = ctx_malloc(c, (void **)&tex, b_ex);
+        if (err == cudaSuccess) err = ctx_malloc(c, (void **)&tnr, b_nr);
+        if (err == cudaSuccess) {
+            ProfScope ps(prof, PROF_PREDICT, st);
+            err = launch_predict_oz(st, M, M.oz_tmB, Xt, t, toff, tperm, route ? 1 : 0, sl, tex, tnr, t_rows, yhat,
+                                    c->d_err);
+        }
+        if (tnr) ctx_free(c, tnr, b_nr);
+        if (tex) ctx_free(c, tex, b_ex);
+        if (sl) ctx_free(c, sl, b_sl);
+    } else {
+        ProfScope ps(prof, PROF_PREDICT, st);
+        launch_predict(st, M, Xt, t, toff, tperm, t, route ? 1 : 0, yhat);
+        err = cudaGetLastError();
+    }
+    if (toff) ctx_free(c, toff, (size_t)(M.p + 1) * 8);
+    if (tperm) ctx_free(c, tperm, (size_t)t * 8);
+    API_TRY(c, err);
+    return KRR_OK;
 }
 
 krr_status krr_select(krr_ctx *ctx, const double *yhat, const double *yt, int64_t t, int32_t p, int32_t G,

@@ -140,6 +140,10 @@ struct Model {
     float *Xl = nullptr;       // lo part FP32 [prows x dp]
     float2 *nrm = nullptr;     // squared norms as (hi, lo) [prows]
     double *alpha = nullptr;   // per-solve coefficients, padded [nvec]
+    void *ozS = nullptr;       // integer bf16 slices of the padded rows [5][prows][dpz] (tensor-core predict)
+    int32_t *ozex = nullptr;   // per-row slice exponent [prows]
+    int32_t dpz = 0;           // features padded to the slice K chunk
+    CUtensorMap oz_tmB;        // TMA view of ozS for the training-row operand
     std::vector<int32_t> st_iters, st_status;  // per-solve refinement statistics
     std::vector<double> st_kappa, st_resid;
     std::vector<std::pair<void *, size_t>> allocs;

@@ -1,0 +1,460 @@
+// predict_oz.cu -- fused prediction (Eq. 7) with the distance Gram on the
+// tcgen05 tensor cores, exactly.
+//
+// Every row x (FP64, d <= 96 features) is written as x = 2^e sum_s c_s 2^(-7-8s),
+// s = 0..4, with integer slices |c_s| <= 128 (exact in bf16) and a residual
+// below 2^(e-40).  The dot product of two rows is then
+//   x_a . x_b = 2^(e_a+e_b-14) sum_L 2^(-8L) S_L,   S_L = sum_{s+t=L} C_a,s . C_b,t
+// for L = 0..4 (the 15 slice products with s + t <= 4; the dropped terms are
+// below 2^(e_a+e_b) * 96 * 2^-37).  Each S_L is an integer below 2^23, so the
+// bf16 MMAs accumulate it exactly in FP32: no rounding happens on the tensor
+// cores at all, and the distance ||a||^2 + ||b||^2 - 2 a.b is assembled in
+// double-float (~1e-10 relative, what the kernel values need: see the design doc).
+//
+// Kernel layout, one CTA per (partition, 128 test rows):
+//   warp 0, one thread: TMA producer -- the 5 slices of the next 64 training
+//     rows (B operand, N = 64) and, per slice s, the 5 slices of the test rows
+//     (A operand, M = 128) through a 3-stage ring; 64-byte swizzle, K chunks
+//     of 32 features;
+//   warp 1, one thread: MMA issuer -- 15 x (d/16) kind::f16 MMAs per chunk into
+//     five 64-column FP32 accumulators in tensor memory;
+//   warps 4..11: epilogue -- tcgen05.ld of the five levels, distance, every
+//     sigma's double-float exponential and every lambda's alpha contraction
+//     into double-float accumulators; the two column halves of a test row are
+//     combined in a fixed order at the end.  K(test, train) is never stored.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace krr {
+
+constexpr int OZ_SLICES = 5;
+constexpr int OZ_M = 128;          // test rows per CTA
+constexpr int OZ_N = 64;           // training rows per chunk
+constexpr int OZ_KC = 32;          // features per K chunk (64 bytes of bf16)
+constexpr int OZ_MAXKC = 3;        // d <= 96
+constexpr int OZ_ASTAGES = 3;
+constexpr int OZ_NSP = 4, OZ_NLP = 2;  // sigmas / lambdas per pass
+constexpr int OZ_THREADS = 384;    // 12 warps
+constexpr int OZ_EPI_WARP0 = 4;
+
+constexpr uint32_t OZ_A_CHUNK = OZ_M * 64;                 // bytes of one K chunk of one A slice
+constexpr uint32_t OZ_B_CHUNK = OZ_N * 64;
+constexpr uint32_t OZ_A_STAGE = OZ_MAXKC * OZ_A_CHUNK;     // 24 KB
+constexpr uint32_t OZ_B_BYTES = OZ_SLICES * OZ_MAXKC * OZ_B_CHUNK;  // 60 KB
+constexpr uint32_t OZ_IDESC = make_idesc(1u /*BF16*/, OZ_M, OZ_N);
+
+struct OzChunkData {  // per training column of a chunk
+    float nh[OZ_N], nl[OZ_N];
+    int e[OZ_N];
+    float ah[OZ_NSP * OZ_NLP][OZ_N], al[OZ_NSP * OZ_NLP][OZ_N];
+};
+
+struct OzSmem {
+    unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
+    unsigned char b[OZ_B_BYTES];
+    OzChunkData cd[2];
+    float2 exptab[256];
+    float2 comb[OZ_NSP * OZ_NLP][OZ_M];
+    float2 dist[256][17];                        // per epilogue thread: 16 distances (padded row)
+    uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
+    uint64_t b_full, b_empty, t_full, t_empty;
+    uint32_t tmem;
+};
+
+struct OzParams {
+    int nsig, nlam, sig0, lam0, Gtot, nl_total;
+    float c_hi[OZ_NSP], c_lo[OZ_NSP];  // -1 / (2 sigma^2) as df
+    int kc;                              // K chunks of 32 features
+    int64_t t_rows;                      // rows per slice in the test slice array
+};
+
+// Shared-memory descriptor, K-major operand with the 64-byte swizzle
+// (8-row x 64-byte atoms, 512 bytes apart along M/N).
+__device__ __forceinline__ uint64_t smem_desc_sw64(const void *p) {
+    uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;  // 64-byte swizzle
+    return d;
+}
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float *v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+
+__device__ __forceinline__ uint64_t oz_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool oz_wait(uint64_t *bar, uint32_t parity, int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = oz_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (oz_ns() - t0 > 2000000000ull) {
+            atomicExch(err, KRR_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- slicing
+// Row r of the output takes source row map[r] (or r); rows >= nreal are zero.
+// S: [5][nout][dpz] bf16; ex: exponent per row; nrm (optional): ||x||^2 as df.
+__global__ void oz_slice_kernel(const double *__restrict__ X, int32_t d, int32_t dpz, const int64_t *__restrict__ map,
+                                int64_t nreal, int64_t nout, __nv_bfloat16 *__restrict__ S, int32_t *__restrict__ ex,
+                                float2 *__restrict__ nrm) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nout) return;
+    const bool real = r < nreal;
+    const double *x = X + (real ? (map ? map[r] : r) : 0) * d;
+    double mx = 0.0;
+    df_acc a;
+    dfa_zero(a);
+    if (real)
+        for (int f = 0; f < d; ++f) {
+            const double v = x[f];
+            mx = fmax(mx, fabs(v));
+            const float h = __double2float_rn(v), l = __double2float_rn(v - (double)h);
+            dfa_fma(a, h, l, h, l);
+        }
+    int e = 0;
+    if (mx > 0.0) frexp(mx, &e);  // mx = m 2^e, m in [0.5, 1): |x| 2^-e < 1
+    ex[r] = e;
+    if (nrm) {
+        const df v = dfa_value(a);
+        nrm[r] = make_float2(v.hi, v.lo);
+    }
+    for (int f = 0; f < dpz; ++f) {
+        double v = (real && f < d) ? ldexp(x[f], 7 - e) : 0.0;  // |v| < 128
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s) {
+            const double c = rint(v);
+            S[((int64_t)s * nout + r) * dpz + f] = __float2bfloat16_rn((float)c);
+            v = (v - c) * 256.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- predict
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                  const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
+                  const double *__restrict__ alpha, const int32_t *__restrict__ ex_train,
+                  const float2 *__restrict__ nrm_train, const int32_t *__restrict__ ex_test,
+                  const float2 *__restrict__ nrm_test, int64_t t, const int64_t *__restrict__ toff,
+                  const int64_t *__restrict__ tidx, OzParams pp, int routed, int64_t prows,
+                  double *__restrict__ out, int *__restrict__ err) {
+    extern __shared__ unsigned char oz_dyn[];
+    const uint32_t base = smem_u32(oz_dyn);
+    OzSmem &sm = *reinterpret_cast<OzSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int j = blockIdx.x;
+    const PartDesc P = parts[j];
+    const int64_t cnt = toff ? toff[j + 1] - toff[j] : t;
+    const int64_t tstart = toff ? toff[j] : 0;
+    const int64_t q0 = (int64_t)blockIdx.y * OZ_M;
+    if (q0 >= cnt) return;
+    const int nchunks = P.T * (KRR_TILE / OZ_N);
+    const int G = pp.nsig * pp.nlam;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < OZ_ASTAGES; ++i) {
+            mbar_init(&sm.a_full[i], 1);
+            mbar_init(&sm.a_empty[i], 1);
+        }
+        mbar_init(&sm.b_full, 1);
+        mbar_init(&sm.b_empty, 1);
+        mbar_init(&sm.t_full, 1);
+        mbar_init(&sm.t_empty, 8);
+        fence_mbar_init();
+    }
+    exp_table_init(sm.exptab);
+    if (warp == 0) {
+        tmem_alloc(&sm.tmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+
+    if (nchunks > 0 && threadIdx.x == 0) {
+        // ---------------- TMA producer
+        const uint32_t bbytes = (uint32_t)(OZ_SLICES * pp.kc) * OZ_B_CHUNK;
+        const uint32_t abytes = (uint32_t)pp.kc * OZ_A_CHUNK;
+        int ait = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            if (c > 0 && !oz_wait(&sm.b_empty, (c - 1) & 1, err)) break;
+            mbar_arrive_expect_tx(&sm.b_full, bbytes);
+            const int brow = (int)(P.prow0 + (int64_t)c * OZ_N);
+            for (int s = 0; s < OZ_SLICES; ++s)
+                for (int kc = 0; kc < pp.kc; ++kc)
+                    tma_load_2d(sm.b + (s * OZ_MAXKC + kc) * OZ_B_CHUNK, &tmB, kc * OZ_KC, (int)(s * prows) + brow,
+                                &sm.b_full);
+            bool ok = true;
+            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                if (use > 0 && !oz_wait(&sm.a_empty[st], (use - 1) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&sm.a_full[st], abytes);
+                const int arow = (int)(s * pp.t_rows + tstart + q0);
+                for (int kc = 0; kc < pp.kc; ++kc)
+                    tma_load_2d(sm.a[st] + kc * OZ_A_CHUNK, &tmA, kc * OZ_KC, arow, &sm.a_full[st]);
+            }
+            if (!ok) break;
+        }
+    } else if (nchunks > 0 && threadIdx.x == 32) {
+        // ---------------- MMA issuer
+        int ait = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            if (c > 0 && !oz_wait(&sm.t_empty, (c - 1) & 1, err)) break;
+            if (!oz_wait(&sm.b_full, c & 1, err)) break;
+            tc_fence_after();
+            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                if (!oz_wait(&sm.a_full[st], use & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int tt = 0; tt + s < OZ_SLICES; ++tt) {
+                    const uint32_t dcol = tmem + (uint32_t)((s + tt) * OZ_N);
+                    for (int kk = 0; kk < 2 * pp.kc; ++kk) {
+                        const uint64_t da = smem_desc_sw64(sm.a[st] + (kk >> 1) * OZ_A_CHUNK) + 2 * (kk & 1);
+                        const uint64_t db =
+                            smem_desc_sw64(sm.b + (tt * OZ_MAXKC + (kk >> 1)) * OZ_B_CHUNK) + 2 * (kk & 1);
+                        tc_mma_f16(dcol, da, db, OZ_IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&sm.a_empty[st]);
+            }
+            tc_commit(&sm.b_empty);
+            tc_commit(&sm.t_full);
+        }
+    } else if (warp >= OZ_EPI_WARP0) {
+        // ---------------- epilogue
+        const int ew = warp - OZ_EPI_WARP0;       // 0..7
+        const int quad = warp & 3;                // TMEM lane quadrant of this warp
+        const int half = ew >> 2;                 // column half of the chunk
+        const int row = quad * 32 + lane;         // test row inside the tile
+        const int64_t grow = tstart + q0 + row;   // row in the (grouped) test slice array
+        const bool live = q0 + row < cnt;
+        const int eq = live ? ex_test[grow] : 0;
+        const float2 nq2 = live ? nrm_test[grow] : make_float2(0.f, 0.f);
+        const df nq = df_make(nq2.x, nq2.y);
+        df_acc acc[OZ_NSP][OZ_NLP];
+#pragma unroll
+        for (int a = 0; a < OZ_NSP; ++a)
+#pragma unroll
+            for (int b = 0; b < OZ_NLP; ++b) dfa_zero(acc[a][b]);
+        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..255
+        for (int c = 0; c < nchunks; ++c) {
+            OzChunkData &cd = sm.cd[c & 1];
+            // training-side data of the chunk
+            for (int e = et; e < OZ_N; e += 256) {
+                const int64_t pr = P.prow0 + (int64_t)c * OZ_N + e;
+                const float2 v = nrm_train[pr];
+                cd.nh[e] = v.x;
+                cd.nl[e] = v.y;
+                cd.e[e] = ex_train[pr];
+            }
+            for (int e = et; e < G * OZ_N; e += 256) {
+                const int g = e / OZ_N, col = e % OZ_N;
+                const int is = g / pp.nlam, il = g % pp.nlam;
+                const SolveDesc S =
+                    solves[(int64_t)j * pp.Gtot + (int64_t)(pp.sig0 + is) * pp.nl_total + pp.lam0 + il];
+                const double av = alpha[S.vec0 + (int64_t)c * OZ_N + col];
+                const float h = __double2float_rn(av);
+                cd.ah[is * OZ_NLP + il][col] = h;
+                cd.al[is * OZ_NLP + il][col] = __double2float_rn(av - (double)h);
+            }
+            epi_bar();
+            if (!oz_wait(&sm.t_full, c & 1, err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int sub = 0; sub < 2; ++sub) {
+                float lv[OZ_SLICES][16];
+                const uint32_t col0 = (uint32_t)(half * 32 + sub * 16);
+#pragma unroll
+                for (int L = 0; L < OZ_SLICES; ++L)
+                    tmem_ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
+                tmem_wait_ld();
+                if (sub == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.t_empty);
+                }
+                // distances of the 16 columns (static register indices), parked in shared memory
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    // G_scaled = S0 + 2^-8 S1 + 2^-16 S2 + 2^-24 S3 + 2^-32 S4 (all exact integers)
+                    float th, tl;
+                    two_sum(lv[3][k] * 0x1p-24f, lv[4][k] * 0x1p-32f, th, tl);
+                    df u = df_make(th, tl);
+                    u = df_add(df_make(lv[2][k] * 0x1p-16f, 0.f), u);
+                    u = df_add(df_make(lv[1][k] * 0x1p-8f, 0.f), u);
+                    u = df_add(df_make(lv[0][k], 0.f), u);
+                    const int col = (int)col0 + k;
+                    const int sc = eq + cd.e[col] - 13;  // factor 2 of -2 a.b folded in
+                    const float s2 = __int_as_float((127 + sc) << 23);
+                    df D = df_add(nq, df_make(cd.nh[col], cd.nl[col]));
+                    D = df_add(D, df_make(-u.hi * s2, -u.lo * s2));
+                    if (D.hi < 0.f) D = df_make(0.f, 0.f);
+                    sm.dist[et][k] = make_float2(D.hi, D.lo);
+                }
+#pragma unroll 1
+                for (int k = 0; k < 16; ++k) {
+                    const int col = (int)col0 + k;
+                    if ((int64_t)c * OZ_N + col >= P.m) break;
+                    const float2 dv = sm.dist[et][k];
+                    const df D = df_make(dv.x, dv.y);
+#pragma unroll
+                    for (int is = 0; is < OZ_NSP; ++is) {
+                        if (is < pp.nsig) {
+                            const df kv =
+                                df_exp_nonpos(df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is])), sm.exptab);
+#pragma unroll
+                            for (int il = 0; il < OZ_NLP; ++il)
+                                if (il < pp.nlam)
+                                    dfa_fma(acc[is][il], kv.hi, kv.lo, cd.ah[is * OZ_NLP + il][col],
+                                            cd.al[is * OZ_NLP + il][col]);
+                        }
+                    }
+                }
+            }
+        }
+        // combine the two column halves in a fixed order: half 0 + half 1
+        epi_bar();
+        if (half == 1) {
+#pragma unroll
+            for (int is = 0; is < OZ_NSP; ++is)
+#pragma unroll
+                for (int il = 0; il < OZ_NLP; ++il) {
+                    const df v = dfa_value(acc[is][il]);
+                    sm.comb[is * OZ_NLP + il][row] = make_float2(v.hi, v.lo);
+                }
+        }
+        epi_bar();
+        if (half == 0 && live) {
+            const int64_t orow_t = toff ? (tidx ? tidx[grow] : grow) : (q0 + row);
+#pragma unroll
+            for (int is = 0; is < OZ_NSP; ++is)
+#pragma unroll
+                for (int il = 0; il < OZ_NLP; ++il) {
+                    if (is < pp.nsig && il < pp.nlam) {
+                        const float2 o = sm.comb[is * OZ_NLP + il][row];
+                        const df v = df_add(dfa_value(acc[is][il]), df_make(o.x, o.y));
+                        const int gm = (pp.sig0 + is) * pp.nl_total + pp.lam0 + il;
+                        const int64_t orow = routed ? (int64_t)gm : (int64_t)j * pp.Gtot + gm;
+                        out[orow * t + orow_t] = df_to_double(v);
+                    }
+                }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
+// ---------------------------------------------------------------- host
+typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                      const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
+                                      CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                      CUtensorMapFloatOOBfill);
+static PFN_encodeTiled_t oz_encode() {
+    static PFN_encodeTiled_t fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_encodeTiled_t)p;
+    }
+    return fn;
+}
+
+// 2-D view of a slice array [rows][dpz] bf16, box 32 x box_rows, 64-byte swizzle
+bool make_slice_tmap(CUtensorMap *map, void *base, int64_t rows, int dpz, int box_rows) {
+    PFN_encodeTiled_t enc = oz_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)dpz, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)dpz * 2};
+    cuuint32_t box[2] = {(cuuint32_t)OZ_KC, (cuuint32_t)box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int oz_dpz(int d) { return ((d + OZ_KC - 1) / OZ_KC) * OZ_KC; }
+bool oz_supported(int d) { return d <= OZ_MAXKC * OZ_KC; }
+
+void launch_oz_slice(cudaStream_t st, const double *X, int d, const int64_t *map, int64_t nreal, int64_t nout,
+                     void *S, int32_t *ex, float2 *nrm) {
+    if (nout <= 0) return;
+    KRR_LAUNCHED(), oz_slice_kernel<<<(unsigned)((nout + 127) / 128), 128, 0, st>>>(
+        X, d, oz_dpz(d), map, nreal, nout, (__nv_bfloat16 *)S, ex, nrm);
+}
+
+size_t oz_smem_bytes() { return sizeof(OzSmem) + 1024; }
+
+// Slices the test rows (grouped by route when given), then launches one pass
+// per (sigma subset, lambda subset).  Xt rows -> workspace owned by the caller.
+cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap &tmB, const double *Xt, int64_t t,
+                              const int64_t *toff, const int64_t *tidx, int routed, void *tslices, int32_t *tex,
+                              float2 *tnrm, int64_t t_rows, double *out, int *d_err) {
+    const int dpz = oz_dpz(M.d);
+    launch_oz_slice(st, Xt, M.d, tidx, t, t_rows, tslices, tex, tnrm);
+    CUtensorMap tmA;
+    if (!make_slice_tmap(&tmA, tslices, (int64_t)OZ_SLICES * t_rows, dpz, OZ_M)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(predict_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+        attr = true;
+    }
+    for (int s0 = 0; s0 < M.nsig; s0 += OZ_NSP)
+        for (int l0 = 0; l0 < M.nlam; l0 += OZ_NLP) {
+            OzParams pp;
+            pp.nsig = std::min(OZ_NSP, M.nsig - s0);
+            pp.nlam = std::min(OZ_NLP, M.nlam - l0);
+            pp.sig0 = s0;
+            pp.lam0 = l0;
+            pp.Gtot = M.nsig * M.nlam;
+            pp.nl_total = M.nlam;
+            pp.kc = dpz / OZ_KC;
+            pp.t_rows = t_rows;
+            for (int i = 0; i < OZ_NSP; ++i) {
+                const double c = i < pp.nsig ? -1.0 / (2.0 * M.sigmas[s0 + i] * M.sigmas[s0 + i]) : 0.0;
+                pp.c_hi[i] = (float)c;
+                pp.c_lo[i] = (float)(c - (double)(float)c);
+            }
+            // for the routed form the grouped rows start at toff[j]; the tile count bounds every partition
+            dim3 grid((unsigned)M.p, (unsigned)((t + OZ_M - 1) / OZ_M));
+            KRR_LAUNCHED(), predict_oz_kernel<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(
+                tmA, tmB, M.d_parts, M.d_solves, M.alpha, M.ozex, M.nrm, tex, tnrm, t, toff, routed ? tidx : nullptr,
+                pp, routed, M.prows, out, d_err);
+        }
+    return cudaGetLastError();
+}
+
+}  // namespace krr
