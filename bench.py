@@ -18,6 +18,7 @@ bounded sample of the same workload (it is the deliberately slow reference).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import multiprocessing as mp
 import os
@@ -148,6 +149,10 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- our arm
+def ctypes_int():
+    return ctypes.c_int(0)
+
+
 def solve_flops(m: int, d: int) -> float:
     """Algorithmic flops of one partition-solve: Cholesky m^3/3, kernel m^2 d,
     two triangular solves 2 m^2."""
@@ -188,6 +193,16 @@ def run_ours(args, rank, world, local_rank):
         mse, best, status = step(X, y, Xt, yt, args.prec)
     torch.cuda.synchronize()
     bad = int((status != K.KRR_OK).sum().item())
+    if args.profile:
+        _, _, perm, offsets, _ = K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+        model, _, _ = K.krr_fit_batch(ctx, X, y, perm, offsets, S, L, args.prec)
+        it, ka, rs = K.krr_model_stats(ctx, model)
+        model.free()
+        Wt = ctypes_int()
+        ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2}[args.prec], n // p // 128,
+                                        ctypes.byref(Wt))
+        sys.stderr.write("refinement iterations per (sigma, lambda): %s; panel width %d\n" % (
+            [sorted(set(int(v) for v in it.view(p, G)[:, g].tolist())) for g in range(G)], Wt.value))
 
     # ---- device-timed steps (inputs resident)
     clocks = Clocks(local_rank)

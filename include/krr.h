@@ -191,11 +191,19 @@ krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t 
  *   W in {1, 2, 4, 8} on its own matrices and keeps the fastest.
  * krr_ctx_get_panel_width: the width in force for (precision, largest tile
  *   count): the explicit one, the tuned one, or 0 if not tuned yet.
+ * krr_ctx_set_target_error: forward-error target of the refinement for the
+ *   refined precisions: a solve stops once its Gershgorin condition estimate
+ *   times its backward error (the scaled residual) is at most `rel` (default
+ *   1e-7, ten times below the 1e-6 parity bar), or at the FP64-class floor
+ *   2^-46 of the scaled residual, whichever comes first.  0 always runs to the
+ *   floor.  The plain FP64 path always runs to its floor 2^-50.  Errors:
+ *   KRR_ERR_ARG (rel < 0 or rel > 1e-2).
  * krr_launch_count: kernels launched by this process through libkrr. */
 krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
 krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
 krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);
+krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel);
 long long krr_launch_count(void);
 
 #ifdef __cplusplus

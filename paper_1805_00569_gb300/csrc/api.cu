@@ -51,7 +51,8 @@ struct PcgBuffers {
     int64_t gtiles;
 };
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
-                    const void *, const void *, bool, int, double, int, const int32_t *, unsigned int *, int, Prof *);
+                    const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
+                    Prof *);
 void launch_predict(cudaStream_t, const Model &, const double *, int64_t, const int64_t *, const int64_t *, int64_t,
                     int, double *);
 void launch_select(cudaStream_t, const double *, const double *, int64_t, int, int, int, double *, int32_t *);
@@ -59,6 +60,7 @@ int oz_dpz(int d);
 bool oz_supported(int d);
 void launch_oz_slice(cudaStream_t, const double *, int, const int64_t *, int64_t, int64_t, void *, int32_t *, float2 *);
 bool make_slice_tmap(CUtensorMap *, void *, int64_t, int, int);
+cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, float *, float *, int *);
 cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
                               const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
                               int *);
@@ -225,6 +227,12 @@ krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, 
     if (!ctx || !W) return KRR_ERR_ARG;
     auto it = ctx->c.tuned_W.find(std::make_pair(prec, max_tiles));
     *W = ctx->c.chol_W > 0 ? ctx->c.chol_W : (it == ctx->c.tuned_W.end() ? 0 : it->second);
+    return KRR_OK;
+}
+
+krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel) {
+    if (!ctx || !(rel >= 0.0) || rel > 1e-2) return KRR_ERR_ARG;
+    ctx->c.target_err = rel;
     return KRR_OK;
 }
 
@@ -450,7 +458,11 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             } else {
                 Kh = (float *)Kst;
                 Kl = Kh + (size_t)ns * ktot * KRR_TILE_ELEMS;
-                launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
+                if (M.ozS) {
+                    FIT_TRY(launch_kbuild_oz(st, M, ktot, Kh, Kl, (float *)Ast, c->d_err));
+                } else {
+                    launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
+                }
             }
         }
         FIT_TRY(cudaGetLastError());
@@ -588,8 +600,11 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.d_gpre = d_gpre;
         B.ng = (int)groups.size();
         B.gtiles = gtiles;
+        // stop at the FP64-class floor, or earlier once kappa_est * residual meets the
+        // context's forward-error target (refined precisions only)
         const double tau = fp64 ? std::ldexp(1.0, -50) : std::ldexp(1.0, -46);
-        FIT_TRY(run_pcg(st, M, B, Kh, Kl, K64, Ast, Zst, fp64, maxT, tau, 80, flags, c->h_flag, 2, prof));
+        const double target = fp64 ? 0.0 : c->target_err;
+        FIT_TRY(run_pcg(st, M, B, Kh, Kl, K64, Ast, Zst, fp64, maxT, tau, target, 80, flags, c->h_flag, 2, prof));
         KRR_LAUNCHED(), export_kernel<<<nsolve, 256, 0, st>>>(M.d_solves, M.d_parts, G, M.alpha, state, solve_status, alpha);
         FIT_TRY(cudaGetLastError());
         int herr = 0;

@@ -124,6 +124,7 @@ struct Ctx {
     unsigned int *h_flag = nullptr;  // pinned host word for polling
     Prof prof;
     int chol_W = 0;            // outer panel width (0 = tuned on first use)
+    double target_err = 1e-7;  // refinement stops once kappa_est * backward error <= this
     std::map<std::pair<int, int>, int> tuned_W;  // (precision, max tiles) -> tuned panel width
 };
 

@@ -18,6 +18,8 @@
 //               solves).
 //   pcg_*       per-solve dot products (fixed-order reductions), updates,
 //               stopping test ||r||_inf <= tau (||A||_inf ||x||_inf + ||y||_inf).
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -33,16 +35,34 @@ __device__ __forceinline__ int find_group(const GroupDesc *gd, const int64_t *gp
     return lo;
 }
 
-// refined: K = Kh + Kl (df), p FP64.  grid = sum over groups of tri(T)
+// df butterfly sum over the 16 lanes that share (lane >> 4); identical in all of them
+__device__ __forceinline__ df df_sum16(df v) {
+#pragma unroll
+    for (int off = 8; off > 0; off >>= 1) {
+        df o;
+        o.hi = __shfl_xor_sync(0xffffffffu, v.hi, off);
+        o.lo = __shfl_xor_sync(0xffffffffu, v.lo, off);
+        v = ((threadIdx.x & off) == 0) ? df_add(v, o) : df_add(o, v);
+    }
+    return v;
+}
+
+// Tile products for every lambda of a group.  256 threads: thread (ty, tx)
+// owns rows ty*8 .. ty*8+7 and columns tx*8 .. tx*8+7, taken four rows at a
+// time.  Row partials are reduced across the 16 lanes of a half-warp by
+// shuffles, column partials across ty through shared memory, both in
+// double-float and in a fixed order.  Refined path: K = K_hi + K_lo; FP64
+// path: K64 with FP64 arithmetic.  grid = sum over groups of tri(T).
 template <bool DF>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 2)
 matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, const double *__restrict__ K64,
                     const GroupDesc *__restrict__ groups, const int64_t *__restrict__ gpre, int ng,
                     const SolveDesc *__restrict__ solves, const PcgState *__restrict__ state,
                     const double *__restrict__ pv, double *__restrict__ slots) {
-    __shared__ float2 sp_row[8][KRR_TILE];  // p of column block (df) per lambda
-    __shared__ float2 sp_col[8][KRR_TILE];  // p of row block
-    __shared__ double sred[16][KRR_TILE + 1];
+    constexpr int NL = 2;  // lambdas per pass
+    __shared__ float2 sp_row[NL][KRR_TILE];   // p of the column block (df)
+    __shared__ float2 sp_col[NL][KRR_TILE];   // p of the row block
+    __shared__ float2 scol[NL][16][KRR_TILE]; // column partials per ty
     const int gi = find_group(groups, gpre, ng, blockIdx.x);
     const GroupDesc G = groups[gi];
     bool any = false;
@@ -51,111 +71,114 @@ matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, 
     int ti, tj;
     tri_decode((int64_t)blockIdx.x - gpre[gi], ti, tj);
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    for (int e = threadIdx.x; e < G.nlam * KRR_TILE; e += 256) {
-        const int l = e >> 7, c = e & 127;
-        const SolveDesc S = solves[G.solve0 + l];
-        const double a = pv[S.vec0 + (int64_t)tj * KRR_TILE + c];
-        const double b = pv[S.vec0 + (int64_t)ti * KRR_TILE + c];
-        const float ah = __double2float_rn(a), bh = __double2float_rn(b);
-        sp_row[l][c] = make_float2(ah, __double2float_rn(a - (double)ah));
-        sp_col[l][c] = make_float2(bh, __double2float_rn(b - (double)bh));
-    }
-    __syncthreads();
     const int64_t tile = G.ktile0 + (int64_t)ti * (ti + 1) / 2 + tj;
-    float kh[8][8], kl[8][8];
-    double k64[8][8];
-    if (DF) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float *rh = Kh + tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8;
-            const float *rl = Kl + tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8;
-            float4 a0 = *reinterpret_cast<const float4 *>(rh), a1 = *reinterpret_cast<const float4 *>(rh + 4);
-            float4 b0 = *reinterpret_cast<const float4 *>(rl), b1 = *reinterpret_cast<const float4 *>(rl + 4);
-            kh[i][0] = a0.x; kh[i][1] = a0.y; kh[i][2] = a0.z; kh[i][3] = a0.w;
-            kh[i][4] = a1.x; kh[i][5] = a1.y; kh[i][6] = a1.z; kh[i][7] = a1.w;
-            kl[i][0] = b0.x; kl[i][1] = b0.y; kl[i][2] = b0.z; kl[i][3] = b0.w;
-            kl[i][4] = b1.x; kl[i][5] = b1.y; kl[i][6] = b1.z; kl[i][7] = b1.w;
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i)
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                k64[i][j] = K64[tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + i) * KRR_TILE + tx * 8 + j];
-    }
     const int T = G.T;
-    for (int l = 0; l < G.nlam; ++l) {
-        const SolveDesc S = solves[G.solve0 + l];
-        double *base = slots + G.scratch0 + (int64_t)l * T * T * KRR_TILE;
-        // row part: out[r] = sum_c K[r][c] p_j[c]  -> slot (ti, tj)
-        double rowp[8], colp[8];
-        if (DF) {
+    for (int l0 = 0; l0 < G.nlam; l0 += NL) {
+        const int nl = min(NL, G.nlam - l0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < nl * KRR_TILE; e += 256) {
+            const int l = e >> 7, c = e & 127;
+            const SolveDesc S = solves[G.solve0 + l0 + l];
+            const double a = pv[S.vec0 + (int64_t)tj * KRR_TILE + c];
+            const double b = pv[S.vec0 + (int64_t)ti * KRR_TILE + c];
+            const float ah = __double2float_rn(a), bh = __double2float_rn(b);
+            sp_row[l][c] = make_float2(ah, __double2float_rn(a - (double)ah));
+            sp_col[l][c] = make_float2(bh, __double2float_rn(b - (double)bh));
+        }
+        __syncthreads();
+        constexpr int RB = 2;  // rows per step
+        using Acc = typename std::conditional<DF, df_acc, double>::type;
+        Acc cacc[NL][8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                df_acc a;
-                dfa_zero(a);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float2 pj = sp_row[l][tx * 8 + j];
-                    dfa_fma(a, kh[i][j], kl[i][j], pj.x, pj.y);
-                }
-                rowp[i] = df_to_double(dfa_value(a));
-            }
+        for (int l = 0; l < NL; ++l)
 #pragma unroll
             for (int j = 0; j < 8; ++j) {
-                df_acc a;
-                dfa_zero(a);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 pi = sp_col[l][ty * 8 + i];
-                    dfa_fma(a, kh[i][j], kl[i][j], pi.x, pi.y);
-                }
-                colp[j] = df_to_double(dfa_value(a));
+                if constexpr (DF) dfa_zero(cacc[l][j]);
+                else cacc[l][j] = 0.0;
             }
-        } else {
+#pragma unroll 1
+        for (int h = 0; h < 8 / RB; ++h) {  // rows ty*8 + RB*h .. + RB-1
+            using KT = typename std::conditional<DF, float, double>::type;
+            KT kh[RB][8], kl[RB][8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                double a = 0.0;
+            for (int i = 0; i < RB; ++i) {
+                const int64_t off = tile * KRR_TILE_ELEMS + (int64_t)(ty * 8 + RB * h + i) * KRR_TILE + tx * 8;
+                if constexpr (DF) {
+                    const float4 a0 = __ldcs(reinterpret_cast<const float4 *>(Kh + off));
+                    const float4 a1 = __ldcs(reinterpret_cast<const float4 *>(Kh + off) + 1);
+                    const float4 b0 = __ldcs(reinterpret_cast<const float4 *>(Kl + off));
+                    const float4 b1 = __ldcs(reinterpret_cast<const float4 *>(Kl + off) + 1);
+                    kh[i][0] = a0.x; kh[i][1] = a0.y; kh[i][2] = a0.z; kh[i][3] = a0.w;
+                    kh[i][4] = a1.x; kh[i][5] = a1.y; kh[i][6] = a1.z; kh[i][7] = a1.w;
+                    kl[i][0] = b0.x; kl[i][1] = b0.y; kl[i][2] = b0.z; kl[i][3] = b0.w;
+                    kl[i][4] = b1.x; kl[i][5] = b1.y; kl[i][6] = b1.z; kl[i][7] = b1.w;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        kh[i][j] = K64[off + j];
+                        kl[i][j] = 0.0;
+                    }
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                if (l >= nl) break;
+                double *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
+#pragma unroll
+                for (int i = 0; i < RB; ++i) {
+                    const int r = ty * 8 + RB * h + i;
+                    df rv;
+                    if constexpr (DF) {
+                        df_acc a;
+                        dfa_zero(a);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 pj = sp_row[l][tx * 8 + j];
+                            dfa_fma(a, kh[i][j], kl[i][j], pj.x, pj.y);
+                        }
+                        rv = df_sum16(dfa_value(a));
+                    } else {
+                        double a = 0.0;
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float2 pj = sp_row[l][tx * 8 + j];
+                            a = fma(kh[i][j], (double)pj.x + (double)pj.y, a);
+                        }
+                        rv = df_sum16(df_from_double(a));
+                    }
+                    if (tx == 0) base[((int64_t)ti * T + tj) * KRR_TILE + r] = df_to_double(rv);
+                    const float2 pr = sp_col[l][r];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if constexpr (DF) dfa_fma(cacc[l][j], kh[i][j], kl[i][j], pr.x, pr.y);
+                        else cacc[l][j] = fma(kh[i][j], (double)pr.x + (double)pr.y, cacc[l][j]);
+                    }
+                }
+            }
+        }
+        if (ti != tj) {  // column partials -> slot (tj, ti)
+#pragma unroll
+            for (int l = 0; l < NL; ++l) {
+                if (l >= nl) break;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    const float2 pj = sp_row[l][tx * 8 + j];
-                    a = fma(k64[i][j], (double)pj.x + (double)pj.y, a);
+                    df v;
+                    if constexpr (DF) v = dfa_value(cacc[l][j]);
+                    else v = df_from_double(cacc[l][j]);
+                    scol[l][ty][tx * 8 + j] = make_float2(v.hi, v.lo);
                 }
-                rowp[i] = a;
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                double a = 0.0;
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float2 pi = sp_col[l][ty * 8 + i];
-                    a = fma(k64[i][j], (double)pi.x + (double)pi.y, a);
+            __syncthreads();
+            {
+                const int l = threadIdx.x >> 7, c = threadIdx.x & 127;
+                if (l < nl) {
+                    df s = df_make(scol[l][0][c].x, scol[l][0][c].y);
+                    for (int u = 1; u < 16; ++u) s = df_add(s, df_make(scol[l][u][c].x, scol[l][u][c].y));
+                    double *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
+                    base[((int64_t)tj * T + ti) * KRR_TILE + c] = df_to_double(s);
                 }
-                colp[j] = a;
             }
         }
-        // reduce row partials over tx (fixed order)
-        __syncthreads();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) sred[tx][ty * 8 + i] = rowp[i];
-        __syncthreads();
-        if (threadIdx.x < KRR_TILE) {
-            double s = 0.0;
-            for (int u = 0; u < 16; ++u) s += sred[u][threadIdx.x];
-            base[((int64_t)ti * T + tj) * KRR_TILE + threadIdx.x] = s;
-        }
-        if (ti != tj) {
-            __syncthreads();
-#pragma unroll
-            for (int j = 0; j < 8; ++j) sred[ty][tx * 8 + j] = colp[j];
-            __syncthreads();
-            if (threadIdx.x < KRR_TILE) {
-                double s = 0.0;
-                for (int u = 0; u < 16; ++u) s += sred[u][threadIdx.x];
-                base[((int64_t)tj * T + ti) * KRR_TILE + threadIdx.x] = s;
-            }
-        }
-        (void)S;
     }
 }
 
@@ -458,7 +481,7 @@ __global__ void pcg_start_kernel(const SolveDesc *__restrict__ solves, PcgState 
 // step 1: a = rz / p.q ; x += a p ; r -= a q ; stopping test
 __global__ void pcg_step1_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
                                  double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
-                                 const double *__restrict__ q, double tau, int maxit,
+                                 const double *__restrict__ q, double tau_min, double target, int maxit,
                                  unsigned int *__restrict__ nactive) {
     __shared__ double sh[256];
     const int s = blockIdx.x;
@@ -491,6 +514,9 @@ __global__ void pcg_step1_kernel(const SolveDesc *__restrict__ solves, PcgState 
     if (threadIdx.x == 0) {
         const double scale = st.anorm * xmax + st.ymax;
         const double rel = scale > 0.0 ? rmax / scale : 0.0;
+        // forward error <= kappa * backward error: stop once the bound meets the target
+        const double kappa = S.lambda_m > 0.0 ? st.anorm / S.lambda_m : 1e300;
+        const double tau = fmax(tau_min, target / kappa);
         state[s].resid = rel;
         state[s].iters = st.iters + 1;
         if (rel <= tau) {
@@ -572,7 +598,8 @@ size_t precond_smem_bytes(bool fp64, int maxT) {
 
 // Runs the whole refinement; returns the CUDA status of the last launch.
 cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
-                    const double *K64, const void *L, const void *Z, bool fp64, int maxT, double tau, int maxit,
+                    const double *K64, const void *L, const void *Z, bool fp64, int maxT, double tau, double target,
+                    int maxit,
                     const int32_t *flags, unsigned int *h_nactive, int check_every, Prof *prof) {
     const unsigned ns = (unsigned)M.solves.size();
     KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, flags, B.x, B.p);
@@ -584,7 +611,8 @@ cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const 
     for (int it = 0; it < maxit; ++it) {
         cudaMemsetAsync(B.nactive, 0, sizeof(unsigned int), st);
         launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
-        KRR_LAUNCHED(), pcg_step1_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.x, B.r, B.p, B.q, tau, maxit, B.nactive);
+        KRR_LAUNCHED(), pcg_step1_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.x, B.r, B.p, B.q, tau, target, maxit,
+                                                              B.nactive);
         e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
         if (e != cudaSuccess) return e;
         KRR_LAUNCHED(), pcg_step2_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);

@@ -61,6 +61,7 @@ struct OzSmem {
     uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
     uint64_t b_full, b_empty, t_full, t_empty;
     uint32_t tmem;
+    float2 cs[8];  // -1/(2 sigma^2) as df (kernel-tile build)
 };
 
 struct OzParams {
@@ -375,6 +376,221 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
+// ---------------------------------------------------------------- kernel tiles
+// Gaussian kernel tiles of the training partitions from the same exact slice
+// Gram: one CTA per lower tile (i, j) of a partition; the tile's 128 x 128
+// Gram is formed as two 64-column chunks (A = rows of block i, B = rows of
+// block j).  The epilogue writes, per sigma, K_hi + K_lo (df split) and, per
+// lambda, K_hi + lambda m I into the factor store.  Diagonal entries are
+// exactly 1; padding rows and columns form an identity block.
+struct OzKParams {
+    int nsig, nlam, np;
+    float c_hi[8], c_lo[8];
+    int kc;
+    int64_t ktot;
+};
+
+__device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64_t tile) {
+    int lo = 0, hi = np - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (parts[mid].ktile0 <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(OZ_THREADS, 1)
+kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                 const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
+                 const int32_t *__restrict__ ex, const float2 *__restrict__ nrm, OzKParams kp, int64_t prows,
+                 float *__restrict__ Kh, float *__restrict__ Kl, float *__restrict__ A, int *__restrict__ err) {
+    extern __shared__ unsigned char oz_dyn[];
+    const uint32_t base = smem_u32(oz_dyn);
+    OzSmem &sm = *reinterpret_cast<OzSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tile = blockIdx.x;
+    const int pj = oz_find_part(parts, kp.np, tile);
+    const PartDesc P = parts[pj];
+    int ti, tj;
+    tri_decode(tile - P.ktile0, ti, tj);
+    const int64_t lt = tile - P.ktile0;
+    constexpr int nchunks = KRR_TILE / OZ_N;  // 2
+    if (threadIdx.x < 8) sm.cs[threadIdx.x] = make_float2(kp.c_hi[threadIdx.x], kp.c_lo[threadIdx.x]);
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < OZ_ASTAGES; ++i) {
+            mbar_init(&sm.a_full[i], 1);
+            mbar_init(&sm.a_empty[i], 1);
+        }
+        mbar_init(&sm.b_full, 1);
+        mbar_init(&sm.b_empty, 1);
+        mbar_init(&sm.t_full, 1);
+        mbar_init(&sm.t_empty, 8);
+        fence_mbar_init();
+    }
+    exp_table_init(sm.exptab);
+    if (warp == 0) {
+        tmem_alloc(&sm.tmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = sm.tmem;
+
+    if (threadIdx.x == 0) {
+        const uint32_t bbytes = (uint32_t)(OZ_SLICES * kp.kc) * OZ_B_CHUNK;
+        const uint32_t abytes = (uint32_t)kp.kc * OZ_A_CHUNK;
+        int ait = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            if (c > 0 && !oz_wait(&sm.b_empty, (c - 1) & 1, err)) break;
+            mbar_arrive_expect_tx(&sm.b_full, bbytes);
+            const int brow = (int)(P.prow0 + (int64_t)tj * KRR_TILE + c * OZ_N);
+            for (int s = 0; s < OZ_SLICES; ++s)
+                for (int kc = 0; kc < kp.kc; ++kc)
+                    tma_load_2d(sm.b + (s * OZ_MAXKC + kc) * OZ_B_CHUNK, &tmB, kc * OZ_KC, (int)(s * prows) + brow,
+                                &sm.b_full);
+            bool ok = true;
+            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                if (use > 0 && !oz_wait(&sm.a_empty[st], (use - 1) & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                mbar_arrive_expect_tx(&sm.a_full[st], abytes);
+                const int arow = (int)(s * prows + P.prow0 + (int64_t)ti * KRR_TILE);
+                for (int kc = 0; kc < kp.kc; ++kc)
+                    tma_load_2d(sm.a[st] + kc * OZ_A_CHUNK, &tmA, kc * OZ_KC, arow, &sm.a_full[st]);
+            }
+            if (!ok) break;
+        }
+    } else if (threadIdx.x == 32) {
+        int ait = 0;
+        bool ok = true;
+        for (int c = 0; c < nchunks && ok; ++c) {
+            if (c > 0 && !oz_wait(&sm.t_empty, (c - 1) & 1, err)) break;
+            if (!oz_wait(&sm.b_full, c & 1, err)) break;
+            tc_fence_after();
+            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                if (!oz_wait(&sm.a_full[st], use & 1, err)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int tt = 0; tt + s < OZ_SLICES; ++tt) {
+                    const uint32_t dcol = tmem + (uint32_t)((s + tt) * OZ_N);
+                    for (int kk = 0; kk < 2 * kp.kc; ++kk) {
+                        const uint64_t da = smem_desc_sw64(sm.a[st] + (kk >> 1) * OZ_A_CHUNK) + 2 * (kk & 1);
+                        const uint64_t db =
+                            smem_desc_sw64(sm.b + (tt * OZ_MAXKC + (kk >> 1)) * OZ_B_CHUNK) + 2 * (kk & 1);
+                        tc_mma_f16(dcol, da, db, OZ_IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+                    }
+                }
+                tc_commit(&sm.a_empty[st]);
+            }
+            tc_commit(&sm.b_empty);
+            tc_commit(&sm.t_full);
+        }
+    } else if (warp >= OZ_EPI_WARP0) {
+        const int ew = warp - OZ_EPI_WARP0;
+        const int quad = warp & 3, half = ew >> 2;
+        const int r = quad * 32 + lane;            // row inside the tile
+        const int gr = ti * KRR_TILE + r;          // row inside the partition
+        const int64_t prow = P.prow0 + gr;
+        const int er = ex[prow];
+        const float2 nr2 = nrm[prow];
+        const df nr = df_make(nr2.x, nr2.y);
+        const int G = kp.nsig * kp.nlam;
+        for (int c = 0; c < nchunks; ++c) {
+            if (!oz_wait(&sm.t_full, c & 1, err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int sub = 0; sub < 2; ++sub) {
+                float lv[OZ_SLICES][16];
+                const uint32_t col0 = (uint32_t)(half * 32 + sub * 16);
+#pragma unroll
+                for (int L = 0; L < OZ_SLICES; ++L)
+                    tmem_ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
+                tmem_wait_ld();
+                if (sub == 1 && c == nchunks - 1) {
+                    // nothing follows the last chunk
+                } else if (sub == 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&sm.t_empty);
+                }
+                const int cbase = c * OZ_N + (int)col0;  // column inside the tile
+                float dh[16], dl[16];
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
+                    float th, tl;
+                    two_sum(lv[3][k] * 0x1p-24f, lv[4][k] * 0x1p-32f, th, tl);
+                    df u = df_make(th, tl);
+                    u = df_add(df_make(lv[2][k] * 0x1p-16f, 0.f), u);
+                    u = df_add(df_make(lv[1][k] * 0x1p-8f, 0.f), u);
+                    u = df_add(df_make(lv[0][k], 0.f), u);
+                    const float2 nc2 = nrm[pc];
+                    const int sc = er + ex[pc] - 13;
+                    const float s2 = __int_as_float((127 + sc) << 23);
+                    df D = df_add(nr, df_make(nc2.x, nc2.y));
+                    D = df_add(D, df_make(-u.hi * s2, -u.lo * s2));
+                    if (D.hi < 0.f) D = df_make(0.f, 0.f);
+                    dh[k] = D.hi;
+                    dl[k] = D.lo;
+                }
+                const bool diag_here = (ti == tj);
+#pragma unroll 1
+                for (int is = 0; is < kp.nsig; ++is) {
+                    const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
+                    float hv[16], lw[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int gc = tj * KRR_TILE + cbase + k;
+                        df kv;
+                        if (gr >= P.m || gc >= P.m) kv = df_make(gr == gc ? 1.f : 0.f, 0.f);
+                        else if (gr == gc) kv = df_make(1.f, 0.f);
+                        else kv = df_exp_nonpos(df_mul(df_make(dh[k], dl[k]), cs), sm.exptab);
+                        hv[k] = kv.hi;
+                        lw[k] = kv.lo;
+                    }
+                    const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
+                    float4 *oh = reinterpret_cast<float4 *>(Kh + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
+                    float4 *ol = reinterpret_cast<float4 *>(Kl + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        oh[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                        ol[q] = make_float4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                    }
+#pragma unroll 1
+                    for (int il = 0; il < kp.nlam; ++il) {
+                        const SolveDesc S = solves[(int64_t)pj * G + is * kp.nlam + il];
+                        const float lm = (float)S.lambda_m;
+                        float4 *oa = reinterpret_cast<float4 *>(A + (S.ltile0 + lt) * KRR_TILE_ELEMS +
+                                                                 (int64_t)r * KRR_TILE + cbase);
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            float4 v = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                            if (diag_here && gr < P.m) {
+                                const int d0 = gr - (tj * KRR_TILE + cbase + 4 * q);
+                                if (d0 == 0) v.x += lm;
+                                else if (d0 == 1) v.y += lm;
+                                else if (d0 == 2) v.z += lm;
+                                else if (d0 == 3) v.w += lm;
+                            }
+                            oa[q] = v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 512);
+}
+
 // ---------------------------------------------------------------- host
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
@@ -417,6 +633,33 @@ void launch_oz_slice(cudaStream_t st, const double *X, int d, const int64_t *map
 }
 
 size_t oz_smem_bytes() { return sizeof(OzSmem) + 1024; }
+
+// Kernel tiles of every partition and sigma, plus the factor matrices.
+cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
+                             int *d_err) {
+    if (ktot == 0) return cudaSuccess;
+    CUtensorMap tmA;
+    if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(kbuild_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
+        attr = true;
+    }
+    OzKParams kp;
+    kp.nsig = M.nsig;
+    kp.nlam = M.nlam;
+    kp.np = M.p;
+    kp.kc = M.dpz / OZ_KC;
+    kp.ktot = ktot;
+    for (int i = 0; i < 8; ++i) {
+        const double c = i < M.nsig ? -1.0 / (2.0 * M.sigmas[i] * M.sigmas[i]) : 0.0;
+        kp.c_hi[i] = (float)c;
+        kp.c_lo[i] = (float)(c - (double)(float)c);
+    }
+    KRR_LAUNCHED(), kbuild_oz_kernel<<<(unsigned)ktot, OZ_THREADS, oz_smem_bytes(), st>>>(
+        tmA, M.oz_tmB, M.d_parts, M.d_solves, M.ozex, M.nrm, kp, M.prows, Kh, Kl, A, d_err);
+    return cudaGetLastError();
+}
 
 // Slices the test rows (grouped by route when given), then launches one pass
 // per (sigma subset, lambda subset).  Xt rows -> workspace owned by the caller.
