@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print per-kernel-class times to stderr")
+    ap.add_argument("--n", type=int, default=65536, help="training rows (smaller values: profiling cases)")
+    ap.add_argument("--t", type=int, default=8192, help="test rows")
+    ap.add_argument("--p", type=int, default=16, help="partitions")
     return ap.parse_args()
 
 
@@ -165,7 +168,7 @@ def run_ours(args, rank, world, local_rank):
     from paper_1805_00569_gb300 import dist as kd, synth
 
     torch.cuda.set_device(local_rank)
-    w = synth.bkrr2(seed=1 + rank)
+    w = synth.bkrr2(seed=1 + rank, n=args.n, t=args.t, p=args.p)
     n, d = w["X"].shape
     t = w["Xt"].shape[0]
     p = w["p"]

@@ -37,7 +37,8 @@ struct CholLaunch {
 };
 void build_chol_plan(const std::vector<int> &, int, std::vector<CholLaunch> &, std::vector<int64_t> &);
 cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
-                          const SolveDesc *, int, int32_t *, bool, const CUtensorMap *, int *, Prof *);
+                          const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, int *,
+                          Prof *);
 bool make_tile_tmap(CUtensorMap *, float *, int64_t);
 size_t pcg_state_size();
 size_t precond_smem_bytes(bool, int);
@@ -470,9 +471,11 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         // Cholesky schedule
         std::vector<int> Ts(nsolve);
         for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
-        CUtensorMap tmap;
+        CUtensorMap tmap, tmapZ;
         memset(&tmap, 0, sizeof(tmap));
-        if (tf32 && !make_tile_tmap(&tmap, (float *)Ast, ltiles))
+        memset(&tmapZ, 0, sizeof(tmapZ));
+        const int tc = fp64 ? 0 : (tf32 ? 1 : 3);  // tensor-core mode of the factor
+        if (tc && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles)))
             return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
         // outer panel width: explicit, cached per (precision, max tiles), or tuned now by timing
         // each candidate schedule on these matrices (restored from K_hi between trials)
@@ -508,8 +511,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
                                                                                      (float *)Ast, 0.f);
                 cudaEventRecord(e0, st);
-                FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tf32, &tmap,
-                                      c->d_err, nullptr));
+                FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tc, &tmap,
+                                      &tmapZ, c->d_err, nullptr));
                 cudaEventRecord(e1, st);
                 FIT_TRY(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -533,8 +536,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         FIT_TRY(W.get(&d_plan, sizeof(int64_t) * std::max<size_t>(pre.size(), 1)));
         if (!pre.empty())
             FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
-        FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tf32, &tmap, c->d_err,
-                              prof));
+        FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tc, &tmap, &tmapZ,
+                              c->d_err, prof));
 
         // breakdown of the low-precision factor: refactor those solves with a diagonal shift
         if (!fp64) {
@@ -572,7 +575,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 FIT_TRY(R.get(&d_rplan, sizeof(int64_t) * std::max<size_t>(rp.size(), 1)));
                 FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
                                         st));
-                FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, tf32, &tmap,
+                FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, tc, &tmap, &tmapZ,
                                       c->d_err, prof));
                 std::vector<int32_t> hr(nsub);
                 FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));

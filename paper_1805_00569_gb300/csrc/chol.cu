@@ -19,11 +19,9 @@
 // uneven partitions need no padding launches.
 //
 // Trailing-update arithmetic by precision: FP64 and FP32 run a SIMT GEMM tile;
-// TF32 runs on the tcgen05 tensor cores: one elected thread streams the
-// operand tiles with 2-D TMA loads (128-byte swizzle) through a 3-stage
-// mbarrier ring, one elected thread issues kind::tf32 MMAs (M = N = 128,
-// K = 8) into a 128-column FP32 accumulator in tensor memory, and all four
-// warps read it back with tcgen05.ld for the A_ij -= C epilogue.
+// TF32 and FP32 run on the tcgen05 tensor cores (tile_mma_kernel): TF32 as one
+// kind::tf32 pass, FP32 as three passes over a hi/lo split; the panel solve
+// L_ik = A_ik Z_kk^T always runs as three passes (an FP32-class product).
 #include "common.cuh"
 #include "internal.h"
 
@@ -134,6 +132,153 @@ __global__ void __launch_bounds__(512) potrf_tile_kernel(T *__restrict__ A, T *_
     }
 }
 
+// Blocked FP32 version: 32 x 32 diagonal blocks factored and inverted by one
+// warp in registers (shuffles, no block barrier), panel solve and trailing
+// update block-parallel; ~20 barriers per tile instead of ~380.
+constexpr int PB = 32;
+__global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
+                                                                 const SolveDesc *__restrict__ solves,
+                                                                 const int64_t *__restrict__ pre, int nsolve, int k,
+                                                                 int32_t *__restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char po_dyn[];
+    float *L = reinterpret_cast<float *>(po_dyn);  // [128][129]
+    float *Zs = L + KRR_TILE * 129;                // [128][129]
+    __shared__ int bad_sh;
+    const int s = find_solve(pre, nsolve, blockIdx.x);
+    const SolveDesc S = solves[s];
+    const int64_t tile = S.ltile0 + (int64_t)k * (k + 1) / 2 + k;
+    float *g = A + tile * KRR_TILE_ELEMS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) bad_sh = 0;
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) L[(e >> 7) * 129 + (e & 127)] = g[e];
+    __syncthreads();
+    for (int b = 0; b < KRR_TILE / PB; ++b) {
+        const int rb = b * PB;
+        // (1) diagonal block: lane i owns row rb + i
+        if (warp == 0) {
+            float a[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) a[j] = L[(rb + lane) * 129 + rb + j];
+            bool badl = false;
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                float dg = __shfl_sync(0xffffffffu, a[c], c);
+                if (!(dg > 0.f)) {
+                    badl = true;
+                    dg = 1.f;
+                }
+                const float dc = sqrtf(dg);
+                if (lane == c) a[c] = dc;
+                else if (lane > c) a[c] = a[c] / dc;
+#pragma unroll
+                for (int j = c + 1; j < PB; ++j) {
+                    const float ljc = __shfl_sync(0xffffffffu, a[c], j);
+                    if (lane >= j) a[j] -= a[c] * ljc;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < PB; ++j) L[(rb + lane) * 129 + rb + j] = (j <= lane) ? a[j] : 0.f;
+            if (badl && lane == 0) bad_sh = 1;
+        }
+        __syncthreads();
+        // (2) panel below: x L_bb^T = a for every row r >= rb + 32
+        const int r = rb + PB + threadIdx.x;
+        if (r < KRR_TILE) {
+            float x[PB];
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                float v = L[r * 129 + rb + c];
+#pragma unroll
+                for (int q = 0; q < c; ++q) v -= x[q] * L[(rb + c) * 129 + rb + q];
+                x[c] = v / L[(rb + c) * 129 + rb + c];
+            }
+#pragma unroll
+            for (int c = 0; c < PB; ++c) L[r * 129 + rb + c] = x[c];
+        }
+        __syncthreads();
+        // (3) trailing update of rows/cols >= rb + 32 (lower part), 2 x 2 per thread
+        const int n2 = KRR_TILE - rb - PB;
+        if (n2 > 0) {
+            const int nb2 = n2 / 2;
+            for (int e = threadIdx.x; e < nb2 * nb2; e += blockDim.x) {
+                const int bi = e / nb2, bj = e % nb2;
+                if (bj > bi) continue;
+                const int r0 = rb + PB + 2 * bi, q0 = rb + PB + 2 * bj;
+                float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
+#pragma unroll 8
+                for (int kk = 0; kk < PB; ++kk) {
+                    const float a0 = L[r0 * 129 + rb + kk], a1 = L[(r0 + 1) * 129 + rb + kk];
+                    const float b0 = L[q0 * 129 + rb + kk], b1 = L[(q0 + 1) * 129 + rb + kk];
+                    s00 = fmaf(a0, b0, s00);
+                    s01 = fmaf(a0, b1, s01);
+                    s10 = fmaf(a1, b0, s10);
+                    s11 = fmaf(a1, b1, s11);
+                }
+                L[r0 * 129 + q0] -= s00;
+                L[(r0 + 1) * 129 + q0] -= s10;
+                L[(r0 + 1) * 129 + q0 + 1] -= s11;
+                if (bi != bj) L[r0 * 129 + q0 + 1] -= s01;
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && bad_sh) flags[s] = 1;
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int rr = e >> 7, cc = e & 127;
+        g[e] = (rr >= cc) ? L[rr * 129 + cc] : 0.f;
+    }
+    // inverse: diagonal blocks by warps 0..3 (lane j owns column j of the block)
+    if (warp < KRR_TILE / PB) {
+        const int rb = warp * PB;
+        float zc[PB];
+#pragma unroll
+        for (int i = 0; i < PB; ++i) {
+            float v = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+            for (int q = 0; q < i; ++q) v -= L[(rb + i) * 129 + rb + q] * zc[q];
+            zc[i] = (i >= lane) ? v / L[(rb + i) * 129 + rb + i] : 0.f;
+        }
+#pragma unroll
+        for (int i = 0; i < PB; ++i) Zs[(rb + i) * 129 + rb + lane] = zc[i];
+    }
+    // zero the strictly upper blocks of Z
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int rr = e >> 7, cc = e & 127;
+        if (cc / PB > rr / PB) Zs[rr * 129 + cc] = 0.f;
+    }
+    __syncthreads();
+    // off-diagonal blocks by distance d: Z_ij = -Z_ii sum_{q=j}^{i-1} L_iq Z_qj
+    float *T = reinterpret_cast<float *>(po_dyn) + 2 * KRR_TILE * 129;  // [3][32][33] scratch
+    for (int d = 1; d < KRR_TILE / PB; ++d) {
+        const int nblk = KRR_TILE / PB - d;
+        // T_j = sum_q L_{j+d,q} Z_{q,j}
+        for (int e = threadIdx.x; e < nblk * PB * PB; e += blockDim.x) {
+            const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
+            const int ib = jb + d;
+            float v = 0.f;
+            for (int qb = jb; qb < ib; ++qb)
+#pragma unroll 8
+                for (int q = 0; q < PB; ++q) v += L[(ib * PB + rr) * 129 + qb * PB + q] * Zs[(qb * PB + q) * 129 + jb * PB + cc];
+            T[(jb * PB + rr) * 33 + cc] = v;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nblk * PB * PB; e += blockDim.x) {
+            const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
+            const int ib = jb + d;
+            float v = 0.f;
+#pragma unroll 8
+            for (int q = 0; q < PB; ++q) v += Zs[(ib * PB + rr) * 129 + ib * PB + q] * T[(jb * PB + q) * 33 + cc];
+            Zs[(ib * PB + rr) * 129 + jb * PB + cc] = -v;
+        }
+        __syncthreads();
+    }
+    float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int rr = e >> 7, cc = e & 127;
+        z[e] = (rr >= cc) ? Zs[rr * 129 + cc] : 0.f;
+    }
+}
+
 // ---------------------------------------------------------------- SIMT GEMM tile
 // UPD_TRAIL / UPD_COLUMN: A_ij -= sum_{k in [kb,ke)} L_ik L_jk^T
 // UPD_TRSM:               A_ik  = A_ik Z_kk^T
@@ -197,11 +342,23 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 }
 
 // ---------------------------------------------------------------- tcgen05 TF32
-constexpr int TC_STAGES = 3;
-constexpr int TC_CHUNK = 32;                                     // floats of K per stage (128 bytes)
-constexpr uint32_t TC_STAGE_BYTES = 2u * KRR_TILE * TC_CHUNK * 4;  // A + B, 32 KB
+// One CTA per task, 192 threads: warp 0 lane 0 streams the operand tiles with
+// 2-D TMA loads (128-byte swizzle) through an mbarrier ring; warp 1 lane 0
+// issues the MMAs into a 128 x 128 FP32 accumulator in tensor memory; warps
+// 2..5 read it back (tcgen05.ld) for the epilogue (A_ij -= C, or A_ik = C for
+// the panel solve).  X3 = false: one kind::tf32 MMA per K step (the tensor
+// core reads the top 19 bits of each FP32 operand).  X3 = true: warps 2..5
+// also split each landed stage into hi = x with the low 13 mantissa bits
+// cleared and lo = x - hi (exact), and three MMAs per K step form
+// hi*hi + hi*lo + lo*hi: FP32-class products on the tensor cores.
+constexpr int TC_CHUNK = 32;                                       // floats of K per stage (128 bytes)
+constexpr uint32_t TC_HALF = (uint32_t)KRR_TILE * TC_CHUNK * 4;     // one operand tile chunk, 16 KB
 constexpr uint32_t TC_IDESC = make_idesc(2u /*TF32*/, 128u, 128u);
-constexpr size_t TC_SMEM = TC_STAGES * TC_STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+template <bool X3> struct TcCfg {
+    static constexpr int STAGES = X3 ? 2 : 3;
+    static constexpr uint32_t STAGE_BYTES = (X3 ? 4u : 2u) * TC_HALF;  // A, B (+ A_lo, B_lo)
+    static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+};
 
 __device__ __forceinline__ uint64_t global_ns() {
     uint64_t t;
@@ -222,16 +379,19 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
     }
 }
 
-__global__ void __launch_bounds__(128, 1)
-update_tf32_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__ A,
-                   const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre, int nsolve, int mode,
-                   int K0, int W, int *__restrict__ err) {
+template <bool X3>
+__global__ void __launch_bounds__(192, 1)
+tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
+                float *__restrict__ A, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
+                int nsolve, int mode, int K0, int W, int *__restrict__ err) {
+    using Cfg = TcCfg<X3>;
     extern __shared__ unsigned char tc_dyn[];
     const uint32_t base = smem_u32(tc_dyn);
     unsigned char *buf = tc_dyn + (((base + 1023u) & ~1023u) - base);  // 1024-aligned stage ring
-    uint64_t *full = reinterpret_cast<uint64_t *>(buf + TC_STAGES * TC_STAGE_BYTES);
-    uint64_t *empty = full + TC_STAGES;
-    uint64_t *done = empty + TC_STAGES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(buf + Cfg::STAGES * Cfg::STAGE_BYTES);
+    uint64_t *empty = full + Cfg::STAGES;
+    uint64_t *split = empty + Cfg::STAGES;
+    uint64_t *done = split + Cfg::STAGES;
     uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -241,9 +401,10 @@ update_tf32_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__
     const int nchunks = (g.ke - g.kb) * (KRR_TILE / TC_CHUNK);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < TC_STAGES; ++i) {
+        for (int i = 0; i < Cfg::STAGES; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], 1);
+            mbar_init(&split[i], 4);
         }
         mbar_init(done, 1);
         fence_mbar_init();
@@ -259,56 +420,102 @@ update_tf32_kernel(const __grid_constant__ CUtensorMap tmap, float *__restrict__
 
     if (threadIdx.x == 0) {  // TMA producer
         for (int q = 0; q < nchunks; ++q) {
-            const int st = q % TC_STAGES, use = q / TC_STAGES;
+            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
             if (use > 0 && !mbar_wait_deadline(&empty[st], (use - 1) & 1, err)) break;
-            unsigned char *sa = buf + st * TC_STAGE_BYTES;
-            unsigned char *sb = sa + TC_STAGE_BYTES / 2;
+            unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
+            unsigned char *sb = sa + TC_HALF;
             const int kt = g.kb + q / (KRR_TILE / TC_CHUNK);
             const int x = (q % (KRR_TILE / TC_CHUNK)) * TC_CHUNK;
             const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
-            const int yb = (int)((S.ltile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE);
-            mbar_arrive_expect_tx(&full[st], TC_STAGE_BYTES);
+            mbar_arrive_expect_tx(&full[st], 2 * TC_HALF);
             tma_load_2d(sa, &tmap, x, ya, &full[st]);
-            tma_load_2d(sb, &tmap, x, yb, &full[st]);
+            if (mode == UPD_TRSM) {
+                tma_load_2d(sb, &tmapZ, x, (int)((S.dtile0 + kt) * KRR_TILE), &full[st]);
+            } else {
+                const int yb = (int)((S.ltile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE);
+                tma_load_2d(sb, &tmap, x, yb, &full[st]);
+            }
         }
     } else if (threadIdx.x == 32) {  // MMA issuer
         bool ok = true;
         for (int q = 0; q < nchunks && ok; ++q) {
-            const int st = q % TC_STAGES, use = q / TC_STAGES;
-            if (!mbar_wait_deadline(&full[st], use & 1, err)) {
+            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
+            if (!mbar_wait_deadline(X3 ? &split[st] : &full[st], use & 1, err)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            unsigned char *sa = buf + st * TC_STAGE_BYTES;
-            unsigned char *sb = sa + TC_STAGE_BYTES / 2;
+            unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
+            unsigned char *sb = sa + TC_HALF;
             const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
 #pragma unroll
-            for (int kk = 0; kk < TC_CHUNK / 8; ++kk)  // K = 8 TF32 = 32 bytes per MMA
-                tc_mma_tf32(tmem, da + 2 * kk, db + 2 * kk, TC_IDESC, (q > 0 || kk > 0) ? 1u : 0u);
+            for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
+                const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
+                tc_mma_tf32(tmem, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
+                if (X3) {
+                    const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF), dbl = smem_desc_sw128(sb + 2 * TC_HALF);
+                    tc_mma_tf32(tmem, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
+                    tc_mma_tf32(tmem, dal + 2 * kk, db + 2 * kk, TC_IDESC, 1u);
+                }
+            }
             tc_commit(&empty[st]);
         }
         tc_commit(done);
+    } else if (warp >= 2 && X3) {  // split landed stages into hi / lo
+        const int t = threadIdx.x - 64;  // 0..127
+        for (int q = 0; q < nchunks; ++q) {
+            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
+            if (!mbar_wait_deadline(&full[st], use & 1, err)) break;
+            float4 *hi = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES);
+            float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
+#pragma unroll 4
+            for (int e = t; e < (int)(2 * TC_HALF / 16); e += 128) {
+                float4 v = hi[e], h, l;
+                h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                l.x = v.x - h.x;
+                l.y = v.y - h.y;
+                l.z = v.z - h.z;
+                l.w = v.w - h.w;
+                hi[e] = h;
+                lo[e] = l;
+            }
+            fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&split[st]);
+        }
     }
     __syncwarp();
-    const bool have = mbar_wait_deadline(done, 0, err);
-    tc_fence_after();
-    if (have && *err == 0) {
-        const int r = warp * 32 + lane;
-        float *dst = A + (S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE;
+    if (warp >= 2) {  // epilogue
+        const bool have = mbar_wait_deadline(done, 0, err);
+        tc_fence_after();
+        if (have && *err == 0) {
+            const int quad = warp & 3;
+            const int r = quad * 32 + lane;
+            float *dst =
+                A + (S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE;
 #pragma unroll 1
-        for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
-            float v[32];
-            tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 32), v);
-            float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
+            for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
+                float v[32];
+                tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), v);
+                float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
+                if (mode == UPD_TRSM) {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                float4 o = d4[q];
-                o.x -= v[4 * q + 0];
-                o.y -= v[4 * q + 1];
-                o.z -= v[4 * q + 2];
-                o.w -= v[4 * q + 3];
-                d4[q] = o;
+                    for (int qq = 0; qq < 8; ++qq)
+                        d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                } else {
+#pragma unroll
+                    for (int qq = 0; qq < 8; ++qq) {
+                        float4 o = d4[qq];
+                        o.x -= v[4 * qq + 0];
+                        o.y -= v[4 * qq + 1];
+                        o.z -= v[4 * qq + 2];
+                        o.w -= v[4 * qq + 3];
+                        d4[qq] = o;
+                    }
+                }
             }
         }
     }
@@ -338,6 +545,7 @@ static PFN_encodeTiled get_encode() {
 
 // 2-D view of a float tile store: rows of 128 floats, box 32 x 128, 128B swizzle
 bool make_tile_tmap(CUtensorMap *map, float *store, int64_t ntiles) {
+    if (ntiles <= 0) ntiles = 1;
     PFN_encodeTiled enc = get_encode();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)KRR_TILE, (cuuint64_t)(ntiles * KRR_TILE)};
@@ -397,45 +605,62 @@ void build_chol_plan(const std::vector<int> &T, int W, std::vector<CholLaunch> &
 
 template <typename T>
 cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, T *A, T *Z,
-                            const SolveDesc *d_solves, int nsolve, int32_t *flags, bool tf32, const CUtensorMap *tmap,
-                            int *d_err, Prof *prof) {
+                            const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc, const CUtensorMap *tmap,
+                            const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     cudaFuncSetAttribute(potrf_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_sm);
+    const size_t po_blk_sm = (2 * (size_t)KRR_TILE * 129 + 3 * 32 * 33) * sizeof(float);
+    cudaFuncSetAttribute(potrf_tile_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_blk_sm);
     for (const CholLaunch &L : plan) {
         const unsigned grid = (unsigned)L.tasks;
         const int64_t *p = d_pre + L.pre;
         ProfScope ps(prof, L.kind == 0 ? PROF_POTRF : (L.kind == 1 ? PROF_TRSM : PROF_UPDATE), st);
         if (L.kind == 0) {
-            KRR_LAUNCHED(), potrf_tile_kernel<T><<<grid, 512, po_sm, st>>>(A, Z, d_solves, p, nsolve, L.K0, flags);
-        } else if (L.kind == 1) {
-            KRR_LAUNCHED(), gemm_tile_simt_kernel<T><<<grid, 256, 0, st>>>(A, Z, d_solves, p, nsolve, UPD_TRSM, L.K0, 0);
-        } else {
-            const int mode = (L.kind == 2) ? UPD_TRAIL : UPD_COLUMN;
-            if constexpr (sizeof(T) == 4) {
-                if (tf32) {
-                    KRR_LAUNCHED(), update_tf32_kernel<<<grid, 128, TC_SMEM, st>>>(*tmap, reinterpret_cast<float *>(A), d_solves, p,
-                                                                   nsolve, mode, L.K0, L.W, d_err);
-                    continue;
-                }
-            }
-            KRR_LAUNCHED(), gemm_tile_simt_kernel<T><<<grid, 256, 0, st>>>(A, Z, d_solves, p, nsolve, mode, L.K0, L.W);
+            if constexpr (sizeof(T) == 4)
+                KRR_LAUNCHED(), potrf_tile_blocked_kernel<<<grid, 256, po_blk_sm, st>>>(
+                    reinterpret_cast<float *>(A), reinterpret_cast<float *>(Z), d_solves, p, nsolve, L.K0, flags);
+            else
+                KRR_LAUNCHED(), potrf_tile_kernel<T><<<grid, 512, po_sm, st>>>(A, Z, d_solves, p, nsolve, L.K0,
+                                                                               flags);
+            continue;
         }
+        const int mode = L.kind == 1 ? UPD_TRSM : (L.kind == 2 ? UPD_TRAIL : UPD_COLUMN);
+        const int W = L.kind == 1 ? 0 : L.W;
+        if constexpr (sizeof(T) == 4) {
+            // tensor cores: the panel solve always FP32-class (3 passes); the
+            // trailing updates 1 pass (TF32) or 3 passes (FP32)
+            if (tc != 0) {
+                const bool x3 = (L.kind == 1) || tc == 3;
+                if (x3)
+                    KRR_LAUNCHED(), tile_mma_kernel<true><<<grid, 192, TcCfg<true>::SMEM, st>>>(
+                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, mode, L.K0, W, d_err);
+                else
+                    KRR_LAUNCHED(), tile_mma_kernel<false><<<grid, 192, TcCfg<false>::SMEM, st>>>(
+                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, mode, L.K0, W, d_err);
+                continue;
+            }
+        }
+        KRR_LAUNCHED(), gemm_tile_simt_kernel<T><<<grid, 256, 0, st>>>(A, Z, d_solves, p, nsolve, mode, L.K0, W);
     }
     return cudaGetLastError();
 }
 
+// tc: 0 = SIMT trailing updates, 1 = TF32 (1 pass), 3 = FP32-class (3 passes)
 cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, void *A, void *Z,
-                          bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, bool tf32,
-                          const CUtensorMap *tmap, int *d_err, Prof *prof) {
+                          bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
+                          const CUtensorMap *tmap, const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(update_tf32_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM);
+        cudaFuncSetAttribute(tile_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcCfg<false>::SMEM);
+        cudaFuncSetAttribute(tile_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)TcCfg<true>::SMEM);
         attr = true;
     }
     if (fp64)
-        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, d_solves, nsolve, flags, false,
-                                       tmap, d_err, prof);
-    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, d_solves, nsolve, flags, tf32, tmap,
+        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, d_solves, nsolve, flags, 0, tmap,
+                                       tmapZ, d_err, prof);
+    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, d_solves, nsolve, flags, tc, tmap, tmapZ,
                                   d_err, prof);
 }
 

@@ -36,8 +36,8 @@ constexpr int OZ_KC = 32;          // features per K chunk (64 bytes of bf16)
 constexpr int OZ_MAXKC = 3;        // d <= 96
 constexpr int OZ_ASTAGES = 3;
 constexpr int OZ_NSP = 4, OZ_NLP = 2;  // sigmas / lambdas per pass
-constexpr int OZ_THREADS = 384;    // 12 warps
-constexpr int OZ_EPI_WARP0 = 4;
+constexpr int OZ_THREADS = 320;    // 10 warps: producer, MMA issuer, 8 epilogue warps
+constexpr int OZ_EPI_WARP0 = 2;
 
 constexpr uint32_t OZ_A_CHUNK = OZ_M * 64;                 // bytes of one K chunk of one A slice
 constexpr uint32_t OZ_B_CHUNK = OZ_N * 64;
@@ -322,22 +322,28 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     if (D.hi < 0.f) D = df_make(0.f, 0.f);
                     sm.dist[et][k] = make_float2(D.hi, D.lo);
                 }
+                // two columns per iteration: their exponentials are independent
+                // chains the scheduler can interleave.  Padded training rows have
+                // alpha = 0 exactly, so they need no test.
 #pragma unroll 1
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < 16; k += 2) {
                     const int col = (int)col0 + k;
-                    if ((int64_t)c * OZ_N + col >= P.m) break;
-                    const float2 dv = sm.dist[et][k];
-                    const df D = df_make(dv.x, dv.y);
+                    const float2 dv0 = sm.dist[et][k], dv1 = sm.dist[et][k + 1];
+                    const df D0 = df_make(dv0.x, dv0.y), D1 = df_make(dv1.x, dv1.y);
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
                         if (is < pp.nsig) {
-                            const df kv =
-                                df_exp_nonpos(df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is])), sm.exptab);
+                            const df cs = df_make(pp.c_hi[is], pp.c_lo[is]);
+                            const df k0 = df_exp_nonpos(df_mul(D0, cs), sm.exptab);
+                            const df k1 = df_exp_nonpos(df_mul(D1, cs), sm.exptab);
 #pragma unroll
                             for (int il = 0; il < OZ_NLP; ++il)
-                                if (il < pp.nlam)
-                                    dfa_fma(acc[is][il], kv.hi, kv.lo, cd.ah[is * OZ_NLP + il][col],
+                                if (il < pp.nlam) {
+                                    dfa_fma(acc[is][il], k0.hi, k0.lo, cd.ah[is * OZ_NLP + il][col],
                                             cd.al[is * OZ_NLP + il][col]);
+                                    dfa_fma(acc[is][il], k1.hi, k1.lo, cd.ah[is * OZ_NLP + il][col + 1],
+                                            cd.al[is * OZ_NLP + il][col + 1]);
+                                }
                         }
                     }
                 }
