@@ -49,9 +49,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print per-kernel-class times to stderr")
-    ap.add_argument("--n", type=int, default=65536, help="training rows (smaller values: profiling cases)")
-    ap.add_argument("--t", type=int, default=8192, help="test rows")
-    ap.add_argument("--p", type=int, default=16, help="partitions")
+    ap.add_argument("--workload", default="bkrr2", choices=["bkrr2", "kkrr2", "sweep", "dkrr"],
+                    help="bkrr2: the headline configuration; kkrr2: K-means partitions (uneven, routed); "
+                         "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows")
+    ap.add_argument("--n", type=int, default=0, help="training rows (0 = the workload's; smaller: profiling cases)")
+    ap.add_argument("--t", type=int, default=0, help="test rows (0 = the workload's)")
+    ap.add_argument("--p", type=int, default=0, help="partitions (0 = the workload's)")
     return ap.parse_args()
 
 
@@ -152,6 +155,31 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- our arm
+def make_workload(args, rank):
+    from paper_1805_00569_gb300 import synth
+    kw = {}
+    if args.n:
+        kw["n"] = args.n
+    if args.t:
+        kw["t"] = args.t
+    if args.workload == "bkrr2":
+        if args.p:
+            kw["p"] = args.p
+        return synth.bkrr2(seed=1 + rank, **kw)
+    if args.workload == "kkrr2":
+        if args.p:
+            kw["k"] = args.p
+        if args.n and args.n < 262144:  # keep the mixture's size range proportional
+            kw["lo"] = max(16, int(500 * args.n / 262144))
+            kw["hi"] = max(kw["lo"] + 1, int(16000 * args.n / 262144))
+        return synth.kkrr2(seed=2 + rank, **kw)
+    if args.workload == "sweep":
+        if args.p:
+            kw["p"] = args.p
+        return synth.sweep(seed=3 + rank, **kw)
+    return synth.dkrr(seed=0 + rank, **kw)
+
+
 def ctypes_int():
     return ctypes.c_int(0)
 
@@ -168,10 +196,11 @@ def run_ours(args, rank, world, local_rank):
     from paper_1805_00569_gb300 import dist as kd, synth
 
     torch.cuda.set_device(local_rank)
-    w = synth.bkrr2(seed=1 + rank, n=args.n, t=args.t, p=args.p)
+    w = make_workload(args, rank)
     n, d = w["X"].shape
     t = w["Xt"].shape[0]
     p = w["p"]
+    kmeans = args.workload == "kkrr2"
     S, L = w["sigmas"], w["lambdas"]
     G = len(S) * len(L)
     nsolve = p * G
@@ -184,12 +213,26 @@ def run_ours(args, rank, world, local_rank):
     yhat_buf = torch.empty((nsolve, t), dtype=torch.float64, device="cuda")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    init_idx = dev(w["init_idx"], torch.int64) if kmeans else None
+    if kmeans:
+        yhat_buf = torch.empty((G, t), dtype=torch.float64, device="cuda")
+
+    last_offsets = [None]
+
     def step(Xd, yd, Xtd, ytd, prec):
-        _, _, perm, offsets, _ = K.krr_partition(ctx, Xd, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
-        model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
-        yh = K.krr_predict(ctx, model, Xtd, out=yhat_buf)
-        mse, best = K.krr_select(ctx, yh, ytd, p, G, K.KRR_SEL_PER_MODEL)
+        if kmeans:  # KKRR2: K-means partitions, routed prediction, routed selection
+            _, route, perm, offsets, _ = K.krr_partition(ctx, Xd, Xtd, K.KRR_PART_KMEANS, p, iters=w["iters"],
+                                                         init_idx=init_idx)
+            model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
+            yh = K.krr_predict(ctx, model, Xtd, route=route, out=yhat_buf)
+            mse, best = K.krr_select(ctx, yh, ytd, p, G, K.KRR_SEL_ROUTED)
+        else:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, Xd, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+            model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
+            yh = K.krr_predict(ctx, model, Xtd, out=yhat_buf)
+            mse, best = K.krr_select(ctx, yh, ytd, p, G, K.KRR_SEL_PER_MODEL)
         model.free()
+        last_offsets[0] = offsets
         return mse, best, status
 
     for _ in range(args.warmup):
@@ -197,13 +240,19 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     bad = int((status != K.KRR_OK).sum().item())
     if args.profile:
-        _, _, perm, offsets, _ = K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+        if kmeans:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, X, Xt, K.KRR_PART_KMEANS, p, iters=w["iters"],
+                                                     init_idx=init_idx)
+        else:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
         model, _, _ = K.krr_fit_batch(ctx, X, y, perm, offsets, S, L, args.prec)
         it, ka, rs = K.krr_model_stats(ctx, model)
         model.free()
         Wt = ctypes_int()
-        ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2}[args.prec], n // p // 128,
-                                        ctypes.byref(Wt))
+        sizes = np.diff(offsets.cpu().numpy())
+        ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2}[args.prec],
+                                        int((sizes.max() + 127) // 128), ctypes.byref(Wt))
+        sys.stderr.write("partition sizes: min %d max %d\n" % (sizes.min(), sizes.max()))
         sys.stderr.write("refinement iterations per (sigma, lambda): %s; panel width %d\n" % (
             [sorted(set(int(v) for v in it.view(p, G)[:, g].tolist())) for g in range(G)], Wt.value))
 
@@ -242,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
                         (w["X"], w["y"], w["Xt"], w["yt"]))
     dX, dy, dXt, dyt = (torch.empty_like(a, device="cuda") for a in (hX, hy, hXt, hyt))
     hbest = torch.empty(1, dtype=torch.int32).pin_memory()
-    hmse = torch.empty(nsolve, dtype=torch.float64).pin_memory()
+    hmse = torch.empty(G if kmeans else nsolve, dtype=torch.float64).pin_memory()
     e2e_times = []
     for it in range(args.steps):
         flush.zero_()
@@ -277,9 +326,9 @@ def run_ours(args, rank, world, local_rank):
 
     ms_per_step = total_ms / args.steps
     value = world * nsolve * args.steps / (total_ms / 1e3)
-    m = n // p
-    tflops = world * nsolve * solve_flops(m, d) * args.steps / (total_ms / 1e3) / 1e12
-    return dict(w=w, value=value, ms_per_step=ms_per_step, tflops=tflops, prof=prof, clocks=clk,
+    sizes = np.diff(last_offsets[0].cpu().numpy())
+    tflops = world * G * sum(solve_flops(int(m), d) for m in sizes) * args.steps / (total_ms / 1e3) / 1e12
+    return dict(w=w, sizes=sizes, value=value, ms_per_step=ms_per_step, tflops=tflops, prof=prof, clocks=clk,
                 launches=launches + flush_launches, e2e=dict(value=world * nsolve * args.steps / e2e_s, unit=UNIT,
                                                          h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                 fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times)
@@ -291,6 +340,7 @@ def roofline(res, steps, peaks):
     w = res["w"]
     n, d = w["X"].shape
     p = w["p"]
+    sizes = [int(v) for v in res["sizes"]]
     m = n // p
     G = len(w["sigmas"]) * len(w["lambdas"])
     t = w["Xt"].shape[0]
@@ -302,14 +352,14 @@ def roofline(res, steps, peaks):
     out = {"kernel": dom, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
            "share": ms / sum(v[0] for v in prof.values())}
     if dom == "update":
-        flops = steps * p * G * m ** 3 / 3.0
+        flops = steps * G * sum(mm ** 3 / 3.0 for mm in sizes)
         out.update(bound="tensor", achieved=flops / (ms / 1e3) / 1e12, peak=tf32_peak, unit="TFLOP/s",
                    peak_note="TF32 = measured bf16 sustained x nominal TF32/BF16 ratio (1.1/2.25), of measured")
     elif dom in ("kbuild", "predict"):
         if dom == "kbuild":
-            flops = steps * p * (m * m * d + len(w["sigmas"]) * m * m / 2.0 * 20)
+            flops = steps * sum(mm * mm * d + len(w["sigmas"]) * mm * mm / 2.0 * 20 for mm in sizes)
         else:
-            flops = steps * p * t * m * (2.0 * d + len(w["sigmas"]) * 20 + 2 * G)
+            flops = steps * sum(t * mm for mm in sizes) * (2.0 * d + len(w["sigmas"]) * 20 + 2 * G)
         out.update(bound="alu", achieved=flops / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
                    peak_note="FP32 FFMA peak = 152 SMs x 128 lanes x 2 x sampled SM clock; algorithmic FP64-class "
                              "flops (each costs ~12 FP32 ops in double-float)")

@@ -132,10 +132,16 @@ __global__ void __launch_bounds__(512) potrf_tile_kernel(T *__restrict__ A, T *_
     }
 }
 
-// Blocked FP32 version: 32 x 32 diagonal blocks factored and inverted by one
-// warp in registers (shuffles, no block barrier), panel solve and trailing
-// update block-parallel; ~20 barriers per tile instead of ~380.
+// Blocked FP32 version.  For each 32-column block b: warp 0 factors the
+// 32 x 32 diagonal block in shared memory (lane i owns row i), the rows below
+// solve against it in place (one thread per row), and the trailing part is
+// updated block-parallel.  At the end warps 0..3 invert the four diagonal
+// blocks in parallel (lane j owns column j) and the off-diagonal blocks of
+// the tile inverse follow by block products.  Every serial phase is a compact
+// rolled loop: the kernel runs once per tile and column, so straight-line
+// unrolled code would be fetched from L2 on every SM.
 constexpr int PB = 32;
+
 __global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
                                                                  const SolveDesc *__restrict__ solves,
                                                                  const int64_t *__restrict__ pre, int nsolve, int k,
@@ -143,6 +149,7 @@ __global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restri
     extern __shared__ __align__(16) unsigned char po_dyn[];
     float *L = reinterpret_cast<float *>(po_dyn);  // [128][129]
     float *Zs = L + KRR_TILE * 129;                // [128][129]
+    float *T = Zs + KRR_TILE * 129;                // [96][33] scratch
     __shared__ int bad_sh;
     const int s = find_solve(pre, nsolve, blockIdx.x);
     const SolveDesc S = solves[s];
@@ -150,53 +157,53 @@ __global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restri
     float *g = A + tile * KRR_TILE_ELEMS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) bad_sh = 0;
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) L[(e >> 7) * 129 + (e & 127)] = g[e];
+    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int rr = e >> 7, cc = e & 127;
+        L[rr * 129 + cc] = g[e];
+        if (cc / PB > rr / PB) Zs[rr * 129 + cc] = 0.f;  // strictly upper blocks of Z
+    }
     __syncthreads();
+#pragma unroll 1
     for (int b = 0; b < KRR_TILE / PB; ++b) {
         const int rb = b * PB;
-        // (1) diagonal block: lane i owns row rb + i
-        if (warp == 0) {
-            float a[PB];
-#pragma unroll
-            for (int j = 0; j < PB; ++j) a[j] = L[(rb + lane) * 129 + rb + j];
-            bool badl = false;
-#pragma unroll
+        if (warp == 0) {  // diagonal block, right-looking, lane = row
+            float *D = L + rb * 129 + rb;
+#pragma unroll 1
             for (int c = 0; c < PB; ++c) {
-                float dg = __shfl_sync(0xffffffffu, a[c], c);
+                float dg = D[c * 129 + c];
                 if (!(dg > 0.f)) {
-                    badl = true;
                     dg = 1.f;
+                    if (lane == 0) bad_sh = 1;
                 }
                 const float dc = sqrtf(dg);
-                if (lane == c) a[c] = dc;
-                else if (lane > c) a[c] = a[c] / dc;
-#pragma unroll
-                for (int j = c + 1; j < PB; ++j) {
-                    const float ljc = __shfl_sync(0xffffffffu, a[c], j);
-                    if (lane >= j) a[j] -= a[c] * ljc;
+                __syncwarp();
+                if (lane > c) D[lane * 129 + c] /= dc;
+                __syncwarp();
+                if (lane == c) D[c * 129 + c] = dc;
+                if (lane > c) {
+                    const float lc = D[lane * 129 + c];
+#pragma unroll 1
+                    for (int j = c + 1; j <= lane; ++j) D[lane * 129 + j] -= lc * D[j * 129 + c];
                 }
+                __syncwarp();
             }
-#pragma unroll
-            for (int j = 0; j < PB; ++j) L[(rb + lane) * 129 + rb + j] = (j <= lane) ? a[j] : 0.f;
-            if (badl && lane == 0) bad_sh = 1;
         }
         __syncthreads();
-        // (2) panel below: x L_bb^T = a for every row r >= rb + 32
+        // rows below: x L_bb^T = a, solved in place, one thread per row
         const int r = rb + PB + threadIdx.x;
         if (r < KRR_TILE) {
-            float x[PB];
-#pragma unroll
+            float *x = L + r * 129 + rb;
+            const float *D = L + rb * 129 + rb;
+#pragma unroll 1
             for (int c = 0; c < PB; ++c) {
-                float v = L[r * 129 + rb + c];
-#pragma unroll
-                for (int q = 0; q < c; ++q) v -= x[q] * L[(rb + c) * 129 + rb + q];
-                x[c] = v / L[(rb + c) * 129 + rb + c];
+                float v = x[c];
+#pragma unroll 4
+                for (int q = 0; q < c; ++q) v -= x[q] * D[c * 129 + q];
+                x[c] = v / D[c * 129 + c];
             }
-#pragma unroll
-            for (int c = 0; c < PB; ++c) L[r * 129 + rb + c] = x[c];
         }
         __syncthreads();
-        // (3) trailing update of rows/cols >= rb + 32 (lower part), 2 x 2 per thread
+        // trailing update of rows/cols >= rb + 32 (lower part), 2 x 2 per thread
         const int n2 = KRR_TILE - rb - PB;
         if (n2 > 0) {
             const int nb2 = n2 / 2;
@@ -227,38 +234,32 @@ __global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restri
         const int rr = e >> 7, cc = e & 127;
         g[e] = (rr >= cc) ? L[rr * 129 + cc] : 0.f;
     }
-    // inverse: diagonal blocks by warps 0..3 (lane j owns column j of the block)
+    // diagonal blocks of the inverse: warp w inverts block w, lane j = column j
     if (warp < KRR_TILE / PB) {
         const int rb = warp * PB;
-        float zc[PB];
-#pragma unroll
+        const float *D = L + rb * 129 + rb;
+        float *Zb = Zs + rb * 129 + rb;
+#pragma unroll 1
         for (int i = 0; i < PB; ++i) {
             float v = (i == lane) ? 1.f : 0.f;
-#pragma unroll
-            for (int q = 0; q < i; ++q) v -= L[(rb + i) * 129 + rb + q] * zc[q];
-            zc[i] = (i >= lane) ? v / L[(rb + i) * 129 + rb + i] : 0.f;
+#pragma unroll 4
+            for (int q = lane; q < i; ++q) v -= D[i * 129 + q] * Zb[q * 129 + lane];
+            Zb[i * 129 + lane] = (i >= lane) ? v / D[i * 129 + i] : 0.f;
         }
-#pragma unroll
-        for (int i = 0; i < PB; ++i) Zs[(rb + i) * 129 + rb + lane] = zc[i];
-    }
-    // zero the strictly upper blocks of Z
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int rr = e >> 7, cc = e & 127;
-        if (cc / PB > rr / PB) Zs[rr * 129 + cc] = 0.f;
     }
     __syncthreads();
-    // off-diagonal blocks by distance d: Z_ij = -Z_ii sum_{q=j}^{i-1} L_iq Z_qj
-    float *T = reinterpret_cast<float *>(po_dyn) + 2 * KRR_TILE * 129;  // [3][32][33] scratch
+    // off-diagonal blocks of Z by distance d: Z_ij = -Z_ii sum_{q=j}^{i-1} L_iq Z_qj
+#pragma unroll 1
     for (int d = 1; d < KRR_TILE / PB; ++d) {
         const int nblk = KRR_TILE / PB - d;
-        // T_j = sum_q L_{j+d,q} Z_{q,j}
         for (int e = threadIdx.x; e < nblk * PB * PB; e += blockDim.x) {
             const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
             const int ib = jb + d;
             float v = 0.f;
             for (int qb = jb; qb < ib; ++qb)
 #pragma unroll 8
-                for (int q = 0; q < PB; ++q) v += L[(ib * PB + rr) * 129 + qb * PB + q] * Zs[(qb * PB + q) * 129 + jb * PB + cc];
+                for (int q = 0; q < PB; ++q)
+                    v = fmaf(L[(ib * PB + rr) * 129 + qb * PB + q], Zs[(qb * PB + q) * 129 + jb * PB + cc], v);
             T[(jb * PB + rr) * 33 + cc] = v;
         }
         __syncthreads();
@@ -266,8 +267,9 @@ __global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restri
             const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
             const int ib = jb + d;
             float v = 0.f;
-#pragma unroll 8
-            for (int q = 0; q < PB; ++q) v += Zs[(ib * PB + rr) * 129 + ib * PB + q] * T[(jb * PB + q) * 33 + cc];
+#pragma unroll 4
+            for (int q = 0; q <= rr; ++q)
+                v = fmaf(Zs[(ib * PB + rr) * 129 + ib * PB + q], T[(jb * PB + q) * 33 + cc], v);
             Zs[(ib * PB + rr) * 129 + jb * PB + cc] = -v;
         }
         __syncthreads();
@@ -609,7 +611,7 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                             const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     cudaFuncSetAttribute(potrf_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_sm);
-    const size_t po_blk_sm = (2 * (size_t)KRR_TILE * 129 + 3 * 32 * 33) * sizeof(float);
+    const size_t po_blk_sm = (2 * (size_t)KRR_TILE * 129 + 96 * 33) * sizeof(float);
     cudaFuncSetAttribute(potrf_tile_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_blk_sm);
     for (const CholLaunch &L : plan) {
         const unsigned grid = (unsigned)L.tasks;
