@@ -198,12 +198,18 @@ krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t 
  *   2^-46 of the scaled residual, whichever comes first.  0 always runs to the
  *   floor.  The plain FP64 path always runs to its floor 2^-50.  Errors:
  *   KRR_ERR_ARG (rel < 0 or rel > 1e-2).
+ * krr_ctx_set_escalation: with KRR_PREC_TF32, a solve whose Gershgorin
+ *   condition estimate times 2^-11 exceeds `kappa_u` (default 32) has its
+ *   trailing updates run in the FP32-class three-pass mode instead of one TF32
+ *   pass (a TF32 factor is then too poor a preconditioner); 0 escalates every
+ *   solve.  Errors: KRR_ERR_ARG (negative).
  * krr_launch_count: kernels launched by this process through libkrr. */
 krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
 krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
 krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);
 krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel);
+krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u);
 long long krr_launch_count(void);
 
 #ifdef __cplusplus

@@ -66,6 +66,7 @@ def load(build_if_missing: bool = True):
     L.krr_ctx_set_panel_width.argtypes = [P, ctypes.c_int]
     L.krr_ctx_get_panel_width.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.krr_ctx_set_target_error.argtypes = [P, ctypes.c_double]
+    L.krr_ctx_set_escalation.argtypes = [P, ctypes.c_double]
     L.krr_launch_count.restype = ctypes.c_longlong
     L.krr_partition.argtypes = [P, P, i64, i32, P, i64, ctypes.c_int, i32, i32, u64, P, P, P, P, P, P]
     L.krr_fit_batch.argtypes = [P, P, P, i64, i32, P, P, i32, P, i32, P, i32, ctypes.c_int,
@@ -75,7 +76,8 @@ def load(build_if_missing: bool = True):
     L.krr_model_stats.argtypes = [P, P, P, P, P]
     L.krr_model_free.argtypes = [P, P]
     for name in ("krr_ctx_create", "krr_ctx_destroy", "krr_ctx_set_profiling", "krr_ctx_profile",
-                 "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
+                 "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error",
+                 "krr_ctx_set_escalation", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
                  "krr_model_stats", "krr_model_free"):
         getattr(L, name).restype = st
     _lib = L
@@ -171,6 +173,10 @@ def krr_ctx_set_panel_width(ctx: Context, W: int):
 
 def krr_ctx_set_target_error(ctx: Context, rel: float):
     ctx.check(ctx.lib.krr_ctx_set_target_error(ctx.handle, float(rel)), "krr_ctx_set_target_error")
+
+
+def krr_ctx_set_escalation(ctx: Context, kappa_u: float):
+    ctx.check(ctx.lib.krr_ctx_set_escalation(ctx.handle, float(kappa_u)), "krr_ctx_set_escalation")
 
 
 def krr_partition(ctx: Context, X: torch.Tensor, Xt: torch.Tensor | None, mode: int, p: int, iters: int = 0,

@@ -34,8 +34,10 @@ struct CholLaunch {
     int K0, W;
     int64_t pre;
     int64_t tasks;
+    int tc;
 };
-void build_chol_plan(const std::vector<int> &, int, std::vector<CholLaunch> &, std::vector<int64_t> &);
+void build_chol_plan(const std::vector<int> &, const std::vector<int> &, int, std::vector<CholLaunch> &,
+                     std::vector<int64_t> &);
 cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
                           const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, int *,
                           Prof *);
@@ -54,6 +56,8 @@ struct PcgBuffers {
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
                     Prof *);
+cudaError_t run_pcg_norms(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *,
+                          const double *, bool, Prof *);
 void launch_predict(cudaStream_t, const Model &, const double *, int64_t, const int64_t *, const int64_t *, int64_t,
                     int, double *);
 void launch_select(cudaStream_t, const double *, const double *, int64_t, int, int, int, double *, int32_t *);
@@ -237,6 +241,12 @@ krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel) {
     return KRR_OK;
 }
 
+krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u) {
+    if (!ctx || !(kappa_u >= 0.0)) return KRR_ERR_ARG;
+    ctx->c.escalate = kappa_u;
+    return KRR_OK;
+}
+
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W) {
     if (!ctx || W < 0 || W > 64) return KRR_ERR_ARG;
     ctx->c.chol_W = W;
@@ -413,7 +423,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         PcgState *state = nullptr;
         unsigned int *nactive = nullptr;
         GroupDesc *d_groups = nullptr;
-        int64_t *d_gpre = nullptr, *d_plan = nullptr;
+        int64_t *d_gpre = nullptr;
         int32_t *flags = nullptr;
         FIT_TRY(W.get(&yg, (size_t)prow * 8));
         FIT_TRY(W.get(&Kst, (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb));
@@ -468,126 +478,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         }
         FIT_TRY(cudaGetLastError());
 
-        // Cholesky schedule
-        std::vector<int> Ts(nsolve);
-        for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
-        CUtensorMap tmap, tmapZ;
-        memset(&tmap, 0, sizeof(tmap));
-        memset(&tmapZ, 0, sizeof(tmapZ));
-        const int tc = fp64 ? 0 : (tf32 ? 1 : 3);  // tensor-core mode of the factor
-        if (tc && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles)))
-            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
-        // outer panel width: explicit, cached per (precision, max tiles), or tuned now by timing
-        // each candidate schedule on these matrices (restored from K_hi between trials)
-        int Wp = c->chol_W;
-        const std::pair<int, int> key((int)prec, maxT);
-        if (Wp <= 0 && c->tuned_W.count(key)) Wp = c->tuned_W[key];
-        if (Wp <= 0 && (fp64 || maxT < 4)) Wp = 1;
-        if (Wp <= 0) {
-            DevBuf TW(c);
-            SolveDesc *dummy = nullptr;
-            (void)dummy;
-            int64_t *d_rpre = nullptr, *d_tplan = nullptr;
-            std::vector<int64_t> rpre(nsolve + 1, 0);
-            for (int s = 0; s < nsolve; ++s) rpre[s + 1] = rpre[s] + tri(M.solves[s].T);
-            FIT_TRY(TW.get(&d_rpre, sizeof(int64_t) * (nsolve + 1)));
-            FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsolve + 1), cudaMemcpyHostToDevice, st));
-            cudaEvent_t e0, e1;
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            float best_ms = 1e30f;
-            int best_W = 1;
-            const int cands[4] = {1, 2, 4, 8};
-            for (int ci = 0; ci < 4; ++ci) {
-                const int Wc = cands[ci];
-                if (Wc > maxT) break;
-                std::vector<CholLaunch> tplan;
-                std::vector<int64_t> tpre;
-                build_chol_plan(Ts, Wc, tplan, tpre);
-                if (d_tplan) ctx_free(c, d_tplan, 0), TW.list.pop_back();
-                FIT_TRY(TW.get(&d_tplan, sizeof(int64_t) * std::max<size_t>(tpre.size(), 1)));
-                FIT_TRY(cudaMemcpyAsync(d_tplan, tpre.data(), sizeof(int64_t) * tpre.size(), cudaMemcpyHostToDevice,
-                                        st));
-                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
-                                                                                     (float *)Ast, 0.f);
-                cudaEventRecord(e0, st);
-                FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tc, &tmap,
-                                      &tmapZ, c->d_err, nullptr));
-                cudaEventRecord(e1, st);
-                FIT_TRY(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best_ms) {
-                    best_ms = ms;
-                    best_W = Wc;
-                }
-            }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            Wp = best_W;
-            c->tuned_W[key] = best_W;
-            KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
-                                                                                 (float *)Ast, 0.f);
-            FIT_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * nsolve, st));
-        }
-        std::vector<CholLaunch> plan;
-        std::vector<int64_t> pre;
-        build_chol_plan(Ts, Wp, plan, pre);
-        FIT_TRY(W.get(&d_plan, sizeof(int64_t) * std::max<size_t>(pre.size(), 1)));
-        if (!pre.empty())
-            FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
-        FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tc, &tmap, &tmapZ,
-                              c->d_err, prof));
-
-        // breakdown of the low-precision factor: refactor those solves with a diagonal shift
-        if (!fp64) {
-            for (int attempt = 0; attempt < 3; ++attempt) {
-                std::vector<int32_t> hf(nsolve);
-                FIT_TRY(cudaMemcpyAsync(hf.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
-                FIT_TRY(cudaStreamSynchronize(st));
-                std::vector<SolveDesc> sub;
-                for (int s = 0; s < nsolve; ++s)
-                    if (hf[s]) sub.push_back(M.solves[s]);
-                if (sub.empty()) break;
-                // the sub-batch reuses the solves' own tiles; status of the originals stays flagged
-                // until the retry succeeds
-                DevBuf R(c);
-                SolveDesc *d_sub = nullptr;
-                int64_t *d_rpre = nullptr, *d_rplan = nullptr;
-                int32_t *rflags = nullptr;
-                const int nsub = (int)sub.size();
-                std::vector<int64_t> rpre(nsub + 1, 0);
-                for (int i = 0; i < nsub; ++i) rpre[i + 1] = rpre[i] + tri(sub[i].T);
-                FIT_TRY(R.get(&d_sub, sizeof(SolveDesc) * nsub));
-                FIT_TRY(R.get(&d_rpre, sizeof(int64_t) * (nsub + 1)));
-                FIT_TRY(R.get(&rflags, sizeof(int32_t) * nsub));
-                FIT_TRY(cudaMemcpyAsync(d_sub, sub.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
-                FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice,
-                                        st));
-                FIT_TRY(cudaMemsetAsync(rflags, 0, sizeof(int32_t) * nsub, st));
-                const float shift = (float)(std::pow(10.0, attempt) * 1e-4 * 0.5 * (double)sub[0].m + 1e-6);
-                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsub], 256, 0, st>>>(d_sub, d_rpre, nsub, Kh, (float *)Ast, shift);
-                std::vector<int> rT(nsub);
-                for (int i = 0; i < nsub; ++i) rT[i] = sub[i].T;
-                std::vector<CholLaunch> rplan;
-                std::vector<int64_t> rp;
-                build_chol_plan(rT, Wp, rplan, rp);
-                FIT_TRY(R.get(&d_rplan, sizeof(int64_t) * std::max<size_t>(rp.size(), 1)));
-                FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
-                                        st));
-                FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, tc, &tmap, &tmapZ,
-                                      c->d_err, prof));
-                std::vector<int32_t> hr(nsub);
-                FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
-                FIT_TRY(cudaStreamSynchronize(st));
-                int k = 0;
-                for (int s = 0; s < nsolve; ++s)
-                    if (hf[s]) hf[s] = hr[k++];
-                FIT_TRY(cudaMemcpyAsync(flags, hf.data(), sizeof(int32_t) * nsolve, cudaMemcpyHostToDevice, st));
-            }
-        }
-
-        // refinement
+        // condition estimates before factorising: ||K + lambda m I||_inf per solve
+        // (the first refinement phase), read back to choose each solve's factor
         KRR_LAUNCHED(), fill_rhs_kernel<<<nsolve, 256, 0, st>>>(M.d_solves, M.d_parts, yg, yv);
         PcgBuffers B;
         B.x = M.alpha;
@@ -603,8 +495,153 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.d_gpre = d_gpre;
         B.ng = (int)groups.size();
         B.gtiles = gtiles;
-        // stop at the FP64-class floor, or earlier once kappa_est * residual meets the
-        // context's forward-error target (refined precisions only)
+        FIT_TRY(run_pcg_norms(st, M, B, Kh, Kl, K64, fp64, prof));
+        std::vector<PcgState> hs0(nsolve);
+        FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));
+        FIT_TRY(cudaStreamSynchronize(st));
+
+        // factor class per solve: FP64 path -> FP64; FP32 -> 3-pass; TF32 -> 1-pass
+        // unless kappa_est * 2^-11 exceeds the escalation threshold (then 3-pass)
+        CUtensorMap tmap, tmapZ;
+        memset(&tmap, 0, sizeof(tmap));
+        memset(&tmapZ, 0, sizeof(tmapZ));
+        if (!fp64 && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles)))
+            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
+        std::vector<int> cls(nsolve, fp64 ? 0 : (tf32 ? 1 : 3));  // update class per solve
+        M.st_class.assign(nsolve, 0);
+        if (tf32 && c->escalate > 0.0)
+            for (int s = 0; s < nsolve; ++s) {
+                const double lm = M.solves[s].lambda_m;
+                const double kap = lm > 0.0 ? hs0[s].anorm / lm : INFINITY;
+                if (kap * std::ldexp(1.0, -11) > c->escalate) cls[s] = 3;
+            }
+        for (int s = 0; s < nsolve; ++s) M.st_class[s] = cls[s];
+
+        // one joint schedule: shared diagonal factorisations and panel solves,
+        // one update launch per class; outer panel width W explicit, cached per
+        // (precision, largest tile count), or tuned now by timing each candidate
+        // on these matrices (restored from K_hi between trials)
+        std::vector<int> Ts(nsolve);
+        for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
+        const int tcmode = fp64 ? 0 : (tf32 ? 1 : 3);  // tensor-core mode of the factor (0: SIMT FP64)
+        int Wp = c->chol_W;
+        const std::pair<int, int> key((int)prec, maxT);
+        if (Wp <= 0 && c->tuned_W.count(key)) Wp = c->tuned_W[key];
+        if (Wp <= 0 && (fp64 || maxT < 4)) Wp = 1;
+        std::vector<int32_t> hflags(nsolve, 0);
+        {
+            DevBuf CB(c);
+            if (Wp <= 0) {
+                std::vector<int64_t> rpre(nsolve + 1, 0);
+                for (int s = 0; s < nsolve; ++s) rpre[s + 1] = rpre[s] + tri(M.solves[s].T);
+                int64_t *d_rpre = nullptr;
+                FIT_TRY(CB.get(&d_rpre, sizeof(int64_t) * (nsolve + 1)));
+                FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsolve + 1), cudaMemcpyHostToDevice,
+                                        st));
+                cudaEvent_t e0, e1;
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+                float best_ms = 1e30f;
+                int best_W = 1;
+                const int cands[4] = {1, 2, 4, 8};
+                for (int ci = 0; ci < 4; ++ci) {
+                    const int Wc = cands[ci];
+                    if (Wc > maxT) break;
+                    std::vector<CholLaunch> tplan;
+                    std::vector<int64_t> tpre;
+                    build_chol_plan(Ts, cls, Wc, tplan, tpre);
+                    int64_t *d_tplan = nullptr;
+                    FIT_TRY(CB.get(&d_tplan, sizeof(int64_t) * std::max<size_t>(tpre.size(), 1)));
+                    FIT_TRY(cudaMemcpyAsync(d_tplan, tpre.data(), sizeof(int64_t) * tpre.size(),
+                                            cudaMemcpyHostToDevice, st));
+                    KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve,
+                                                                                         Kh, (float *)Ast, 0.f);
+                    cudaEventRecord(e0, st);
+                    FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tcmode,
+                                          &tmap, &tmapZ, c->d_err, nullptr));
+                    cudaEventRecord(e1, st);
+                    FIT_TRY(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_W = Wc;
+                    }
+                }
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                Wp = best_W;
+                c->tuned_W[key] = best_W;
+                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsolve], 256, 0, st>>>(M.d_solves, d_rpre, nsolve, Kh,
+                                                                                     (float *)Ast, 0.f);
+                FIT_TRY(cudaMemsetAsync(flags, 0, sizeof(int32_t) * nsolve, st));
+            }
+            std::vector<CholLaunch> plan;
+            std::vector<int64_t> pre;
+            build_chol_plan(Ts, cls, Wp, plan, pre);
+            int64_t *d_plan = nullptr;
+            FIT_TRY(CB.get(&d_plan, sizeof(int64_t) * std::max<size_t>(pre.size(), 1)));
+            if (!pre.empty())
+                FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
+            FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tcmode, &tmap, &tmapZ,
+                                  c->d_err, prof));
+            FIT_TRY(cudaMemcpyAsync(hflags.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
+            FIT_TRY(cudaStreamSynchronize(st));
+        }
+
+        // breakdown of a low-precision factor: refactor those solves in the
+        // 3-pass mode with a growing diagonal shift (it only changes the preconditioner)
+        if (!fp64) {
+            for (int attempt = 0; attempt < 3; ++attempt) {
+                std::vector<int> failed;
+                for (int s = 0; s < nsolve; ++s)
+                    if (hflags[s]) failed.push_back(s);
+                if (failed.empty()) break;
+                DevBuf R(c);
+                const int nsub = (int)failed.size();
+                std::vector<SolveDesc> sub(nsub);
+                std::vector<int64_t> rpre(nsub + 1, 0);
+                for (int i = 0; i < nsub; ++i) {
+                    sub[i] = M.solves[failed[i]];
+                    rpre[i + 1] = rpre[i] + tri(sub[i].T);
+                }
+                SolveDesc *d_sub = nullptr;
+                int64_t *d_rpre = nullptr;
+                int32_t *rflags = nullptr;
+                FIT_TRY(R.get(&d_sub, sizeof(SolveDesc) * nsub));
+                FIT_TRY(R.get(&d_rpre, sizeof(int64_t) * (nsub + 1)));
+                FIT_TRY(R.get(&rflags, sizeof(int32_t) * nsub));
+                FIT_TRY(cudaMemcpyAsync(d_sub, sub.data(), sizeof(SolveDesc) * nsub, cudaMemcpyHostToDevice, st));
+                FIT_TRY(cudaMemcpyAsync(d_rpre, rpre.data(), sizeof(int64_t) * (nsub + 1), cudaMemcpyHostToDevice,
+                                        st));
+                FIT_TRY(cudaMemsetAsync(rflags, 0, sizeof(int32_t) * nsub, st));
+                const float shift = (float)(std::pow(10.0, attempt) * 1e-4 * 0.5 * (double)sub[0].m + 1e-6);
+                KRR_LAUNCHED(), reform_kernel<<<(unsigned)rpre[nsub], 256, 0, st>>>(d_sub, d_rpre, nsub, Kh,
+                                                                                   (float *)Ast, shift);
+                std::vector<int> rT(nsub);
+                for (int i = 0; i < nsub; ++i) rT[i] = sub[i].T;
+                std::vector<CholLaunch> rplan;
+                std::vector<int64_t> rp;
+                build_chol_plan(rT, std::vector<int>(nsub, 3), 1, rplan, rp);
+                int64_t *d_rplan = nullptr;
+                FIT_TRY(R.get(&d_rplan, sizeof(int64_t) * std::max<size_t>(rp.size(), 1)));
+                FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
+                                        st));
+                FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, 3, &tmap, &tmapZ,
+                                      c->d_err, prof));
+                std::vector<int32_t> hr(nsub);
+                FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
+                FIT_TRY(cudaStreamSynchronize(st));
+                for (int i = 0; i < nsub; ++i) {
+                    hflags[failed[i]] = hr[i];
+                    if (!hr[i]) M.st_class[failed[i]] = 3;
+                }
+            }
+        }
+        FIT_TRY(cudaMemcpyAsync(flags, hflags.data(), sizeof(int32_t) * nsolve, cudaMemcpyHostToDevice, st));
+
+        // refinement: stop at the FP64-class floor, or earlier once
+        // kappa_est * residual meets the context's forward-error target (refined precisions)
         const double tau = fp64 ? std::ldexp(1.0, -50) : std::ldexp(1.0, -46);
         const double target = fp64 ? 0.0 : c->target_err;
         FIT_TRY(run_pcg(st, M, B, Kh, Kl, K64, Ast, Zst, fp64, maxT, tau, target, 80, flags, c->h_flag, 2, prof));

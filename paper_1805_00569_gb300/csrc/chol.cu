@@ -22,6 +22,8 @@
 // TF32 and FP32 run on the tcgen05 tensor cores (tile_mma_kernel): TF32 as one
 // kind::tf32 pass, FP32 as three passes over a hi/lo split; the panel solve
 // L_ik = A_ik Z_kk^T always runs as three passes (an FP32-class product).
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -566,25 +568,35 @@ struct CholLaunch {
     int K0, W;     // step parameters (see decode_task)
     int64_t pre;   // offset of this launch's prefix array in the plan buffer
     int64_t tasks; // total CTAs
+    int tc;        // update arithmetic: 0 SIMT, 1 TF32 one pass, 3 three passes
 };
 
-// Build the schedule for a batch of solves with tile counts T[s].
-void build_chol_plan(const std::vector<int> &T, int W, std::vector<CholLaunch> &plan, std::vector<int64_t> &pre) {
+// Build the schedule for a batch of solves with tile counts T[s] and update
+// classes cls[s] (0 SIMT, 1 TF32, 3 three-pass): the diagonal factorisations
+// and panel solves of all solves share their launches; each update step is
+// one launch per class present.
+void build_chol_plan(const std::vector<int> &T, const std::vector<int> &cls, int W, std::vector<CholLaunch> &plan,
+                     std::vector<int64_t> &pre) {
     const int ns = (int)T.size();
     int Tmax = 0;
     for (int t : T) Tmax = std::max(Tmax, t);
+    std::vector<int> classes;
+    for (int s = 0; s < ns; ++s)
+        if (std::find(classes.begin(), classes.end(), cls[s]) == classes.end()) classes.push_back(cls[s]);
+    std::sort(classes.begin(), classes.end());
     plan.clear();
     pre.clear();
-    auto add = [&](int kind, int K0, int Wp, auto count) {
+    auto add = [&](int kind, int K0, int Wp, int tc, auto count) {
         CholLaunch L;
         L.kind = kind;
         L.K0 = K0;
         L.W = Wp;
+        L.tc = tc;
         L.pre = (int64_t)pre.size();
         int64_t run = 0;
         for (int s = 0; s < ns; ++s) {
             pre.push_back(run);
-            run += count(T[s]);
+            if (kind < 2 || cls[s] == tc) run += count(T[s]);
         }
         pre.push_back(run);
         L.tasks = run;
@@ -594,14 +606,16 @@ void build_chol_plan(const std::vector<int> &T, int W, std::vector<CholLaunch> &
         const int Wb = std::min(W, Tmax - K0);
         for (int c = K0; c < K0 + Wb; ++c) {
             if (c > K0)
-                add(3, K0, c, [&](int t) -> int64_t { return t > c ? (int64_t)(t - c) : 0; });
-            add(0, c, 0, [&](int t) -> int64_t { return t > c ? 1 : 0; });
-            add(1, c, 0, [&](int t) -> int64_t { return t > c + 1 ? (int64_t)(t - c - 1) : 0; });
+                for (int tc : classes)
+                    add(3, K0, c, tc, [&](int t) -> int64_t { return t > c ? (int64_t)(t - c) : 0; });
+            add(0, c, 0, 0, [&](int t) -> int64_t { return t > c ? 1 : 0; });
+            add(1, c, 0, 0, [&](int t) -> int64_t { return t > c + 1 ? (int64_t)(t - c - 1) : 0; });
         }
-        add(2, K0, Wb, [&](int t) -> int64_t {
-            int64_t r = (int64_t)t - K0 - Wb;
-            return r > 0 ? r * (r + 1) / 2 : 0;
-        });
+        for (int tc : classes)
+            add(2, K0, Wb, tc, [&](int t) -> int64_t {
+                int64_t r = (int64_t)t - K0 - Wb;
+                return r > 0 ? r * (r + 1) / 2 : 0;
+            });
     }
 }
 
@@ -630,9 +644,9 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
         const int W = L.kind == 1 ? 0 : L.W;
         if constexpr (sizeof(T) == 4) {
             // tensor cores: the panel solve always FP32-class (3 passes); the
-            // trailing updates 1 pass (TF32) or 3 passes (FP32)
+            // trailing updates 1 pass (TF32) or 3 passes (FP32), per launch class
             if (tc != 0) {
-                const bool x3 = (L.kind == 1) || tc == 3;
+                const bool x3 = (L.kind == 1) || L.tc == 3;
                 if (x3)
                     KRR_LAUNCHED(), tile_mma_kernel<true><<<grid, 192, TcCfg<true>::SMEM, st>>>(
                         *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, mode, L.K0, W, d_err);

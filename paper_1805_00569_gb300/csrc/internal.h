@@ -125,6 +125,7 @@ struct Ctx {
     Prof prof;
     int chol_W = 0;            // outer panel width (0 = tuned on first use)
     double target_err = 1e-7;  // refinement stops once kappa_est * backward error <= this
+    double escalate = 32.0;    // TF32: factor a solve in 3 passes when kappa_est * 2^-11 exceeds this
     std::map<std::pair<int, int>, int> tuned_W;  // (precision, max tiles) -> tuned panel width
 };
 
@@ -145,7 +146,7 @@ struct Model {
     int32_t *ozex = nullptr;   // per-row slice exponent [prows]
     int32_t dpz = 0;           // features padded to the slice K chunk
     CUtensorMap oz_tmB;        // TMA view of ozS for the training-row operand
-    std::vector<int32_t> st_iters, st_status;  // per-solve refinement statistics
+    std::vector<int32_t> st_iters, st_status, st_class;  // per-solve refinement statistics, factor class
     std::vector<double> st_kappa, st_resid;
     std::vector<std::pair<void *, size_t>> allocs;
 };

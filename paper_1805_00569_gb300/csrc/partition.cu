@@ -68,73 +68,84 @@ __global__ void random_offsets_kernel(int64_t n, int32_t p, int64_t *offsets, in
 // ------------------------------------------------------------ K-means assign
 constexpr int ASSIGN_THREADS = 128;
 
-// X [n x d] FP64; C64 [k x d] FP64; C32 [k x d] FP32 copy.  prev may be null.
+// One thread per point.  X32: FP32 copy of the rows (converted once per
+// K-means run: on GB300 the FP64 -> FP32 conversion runs on the slow FP64
+// pipe); C32 / C64: FP32 and FP64 centres.  The FP32 distance of every centre
+// carries the bound |d32 - d64| <= (d + 16) 2^-24 1.27 * 2 (||x||^2 + ||c||^2)
+// (rounding of the inputs, the differences, the squares and the sum; the
+// factor 2 bounds sum (|x|+|c|)^2).  Centres within the bound of the best
+// upper bound are candidates; with two or more, the FP64 distances in the
+// definition's order decide (strict <, lowest index).
 __global__ void __launch_bounds__(ASSIGN_THREADS)
-kmeans_assign_kernel(const double *__restrict__ X, int64_t n, int32_t d, const double *__restrict__ C64,
-                     const float *__restrict__ C32, int32_t k, const int32_t *__restrict__ prev,
-                     int32_t *__restrict__ out, unsigned long long *delta) {
-    extern __shared__ unsigned char smem_raw[];
-    float *sC = reinterpret_cast<float *>(smem_raw);                  // k*d
-    float *sCabs2 = sC + (size_t)k * d;                                 // unused padding guard
-    (void)sCabs2;
+kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X, int64_t n, int32_t d,
+                     const double *__restrict__ C64, const float *__restrict__ C32, int32_t k,
+                     const int32_t *__restrict__ prev, int32_t *__restrict__ out, unsigned long long *delta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *sC = reinterpret_cast<float *>(smem_raw);   // [k][d]
+    float *sCn = sC + (size_t)k * d;                     // [k] ||c||^2
+    float *sX = sCn + k;                                 // [d][ASSIGN_THREADS]
     for (int e = threadIdx.x; e < k * d; e += blockDim.x) sC[e] = C32[e];
-    __syncthreads();
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double *x = X + i * d;
-    // pass 1: FP32 distances and their error bounds
-    const float u = 5.9604644775390625e-8f;  // 2^-24
-    const float bscale = (float)(d + 16) * u * 1.25f;
-    float best_hi = INFINITY;
-    for (int j = 0; j < k; ++j) {
-        const float *c = sC + (size_t)j * d;
-        float acc = 0.f, mag = 0.f;
-        for (int f = 0; f < d; ++f) {
-            float xf = __double2float_rn(x[f]);
-            float df_ = xf - c[f];
-            acc = fmaf(df_, df_, acc);
-            float a = fabsf(xf) + fabsf(c[f]);
-            mag = fmaf(a, a, mag);
-        }
-        float hi = acc + bscale * mag * 1.01f;
-        best_hi = fminf(best_hi, hi);
+    const int64_t i0 = (int64_t)blockIdx.x * blockDim.x;
+    const int nrow = (int)((n - i0) < (int64_t)blockDim.x ? (n - i0) : (int64_t)blockDim.x);
+    for (int e = threadIdx.x; e < nrow * d; e += blockDim.x) {
+        const int r = e / d, f = e % d;
+        sX[f * ASSIGN_THREADS + r] = X32[(i0 + r) * d + f];
     }
-    // pass 2: candidates within the bound; FP64 recheck only if ambiguous
-    int ncand = 0, first = -1;
+    __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        float s = 0.f;
+        for (int f = 0; f < d; ++f) s = fmaf(sC[j * d + f], sC[j * d + f], s);
+        sCn[j] = s;
+    }
+    __syncthreads();
+    const int r = threadIdx.x;
+    if (r >= nrow) return;
+    const int64_t i = i0 + r;
+    float xn = 0.f;
+    for (int f = 0; f < d; ++f) xn = fmaf(sX[f * ASSIGN_THREADS + r], sX[f * ASSIGN_THREADS + r], xn);
+    const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
+    float best_hi = INFINITY;
+#pragma unroll 1
     for (int j = 0; j < k; ++j) {
-        const float *c = sC + (size_t)j * d;
-        float acc = 0.f, mag = 0.f;
+        const float *c = sC + j * d;
+        float acc = 0.f;
         for (int f = 0; f < d; ++f) {
-            float xf = __double2float_rn(x[f]);
-            float df_ = xf - c[f];
-            acc = fmaf(df_, df_, acc);
-            float a = fabsf(xf) + fabsf(c[f]);
-            mag = fmaf(a, a, mag);
+            const float t = sX[f * ASSIGN_THREADS + r] - c[f];
+            acc = fmaf(t, t, acc);
         }
-        float lo = acc - bscale * mag * 1.01f;
-        if (lo <= best_hi) {
+        best_hi = fminf(best_hi, acc + bscale * (xn + sCn[j]));
+    }
+    int ncand = 0, first = -1;
+#pragma unroll 1
+    for (int j = 0; j < k; ++j) {
+        const float *c = sC + j * d;
+        float acc = 0.f;
+        for (int f = 0; f < d; ++f) {
+            const float t = sX[f * ASSIGN_THREADS + r] - c[f];
+            acc = fmaf(t, t, acc);
+        }
+        if (acc - bscale * (xn + sCn[j]) <= best_hi) {
             if (ncand == 0) first = j;
             ++ncand;
         }
     }
     int arg = first;
     if (ncand > 1) {
+        const double *x = X + i * d;
         double best = INFINITY;
+#pragma unroll 1
         for (int j = 0; j < k; ++j) {
-            const float *c = sC + (size_t)j * d;
-            float acc = 0.f, mag = 0.f;
+            const float *c = sC + j * d;
+            float acc = 0.f;
             for (int f = 0; f < d; ++f) {
-                float xf = __double2float_rn(x[f]);
-                float df_ = xf - c[f];
-                acc = fmaf(df_, df_, acc);
-                float a = fabsf(xf) + fabsf(c[f]);
-                mag = fmaf(a, a, mag);
+                const float t = sX[f * ASSIGN_THREADS + r] - c[f];
+                acc = fmaf(t, t, acc);
             }
-            if (acc - bscale * mag * 1.01f > best_hi) continue;
+            if (acc - bscale * (xn + sCn[j]) > best_hi) continue;
             const double *c64 = C64 + (size_t)j * d;
             double s = 0.0;
             for (int f = 0; f < d; ++f) {
-                double t = __dsub_rn(x[f], c64[f]);
+                const double t = __dsub_rn(x[f], c64[f]);
                 s = __dadd_rn(s, __dmul_rn(t, t));
             }
             if (s < best) {
@@ -300,10 +311,10 @@ krr_status run_partition_random(Ctx *ctx, int64_t n, int32_t p, uint64_t seed, i
     return KRR_OK;
 }
 
-krr_status run_assign(Ctx *ctx, const double *X, int64_t n, int32_t d, const double *C64, const float *C32,
-                      int32_t k, const int32_t *prev, int32_t *out, unsigned long long *delta) {
+krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, int32_t d, const double *C64,
+                      const float *C32, int32_t k, const int32_t *prev, int32_t *out, unsigned long long *delta) {
     if (n == 0) return KRR_OK;
-    size_t sm = (size_t)k * d * sizeof(float) + 16;
+    size_t sm = ((size_t)k * d + k + (size_t)d * ASSIGN_THREADS) * sizeof(float) + 16;
     if (sm > 200 * 1024) {
         ctx->last_error = "kmeans: k*d too large for the shared-memory centre copy";
         return KRR_ERR_UNSUPPORTED;
@@ -311,8 +322,8 @@ krr_status run_assign(Ctx *ctx, const double *X, int64_t n, int32_t d, const dou
     if (sm > 48 * 1024)
         KRR_CUDA_TRY(ctx, cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)sm));
-    KRR_LAUNCHED(), kmeans_assign_kernel<<<grid_for(n, ASSIGN_THREADS), ASSIGN_THREADS, sm, ctx->stream>>>(X, n, d, C64, C32, k,
-                                                                                          prev, out, delta);
+    KRR_LAUNCHED(), kmeans_assign_kernel<<<grid_for(n, ASSIGN_THREADS), ASSIGN_THREADS, sm, ctx->stream>>>(
+        X32, X, n, d, C64, C32, k, prev, out, delta);
     KRR_CUDA_TRY(ctx, cudaGetLastError());
     return KRR_OK;
 }
@@ -346,6 +357,9 @@ krr_status run_partition_kmeans(Ctx *ctx, const double *X, int64_t n, int32_t d,
     long long *counts = nullptr;
     int32_t *prev = nullptr;
     unsigned long long *delta = nullptr;
+    float *X32 = nullptr, *Xt32 = nullptr;
+    size_t b_x32 = (size_t)std::max<int64_t>(n, 1) * d * sizeof(float);
+    size_t b_xt32 = (size_t)std::max<int64_t>(t, 1) * d * sizeof(float);
     size_t b_c32 = (size_t)k * d * sizeof(float);
     size_t b_part = (size_t)std::max<int64_t>(nblk, 1) * k * d * sizeof(double);
     size_t b_cnt = (size_t)std::max<int64_t>(nblk, 1) * k * sizeof(long long);
@@ -366,22 +380,26 @@ krr_status run_partition_kmeans(Ctx *ctx, const double *X, int64_t n, int32_t d,
     KM_ALLOC(counts, b_cnt);
     KM_ALLOC(prev, b_prev);
     KM_ALLOC(delta, b_delta);
+    KM_ALLOC(X32, b_x32);
+    if (route && t > 0) KM_ALLOC(Xt32, b_xt32);
     {
+        if (n > 0) KRR_LAUNCHED(), to_float_kernel<<<grid_for(n * d, 256), 256, 0, st>>>(X, X32, n * d);
+        if (Xt32) KRR_LAUNCHED(), to_float_kernel<<<grid_for(t * d, 256), 256, 0, st>>>(Xt, Xt32, t * d);
         cudaMemsetAsync(delta, 0, b_delta, st);
         KRR_LAUNCHED(), init_centres_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(X, d, init_idx, k, C);
         for (int it = 0; it < iters; ++it) {
             KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
-            rc = run_assign(ctx, X, n, d, C, C32, k, it == 0 ? nullptr : prev, assign, delta + it);
+            rc = run_assign(ctx, X32, X, n, d, C, C32, k, it == 0 ? nullptr : prev, assign, delta + it);
             if (rc != KRR_OK) goto done;
             rc = run_update(ctx, X, n, d, assign, k, C, partial, counts);
             if (rc != KRR_OK) goto done;
             cudaMemcpyAsync(prev, assign, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
         }
         KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
-        rc = run_assign(ctx, X, n, d, C, C32, k, nullptr, assign, nullptr);
+        rc = run_assign(ctx, X32, X, n, d, C, C32, k, nullptr, assign, nullptr);
         if (rc != KRR_OK) goto done;
         if (route && t > 0) {
-            rc = run_assign(ctx, Xt, t, d, C, C32, k, nullptr, route, nullptr);
+            rc = run_assign(ctx, Xt32, Xt, t, d, C, C32, k, nullptr, route, nullptr);
             if (rc != KRR_OK) goto done;
         }
         rc = run_gather(ctx, assign, n, k, perm, offsets);
@@ -394,6 +412,8 @@ krr_status run_partition_kmeans(Ctx *ctx, const double *X, int64_t n, int32_t d,
     }
 done:
 #undef KM_ALLOC
+    if (Xt32) ctx_free(ctx, Xt32, b_xt32);
+    if (X32) ctx_free(ctx, X32, b_x32);
     if (delta) ctx_free(ctx, delta, b_delta);
     if (prev) ctx_free(ctx, prev, b_prev);
     if (counts) ctx_free(ctx, counts, b_cnt);

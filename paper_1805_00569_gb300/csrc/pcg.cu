@@ -478,6 +478,15 @@ __global__ void pcg_start_kernel(const SolveDesc *__restrict__ solves, PcgState 
     if (threadIdx.x == 0) state[s].rz = acc;
 }
 
+// solves whose factorisation failed for good: NOT_SPD, skipped by the iterations
+__global__ void pcg_apply_flags_kernel(PcgState *__restrict__ state, const int32_t *__restrict__ flags, int n) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s < n && flags && flags[s] != 0) {
+        state[s].active = 0;
+        state[s].status = KRR_ERR_NOT_SPD;
+    }
+}
+
 // step 1: a = rz / p.q ; x += a p ; r -= a q ; stopping test
 __global__ void pcg_step1_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
                                  double *__restrict__ x, double *__restrict__ r, const double *__restrict__ p,
@@ -596,15 +605,24 @@ size_t precond_smem_bytes(bool fp64, int maxT) {
     return (fp64 ? 8 : 4) * ((size_t)maxT * KRR_TILE + 33 * KRR_TILE);
 }
 
-// Runs the whole refinement; returns the CUDA status of the last launch.
-cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
-                    const double *K64, const void *L, const void *Z, bool fp64, int maxT, double tau, double target,
-                    int maxit,
-                    const int32_t *flags, unsigned int *h_nactive, int check_every, Prof *prof) {
+// Phase 1 of the refinement, also used before the factorisation: x = 0 and
+// ||A||_inf = max(A 1) (A >= 0 entrywise), ||y||_inf, r = y per solve.
+cudaError_t run_pcg_norms(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
+                          const double *K64, bool fp64, Prof *prof) {
     const unsigned ns = (unsigned)M.solves.size();
-    KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, flags, B.x, B.p);
+    KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, nullptr, B.x, B.p);
     launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
     KRR_LAUNCHED(), pcg_norms_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.y, B.q, B.r);
+    return cudaGetLastError();
+}
+
+// Phase 2: the iterations (state from run_pcg_norms; solves whose factor
+// failed for good are marked NOT_SPD and skipped).
+cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
+                    const double *K64, const void *L, const void *Z, bool fp64, int maxT, double tau, double target,
+                    int maxit, const int32_t *flags, unsigned int *h_nactive, int check_every, Prof *prof) {
+    const unsigned ns = (unsigned)M.solves.size();
+    KRR_LAUNCHED(), pcg_apply_flags_kernel<<<(ns + 127) / 128, 128, 0, st>>>(B.state, flags, (int)ns);
     cudaError_t e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
     if (e != cudaSuccess) return e;
     KRR_LAUNCHED(), pcg_start_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);
