@@ -49,9 +49,13 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print per-kernel-class times to stderr")
-    ap.add_argument("--workload", default="bkrr2", choices=["bkrr2", "kkrr2", "sweep", "dkrr"],
+    ap.add_argument("--workload", default="bkrr2", choices=["bkrr2", "kkrr2", "sweep", "dkrr", "serve"],
                     help="bkrr2: the headline configuration; kkrr2: K-means partitions (uneven, routed); "
-                         "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows")
+                         "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows; serve: the request "
+                         "stream (Poisson 200/s, n log-uniform in [512, 16384]) through the serving loop")
+    ap.add_argument("--requests", type=int, default=1500, help="serve: requests replayed from the stream")
+    ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (one stream each)")
+    ap.add_argument("--fp64-sample", type=int, default=24, help="serve: requests in the sequential FP64 sample")
     ap.add_argument("--n", type=int, default=0, help="training rows (0 = the workload's; smaller: profiling cases)")
     ap.add_argument("--t", type=int, default=0, help="test rows (0 = the workload's)")
     ap.add_argument("--p", type=int, default=0, help="partitions (0 = the workload's)")
@@ -373,6 +377,91 @@ def roofline(res, steps, peaks):
     return out
 
 
+def run_serve(args, rank, world, local_rank):
+    """Serving stream: `--requests` fit+predict requests (a fraction are
+    repeat predicts of an earlier model) replayed through the serving loop,
+    once at their Poisson arrival times (latency at the offered load) and once
+    with every request queued at the start (capacity).  A step is one request;
+    every request's time includes its host->device copies and the read-back
+    of its predictions."""
+    import torch
+    from paper_1805_00569_gb300 import synth
+    from paper_1805_00569_gb300.serving import GpuExecutor, Scheduler, latency_summary, make_stream_requests
+
+    torch.cuda.set_device(local_rank)
+    data = lambda seed, n, d, t: synth.serve_request_data(seed, n, d, t)
+    st = synth.serve_stream(seed=4 + rank, requests=args.requests)
+    t = int(st["t"])
+    reqs = make_stream_requests(st, args.requests, data, t=t)
+    warm = make_stream_requests(synth.serve_stream(seed=1000 + rank, requests=max(args.warmup, 1) * 8),
+                                max(args.warmup, 1) * 8, data, t=t)
+    budget = 120 << 30
+
+    def replay(rq, slots, prec, realtime):
+        ex = GpuExecutor(slots, prec=prec, device=local_rank, resident_bytes=16 << 30)
+        try:
+            Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t).run(
+                warm[:2 * slots] if prec != "fp64" else warm[:1], realtime=False)
+            sc = Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t)
+            torch.cuda.synchronize()
+            res = sc.run(rq, realtime=realtime)
+            torch.cuda.synchronize()
+            return res, sc
+        finally:
+            ex.close()
+
+    import paper_1805_00569_gb300 as K
+    launches0 = K.load().krr_launch_count()
+    clocks = Clocks(local_rank)
+    clocks.start()
+    live, sc_live = replay(reqs, args.slots, args.prec, True)
+    cap, sc_cap = replay(reqs, args.slots, args.prec, False)
+    clk = clocks.stop()
+    launches = K.load().krr_launch_count() - launches0
+    span = max(r.done for r in cap) - min(r.start for r in cap)
+    ok = sum(r.status == K.KRR_OK for r in cap)
+    fits = sum(1 for r in cap if not r.resident_hit)
+    seq = None
+    if not args.no_fp64_path:
+        sample = reqs[:args.fp64_sample]
+        r64, _ = replay(sample, 1, "fp64", False)
+        span64 = max(r.done for r in r64) - min(r.start for r in r64)
+        seq = {"value": len(sample) / span64, "unit": "requests/s", "requests": len(sample),
+               "note": "plain FP64 path, one request at a time, first %d requests of the stream" % len(sample)}
+    by_id = {r.rid: r for r in reqs}  # a resident hit copies only its test rows
+    h2d = sum(by_id[r.rid].payload["Xt"].nbytes + (0 if r.resident_hit else by_id[r.rid].payload["X"].nbytes
+                                                   + by_id[r.rid].payload["y"].nbytes) for r in cap) / len(cap)
+    return dict(value=ok / span, span=span, ok=ok, fits=fits, live=latency_summary(live),
+                cap=latency_summary(cap), peak_conc=(sc_live.peak_concurrency, sc_cap.peak_concurrency),
+                peak_bytes=(sc_live.peak_in_use, sc_cap.peak_in_use), seq=seq, clocks=clk, launches=launches,
+                h2d=h2d, offered=float(len(reqs) / st["arrival"][len(reqs) - 1]))
+
+
+def main_serve(args, rank, world, local_rank):
+    res = run_serve(args, rank, world, local_rank)
+    if rank != 0:
+        return
+    print(json.dumps({
+        "metric": METRIC, "value": res["value"], "unit": "requests/s", "n_gpus": world, "steps": args.requests,
+        "warmup": args.warmup, "ms_per_step": 1e3 * res["span"] / args.requests, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64" if args.prec == "tf32" else args.prec,
+        "data": "synthetic",
+        "config": {"workload": "serve: %d requests, Poisson %.0f/s, n log-uniform [512, 16384], d in {8, 32, 90}, "
+                               "256 test rows each, repeat predicts 20%%" % (args.requests, res["offered"]),
+                   "slots": args.slots, "hbm_budget_gb": 120, "prec": args.prec,
+                   "l2": "inputs of concurrent requests exceed L2; no flush between requests"},
+        "serve": {"offered_rps": res["offered"], "at_offered_load": res["live"], "saturated": res["cap"],
+                  "peak_concurrency": res["peak_conc"], "peak_admitted_bytes": res["peak_bytes"],
+                  "fits": res["fits"]},
+        "fp64_sequential": res["seq"],
+        "roofline": None, "roofline_note": "concurrent streams: per-kernel durations overlap; see the bkrr2 line",
+        "cpu_baseline": None,
+        "e2e": {"value": res["value"], "unit": "requests/s", "h2d_bytes_per_step": res["h2d"],
+                "d2h_bytes_per_step": 256 * 8},
+        "clocks": res["clocks"], "gpu_launches": res["launches"],
+    }))
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -380,6 +469,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "serve":
+        return main_serve(args, rank, world, local_rank)
     if world > 1:
         import torch
         import torch.distributed as tdist

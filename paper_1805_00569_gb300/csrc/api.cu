@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <set>
 
 #include "common.cuh"
 #include "internal.h"
@@ -69,6 +71,29 @@ cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, floa
 cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
                               const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
                               int *);
+
+// ---- kernel attributes
+cudaError_t allow_max_dyn_smem_fn(const void *fn) {
+    static std::mutex mu;
+    static std::set<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (done.count({fn, dev})) return cudaSuccess;
+    }
+    int optin = 0;
+    cudaFuncAttributes fa;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess ||
+        (e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess ||
+        (e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  optin - (int)fa.sharedSizeBytes)) != cudaSuccess)
+        return e;
+    std::lock_guard<std::mutex> lk(mu);
+    done.insert({fn, dev});
+    return cudaSuccess;
+}
 
 // ---- budgeted stream-ordered allocation
 cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes) {

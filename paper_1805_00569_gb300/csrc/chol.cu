@@ -66,220 +66,170 @@ __device__ __forceinline__ TaskGeom decode_task(int mode, int64_t local, int K0,
 }
 
 // ---------------------------------------------------------------- potrf
-// 512 threads; row r handled by the 4 threads 4r .. 4r+3.
+// Cholesky factor L and inverse Z = L^-1 of one 128 x 128 diagonal tile in a
+// single right-looking sweep with the tile held in registers.  512 threads:
+// thread (rg = tid / 16, cg = tid % 16) owns the 4 x 8 block of rows
+// 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7, so a step reads 4 row and 8
+// column values of the broadcast vector for its 32 updates.  An entry (i, j)
+// holds A_ij until column j is eliminated and from then on the entry X_ij of
+// the inverse being formed, so every step is one broadcast and one rank-1
+// update of the same registers.  Step q:
+//   publish  b[i] = A_iq (i > q, unscaled column q), b[q] = A_qq + 1,
+//            b[j] = X~_qj (j < q, row q of the inverse before its scaling),
+//            and the pivot's rl = 1 / sqrt(A_qq);
+//   L(:, q) = b(:) rl (L_qq = A_qq rl);
+//   update   every row i > q: v_ij -= (b[i] rl^2) b[j]
+// For j > q this is A_ij -= L_iq L_jq; for j < q it is X_ij -= L_iq X_qj with
+// X_qj = X~_qj rl; for j = q the entry turns into X_iq = -L_iq / L_qq, which
+// the shifted b[q] produces from A_iq in the same fused multiply-add.  Row q
+// of the inverse is final once scaled by rl (X_qq = rl).  The step loop is
+// rolled (the kernel runs once per tile column, so a straight-line body would
+// be fetched from L2 on every SM); the 4 x 8 update is unrolled.
 template <typename T>
-__global__ void __launch_bounds__(512) potrf_tile_kernel(T *__restrict__ A, T *__restrict__ Z,
-                                                         const SolveDesc *__restrict__ solves,
-                                                         const int64_t *__restrict__ pre, int nsolve, int k,
-                                                         int32_t *__restrict__ flags) {
-    extern __shared__ __align__(16) unsigned char po_dyn[];
-    T *sm = reinterpret_cast<T *>(po_dyn);  // [128][129]
-    const int s = find_solve(pre, nsolve, blockIdx.x);
-    const SolveDesc S = solves[s];
-    const int64_t tile = S.ltile0 + (int64_t)k * (k + 1) / 2 + k;
-    T *g = A + tile * KRR_TILE_ELEMS;
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) sm[(e >> 7) * 129 + (e & 127)] = g[e];
-    __syncthreads();
-    const int r = threadIdx.x >> 2, part = threadIdx.x & 3;
-    bool bad = false;
-    for (int c = 0; c < KRR_TILE; ++c) {
-        T piv = sm[c * 129 + c];
-        if (!(piv > T(0))) {  // not positive: record and continue without NaNs
-            bad = true;
-            piv = T(1);
-            __syncthreads();
-            if (threadIdx.x == 0) sm[c * 129 + c] = T(1);
-            __syncthreads();
-        }
-        const T inv = T(1) / piv;
-        if (r > c) {
-            const T lrc = sm[r * 129 + c] * inv;
-            for (int q = c + 1 + part; q <= r; q += 4) sm[r * 129 + q] -= lrc * sm[q * 129 + c];
-        }
-        __syncthreads();
-    }
-    if (bad && threadIdx.x == 0) flags[s] = 1;
-    // L: column c scaled by 1/sqrt(pivot c)
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int rr = e >> 7, cc = e & 127;
-        T v;
-        if (rr > cc) v = sm[rr * 129 + cc] / sqrt(sm[cc * 129 + cc]);
-        else if (rr == cc) v = sqrt(sm[cc * 129 + cc]);
-        else v = T(0);
-        g[e] = v;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) sm[(e >> 7) * 129 + (e & 127)] = g[e];
-    __syncthreads();
-    // in-place inverse of the lower-triangular L, columns right to left:
-    // Z_jj = 1 / L_jj, Z_rj = -(sum_{q=j+1..r} Z_rq L_qj) Z_jj
-    for (int j = KRR_TILE - 1; j >= 0; --j) {
-        const T zjj = T(1) / sm[j * 129 + j];
-        T acc = T(0);
-        if (r > j)
-            for (int q = j + 1 + part; q <= r; q += 4) acc += sm[r * 129 + q] * sm[q * 129 + j];
-        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-        __syncthreads();
-        if (part == 0) {
-            if (r > j) sm[r * 129 + j] = -acc * zjj;
-            else if (r == j) sm[j * 129 + j] = zjj;
-        }
-        __syncthreads();
-    }
-    T *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int rr = e >> 7, cc = e & 127;
-        z[e] = (rr >= cc) ? sm[rr * 129 + cc] : T(0);
+__device__ __forceinline__ T potrf_rsqrt(T x);
+template <>
+__device__ __forceinline__ float potrf_rsqrt<float>(float x) {
+    const float r = rsqrtf(x);
+    return r * fmaf(-0.5f * x * r, r, 1.5f);  // one Newton step
+}
+template <>
+__device__ __forceinline__ double potrf_rsqrt<double>(double x) { return 1.0 / sqrt(x); }
+
+// padded broadcast index: 4 extra words per 32 columns, so the 8-lane phases
+// of a warp's 16-byte loads of 8-column groups hit distinct banks
+__device__ __forceinline__ int po_idx(int c) { return c + ((c >> 5) << 2); }
+
+template <typename T> struct PoVec;
+template <> struct PoVec<float> { using V = float4; static constexpr int N = 4; };
+template <> struct PoVec<double> { using V = double2; static constexpr int N = 2; };
+template <typename T, typename V>
+__device__ __forceinline__ void po_unpack(const V &w, T *dst) {
+    if constexpr (sizeof(V) / sizeof(T) == 4) {
+        dst[0] = w.x; dst[1] = w.y; dst[2] = w.z; dst[3] = w.w;
+    } else {
+        dst[0] = w.x; dst[1] = w.y;
     }
 }
 
-// Blocked FP32 version.  For each 32-column block b: warp 0 factors the
-// 32 x 32 diagonal block in shared memory (lane i owns row i), the rows below
-// solve against it in place (one thread per row), and the trailing part is
-// updated block-parallel.  At the end warps 0..3 invert the four diagonal
-// blocks in parallel (lane j owns column j) and the off-diagonal blocks of
-// the tile inverse follow by block products.  Every serial phase is a compact
-// rolled loop: the kernel runs once per tile and column, so straight-line
-// unrolled code would be fetched from L2 on every SM.
-constexpr int PB = 32;
-
-__global__ void __launch_bounds__(256) potrf_tile_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
-                                                                 const SolveDesc *__restrict__ solves,
-                                                                 const int64_t *__restrict__ pre, int nsolve, int k,
-                                                                 int32_t *__restrict__ flags) {
+template <typename T>
+__global__ void __launch_bounds__(512, 1) potrf_tile_kernel(T *__restrict__ A, T *__restrict__ Z,
+                                                            const SolveDesc *__restrict__ solves,
+                                                            const int64_t *__restrict__ pre, int nsolve, int k,
+                                                            int32_t *__restrict__ flags) {
+    using V = typename PoVec<T>::V;
+    constexpr int VN = PoVec<T>::N;
     extern __shared__ __align__(16) unsigned char po_dyn[];
-    float *L = reinterpret_cast<float *>(po_dyn);  // [128][129]
-    float *Zs = L + KRR_TILE * 129;                // [128][129]
-    float *T = Zs + KRR_TILE * 129;                // [96][33] scratch
+    T *Ls = reinterpret_cast<T *>(po_dyn);  // [128][129] the factor, column by column
+    __shared__ __align__(16) T bsh[2][KRR_TILE + 16];
+    __shared__ T psh[2][2];  // (pivot, 1 / sqrt(pivot))
     __shared__ int bad_sh;
     const int s = find_solve(pre, nsolve, blockIdx.x);
     const SolveDesc S = solves[s];
     const int64_t tile = S.ltile0 + (int64_t)k * (k + 1) / 2 + k;
-    float *g = A + tile * KRR_TILE_ELEMS;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T *g = A + tile * KRR_TILE_ELEMS;
+    const int rg = threadIdx.x >> 4, cg = threadIdx.x & 15;
+    const int r0 = rg * 4, c0 = cg * 8;
+    T v[4][8];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const V *src = reinterpret_cast<const V *>(g + (r0 + r) * KRR_TILE + c0);
+#pragma unroll
+        for (int m = 0; m < 8 / VN; ++m) po_unpack<T>(src[m], &v[r][VN * m]);
+    }
     if (threadIdx.x == 0) bad_sh = 0;
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int rr = e >> 7, cc = e & 127;
-        L[rr * 129 + cc] = g[e];
-        if (cc / PB > rr / PB) Zs[rr * 129 + cc] = 0.f;  // strictly upper blocks of Z
+#pragma unroll 1
+    for (int q = 0; q < KRR_TILE; ++q) {
+        T *b = bsh[q & 1];
+        if (cg == (q >> 3) && r0 + 3 >= q) {  // column q of A, rows >= q
+            T col[4];
+            switch (q & 7) {
+#define KRR_COL(c) \
+    case c: col[0] = v[0][c]; col[1] = v[1][c]; col[2] = v[2][c]; col[3] = v[3][c]; break;
+                KRR_COL(0) KRR_COL(1) KRR_COL(2) KRR_COL(3) KRR_COL(4) KRR_COL(5) KRR_COL(6) KRR_COL(7)
+#undef KRR_COL
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                if (r0 + r == q) {
+                    T pv = col[r];
+                    if (!(pv > T(0))) {  // not positive: record, continue with 1 (no NaNs)
+                        bad_sh = 1;
+                        pv = T(1);
+                    }
+                    psh[q & 1][0] = pv;
+                    psh[q & 1][1] = potrf_rsqrt<T>(pv);
+                    b[po_idx(q)] = pv + T(1);
+                } else if (r0 + r > q) {
+                    b[po_idx(r0 + r)] = col[r];
+                }
+            }
+        }
+        if (rg == (q >> 2)) {  // row q of the inverse, before scaling
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                if (r0 + r == q) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (c0 + c < q) b[po_idx(c0 + c)] = v[r][c];
+                }
+        }
+        __syncthreads();
+        const T rl = psh[q & 1][1];
+        if (threadIdx.x < KRR_TILE && (int)threadIdx.x >= q)
+            Ls[threadIdx.x * 129 + q] =
+                ((int)threadIdx.x == q) ? psh[q & 1][0] * rl : b[po_idx(threadIdx.x)] * rl;
+        if (r0 + 3 >= q) {
+            const T inv = rl * rl;
+            T rb[4], cb[8];
+            const T *br = b + po_idx(r0), *bc = b + po_idx(c0);  // contiguous: no 32-column crossing
+            po_unpack<T>(*reinterpret_cast<const V *>(br), rb);
+            if constexpr (VN == 2) po_unpack<T>(*reinterpret_cast<const V *>(br + 2), rb + 2);
+#pragma unroll
+            for (int m = 0; m < 8 / VN; ++m) po_unpack<T>(*reinterpret_cast<const V *>(bc + VN * m), cb + VN * m);
+            // rows <= q take a zero multiplier (x + 0 b = x exactly): no divergence
+            T ci[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) ci[r] = (r0 + r > q) ? -rb[r] * inv : T(0);
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 8; ++c) v[r][c] = fma(ci[r], cb[c], v[r][c]);
+            if (rg == (q >> 2)) {  // row q of the inverse: scale by rl
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    if (r0 + r == q) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            if (c0 + c < q) v[r][c] *= rl;
+                            else if (c0 + c == q) v[r][c] = rl;
+                        }
+                    }
+            }
+        }
     }
     __syncthreads();
-#pragma unroll 1
-    for (int b = 0; b < KRR_TILE / PB; ++b) {
-        const int rb = b * PB;
-        if (warp == 0) {  // diagonal block, right-looking, lane = row
-            float *D = L + rb * 129 + rb;
-#pragma unroll 1
-            for (int c = 0; c < PB; ++c) {
-                float dg = D[c * 129 + c];
-                if (!(dg > 0.f)) {
-                    dg = 1.f;
-                    if (lane == 0) bad_sh = 1;
-                }
-                const float dc = sqrtf(dg);
-                __syncwarp();
-                if (lane > c) D[lane * 129 + c] /= dc;
-                __syncwarp();
-                if (lane == c) D[c * 129 + c] = dc;
-                if (lane > c) {
-                    const float lc = D[lane * 129 + c];
-#pragma unroll 1
-                    for (int j = c + 1; j <= lane; ++j) D[lane * 129 + j] -= lc * D[j * 129 + c];
-                }
-                __syncwarp();
-            }
-        }
-        __syncthreads();
-        // rows below: x L_bb^T = a, solved in place, one thread per row
-        const int r = rb + PB + threadIdx.x;
-        if (r < KRR_TILE) {
-            float *x = L + r * 129 + rb;
-            const float *D = L + rb * 129 + rb;
-#pragma unroll 1
-            for (int c = 0; c < PB; ++c) {
-                float v = x[c];
-#pragma unroll 4
-                for (int q = 0; q < c; ++q) v -= x[q] * D[c * 129 + q];
-                x[c] = v / D[c * 129 + c];
-            }
-        }
-        __syncthreads();
-        // trailing update of rows/cols >= rb + 32 (lower part), 2 x 2 per thread
-        const int n2 = KRR_TILE - rb - PB;
-        if (n2 > 0) {
-            const int nb2 = n2 / 2;
-            for (int e = threadIdx.x; e < nb2 * nb2; e += blockDim.x) {
-                const int bi = e / nb2, bj = e % nb2;
-                if (bj > bi) continue;
-                const int r0 = rb + PB + 2 * bi, q0 = rb + PB + 2 * bj;
-                float s00 = 0.f, s01 = 0.f, s10 = 0.f, s11 = 0.f;
-#pragma unroll 8
-                for (int kk = 0; kk < PB; ++kk) {
-                    const float a0 = L[r0 * 129 + rb + kk], a1 = L[(r0 + 1) * 129 + rb + kk];
-                    const float b0 = L[q0 * 129 + rb + kk], b1 = L[(q0 + 1) * 129 + rb + kk];
-                    s00 = fmaf(a0, b0, s00);
-                    s01 = fmaf(a0, b1, s01);
-                    s10 = fmaf(a1, b0, s10);
-                    s11 = fmaf(a1, b1, s11);
-                }
-                L[r0 * 129 + q0] -= s00;
-                L[(r0 + 1) * 129 + q0] -= s10;
-                L[(r0 + 1) * 129 + q0 + 1] -= s11;
-                if (bi != bj) L[r0 * 129 + q0 + 1] -= s01;
-            }
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0 && bad_sh) flags[s] = 1;
     for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
         const int rr = e >> 7, cc = e & 127;
-        g[e] = (rr >= cc) ? L[rr * 129 + cc] : 0.f;
+        g[e] = (rr >= cc) ? Ls[rr * 129 + cc] : T(0);
     }
-    // diagonal blocks of the inverse: warp w inverts block w, lane j = column j
-    if (warp < KRR_TILE / PB) {
-        const int rb = warp * PB;
-        const float *D = L + rb * 129 + rb;
-        float *Zb = Zs + rb * 129 + rb;
-#pragma unroll 1
-        for (int i = 0; i < PB; ++i) {
-            float v = (i == lane) ? 1.f : 0.f;
-#pragma unroll 4
-            for (int q = lane; q < i; ++q) v -= D[i * 129 + q] * Zb[q * 129 + lane];
-            Zb[i * 129 + lane] = (i >= lane) ? v / D[i * 129 + i] : 0.f;
+    T *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        T w[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) w[c] = (c0 + c <= r0 + r) ? v[r][c] : T(0);
+        V *dst = reinterpret_cast<V *>(z + (r0 + r) * KRR_TILE + c0);
+#pragma unroll
+        for (int m = 0; m < 8 / VN; ++m) {
+            V o;
+            if constexpr (VN == 4) {
+                o.x = w[4 * m]; o.y = w[4 * m + 1]; o.z = w[4 * m + 2]; o.w = w[4 * m + 3];
+            } else {
+                o.x = w[2 * m]; o.y = w[2 * m + 1];
+            }
+            dst[m] = o;
         }
-    }
-    __syncthreads();
-    // off-diagonal blocks of Z by distance d: Z_ij = -Z_ii sum_{q=j}^{i-1} L_iq Z_qj
-#pragma unroll 1
-    for (int d = 1; d < KRR_TILE / PB; ++d) {
-        const int nblk = KRR_TILE / PB - d;
-        for (int e = threadIdx.x; e < nblk * PB * PB; e += blockDim.x) {
-            const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
-            const int ib = jb + d;
-            float v = 0.f;
-            for (int qb = jb; qb < ib; ++qb)
-#pragma unroll 8
-                for (int q = 0; q < PB; ++q)
-                    v = fmaf(L[(ib * PB + rr) * 129 + qb * PB + q], Zs[(qb * PB + q) * 129 + jb * PB + cc], v);
-            T[(jb * PB + rr) * 33 + cc] = v;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < nblk * PB * PB; e += blockDim.x) {
-            const int jb = e / (PB * PB), rr = (e / PB) % PB, cc = e % PB;
-            const int ib = jb + d;
-            float v = 0.f;
-#pragma unroll 4
-            for (int q = 0; q <= rr; ++q)
-                v = fmaf(Zs[(ib * PB + rr) * 129 + ib * PB + q], T[(jb * PB + q) * 33 + cc], v);
-            Zs[(ib * PB + rr) * 129 + jb * PB + cc] = -v;
-        }
-        __syncthreads();
-    }
-    float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
-    for (int e = threadIdx.x; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int rr = e >> 7, cc = e & 127;
-        z[e] = (rr >= cc) ? Zs[rr * 129 + cc] : 0.f;
     }
 }
 
@@ -535,15 +485,15 @@ typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32
                                     CUtensorMapFloatOOBfill);
 
 static PFN_encodeTiled get_encode() {
-    static PFN_encodeTiled fn = nullptr;
-    if (!fn) {
+    static const PFN_encodeTiled fn = []() -> PFN_encodeTiled {  // thread-safe one-time lookup
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_encodeTiled)p;
-    }
+            return (PFN_encodeTiled)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -624,20 +574,13 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                             const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc, const CUtensorMap *tmap,
                             const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
-    cudaFuncSetAttribute(potrf_tile_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_sm);
-    const size_t po_blk_sm = (2 * (size_t)KRR_TILE * 129 + 96 * 33) * sizeof(float);
-    cudaFuncSetAttribute(potrf_tile_blocked_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)po_blk_sm);
+    allow_max_dyn_smem(potrf_tile_kernel<T>);
     for (const CholLaunch &L : plan) {
         const unsigned grid = (unsigned)L.tasks;
         const int64_t *p = d_pre + L.pre;
         ProfScope ps(prof, L.kind == 0 ? PROF_POTRF : (L.kind == 1 ? PROF_TRSM : PROF_UPDATE), st);
         if (L.kind == 0) {
-            if constexpr (sizeof(T) == 4)
-                KRR_LAUNCHED(), potrf_tile_blocked_kernel<<<grid, 256, po_blk_sm, st>>>(
-                    reinterpret_cast<float *>(A), reinterpret_cast<float *>(Z), d_solves, p, nsolve, L.K0, flags);
-            else
-                KRR_LAUNCHED(), potrf_tile_kernel<T><<<grid, 512, po_sm, st>>>(A, Z, d_solves, p, nsolve, L.K0,
-                                                                               flags);
+            KRR_LAUNCHED(), potrf_tile_kernel<T><<<grid, 512, po_sm, st>>>(A, Z, d_solves, p, nsolve, L.K0, flags);
             continue;
         }
         const int mode = L.kind == 1 ? UPD_TRSM : (L.kind == 2 ? UPD_TRAIL : UPD_COLUMN);
@@ -665,14 +608,9 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
 cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, void *A, void *Z,
                           bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
                           const CUtensorMap *tmap, const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tile_mma_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TcCfg<false>::SMEM);
-        cudaFuncSetAttribute(tile_mma_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)TcCfg<true>::SMEM);
-        attr = true;
-    }
+    // set on every call: the attribute is per device
+    allow_max_dyn_smem(tile_mma_kernel<false>);
+    allow_max_dyn_smem(tile_mma_kernel<true>);
     if (fp64)
         return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, d_solves, nsolve, flags, 0, tmap,
                                        tmapZ, d_err, prof);

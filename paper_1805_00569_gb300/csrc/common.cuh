@@ -118,6 +118,33 @@ __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab
     return df_scale2(df_scale2(y, s1), s2);
 }
 
+// Exponent range of a prediction row.  The double-float exponential has the
+// FP32 range (results below e^-87 are 0), while an Eq. 7 sum can be a
+// meaningful number far below that (a test row far from every training row
+// at a small sigma).  A row whose largest exponent argument so far, x_max =
+// D_min * c (c = -1/(2 sigma^2)), is below -64 takes its terms as
+// exp(x - K ln2) = exp(x) 2^-K with the integer
+//   K = ceil((x_max + 1/64) / ln2) <= 0,
+// so every shifted argument is <= -1/64 and the largest term is >= 1/2; the
+// accumulated sum is scaled back by 2^K in FP64.  Rows with x_max >= -64
+// keep K = 0 and the unshifted arithmetic.  K is clamped at KRR_SHIFT_NONE
+// (2^-1100 is 0 in FP64, as is every term the clamp affects); KRR_SHIFT_NONE
+// also marks a row that has seen no term yet.
+#define KRR_SHIFT_NONE (-1100)
+__device__ __forceinline__ int exp_row_shift(float xmax) {
+    if (!(xmax < -64.f)) return 0;
+    const float k = ceilf((xmax + 0.015625f) * 1.44269504088896341f);  // 1 / ln 2
+    return k < (float)KRR_SHIFT_NONE ? KRR_SHIFT_NONE : (int)k;
+}
+// -K ln2 as a double-float, to be added to a shifted row's exponent arguments
+__device__ __forceinline__ float2 exp_shift_arg(int k) {
+    const double v = -(double)k * 0.69314718055994530942;
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+// 2^e for e <= 0 as a float, 0 below the normal range (exact scaling otherwise)
+__device__ __forceinline__ float pow2_nonpos(int e) { return e >= -126 ? __int_as_float((127 + e) << 23) : 0.f; }
+
 // ----------------------------------------------------------------- Philox4x32-10
 struct u32x4 { uint32_t x, y, z, w; };
 __device__ __forceinline__ u32x4 philox4x32_10(u32x4 c, uint32_t k0, uint32_t k1) {

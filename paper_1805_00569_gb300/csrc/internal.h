@@ -14,6 +14,16 @@ namespace krr {
 
 // Kernels launched through the library (process-wide, for launch accounting).
 extern std::atomic<long long> g_launch_count;
+
+// Lets a kernel launch with as much dynamic shared memory as the device's
+// opt-in limit leaves beside its static shared memory.  The value never varies,
+// so host threads launching the same kernel at once (one context each) can
+// never lower the limit under another's launch.  Set once per (kernel, device).
+cudaError_t allow_max_dyn_smem_fn(const void *fn);
+template <typename F>
+inline cudaError_t allow_max_dyn_smem(F *fn) {
+    return allow_max_dyn_smem_fn(reinterpret_cast<const void *>(fn));
+}
 #define KRR_LAUNCHED() (::krr::g_launch_count.fetch_add(1, std::memory_order_relaxed))
 
 constexpr int TILE = 128;

@@ -292,7 +292,7 @@ void launch_kbuild_df(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, 
     KParams kp;
     make_kparams(M, ktot, kp);
     const size_t sm = (size_t)KRR_TILE * (KRR_TILE + 1) * sizeof(float2);
-    cudaFuncSetAttribute(kbuild_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_max_dyn_smem(kbuild_df_kernel);
     KRR_LAUNCHED(), kbuild_df_kernel<<<(unsigned)ktot, KB_THREADS, sm, st>>>(M.Xh, M.Xl, M.nrm, M.dp, M.d_parts, M.p, M.d_solves, kp,
                                                             Kh, Kl, A);
 }
@@ -302,7 +302,7 @@ void launch_kbuild_fp64(cudaStream_t st, const Model &M, int64_t ktot, double *K
     KParams kp;
     make_kparams(M, ktot, kp);
     const size_t sm = (size_t)KRR_TILE * (KRR_TILE + 1) * sizeof(double);
-    cudaFuncSetAttribute(kbuild_fp64_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    allow_max_dyn_smem(kbuild_fp64_kernel);
     KRR_LAUNCHED(), kbuild_fp64_kernel<<<(unsigned)ktot, KB_THREADS, sm, st>>>(M.X64, M.d, M.d_parts, M.p, M.d_solves, kp, K64, A);
 }
 

@@ -320,8 +320,7 @@ krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, in
         return KRR_ERR_UNSUPPORTED;
     }
     if (sm > 48 * 1024)
-        KRR_CUDA_TRY(ctx, cudaFuncSetAttribute(kmeans_assign_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)sm));
+        KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_assign_kernel));
     KRR_LAUNCHED(), kmeans_assign_kernel<<<grid_for(n, ASSIGN_THREADS), ASSIGN_THREADS, sm, ctx->stream>>>(
         X32, X, n, d, C64, C32, k, prev, out, delta);
     KRR_CUDA_TRY(ctx, cudaGetLastError());
@@ -338,8 +337,7 @@ krr_status run_update(Ctx *ctx, const double *X, int64_t n, int32_t d, const int
         return KRR_ERR_UNSUPPORTED;
     }
     if (sm > 48 * 1024)
-        KRR_CUDA_TRY(ctx, cudaFuncSetAttribute(kmeans_block_sums_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_block_sums_kernel));
     KRR_LAUNCHED(), kmeans_block_sums_kernel<<<(unsigned)nblk, 128, sm, ctx->stream>>>(X, n, d, c, k, partial, counts);
     KRR_LAUNCHED(), kmeans_tree_divide_kernel<<<grid_for((int64_t)k * d, 128), 128, 0, ctx->stream>>>(partial, counts, nblk, k, d,
                                                                                      C);

@@ -590,11 +590,11 @@ static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuff
     const size_t esz = fp64 ? 8 : 4;
     const size_t sm = esz * ((size_t)maxT * KRR_TILE + 33 * KRR_TILE);
     if (fp64) {
-        cudaFuncSetAttribute(precond_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_max_dyn_smem(precond_kernel<double>);
         KRR_LAUNCHED(), precond_kernel<double><<<(unsigned)M.solves.size(), 512, sm, st>>>(
             (const double *)L, (const double *)Z, M.d_solves, B.state, B.r, B.z);
     } else {
-        cudaFuncSetAttribute(precond_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        allow_max_dyn_smem(precond_kernel<float>);
         KRR_LAUNCHED(), precond_kernel<float><<<(unsigned)M.solves.size(), 512, sm, st>>>((const float *)L, (const float *)Z,
                                                                            M.d_solves, B.state, B.r, B.z);
     }

@@ -51,6 +51,8 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
     int64_t *sRow = reinterpret_cast<int64_t *>(sTn + PT);           // [PT] test row ids
     float2 *sY = reinterpret_cast<float2 *>(sRow + PT);               // [PG][256] df accumulators
     float2 *sExp = sY + PG * 256;                                     // [256] 2^(j/256) table
+    float2 *sS = sExp + 256;                                          // [PG][256] -K ln2 per sigma (df)
+    int *sK = reinterpret_cast<int *>(sS + PG * 256);                 // [PG][256] range shift per sigma
     exp_table_init(sExp);
 
     const int j = blockIdx.x;
@@ -61,6 +63,11 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
     const int G = pp.nsig * pp.nlam;  // models of this pass
     const int nq = (int)((cnt - q0) < PT ? (cnt - q0) : PT);
     for (int g = 0; g < G; ++g) sY[g * 256 + threadIdx.x] = make_float2(0.f, 0.f);
+    for (int is = 0; is < pp.nsig; ++is) {
+        sK[is * 256 + threadIdx.x] = KRR_SHIFT_NONE;  // no term yet: the shift argument stays 0
+        sS[is * 256 + threadIdx.x] = make_float2(0.f, 0.f);
+    }
+    float dmin = INFINITY;  // smallest distance of this thread's test row to a real training row
     if (threadIdx.x < PT) {
         int64_t pos = (toff ? toff[j] : 0) + q0 + threadIdx.x;
         sRow[threadIdx.x] = (threadIdx.x < nq) ? (tidx ? tidx[pos] : pos) : -1;
@@ -148,6 +155,31 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
             sAl[g * KRR_TILE + r] = make_float2(h, __double2float_rn(av - (double)h));
         }
         __syncthreads();
+        // range shift (exp_row_shift): the chunk's smallest distance of the test
+        // row, the same in its 4 threads; a closer row rescales by 2^(K_old - K_new)
+        float dm = INFINITY;
+        for (int rr = 0; rr < 32; ++rr) {
+            const int r = part * 32 + rr;
+            if ((int64_t)ch * KRR_TILE + r >= P.m) break;
+            dm = fminf(dm, sD[r * PT + qc].x);
+        }
+        dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, 1));
+        dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, 2));
+        if (dm < dmin) {
+            dmin = dm;
+            for (int is = 0; is < pp.nsig; ++is) {
+                const int ko = sK[is * 256 + threadIdx.x], kn = exp_row_shift(dmin * pp.c_hi[is]);
+                if (kn != ko) {
+                    const float f = pow2_nonpos(ko - kn);
+                    for (int il = 0; il < pp.nlam; ++il) {
+                        float2 &y = sY[(is * pp.nlam + il) * 256 + threadIdx.x];
+                        y = make_float2(y.x * f, y.y * f);
+                    }
+                    sK[is * 256 + threadIdx.x] = kn;
+                    sS[is * 256 + threadIdx.x] = exp_shift_arg(kn);
+                }
+            }
+        }
         // exp + contraction: thread (qc, part) takes rows part*32 .. part*32+31
 #pragma unroll 1
         for (int rr = 0; rr < 32; ++rr) {
@@ -157,7 +189,12 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
             const df D = df_make(dv.x, dv.y);
 #pragma unroll 1
             for (int is = 0; is < pp.nsig; ++is) {
-                const df k = df_exp_nonpos(df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is])), sExp);
+                df x = df_mul(D, df_make(pp.c_hi[is], pp.c_lo[is]));
+                if (sK[is * 256 + threadIdx.x] != 0) {
+                    const float2 sv = sS[is * 256 + threadIdx.x];
+                    x = df_add(x, df_make(sv.x, sv.y));
+                }
+                const df k = df_exp_nonpos(x, sExp);
 #pragma unroll 1
                 for (int il = 0; il < pp.nlam; ++il) {
                     const int g = is * pp.nlam + il;
@@ -192,7 +229,8 @@ predict_df_kernel(const float *__restrict__ Xh, const float *__restrict__ Xl, co
             const int64_t row = sRow[qc];
             const int gm = pp.sig0 * pp.nlam + g;
             const int64_t orow = routed ? (int64_t)gm : (int64_t)j * pp.Gtot + gm;
-            out[orow * t + row] = df_to_double(v);
+            const int k = sK[(g / pp.nlam) * 256 + threadIdx.x];  // the same in the row's 4 threads
+            out[orow * t + row] = k == 0 ? df_to_double(v) : ldexp(df_to_double(v), k);
         }
     }
 }
@@ -305,7 +343,7 @@ __global__ void argmin_kernel(const double *__restrict__ v, int n, int32_t *__re
 static size_t predict_df_smem() {
     return (size_t)KRR_TILE * PT * sizeof(float2) + PG * KRR_TILE * sizeof(float2) + 2 * PKC * PT * sizeof(float) +
            2 * PKC * KRR_TILE * sizeof(float) + PT * sizeof(float2) + PT * sizeof(int64_t) +
-           (size_t)PG * 256 * sizeof(float2) + 256 * sizeof(float2);
+           (size_t)PG * 256 * sizeof(float2) + 256 * sizeof(float2) + (size_t)PG * 256 * (sizeof(float2) + sizeof(int));
 }
 
 void launch_predict(cudaStream_t st, const Model &M, const double *Xt, int64_t t, const int64_t *toff,
@@ -330,7 +368,7 @@ void launch_predict(cudaStream_t st, const Model &M, const double *Xt, int64_t t
                                                       tidx, pp, routed, out);
         } else {
             const size_t sm = predict_df_smem();
-            cudaFuncSetAttribute(predict_df_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            allow_max_dyn_smem(predict_df_kernel);
             KRR_LAUNCHED(), predict_df_kernel<<<grid, 256, sm, st>>>(M.Xh, M.Xl, M.nrm, M.dp, M.d_parts, M.d_solves, M.alpha, Xt, t,
                                                      M.d, toff, tidx, pp, routed, out);
         }

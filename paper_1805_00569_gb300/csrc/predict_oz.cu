@@ -57,6 +57,8 @@ struct OzSmem {
     OzChunkData cd[2];
     float2 exptab[256];
     float2 comb[OZ_NSP * OZ_NLP][OZ_M];
+    int combk[OZ_NSP][OZ_M];                     // column half 1's range shift per sigma
+    float2 shift[OZ_NSP][256];                   // per epilogue thread: -K ln2 per sigma (df)
     float2 dist[256][17];                        // per epilogue thread: 16 distances (padded row)
     uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
     uint64_t b_full, b_empty, t_full, t_empty;
@@ -263,11 +265,16 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const float2 nq2 = live ? nrm_test[grow] : make_float2(0.f, 0.f);
         const df nq = df_make(nq2.x, nq2.y);
         df_acc acc[OZ_NSP][OZ_NLP];
+        int ksh[OZ_NSP];       // range shift of the accumulators per sigma (exp_row_shift)
+        float dmin = INFINITY;  // smallest distance to a real training row so far
+        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..255
 #pragma unroll
-        for (int a = 0; a < OZ_NSP; ++a)
+        for (int a = 0; a < OZ_NSP; ++a) {
+            ksh[a] = KRR_SHIFT_NONE;  // no term yet: the shift argument stays 0
+            sm.shift[a][et] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < OZ_NLP; ++b) dfa_zero(acc[a][b]);
-        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..255
+        }
         for (int c = 0; c < nchunks; ++c) {
             OzChunkData &cd = sm.cd[c & 1];
             // training-side data of the chunk
@@ -305,6 +312,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     if (lane == 0) mbar_arrive(&sm.t_empty);
                 }
                 // distances of the 16 columns (static register indices), parked in shared memory
+                float dm = INFINITY;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     // G_scaled = S0 + 2^-8 S1 + 2^-16 S2 + 2^-24 S3 + 2^-32 S4 (all exact integers)
@@ -321,7 +329,34 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     D = df_add(D, df_make(-u.hi * s2, -u.lo * s2));
                     if (D.hi < 0.f) D = df_make(0.f, 0.f);
                     sm.dist[et][k] = make_float2(D.hi, D.lo);
+                    if (c * OZ_N + col < P.m) dm = fminf(dm, D.hi);
                 }
+                // a closer training row raises the range shift: rescale by 2^(K_old - K_new)
+                if (dm < dmin) {
+                    dmin = dm;
+#pragma unroll
+                    for (int is = 0; is < OZ_NSP; ++is) {
+                        const int kn = is < pp.nsig ? exp_row_shift(dmin * pp.c_hi[is]) : 0;
+                        if (is < pp.nsig && kn != ksh[is]) {
+                            const float f = pow2_nonpos(ksh[is] - kn);
+#pragma unroll
+                            for (int il = 0; il < OZ_NLP; ++il) {
+                                acc[is][il].s *= f;
+                                acc[is][il].c *= f;
+                            }
+                            ksh[is] = kn;
+                            sm.shift[is][et] = exp_shift_arg(kn);
+                        }
+                    }
+                }
+                // a sigma's range shift is applied warp-wide when any row of the
+                // warp has one: adding the zero shift of the other rows is exact
+                // (x + 0 = x in double-float), so every row's value is what it
+                // would be alone and the warp does not diverge
+                unsigned wsh = 0;
+#pragma unroll
+                for (int is = 0; is < OZ_NSP; ++is)
+                    wsh |= __any_sync(0xffffffffu, ksh[is] != 0) ? (1u << is) : 0u;
                 // two columns per iteration: their exponentials are independent
                 // chains the scheduler can interleave.  Padded training rows have
                 // alpha = 0 exactly, so they need no test.
@@ -334,8 +369,14 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     for (int is = 0; is < OZ_NSP; ++is) {
                         if (is < pp.nsig) {
                             const df cs = df_make(pp.c_hi[is], pp.c_lo[is]);
-                            const df k0 = df_exp_nonpos(df_mul(D0, cs), sm.exptab);
-                            const df k1 = df_exp_nonpos(df_mul(D1, cs), sm.exptab);
+                            df x0 = df_mul(D0, cs), x1 = df_mul(D1, cs);
+                            if (wsh & (1u << is)) {
+                                const float2 sv = sm.shift[is][et];  // (0, 0) for an unshifted row
+                                x0 = df_add(x0, df_make(sv.x, sv.y));
+                                x1 = df_add(x1, df_make(sv.x, sv.y));
+                            }
+                            const df k0 = df_exp_nonpos(x0, sm.exptab);
+                            const df k1 = df_exp_nonpos(x1, sm.exptab);
 #pragma unroll
                             for (int il = 0; il < OZ_NLP; ++il)
                                 if (il < pp.nlam) {
@@ -353,12 +394,14 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         epi_bar();
         if (half == 1) {
 #pragma unroll
-            for (int is = 0; is < OZ_NSP; ++is)
+            for (int is = 0; is < OZ_NSP; ++is) {
+                sm.combk[is][row] = ksh[is];
 #pragma unroll
                 for (int il = 0; il < OZ_NLP; ++il) {
                     const df v = dfa_value(acc[is][il]);
                     sm.comb[is * OZ_NLP + il][row] = make_float2(v.hi, v.lo);
                 }
+            }
         }
         epi_bar();
         if (half == 0 && live) {
@@ -369,10 +412,14 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 for (int il = 0; il < OZ_NLP; ++il) {
                     if (is < pp.nsig && il < pp.nlam) {
                         const float2 o = sm.comb[is * OZ_NLP + il][row];
-                        const df v = df_add(dfa_value(acc[is][il]), df_make(o.x, o.y));
+                        const int k1 = sm.combk[is][row], km = max(ksh[is], k1);
+                        df a = dfa_value(acc[is][il]), b = df_make(o.x, o.y);
+                        if (ksh[is] != km) a = df_scale2(a, pow2_nonpos(ksh[is] - km));
+                        if (k1 != km) b = df_scale2(b, pow2_nonpos(k1 - km));
+                        const df v = df_add(a, b);
                         const int gm = (pp.sig0 + is) * pp.nl_total + pp.lam0 + il;
                         const int64_t orow = routed ? (int64_t)gm : (int64_t)j * pp.Gtot + gm;
-                        out[orow * t + orow_t] = df_to_double(v);
+                        out[orow * t + orow_t] = km == 0 ? df_to_double(v) : ldexp(df_to_double(v), km);
                     }
                 }
         }
@@ -603,15 +650,15 @@ typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint
                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                       CUtensorMapFloatOOBfill);
 static PFN_encodeTiled_t oz_encode() {
-    static PFN_encodeTiled_t fn = nullptr;
-    if (!fn) {
+    static const PFN_encodeTiled_t fn = []() -> PFN_encodeTiled_t {  // thread-safe one-time lookup
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
         if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
                 cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
-            fn = (PFN_encodeTiled_t)p;
-    }
+            return (PFN_encodeTiled_t)p;
+        return nullptr;
+    }();
     return fn;
 }
 
@@ -646,11 +693,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
     if (ktot == 0) return cudaSuccess;
     CUtensorMap tmA;
     if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(kbuild_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-        attr = true;
-    }
+    allow_max_dyn_smem(kbuild_oz_kernel);
     OzKParams kp;
     kp.nsig = M.nsig;
     kp.nlam = M.nlam;
@@ -676,11 +719,7 @@ cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap
     launch_oz_slice(st, Xt, M.d, tidx, t, t_rows, tslices, tex, tnrm);
     CUtensorMap tmA;
     if (!make_slice_tmap(&tmA, tslices, (int64_t)OZ_SLICES * t_rows, dpz, OZ_M)) return cudaErrorInvalidValue;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(predict_oz_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)oz_smem_bytes());
-        attr = true;
-    }
+    allow_max_dyn_smem(predict_oz_kernel);
     for (int s0 = 0; s0 < M.nsig; s0 += OZ_NSP)
         for (int l0 = 0; l0 < M.nlam; l0 += OZ_NLP) {
             OzParams pp;

@@ -76,7 +76,7 @@ def _mixture_sizes(rng, n: int, k: int, lo: int, hi: int):
     return sizes
 
 
-def _mixture(rng, n: int, t: int, d: int, k: int, lo: int, hi: int):
+def _mixture(rng, n: int, t: int, d: int, k: int, lo: int, hi: int, params: dict | None = None):
     centres = 5.0 * rng.standard_normal((k, d))
     W = rng.standard_normal((k, d))
     b = rng.standard_normal(k)
@@ -93,6 +93,8 @@ def _mixture(rng, n: int, t: int, d: int, k: int, lo: int, hi: int):
                 + np.sin(np.linalg.norm(Z, axis=1)))
     y = target(X, comp) + 0.05 * rng.standard_normal(n)
     yt = target(Xt, comp_t) + 0.05 * rng.standard_normal(t)
+    if params is not None:
+        params.update(centres=centres, weights=tw)
     return X, y, Xt, yt, sizes
 
 
@@ -144,5 +146,13 @@ def serve_stream(seed: int = 4, requests: int = 10000, rate: float = 200.0,
 def serve_request_data(data_seed: int, n: int, d: int, t: int, k: int = 8):
     """Mixture features and the mixture target for one serving request."""
     rng = np.random.default_rng(int(data_seed))
-    X, y, Xt, yt, _ = _mixture(rng, int(n), int(t), int(d), k, 1, int(n))
-    return dict(X=X, y=y, Xt=Xt, yt=yt)
+    mix = {}
+    X, y, Xt, yt, _ = _mixture(rng, int(n), int(t), int(d), k, 1, int(n), mix)
+    return dict(X=X, y=y, Xt=Xt, yt=yt, mix=mix)
+
+
+def serve_repeat_rows(mix: dict, seed: int, t: int):
+    """New test rows from the mixture of an earlier request (a repeat predict)."""
+    rng = np.random.default_rng(int(seed))
+    c = rng.choice(mix["centres"].shape[0], size=int(t), p=mix["weights"])
+    return mix["centres"][c] + rng.standard_normal((int(t), mix["centres"].shape[1]))

@@ -274,6 +274,42 @@ def test_single_row_and_empty_partitions(ctx):
         model.free()
 
 
+@pytest.mark.parametrize("d", [20, 100])  # exact slice-Gram kernel; double-float fallback (d > 96)
+@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+def test_far_test_rows_keep_relative_accuracy(ctx, d, prec):
+    """Test rows far from every training row at a small sigma: their Eq. 7
+    sums (~e^-300) lie far below the FP32 exponent range of the double-float
+    exponential, yet each must match the oracle to 1e-6 relative, row by row;
+    near rows in the same launch keep their accuracy too."""
+    rng = np.random.default_rng(17)
+    n, sigma, lam = 300, 0.5, 1e-3
+    X = rng.standard_normal((n, d))
+    y = rng.standard_normal(n)
+    src = rng.integers(0, n, 96)
+    push = np.sqrt(np.linspace(2.0, 280.0, 96) / d)  # squared distance to the source row: 2 .. 280
+    dirs = rng.standard_normal((96, d))
+    dirs /= np.linalg.norm(dirs, axis=1, keepdims=True)
+    Xt = X[src] + dirs * push[:, None] * np.sqrt(d)
+    perm = np.arange(n, dtype=np.int64)
+    off = np.array([0, 140, n], np.int64)  # two partitions: the shift is per (row, partition)
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(off, torch.int64),
+                                           [sigma], [lam], prec, want_alpha=True)
+    try:
+        assert np.all(status.cpu().numpy() == K.KRR_OK)
+        a = alpha.cpu().numpy()
+        yh = K.krr_predict(ctx, model, cuda(Xt)).cpu().numpy()
+        for j in range(2):
+            Xj, aj = X[off[j]:off[j + 1]], a[off[j]:off[j + 1]]
+            ref = oracle.predict(Xj, aj, Xt, sigma)
+            live = np.abs(ref) > 1e-290  # away from FP64 subnormals
+            assert live.sum() > 20 and np.min(np.abs(ref[live])) < 1e-100
+            err = np.abs(yh[j][live] - ref[live]) / np.abs(ref[live])
+            assert err.max() <= REFINED_TOL, "partition %d: worst row rel err %.3e" % (j, err.max())
+            assert np.all(yh[j][~live] == 0.0) or np.max(np.abs(yh[j][~live])) < 1e-280
+    finally:
+        model.free()
+
+
 @pytest.mark.parametrize("prec", ["fp64", "tf32"])
 def test_indefinite_system_is_reported_per_solve(ctx, prec):
     """A negative shift makes K + lambda m I indefinite: that solve reports
