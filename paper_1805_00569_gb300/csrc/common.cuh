@@ -7,7 +7,7 @@
 //   This gives ~44-bit arithmetic on the FP32 pipes, which on GB300 are 64x
 //   faster than the FP64 pipe.
 // * df exponential: table-driven reduction by ln2/256 (three-part constant,
-//   256-entry df table of 2^(j/256)) and a short series (relative error ~2e-13
+//   256-entry df table of 2^(j/256)) and a short series (relative error ~7e-13
 //   for arguments <= 0).
 // * Philox4x32-10 (Salmon et al., SC'11) for the seeded row shuffle.
 // * thin inline-PTX wrappers for mbarrier, cp.async.bulk(.tensor) and tcgen05.
@@ -77,15 +77,19 @@ __device__ __forceinline__ df dfa_value(const df_acc &a) {
     return r;
 }
 
-// exp(x) for df x <= 0 (x > 0 is clamped to 1); 0 below -87 where the FP32
-// hi part would be subnormal.  Method (table-driven, Tang-style): with
-// n = round(x * 256 / ln 2), x = n ln2/256 + r, |r| <= ln2/512, so
-// exp(x) = 2^(n >> 8) * 2^((n & 255)/256) * exp(r).  ln2/256 is split in three
-// parts (the first with 8 significant bits, so n * C1 is exact for |n| < 2^15
-// and x.hi - n C1 is exact by Sterbenz); exp(r) = 1 + r + q with
-// q = r^2/2 + r^3/6 + r^4/24 taken in FP32 from r.hi (|q| < 1e-6, so its
-// rounding is below 1e-13 absolute); the 256 table values 2^(j/256) are df
-// numbers in shared memory.  Relative error ~2e-13.
+// exp(x) for df x <= 0; 0 below -87, where the FP32 hi part would be
+// subnormal.  Method (table-driven, Tang-style): with n = round(x 256 / ln 2),
+// x = n ln2/256 + r, |r| <= ln2/512, so exp(x) = 2^(n >> 8) 2^((n & 255)/256) exp(r).
+// ln2/256 = C1 + C2 + C3 with C1 of 8 significant bits, so n C1 is exact for
+// |n| < 2^15 and x.hi - n C1 is exact (Sterbenz); n C2 is split exactly into
+// p2 + e2 by an FMA and x.hi - n C1 - p2 = s + u exactly by TwoSum, leaving
+// r = s + rlo with the small terms rlo = u - e2 - n C3 + x.lo (|rlo| < 4e-6,
+// rounded to ~1e-13 absolute).  Then
+//   exp(r) = 1 + s + q(s) + rlo (1 + s + s^2/2 + rlo/2),  q = s^2/2 + s^3/6 + s^4/24,
+// with q and the rlo term in FP32 (both below 1e-6 in size, so their rounding
+// stays below 1e-13) and 1 + s exact as a double-float.  The 256 table values
+// 2^(j/256) are double-float numbers in shared memory.  Relative error ~7e-13
+// for results above ~1e-30 (the lo part runs into FP32 subnormals below that).
 __device__ __forceinline__ void exp_table_init(float2 *tab) {
     for (int j = threadIdx.x; j < 256; j += blockDim.x) {
         const double v = exp2((double)j / 256.0);
@@ -95,44 +99,47 @@ __device__ __forceinline__ void exp_table_init(float2 *tab) {
 }
 __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab) {
     if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
-    if (x.hi >= 0.f) return df_make(1.f, 0.f);
     const float C1 = 0x1.62p-9f, C2 = 0x1.c85fep-18f, C3 = -0x1.718432p-43f;
     const float nf = rintf(x.hi * 369.329930467574632284140718f);  // 256 / ln 2
     const int n = (int)nf;
-    df r = df_add(df_make(__fsub_rn(x.hi, nf * C1), 0.f), df_make(x.lo, 0.f));
-    const float p2 = __fmul_rn(nf, C2), e2 = __fmaf_rn(nf, C2, -p2);
-    r = df_add(r, df_make(-p2, -e2));
-    r = df_add(r, df_make(-nf * C3, 0.f));
-    const float h = r.hi;
-    const float q = h * h * __fmaf_rn(h, __fmaf_rn(h, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f);
-    float s, t;
-    fast_two_sum(1.0f, h, s, t);
-    t = __fadd_rn(t, __fadd_rn(r.lo, q));
-    df e;
-    fast_two_sum(s, t, e.hi, e.lo);
+    const float t1 = __fmaf_rn(-nf, C1, x.hi);  // exact
+    const float p2 = __fmul_rn(nf, C2);
+    const float e2 = __fmaf_rn(nf, C2, -p2);     // n C2 = p2 + e2
+    float s, u;
+    two_sum(t1, -p2, s, u);
+    const float rlo = __fadd_rn(__fadd_rn(u, -e2), __fmaf_rn(-nf, C3, x.lo));
+    const float q = __fmul_rn(__fmul_rn(s, s), __fmaf_rn(s, __fmaf_rn(s, 1.0f / 24.0f, 1.0f / 6.0f), 0.5f));
+    const float w = __fmaf_rn(0.5f, rlo, __fmaf_rn(s, __fmul_rn(0.5f, s), s));  // s + s^2/2 + rlo/2
+    float eh, el;
+    fast_two_sum(1.0f, s, eh, el);
+    el = __fadd_rn(el, __fadd_rn(q, __fmaf_rn(rlo, w, rlo)));
     const float2 tv = tab[n & 255];
-    df y = df_mul(df_make(tv.x, tv.y), e);
-    const int k = n >> 8;  // floor division, k in [-126, 0]
-    const int k1 = k / 2, k2 = k - k1;
-    const float s1 = __int_as_float((127 + k1) << 23), s2 = __int_as_float((127 + k2) << 23);
-    return df_scale2(df_scale2(y, s1), s2);
+    const float p = __fmul_rn(tv.x, eh);
+    float e = __fmaf_rn(tv.x, eh, -p);
+    e = __fmaf_rn(tv.x, el, e);
+    e = __fmaf_rn(tv.y, eh, e);
+    float yh, yl;
+    fast_two_sum(p, e, yh, yl);
+    const float sc = __int_as_float((127 + (n >> 8)) << 23);  // 2^(n >> 8), n >> 8 in [-126, 0]
+    return df_make(yh * sc, yl * sc);
 }
 
 // Exponent range of a prediction row.  The double-float exponential has the
 // FP32 range (results below e^-87 are 0), while an Eq. 7 sum can be a
 // meaningful number far below that (a test row far from every training row
 // at a small sigma).  A row whose largest exponent argument so far, x_max =
-// D_min * c (c = -1/(2 sigma^2)), is below -64 takes its terms as
+// D_min * c (c = -1/(2 sigma^2)), is below -20 takes its terms as
 // exp(x - K ln2) = exp(x) 2^-K with the integer
 //   K = ceil((x_max + 1/64) / ln2) <= 0,
 // so every shifted argument is <= -1/64 and the largest term is >= 1/2; the
-// accumulated sum is scaled back by 2^K in FP64.  Rows with x_max >= -64
-// keep K = 0 and the unshifted arithmetic.  K is clamped at KRR_SHIFT_NONE
-// (2^-1100 is 0 in FP64, as is every term the clamp affects); KRR_SHIFT_NONE
-// also marks a row that has seen no term yet.
+// accumulated sum is scaled back by 2^K in FP64.  Rows with x_max >= -20
+// keep K = 0 and the unshifted arithmetic; the terms the exponential drops
+// (below e^-87) are then below e^-67 of the largest one.  K is clamped at
+// KRR_SHIFT_NONE (2^-1100 is 0 in FP64, as is every term the clamp affects);
+// KRR_SHIFT_NONE also marks a row that has seen no term yet.
 #define KRR_SHIFT_NONE (-1100)
 __device__ __forceinline__ int exp_row_shift(float xmax) {
-    if (!(xmax < -64.f)) return 0;
+    if (!(xmax < -20.f)) return 0;
     const float k = ceilf((xmax + 0.015625f) * 1.44269504088896341f);  // 1 / ln 2
     return k < (float)KRR_SHIFT_NONE ? KRR_SHIFT_NONE : (int)k;
 }
