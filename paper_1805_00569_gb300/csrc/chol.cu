@@ -296,21 +296,26 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 }
 
 // ---------------------------------------------------------------- tcgen05 TF32
-// One CTA per task, 192 threads: warp 0 lane 0 streams the operand tiles with
-// 2-D TMA loads (128-byte swizzle) through an mbarrier ring; warp 1 lane 0
-// issues the MMAs into a 128 x 128 FP32 accumulator in tensor memory; warps
-// 2..5 read it back (tcgen05.ld) for the epilogue (A_ij -= C, or A_ik = C for
-// the panel solve).  X3 = false: one kind::tf32 MMA per K step (the tensor
-// core reads the top 19 bits of each FP32 operand).  X3 = true: warps 2..5
-// also split each landed stage into hi = x with the low 13 mantissa bits
-// cleared and lo = x - hi (exact), and three MMAs per K step form
-// hi*hi + hi*lo + lo*hi: FP32-class products on the tensor cores.
+// Persistent: each CTA takes tasks blockIdx.x, blockIdx.x + gridDim.x, ... of
+// one launch (a task is one 128 x 128 output tile).  Warp 0 lane 0 streams the
+// operand tiles of all its tasks with 2-D TMA loads (128-byte swizzle) through
+// an mbarrier ring; warp 1 lane 0 issues the MMAs of task t into one of two
+// 128-column FP32 accumulators in tensor memory (t % 2); warps 2..5 read the
+// other one back (tcgen05.ld) for the epilogue of the previous task (A_ij -= C,
+// or A_ik = C for the panel solve), so loads, MMAs and epilogues of
+// consecutive tasks overlap and the per-CTA setup is paid once per launch.
+// X3 = false: one kind::tf32 MMA per K step (the tensor core reads the top 19
+// bits of each FP32 operand).  X3 = true: warps 6..9 split each landed stage
+// into hi = x with the low 13 mantissa bits cleared and lo = x - hi (exact),
+// and three MMAs per K step form hi*hi + hi*lo + lo*hi: FP32-class products on
+// the tensor cores.
 constexpr int TC_CHUNK = 32;                                       // floats of K per stage (128 bytes)
 constexpr uint32_t TC_HALF = (uint32_t)KRR_TILE * TC_CHUNK * 4;     // one operand tile chunk, 16 KB
 constexpr uint32_t TC_IDESC = make_idesc(2u /*TF32*/, 128u, 128u);
 template <bool X3> struct TcCfg {
     static constexpr int STAGES = X3 ? 2 : 3;
     static constexpr uint32_t STAGE_BYTES = (X3 ? 4u : 2u) * TC_HALF;  // A, B (+ A_lo, B_lo)
+    static constexpr int THREADS = X3 ? 320 : 192;
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -334,25 +339,32 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
 }
 
 template <bool X3>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(TcCfg<X3>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
                 float *__restrict__ A, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
-                int nsolve, int mode, int K0, int W, int *__restrict__ err) {
+                int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
     using Cfg = TcCfg<X3>;
+    constexpr int KCH = KRR_TILE / TC_CHUNK;  // chunks per K tile
     extern __shared__ unsigned char tc_dyn[];
     const uint32_t base = smem_u32(tc_dyn);
     unsigned char *buf = tc_dyn + (((base + 1023u) & ~1023u) - base);  // 1024-aligned stage ring
     uint64_t *full = reinterpret_cast<uint64_t *>(buf + Cfg::STAGES * Cfg::STAGE_BYTES);
     uint64_t *empty = full + Cfg::STAGES;
     uint64_t *split = empty + Cfg::STAGES;
-    uint64_t *done = split + Cfg::STAGES;
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *tfull = split + Cfg::STAGES;  // accumulator b ready for the epilogue
+    uint64_t *tempty = tfull + 2;           // accumulator b read back by the 4 epilogue warps
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    const int s = find_solve(pre, nsolve, blockIdx.x);
-    const SolveDesc S = solves[s];
-    const TaskGeom g = decode_task(mode, (int64_t)blockIdx.x - pre[s], K0, W);
-    const int nchunks = (g.ke - g.kb) * (KRR_TILE / TC_CHUNK);
+    // task geometry: the solve by binary search, then the tile of that solve
+    auto task = [&](int64_t b, SolveDesc &S, TaskGeom &g) {
+        const int s = find_solve(pre, nsolve, b);
+        S = solves[s];
+        g = decode_task(mode, b - pre[s], K0, W);
+    };
+    auto dst_tile = [&](const SolveDesc &S, const TaskGeom &g) {
+        return A + (S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS;
+    };
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < Cfg::STAGES; ++i) {
@@ -360,11 +372,14 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
             mbar_init(&empty[i], 1);
             mbar_init(&split[i], 4);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 4);
+        }
         fence_mbar_init();
     }
     if (warp == 0) {
-        tmem_alloc(tslot, 128);
+        tmem_alloc(tslot, 256);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -373,87 +388,132 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     const uint32_t tmem = *tslot;
 
     if (threadIdx.x == 0) {  // TMA producer
-        for (int q = 0; q < nchunks; ++q) {
-            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
-            if (use > 0 && !mbar_wait_deadline(&empty[st], (use - 1) & 1, err)) break;
-            unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
-            unsigned char *sb = sa + TC_HALF;
-            const int kt = g.kb + q / (KRR_TILE / TC_CHUNK);
-            const int x = (q % (KRR_TILE / TC_CHUNK)) * TC_CHUNK;
-            const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
-            mbar_arrive_expect_tx(&full[st], 2 * TC_HALF);
-            tma_load_2d(sa, &tmap, x, ya, &full[st]);
-            if (mode == UPD_TRSM) {
-                tma_load_2d(sb, &tmapZ, x, (int)((S.dtile0 + kt) * KRR_TILE), &full[st]);
-            } else {
-                const int yb = (int)((S.ltile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE);
-                tma_load_2d(sb, &tmap, x, yb, &full[st]);
+        int64_t q = 0;       // chunk counter across this CTA's tasks
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+            SolveDesc S;
+            TaskGeom g;
+            task(t, S, g);
+            const int nch = (g.ke - g.kb) * KCH;
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int st = (int)(q % Cfg::STAGES);
+                const int64_t use = q / Cfg::STAGES;
+                if (use > 0 && !mbar_wait_deadline(&empty[st], (uint32_t)((use - 1) & 1), err)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
+                unsigned char *sb = sa + TC_HALF;
+                const int kt = g.kb + c / KCH;
+                const int x = (c % KCH) * TC_CHUNK;
+                const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
+                mbar_arrive_expect_tx(&full[st], 2 * TC_HALF);
+                tma_load_2d(sa, &tmap, x, ya, &full[st]);
+                if (mode == UPD_TRSM) {
+                    tma_load_2d(sb, &tmapZ, x, (int)((S.dtile0 + kt) * KRR_TILE), &full[st]);
+                } else {
+                    const int yb = (int)((S.ltile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE);
+                    tma_load_2d(sb, &tmap, x, yb, &full[st]);
+                }
             }
         }
     } else if (threadIdx.x == 32) {  // MMA issuer
+        int64_t q = 0;
+        int lt = 0;  // local task index
         bool ok = true;
-        for (int q = 0; q < nchunks && ok; ++q) {
-            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
-            if (!mbar_wait_deadline(X3 ? &split[st] : &full[st], use & 1, err)) {
-                ok = false;
-                break;
-            }
+        for (int64_t t = blockIdx.x; t < ntasks && ok; t += gridDim.x, ++lt) {
+            SolveDesc S;
+            TaskGeom g;
+            task(t, S, g);
+            const int nch = (g.ke - g.kb) * KCH;
+            const int b = lt & 1;
+            if (lt >= 2 && !mbar_wait_deadline(&tempty[b], (uint32_t)(((lt >> 1) - 1) & 1), err)) break;
             tc_fence_after();
-            unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
-            unsigned char *sb = sa + TC_HALF;
-            const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
-#pragma unroll
-            for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
-                const uint32_t acc0 = (q > 0 || kk > 0) ? 1u : 0u;
-                tc_mma_tf32(tmem, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
-                if (X3) {
-                    const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF), dbl = smem_desc_sw128(sb + 2 * TC_HALF);
-                    tc_mma_tf32(tmem, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
-                    tc_mma_tf32(tmem, dal + 2 * kk, db + 2 * kk, TC_IDESC, 1u);
+            const uint32_t acc = tmem + (uint32_t)(b * KRR_TILE);
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int st = (int)(q % Cfg::STAGES);
+                const int64_t use = q / Cfg::STAGES;
+                if (!mbar_wait_deadline(X3 ? &split[st] : &full[st], (uint32_t)(use & 1), err)) {
+                    ok = false;
+                    break;
                 }
+                tc_fence_after();
+                unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
+                unsigned char *sb = sa + TC_HALF;
+                const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+#pragma unroll
+                for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
+                    const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+                    tc_mma_tf32(acc, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
+                    if (X3) {
+                        const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF), dbl = smem_desc_sw128(sb + 2 * TC_HALF);
+                        tc_mma_tf32(acc, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
+                        tc_mma_tf32(acc, dal + 2 * kk, db + 2 * kk, TC_IDESC, 1u);
+                    }
+                }
+                tc_commit(&empty[st]);
             }
-            tc_commit(&empty[st]);
+            if (ok) tc_commit(&tfull[b]);
         }
-        tc_commit(done);
-    } else if (warp >= 2 && X3) {  // split landed stages into hi / lo
-        const int t = threadIdx.x - 64;  // 0..127
-        for (int q = 0; q < nchunks; ++q) {
-            const int st = q % Cfg::STAGES, use = q / Cfg::STAGES;
-            if (!mbar_wait_deadline(&full[st], use & 1, err)) break;
-            float4 *hi = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES);
-            float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
+    } else if (X3 && warp >= 6) {  // split landed stages into hi / lo
+        const int tsp = threadIdx.x - 192;  // 0..127
+        int64_t q = 0;
+        bool ok = true;
+        for (int64_t t = blockIdx.x; t < ntasks && ok; t += gridDim.x) {
+            SolveDesc S;
+            TaskGeom g;
+            task(t, S, g);
+            const int nch = (g.ke - g.kb) * KCH;
+            for (int c = 0; c < nch; ++c, ++q) {
+                const int st = (int)(q % Cfg::STAGES);
+                const int64_t use = q / Cfg::STAGES;
+                if (!mbar_wait_deadline(&full[st], (uint32_t)(use & 1), err)) {
+                    ok = false;
+                    break;
+                }
+                float4 *hi = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES);
+                float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
 #pragma unroll 4
-            for (int e = t; e < (int)(2 * TC_HALF / 16); e += 128) {
-                float4 v = hi[e], h, l;
-                h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                l.x = v.x - h.x;
-                l.y = v.y - h.y;
-                l.z = v.z - h.z;
-                l.w = v.w - h.w;
-                hi[e] = h;
-                lo[e] = l;
+                for (int e = tsp; e < (int)(2 * TC_HALF / 16); e += 128) {
+                    float4 v = hi[e], h, l;
+                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                    l.x = v.x - h.x;
+                    l.y = v.y - h.y;
+                    l.z = v.z - h.z;
+                    l.w = v.w - h.w;
+                    hi[e] = h;
+                    lo[e] = l;
+                }
+                fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&split[st]);
             }
-            fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&split[st]);
         }
-    }
-    __syncwarp();
-    if (warp >= 2) {  // epilogue
-        const bool have = mbar_wait_deadline(done, 0, err);
-        tc_fence_after();
-        if (have && *err == 0) {
-            const int quad = warp & 3;
-            const int r = quad * 32 + lane;
-            float *dst =
-                A + (S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE;
+    } else if (warp >= 2 && warp < 6) {  // epilogue
+        const int quad = warp & 3;
+        const int r = quad * 32 + lane;
+        int lt = 0;
+        for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++lt) {
+            SolveDesc S;
+            TaskGeom g;
+            task(t, S, g);
+            float *dst = dst_tile(S, g) + (int64_t)r * KRR_TILE;
+            const int b = lt & 1;
+            if (!mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err)) break;
+            tc_fence_after();
+            if (t + gridDim.x < ntasks && mode != UPD_TRSM) {  // the next destination row into L2
+                SolveDesc S2;
+                TaskGeom g2;
+                task(t + gridDim.x, S2, g2);
+                bulk_prefetch_l2(dst_tile(S2, g2) + (int64_t)r * KRR_TILE, KRR_TILE * sizeof(float));
+            }
 #pragma unroll 1
             for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
                 float v[32];
-                tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(cb * 32), v);
+                tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32), v);
                 float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
                 if (mode == UPD_TRSM) {
 #pragma unroll
@@ -471,11 +531,14 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[b]);
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 128);
+    if (warp == 0) tmem_dealloc(tmem, 256);
 }
 
 // ---------------------------------------------------------------- host side
@@ -575,6 +638,9 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                             const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     allow_max_dyn_smem(potrf_tile_kernel<T>);
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     for (const CholLaunch &L : plan) {
         const unsigned grid = (unsigned)L.tasks;
         const int64_t *p = d_pre + L.pre;
@@ -590,12 +656,15 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
             // trailing updates 1 pass (TF32) or 3 passes (FP32), per launch class
             if (tc != 0) {
                 const bool x3 = (L.kind == 1) || L.tc == 3;
+                const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 if (x3)
-                    KRR_LAUNCHED(), tile_mma_kernel<true><<<grid, 192, TcCfg<true>::SMEM, st>>>(
-                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, mode, L.K0, W, d_err);
+                    KRR_LAUNCHED(), tile_mma_kernel<true><<<pgrid, TcCfg<true>::THREADS, TcCfg<true>::SMEM, st>>>(
+                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, L.tasks, mode, L.K0, W,
+                        d_err);
                 else
-                    KRR_LAUNCHED(), tile_mma_kernel<false><<<grid, 192, TcCfg<false>::SMEM, st>>>(
-                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, mode, L.K0, W, d_err);
+                    KRR_LAUNCHED(), tile_mma_kernel<false><<<pgrid, TcCfg<false>::THREADS, TcCfg<false>::SMEM, st>>>(
+                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, L.tasks, mode, L.K0, W,
+                        d_err);
                 continue;
             }
         }
