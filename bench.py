@@ -40,7 +40,7 @@ UNIT = "partition-solves/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "fp64"])
@@ -106,7 +106,9 @@ def cpu_baseline(w, sample: int):
 
 # ---------------------------------------------------------------- clocks
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    """nvidia-smi sampling of SM clocks and throttle reasons; the summary keeps
+    the samples taken inside the timed window (window(t0, t1), perf_counter
+    times)."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -115,47 +117,56 @@ class Clocks:
         self.device = device
         self.proc = None
         self.lines = []
+        self.win = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
             self.th.start()
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0:  # sampler running before timing starts
+                time.sleep(0.01)
         except (FileNotFoundError, OSError):
             self.proc = None
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def window(self, t0: float, t1: float):
+        self.win = (t0, t1)
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.1)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        parsed = []
+        for ts, ln in self.lines:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
             try:
-                s, m, pw = float(f[1]), float(f[2]), float(f[3])
+                parsed.append((ts, float(f[1]), float(f[2]), float(f[3]),
+                               [nm for nm, v in zip(names, f[5:9]) if v.lower() == "active"]))
             except ValueError:
                 continue
-            mx = max(mx, m)
-            if pw > 200.0:  # under load
-                sm.append(s)
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(self.lines), "samples_under_load": len(sm)}
+        inside = [x for x in parsed if self.win and self.win[0] - 0.05 <= x[0] <= self.win[1] + 0.05]
+        use = inside or parsed
+        sm = [x[1] for x in use]
+        reasons = sorted({r for x in use for r in x[4]})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max((x[2] for x in parsed), default=None),
+                "power_w_max": max((x[3] for x in use), default=None),
+                "reasons": reasons, "samples": len(parsed), "samples_in_timed_region": len(inside)}
 
 
 # ---------------------------------------------------------------- our arm
@@ -270,6 +281,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as tdist
         tdist.barrier()
     torch.cuda.synchronize()
+    t_win0 = time.perf_counter()
     for _ in range(args.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -280,6 +292,7 @@ def run_ours(args, rank, world, local_rank):
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
+    clocks.window(t_win0, time.perf_counter())
     if world > 1:
         tdist.barrier()
     clk = clocks.stop()
@@ -338,6 +351,12 @@ def run_ours(args, rank, world, local_rank):
                 fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times)
 
 
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
+# capture of this bench's workload (profiles/launch_list_bkrr2_n65536_p16.md);
+# an entry is removed whenever its kernel changes.
+TRAFFIC = {("predict", "bkrr2_n65536_t8192_d90_p16"): 276918784 + 7724288}
+
+
 def roofline(res, steps, peaks):
     """Roofline of the kernel class with the largest share of device time."""
     prof = res["prof"]
@@ -351,7 +370,7 @@ def roofline(res, steps, peaks):
     dom = max(prof, key=lambda k: prof[k][0])
     ms, launches = prof[dom]
     clock = (res["clocks"] or {}).get("sm_mhz") or 1455.0
-    fp32_peak = 152 * 128 * 2 * clock * 1e6 / 1e12  # TFLOP/s of FFMA at the sampled clock
+    fp32_peak = 152 * 128 * clock * 1e6 / 1e12  # FP32 operations per second at the sampled clock
     tf32_peak = peaks.get("bf16_tflops_sustained", 1715.4) * (1.1 / 2.25)
     out = {"kernel": dom, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
            "share": ms / sum(v[0] for v in prof.values())}
@@ -360,20 +379,30 @@ def roofline(res, steps, peaks):
         out.update(bound="tensor", achieved=flops / (ms / 1e3) / 1e12, peak=tf32_peak, unit="TFLOP/s",
                    peak_note="TF32 = measured bf16 sustained x nominal TF32/BF16 ratio (1.1/2.25), of measured")
     elif dom in ("kbuild", "predict"):
+        # double-float work in FP32 operations, counted from the kernels' design:
+        # distance assembly from the five exact slice levels 22 per pair; per sigma
+        # a double-float product 7 and exponential 44; per (sigma, lambda) one
+        # double-float multiply-accumulate 12 (predict) or two stores (kbuild)
+        ns = len(w["sigmas"])
         if dom == "kbuild":
-            flops = steps * sum(mm * mm * d + len(w["sigmas"]) * mm * mm / 2.0 * 20 for mm in sizes)
+            per_pair = 22 + ns * (7 + 44 + 4) + G * 2
+            pairs = steps * sum(mm * mm / 2.0 for mm in sizes)
         else:
-            flops = steps * sum(t * mm for mm in sizes) * (2.0 * d + len(w["sigmas"]) * 20 + 2 * G)
-        out.update(bound="alu", achieved=flops / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
-                   peak_note="FP32 FFMA peak = 152 SMs x 128 lanes x 2 x sampled SM clock; algorithmic FP64-class "
-                             "flops (each costs ~12 FP32 ops in double-float)")
+            per_pair = 22 + ns * (7 + 44) + G * 12
+            pairs = steps * sum(t * mm for mm in sizes)
+        out.update(bound="alu", achieved=pairs * per_pair / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
+                   peak_note="FP32 issue peak = 152 SMs x 128 lanes x sampled SM clock (one FP32 op per lane per "
+                             "cycle); achieved = designed FP32 operations of the double-float arithmetic "
+                             "(%d per pair) x pairs / kernel time" % per_pair)
     else:
         tiles = (m // 128) * (m // 128 + 1) // 2 + m // 128
         byts = steps * p * G * tiles * 128 * 128 * 4 * 2 * max(1, launches // max(steps, 1)) / max(1, G)
         out.update(bound="hbm", achieved=byts / (ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6797.9), unit="GB/s",
                    peak_note="measured copy bandwidth; bytes assume every solve active (upper bound)")
     out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = None
+    out["traffic"] = TRAFFIC.get((dom, w["workload"]))
+    if out["traffic"] is not None:
+        out["traffic_unit"] = "bytes per launch (DRAM read + write)"
     return out
 
 
