@@ -250,6 +250,83 @@ def test_bkrr2_full_size_sampled(ctx, prec):
         model.free()
 
 
+def test_kkrr2_full_size_sampled(ctx):
+    """The KKRR2 workload at full size (n = 262144, k = 64, 20 rounds, uneven
+    partitions, 3 sigma x 2 lambda) as the benchmark runs it: partitions,
+    routes and centres bit-exact against the oracle's K-means; three
+    partitions (the two smallest non-empty ones and a mid-sized one) refitted
+    by the oracle for the worst-conditioned and a mid model, and their routed
+    predictions compared on every test row routed to them."""
+    w = synth.kkrr2()
+    X, y, Xt, yt = w["X"], w["y"], w["Xt"], w["yt"]
+    k, iters, init = w["p"], w["iters"], w["init_idx"]
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, k,
+                                                            iters=iters, init_idx=cuda(init, torch.int64))
+    operm, ooff, oassign, oroute, ocent, _ = oracle.partition_kmeans(X, Xt, k, init, iters)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+    assert np.array_equal(perm.cpu().numpy(), operm) and np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(route.cpu().numpy(), oroute)
+    assert np.array_equal(centers.cpu().numpy(), ocent)
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), perm, offsets, w["sigmas"], w["lambdas"], "tf32",
+                                           want_alpha=True)
+    try:
+        G = 6
+        st = status.cpu().numpy()
+        assert np.all(st == K.KRR_OK), np.unique(st, return_counts=True)
+        yr = K.krr_predict(ctx, model, cuda(Xt), route=route).cpu().numpy()
+        galpha = split_alpha(alpha.cpu().numpy(), ooff, G)
+        sizes = np.diff(ooff)
+        nonempty = np.nonzero(sizes > 0)[0]
+        order = nonempty[np.argsort(sizes[nonempty], kind="stable")]
+        mid = nonempty[np.argmin(np.abs(sizes[nonempty] - 2000))]
+        for j in [int(order[0]), int(order[1]), int(mid)]:
+            rows = operm[ooff[j]:ooff[j + 1]]
+            test_rows = np.nonzero(oroute == j)[0]
+            for si, li in [(2, 0), (1, 1)]:  # (sigma 16, lambda 1e-6), (sigma 4, lambda 1e-4)
+                g = si * 2 + li
+                oa, info, rc = oracle.fit(X[rows], y[rows], w["sigmas"][si], w["lambdas"][li])
+                assert rc == 0
+                assert rel(galpha[j][g], oa) <= REFINED_TOL, (j, g, sizes[j], info)
+                if test_rows.size:
+                    oyh = oracle.predict(X[rows], oa, Xt[test_rows], w["sigmas"][si])
+                    assert rel(yr[g][test_rows], oyh) <= REFINED_TOL, (j, g)
+    finally:
+        model.free()
+
+
+def test_sweep_full_size_sampled(ctx):
+    """The precision-sweep workload at full size (n = 520000, p = 128
+    partitions of 4062/4063 rows, heavy-tailed features) in every refined
+    precision: the partition bit-exact, two solves and their predictions on a
+    sample of test rows within 1e-6 of the oracle."""
+    w = synth.sweep()
+    X, y, Xt = w["X"], w["y"], w["Xt"]
+    dX = cuda(X)
+    _, _, perm, offsets, _ = K.krr_partition(ctx, dX, None, K.KRR_PART_RANDOM, 128, seed=w["part_seed"])
+    operm, ooff, _ = oracle.partition_random(X.shape[0], 128, w["part_seed"])
+    assert np.array_equal(perm.cpu().numpy(), operm) and np.array_equal(offsets.cpu().numpy(), ooff)
+    sample = np.random.default_rng(8).choice(Xt.shape[0], 192, replace=False)
+    picks = [0, 127]  # a 4063-row and a 4062-row partition
+    refs = {}
+    for j in picks:
+        rows = operm[ooff[j]:ooff[j + 1]]
+        oa, _, rc = oracle.fit(X[rows], y[rows], w["sigmas"][0], w["lambdas"][0])
+        assert rc == 0
+        refs[j] = (oa, oracle.predict(X[rows], oa, Xt[sample], w["sigmas"][0]))
+    for prec in ("tf32", "fp32"):
+        model, status, alpha = K.krr_fit_batch(ctx, dX, cuda(y), perm, offsets, w["sigmas"], w["lambdas"], prec,
+                                               want_alpha=True)
+        try:
+            assert np.all(status.cpu().numpy() == K.KRR_OK)
+            galpha = split_alpha(alpha.cpu().numpy(), ooff, 1)
+            yhat = K.krr_predict(ctx, model, cuda(Xt[sample])).cpu().numpy()
+            for j in picks:
+                assert rel(galpha[j][0], refs[j][0]) <= REFINED_TOL, (prec, j)
+                assert rel(yhat[j], refs[j][1]) <= REFINED_TOL, (prec, j)
+        finally:
+            model.free()
+
+
 # ------------------------------------------------------------------ edge cases and errors
 def test_single_row_and_empty_partitions(ctx):
     rng = np.random.default_rng(3)
