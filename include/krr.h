@@ -68,8 +68,11 @@ typedef enum {
 
 /* Create a context on `device` that enqueues on `cuda_stream` (a
  * cudaStream_t; NULL = legacy default stream).  hbm_budget_bytes caps the
- * device memory the library allocates (0 = no cap).  Errors: KRR_ERR_ARG,
- * KRR_ERR_CUDA. */
+ * device memory the library allocates (0 = no cap).  The context allocates
+ * from its own stream-ordered pool, which keeps freed blocks for reuse until
+ * krr_ctx_destroy (models still alive then keep theirs until freed).  One
+ * context must not be used by two host threads at once; separate contexts
+ * may.  Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */
 krr_status krr_ctx_create(krr_ctx **out, int device, void *cuda_stream, size_t hbm_budget_bytes);
 /* Destroy a context (models must be freed first).  Synchronises its stream. */
 krr_status krr_ctx_destroy(krr_ctx *ctx);

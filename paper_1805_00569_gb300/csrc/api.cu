@@ -100,7 +100,7 @@ cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) bytes = 256;
     if (c->budget && c->used + bytes > c->budget) return cudaErrorMemoryAllocation;
-    cudaError_t e = cudaMallocAsync(p, bytes, c->stream);
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, c->pool, c->stream);
     if (e == cudaSuccess) c->used += bytes;
     return e;
 }
@@ -212,9 +212,19 @@ krr_status krr_ctx_create(krr_ctx **out, int device, void *cuda_stream, size_t h
     k->c.device = device;
     k->c.stream = (cudaStream_t)cuda_stream;
     k->c.budget = hbm_budget_bytes;
-    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&k->c.d_err, sizeof(int)) != cudaSuccess ||
-        cudaMemset(k->c.d_err, 0, sizeof(int)) != cudaSuccess ||
+    // A private pool whose freed blocks stay mapped (release threshold: never):
+    // with the default threshold a stream synchronisation returns freed memory
+    // to the driver and the next fit maps it again, which costs milliseconds.
+    cudaMemPoolProps pp = {};
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = device;
+    uint64_t keep = UINT64_MAX;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMemPoolCreate(&k->c.pool, &pp) != cudaSuccess ||
+        cudaMemPoolSetAttribute(k->c.pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMalloc(&k->c.d_err, sizeof(int)) != cudaSuccess || cudaMemset(k->c.d_err, 0, sizeof(int)) != cudaSuccess ||
         cudaMallocHost(&k->c.h_flag, sizeof(unsigned int)) != cudaSuccess) {
+        if (k->c.pool) cudaMemPoolDestroy(k->c.pool);
         delete k;
         return KRR_ERR_CUDA;
     }
@@ -228,6 +238,8 @@ krr_status krr_ctx_destroy(krr_ctx *ctx) {
     for (auto e : ctx->c.prof.pool) cudaEventDestroy(e);
     cudaFree(ctx->c.d_err);
     cudaFreeHost(ctx->c.h_flag);
+    // blocks still held by live models keep the pool's memory until they are freed
+    cudaMemPoolDestroy(ctx->c.pool);
     delete ctx;
     return KRR_OK;
 }

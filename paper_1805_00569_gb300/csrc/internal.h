@@ -130,6 +130,7 @@ struct Ctx {
     cudaStream_t stream = nullptr;
     size_t budget = 0, used = 0;
     std::string last_error;
+    cudaMemPool_t pool = nullptr;  // this context's stream-ordered pool (freed blocks stay mapped)
     int *d_err = nullptr;      // device error word (timeouts inside kernels)
     unsigned int *h_flag = nullptr;  // pinned host word for polling
     Prof prof;
