@@ -76,7 +76,10 @@ extern "C" krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assig
         KRR_LAUNCHED(), krr::gather_count_kernel<<<(unsigned)nblk, 256, p * sizeof(int), st>>>(assign, n, p,
                                                                                              scratch);
     }
-    KRR_LAUNCHED(), krr::gather_scan_kernel<<<1, 32, 0, st>>>(scratch, nblk, p, offsets);
+    // the scan keeps one total per partition in shared memory (p <= 12288: 96 KiB)
+    if (krr::allow_max_dyn_smem(krr::gather_scan_kernel) != cudaSuccess) return KRR_ERR_CUDA;
+    KRR_LAUNCHED(), krr::gather_scan_kernel<<<1, 1024, (size_t)p * sizeof(long long), st>>>(scratch, nblk, p,
+                                                                                            offsets);
     if (nblk > 0) {
         KRR_LAUNCHED(), krr::gather_scatter_kernel<<<(unsigned)nblk, 128, KRR_GATHER_BLOCK * sizeof(int32_t), st>>>(
             assign, n, p, scratch, perm);

@@ -158,6 +158,100 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
     if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
 }
 
+// Same assignment (the same FP32 screening with the same bound, the same FP64
+// recheck of every candidate), organised for throughput: one thread per row
+// with the row's DP features in registers (DP = d padded to a multiple of 8,
+// up to 96; padded features are 0 on both sides, so they add exact zeros);
+// the centres in shared memory as [feature][centre] so one 16-byte broadcast
+// load feeds four centres; the k screening distances parked in shared memory
+// (column per thread) for the candidate pass.
+constexpr int ASSIGN2_THREADS = 256;
+template <int DP>
+__global__ void __launch_bounds__(ASSIGN2_THREADS)
+kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict__ X, int64_t n, int32_t d,
+                         const double *__restrict__ C64, const float *__restrict__ C32, int32_t k, int32_t k4,
+                         const int32_t *__restrict__ prev, int32_t *__restrict__ out,
+                         unsigned long long *delta) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *cT = reinterpret_cast<float *>(smem_raw);  // [DP][k4]
+    float *cn = cT + (size_t)DP * k4;                 // [k4] ||c||^2
+    float *dist = cn + k4;                            // [k4][ASSIGN2_THREADS]
+    for (int e = threadIdx.x; e < DP * k4; e += blockDim.x) {
+        const int f = e / k4, j = e % k4;
+        cT[e] = (f < d && j < k) ? C32[(size_t)j * d + f] : 0.f;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < k4; j += blockDim.x) {
+        float sacc = 0.f;
+        for (int f = 0; f < d; ++f) sacc = fmaf(cT[f * k4 + j], cT[f * k4 + j], sacc);
+        cn[j] = sacc;
+    }
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float x[DP];
+#pragma unroll
+    for (int f = 0; f < DP; ++f) x[f] = f < d ? X32[i * d + f] : 0.f;
+    float xn = 0.f;
+#pragma unroll
+    for (int f = 0; f < DP; ++f) xn = fmaf(x[f], x[f], xn);
+    const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
+    float best_hi = INFINITY;
+    const float4 *cT4 = reinterpret_cast<const float4 *>(cT);
+#pragma unroll 1
+    for (int j4 = 0; j4 < k4; j4 += 4) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int f = 0; f < DP; ++f) {
+            const float4 c = cT4[(f * k4 + j4) >> 2];
+            const float t0 = x[f] - c.x, t1 = x[f] - c.y, t2 = x[f] - c.z, t3 = x[f] - c.w;
+            a0 = fmaf(t0, t0, a0);
+            a1 = fmaf(t1, t1, a1);
+            a2 = fmaf(t2, t2, a2);
+            a3 = fmaf(t3, t3, a3);
+        }
+        const float av[4] = {a0, a1, a2, a3};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            dist[(size_t)(j4 + u) * ASSIGN2_THREADS + threadIdx.x] = av[u];
+            if (j4 + u < k) best_hi = fminf(best_hi, av[u] + bscale * (xn + cn[j4 + u]));
+        }
+    }
+    int ncand = 0, first = -1;
+#pragma unroll 1
+    for (int j = 0; j < k; ++j)
+        if (dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x] - bscale * (xn + cn[j]) <= best_hi) {
+            if (ncand == 0) first = j;
+            ++ncand;
+        }
+    int arg = first;
+    if (ncand > 1) {
+        const double *xr = X + i * d;
+        double best = INFINITY;
+#pragma unroll 1
+        for (int j = 0; j < k; ++j) {
+            if (dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x] - bscale * (xn + cn[j]) > best_hi) continue;
+            const double *c64 = C64 + (size_t)j * d;
+            double sd = 0.0;
+            for (int f = 0; f < d; ++f) {
+                const double t = __dsub_rn(xr[f], c64[f]);
+                sd = __dadd_rn(sd, __dmul_rn(t, t));
+            }
+            if (sd < best) {
+                best = sd;
+                arg = j;
+            }
+        }
+    }
+    out[i] = arg;
+    if (delta) {  // one atomic per warp: the counter is a single address
+        const bool changed = prev == nullptr || prev[i] != arg;
+        const unsigned active = __activemask();
+        const unsigned vote = __ballot_sync(active, changed);
+        if ((threadIdx.x & 31) == __ffs(active) - 1 && vote) atomicAdd(delta, (unsigned long long)__popc(vote));
+    }
+}
+
 __global__ void to_float_kernel(const double *__restrict__ a, float *__restrict__ b, int64_t cnt) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < cnt) b[i] = __double2float_rn(a[i]);
@@ -175,53 +269,123 @@ __global__ void init_centres_kernel(const double *__restrict__ X, int32_t d, con
 constexpr int CANON = 1024;
 
 // grid = number of 1024-row blocks; partial [nblk][k][d] FP64, counts [nblk][k]
+// Centre sums of one block of CANON consecutive rows in the canonical order
+// (each centre's rows added in ascending row order, starting from 0).  A
+// stable counting sort groups the block's rows by centre (warp 0 places 32
+// rows at a time with match/popc ranks); then thread (feature chunk, centre
+// group, lane) sums its centres' rows for one feature in a register, loads
+// issued four rows ahead of the additions.  blockDim = 32 * ceil(d/32) * CG.
 __global__ void kmeans_block_sums_kernel(const double *__restrict__ X, int64_t n, int32_t d,
-                                         const int32_t *__restrict__ c, int32_t k, double *__restrict__ partial,
-                                         long long *__restrict__ counts) {
+                                         const int32_t *__restrict__ c, int32_t k, int32_t cg_count,
+                                         double *__restrict__ partial, long long *__restrict__ counts) {
     extern __shared__ unsigned char smem_raw[];
-    double *S = reinterpret_cast<double *>(smem_raw);  // k*d
-    int32_t *sc = reinterpret_cast<int32_t *>(S + (size_t)k * d);
-    int64_t b = blockIdx.x;
-    int64_t lo = b * CANON, hi = min(n, lo + CANON);
-    for (int e = threadIdx.x; e < k * d; e += blockDim.x) S[e] = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) sc[i - lo] = c[i];
+    int32_t *sc = reinterpret_cast<int32_t *>(smem_raw);  // [CANON] centre of each row
+    int32_t *order = sc + CANON;                          // [CANON] rows grouped by centre
+    int32_t *start = order + CANON;                       // [k + 1]
+    int32_t *cursor = start + k + 1;                      // [k]
+    const int64_t b = blockIdx.x;
+    const int64_t lo = b * CANON;
+    const int len = (int)(min(n, lo + CANON) - lo);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cursor[j] = 0;
     __syncthreads();
-    for (int f = threadIdx.x; f < d; f += blockDim.x) {
-        for (int64_t i = lo; i < hi; ++i) {
-            int j = sc[i - lo];
-            S[(size_t)j * d + f] = __dadd_rn(S[(size_t)j * d + f], X[i * d + f]);
+    for (int i = threadIdx.x; i < len; i += blockDim.x) {
+        const int j = c[lo + i];
+        sc[i] = j;
+        atomicAdd(&cursor[j], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int j = 0; j < k; ++j) {
+            start[j] = run;
+            run += cursor[j];
+            cursor[j] = start[j];
+        }
+        start[k] = run;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int base = 0; base < len; base += 32) {
+            const int i = base + lane;
+            const bool valid = i < len;
+            const int j = valid ? sc[i] : -1 - lane;  // invalid lanes match nobody
+            const unsigned mask = __match_any_sync(0xffffffffu, j);
+            const int leader = __ffs(mask) - 1;
+            int pos = 0;
+            if (valid) pos = cursor[j] + __popc(mask & ((1u << lane) - 1u));
+            __syncwarp();
+            if (valid) {
+                order[pos] = i;
+                if (lane == leader) cursor[j] += __popc(mask);
+            }
+            __syncwarp();
         }
     }
     __syncthreads();
+    for (int j = threadIdx.x; j < k; j += blockDim.x) counts[b * k + j] = start[j + 1] - start[j];
+    const int fc = warp / cg_count, cg = warp % cg_count;
+    const int f = fc * 32 + lane;
+    if (f >= d) return;
     double *P = partial + b * (int64_t)k * d;
-    for (int e = threadIdx.x; e < k * d; e += blockDim.x) P[e] = S[e];
-    for (int j = threadIdx.x; j < k; j += blockDim.x) {
-        long long cnt = 0;
-        for (int64_t i = lo; i < hi; ++i) cnt += (sc[i - lo] == j);
-        counts[b * k + j] = cnt;
+    const double *Xb = X + lo * d + f;
+    for (int j = cg; j < k; j += cg_count) {
+        double acc = 0.0;
+        int r = start[j];
+        const int e = start[j + 1];
+        for (; r + 4 <= e; r += 4) {
+            const double v0 = Xb[(int64_t)order[r] * d], v1 = Xb[(int64_t)order[r + 1] * d];
+            const double v2 = Xb[(int64_t)order[r + 2] * d], v3 = Xb[(int64_t)order[r + 3] * d];
+            acc = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn(acc, v0), v1), v2), v3);
+        }
+        for (; r < e; ++r) acc = __dadd_rn(acc, Xb[(int64_t)order[r] * d]);
+        P[(size_t)j * d + f] = acc;
     }
 }
 
-// thread per (cluster, feature): pairwise tree over blocks in place, then divide
-__global__ void kmeans_tree_divide_kernel(double *__restrict__ partial, const long long *__restrict__ counts,
-                                          int64_t nblk, int32_t k, int32_t d, double *__restrict__ C) {
-    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (int64_t)k * d) return;
-    int j = (int)(e / d);
-    const int64_t stride = (int64_t)k * d;
+// Pairwise tree over the block sums (level by level: element q of a level is
+// element 2q + element 2q + 1 of the one below, an odd last element carried
+// up unchanged), then one division by the centre's count.  A CTA takes TE
+// consecutive (centre, feature) entries and keeps both levels of the tree in
+// shared memory (ping-pong), so every addition reads shared memory.
+constexpr int TREE_THREADS = 256;
+__global__ void kmeans_tree_divide_kernel(const double *__restrict__ partial, const long long *__restrict__ counts,
+                                          int64_t nblk, int32_t k, int32_t d, int32_t te, double *__restrict__ C) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double *buf0 = reinterpret_cast<double *>(smem_raw);  // [nblk][te]
+    double *buf1 = buf0 + nblk * te;
+    const int64_t kd = (int64_t)k * d;
+    const int64_t e0 = (int64_t)blockIdx.x * te;
+    const int ne = (int)min((int64_t)te, kd - e0);
+    for (int64_t x = threadIdx.x; x < nblk * te; x += blockDim.x) {
+        const int64_t b = x / te;
+        const int c = (int)(x % te);
+        buf0[x] = c < ne ? partial[b * kd + e0 + c] : 0.0;
+    }
+    __syncthreads();
+    double *src = buf0, *dst = buf1;
     int64_t len = nblk;
     while (len > 1) {
-        int64_t half = (len + 1) / 2;
-        for (int64_t q = 0; q < half; ++q) {
-            double a = partial[(2 * q) * stride + e];
-            double v = (2 * q + 1 < len) ? __dadd_rn(a, partial[(2 * q + 1) * stride + e]) : a;
-            partial[q * stride + e] = v;
+        const int64_t half = (len + 1) / 2;
+        for (int64_t x = threadIdx.x; x < half * te; x += blockDim.x) {
+            const int64_t q = x / te;
+            const int c = (int)(x % te);
+            const double a = src[(2 * q) * te + c];
+            dst[x] = (2 * q + 1 < len) ? __dadd_rn(a, src[(2 * q + 1) * te + c]) : a;
         }
+        __syncthreads();
+        double *tmp = src;
+        src = dst;
+        dst = tmp;
         len = half;
     }
-    long long cnt = 0;
-    for (int64_t b = 0; b < nblk; ++b) cnt += counts[b * k + j];
-    if (cnt > 0) C[e] = __ddiv_rn(partial[e], (double)cnt);
+    for (int c = threadIdx.x; c < ne; c += blockDim.x) {
+        const int64_t e = e0 + c;
+        const int j = (int)(e / d);
+        long long cnt = 0;
+        for (int64_t b = 0; b < nblk; ++b) cnt += counts[b * k + j];
+        if (cnt > 0) C[e] = __ddiv_rn(src[c], (double)cnt);
+    }
 }
 
 // ------------------------------------------------------------ stable gather
@@ -238,21 +402,37 @@ __global__ void gather_count_kernel(const int32_t *__restrict__ a, int64_t n, in
 }
 
 // one thread per partition: offsets and per-block starting positions
+// one CTA: thread j sums partition j's block counts, a scan over partitions
+// gives the partition starts, then each thread turns its counts into block
+// starts (stable: block order, then row order inside a block)
 __global__ void gather_scan_kernel(long long *__restrict__ bcount, int64_t nblk, int32_t p,
                                    int64_t *__restrict__ offsets) {
-    __shared__ long long tot_sh[1];
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
+    extern __shared__ unsigned char smem_raw[];
+    long long *tot = reinterpret_cast<long long *>(smem_raw);  // [p]
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        long long run = 0;
+        for (int64_t b = 0; b < nblk; ++b) run += bcount[b * p + j];
+        tot[j] = run;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         long long run = 0;
         for (int j = 0; j < p; ++j) {
+            const long long c = tot[j];
+            tot[j] = run;
             offsets[j] = run;
-            for (int64_t b = 0; b < nblk; ++b) {
-                long long c = bcount[b * p + j];
-                bcount[b * p + j] = run;
-                run += c;
-            }
+            run += c;
         }
         offsets[p] = run;
-        tot_sh[0] = run;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+        long long run = tot[j];
+        for (int64_t b = 0; b < nblk; ++b) {
+            const long long c = bcount[b * p + j];
+            bcount[b * p + j] = run;
+            run += c;
+        }
     }
 }
 
@@ -282,7 +462,8 @@ krr_status run_gather(Ctx *ctx, const int32_t *assign, int64_t n, int32_t p, int
     if (nblk > 0) {
         KRR_LAUNCHED(), gather_count_kernel<<<(unsigned)nblk, 256, p * sizeof(int), st>>>(assign, n, p, bcount);
     }
-    KRR_LAUNCHED(), gather_scan_kernel<<<1, 32, 0, st>>>(bcount, nblk, p, offsets);
+    KRR_CUDA_TRY(ctx, allow_max_dyn_smem(gather_scan_kernel));
+    KRR_LAUNCHED(), gather_scan_kernel<<<1, 1024, (size_t)p * sizeof(long long), st>>>(bcount, nblk, p, offsets);
     if (nblk > 0) {
         KRR_LAUNCHED(), gather_scatter_kernel<<<(unsigned)nblk, 128, CANON * sizeof(int32_t), st>>>(assign, n, p, bcount, perm);
     }
@@ -314,6 +495,31 @@ krr_status run_partition_random(Ctx *ctx, int64_t n, int32_t p, uint64_t seed, i
 krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, int32_t d, const double *C64,
                       const float *C32, int32_t k, const int32_t *prev, int32_t *out, unsigned long long *delta) {
     if (n == 0) return KRR_OK;
+    const int dp = (d + 7) / 8 * 8, k4 = (k + 3) / 4 * 4;
+    const size_t sm2 = ((size_t)dp * k4 + k4 + (size_t)k4 * ASSIGN2_THREADS) * sizeof(float);
+    if (dp <= 96 && sm2 <= 200 * 1024) {
+        auto launch = [&](auto kern) -> krr_status {
+            KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kern));
+            KRR_LAUNCHED(), kern<<<grid_for(n, ASSIGN2_THREADS), ASSIGN2_THREADS, sm2, ctx->stream>>>(
+                X32, X, n, d, C64, C32, k, k4, prev, out, delta);
+            KRR_CUDA_TRY(ctx, cudaGetLastError());
+            return KRR_OK;
+        };
+        switch (dp) {
+            case 8: return launch(kmeans_assign_reg_kernel<8>);
+            case 16: return launch(kmeans_assign_reg_kernel<16>);
+            case 24: return launch(kmeans_assign_reg_kernel<24>);
+            case 32: return launch(kmeans_assign_reg_kernel<32>);
+            case 40: return launch(kmeans_assign_reg_kernel<40>);
+            case 48: return launch(kmeans_assign_reg_kernel<48>);
+            case 56: return launch(kmeans_assign_reg_kernel<56>);
+            case 64: return launch(kmeans_assign_reg_kernel<64>);
+            case 72: return launch(kmeans_assign_reg_kernel<72>);
+            case 80: return launch(kmeans_assign_reg_kernel<80>);
+            case 88: return launch(kmeans_assign_reg_kernel<88>);
+            default: return launch(kmeans_assign_reg_kernel<96>);
+        }
+    }
     size_t sm = ((size_t)k * d + k + (size_t)d * ASSIGN_THREADS) * sizeof(float) + 16;
     if (sm > 200 * 1024) {
         ctx->last_error = "kmeans: k*d too large for the shared-memory centre copy";
@@ -331,16 +537,26 @@ krr_status run_update(Ctx *ctx, const double *X, int64_t n, int32_t d, const int
                       double *partial, long long *counts) {
     int64_t nblk = (n + CANON - 1) / CANON;
     if (nblk == 0) return KRR_OK;
-    size_t sm = (size_t)k * d * sizeof(double) + CANON * sizeof(int32_t);
-    if (sm > 200 * 1024) {
-        ctx->last_error = "kmeans: k*d too large for the shared-memory block sums";
+    const size_t sm = (2 * (size_t)CANON + 2 * (size_t)k + 1) * sizeof(int32_t);
+    const int fcs = (d + 31) / 32;
+    if (fcs > 32) {
+        ctx->last_error = "kmeans: more than 1024 features";
         return KRR_ERR_UNSUPPORTED;
     }
-    if (sm > 48 * 1024)
-        KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_block_sums_kernel));
-    KRR_LAUNCHED(), kmeans_block_sums_kernel<<<(unsigned)nblk, 128, sm, ctx->stream>>>(X, n, d, c, k, partial, counts);
-    KRR_LAUNCHED(), kmeans_tree_divide_kernel<<<grid_for((int64_t)k * d, 128), 128, 0, ctx->stream>>>(partial, counts, nblk, k, d,
-                                                                                     C);
+    const int cgs = std::max(1, std::min(8, 32 / fcs));  // centre groups: up to 1024 threads
+    KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_block_sums_kernel));
+    KRR_LAUNCHED(), kmeans_block_sums_kernel<<<(unsigned)nblk, 32 * fcs * cgs, sm, ctx->stream>>>(
+        X, n, d, c, k, cgs, partial, counts);
+    int te = 32;  // entries per CTA: both tree levels within ~128 KiB of shared memory
+    while (te > 1 && 2 * (size_t)nblk * te * sizeof(double) > 128 * 1024) te /= 2;
+    if (2 * (size_t)nblk * te * sizeof(double) > 200 * 1024) {
+        ctx->last_error = "kmeans: too many row blocks for the shared-memory centre tree";
+        return KRR_ERR_UNSUPPORTED;
+    }
+    KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_tree_divide_kernel));
+    KRR_LAUNCHED(), kmeans_tree_divide_kernel<<<(unsigned)(((int64_t)k * d + te - 1) / te), TREE_THREADS,
+                                                2 * (size_t)nblk * te * sizeof(double), ctx->stream>>>(
+        partial, counts, nblk, k, d, te, C);
     KRR_CUDA_TRY(ctx, cudaGetLastError());
     return KRR_OK;
 }
