@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "fp32", "fp64"])
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "bf16x3", "fp32", "fp64"])
     ap.add_argument("--panel", type=int, default=0, help="Cholesky outer panel width (0 = library default)")
     ap.add_argument("--cpu-sample", type=int, default=0, help="oracle solves in the CPU baseline (0 = auto)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -265,7 +265,7 @@ def run_ours(args, rank, world, local_rank):
         model.free()
         Wt = ctypes_int()
         sizes = np.diff(offsets.cpu().numpy())
-        ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2}[args.prec],
+        ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}[args.prec],
                                         int((sizes.max() + 127) // 128), ctypes.byref(Wt))
         sys.stderr.write("partition sizes: min %d max %d\n" % (sizes.min(), sizes.max()))
         sys.stderr.write("refinement iterations per (sigma, lambda): %s; panel width %d\n" % (
@@ -527,7 +527,7 @@ def main():
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32+f64" if args.prec == "tf32" else ("f32+f64" if args.prec == "fp32" else "f64"),
+        "vs_baseline": None, "dtype": {"tf32": "tf32+f64", "bf16x3": "bf16x3+f64", "fp32": "f32+f64"}.get(args.prec, "f64"),
         "data": "synthetic",
         "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": args.prec,
                    "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]),

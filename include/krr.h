@@ -44,12 +44,15 @@ typedef enum {
 typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1 } krr_part_mode;
 
 /* Arithmetic of the kernel build, the Cholesky factor and its refinement.
- * FP64:  FP64 kernel, FP64 Cholesky, FP64 refinement (the plain path).
- * FP32:  FP32 factor of the double-float (~44-bit) kernel, FP32 trailing
- *        updates; conjugate-gradient refinement with double-float residuals.
- * TF32:  as FP32 but the Cholesky trailing updates run on the tcgen05 tensor
- *        cores in TF32 with FP32 accumulation.                               */
-typedef enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_TF32 = 2 } krr_prec;
+ * FP64:   FP64 kernel, FP64 Cholesky, FP64 refinement (the plain path).
+ * FP32:   FP32 factor of the double-float (~44-bit) kernel with FP32-class
+ *         trailing updates (three TF32 tensor-core passes on hi/lo splits);
+ *         conjugate-gradient refinement with double-float residuals.
+ * TF32:   as FP32 but the trailing updates take one TF32 pass.
+ * BF16X3: as FP32 but the trailing updates take three BF16 passes on
+ *         split-BF16 operands (hi = rn(x), lo = rn(x - hi)), ~16-bit
+ *         products with FP32 accumulation.                                   */
+typedef enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_TF32 = 2, KRR_PREC_BF16X3 = 3 } krr_prec;
 
 /* Model choice (Eq. 3 scores):
  * PER_MODEL: one MSE per (partition, sigma, lambda) model; best model.
@@ -201,11 +204,11 @@ krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t 
  *   2^-46 of the scaled residual, whichever comes first.  0 always runs to the
  *   floor.  The plain FP64 path always runs to its floor 2^-50.  Errors:
  *   KRR_ERR_ARG (rel < 0 or rel > 1e-2).
- * krr_ctx_set_escalation: with KRR_PREC_TF32, a solve whose Gershgorin
- *   condition estimate times 2^-11 exceeds `kappa_u` (default 32) has its
- *   trailing updates run in the FP32-class three-pass mode instead of one TF32
- *   pass (a TF32 factor is then too poor a preconditioner); 0 escalates every
- *   solve.  Errors: KRR_ERR_ARG (negative).
+ * krr_ctx_set_escalation: with KRR_PREC_TF32 (KRR_PREC_BF16X3), a solve whose
+ *   Gershgorin condition estimate times 2^-11 (2^-16) exceeds `kappa_u`
+ *   (default 32) has its trailing updates run in the FP32-class three-pass
+ *   TF32 mode instead (the cheaper factor is then too poor a preconditioner);
+ *   0 escalates every solve.  Errors: KRR_ERR_ARG (negative).
  * krr_launch_count: kernels launched by this process through libkrr. */
 krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
 krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);

@@ -20,9 +20,9 @@ from . import build as _build
 KRR_OK, KRR_ERR_ARG, KRR_ERR_OOM, KRR_ERR_BUDGET, KRR_ERR_CUDA = 0, 1, 2, 3, 4
 KRR_ERR_NOT_SPD, KRR_ERR_NO_CONVERGE, KRR_ERR_TIMEOUT, KRR_ERR_UNSUPPORTED = 5, 6, 7, 8
 KRR_PART_RANDOM, KRR_PART_KMEANS = 0, 1
-KRR_PREC_FP64, KRR_PREC_FP32, KRR_PREC_TF32 = 0, 1, 2
+KRR_PREC_FP64, KRR_PREC_FP32, KRR_PREC_TF32, KRR_PREC_BF16X3 = 0, 1, 2, 3
 KRR_SEL_PER_MODEL, KRR_SEL_ROUTED, KRR_SEL_AVERAGE, KRR_SEL_ORACLE = 0, 1, 2, 3
-PREC_NAMES = {"fp64": KRR_PREC_FP64, "fp32": KRR_PREC_FP32, "tf32": KRR_PREC_TF32}
+PREC_NAMES = {"fp64": KRR_PREC_FP64, "fp32": KRR_PREC_FP32, "tf32": KRR_PREC_TF32, "bf16x3": KRR_PREC_BF16X3}
 STATUS_NAMES = {0: "OK", 1: "ARG", 2: "OOM", 3: "BUDGET", 4: "CUDA", 5: "NOT_SPD", 6: "NO_CONVERGE",
                 7: "TIMEOUT", 8: "UNSUPPORTED"}
 # kernel classes timed by krr_ctx_profile

@@ -317,7 +317,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     if (!ctx) return KRR_ERR_ARG;
     Ctx *c = &ctx->c;
     if (!out || !X || !y || !perm || !offsets || !sigmas || !lambdas || n <= 0 || d <= 0 || p <= 0 || ns <= 0 ||
-        nl <= 0 || ns > 8 || nl > 8 || (prec != KRR_PREC_FP64 && prec != KRR_PREC_FP32 && prec != KRR_PREC_TF32))
+        nl <= 0 || ns > 8 || nl > 8 || (prec != KRR_PREC_FP64 && prec != KRR_PREC_FP32 && prec != KRR_PREC_TF32 && prec != KRR_PREC_BF16X3))
         return fail(c, KRR_ERR_ARG, "krr_fit_batch: invalid argument (1 <= ns, nl <= 8)");
     for (int i = 0; i < ns; ++i)
         if (!(sigmas[i] > 0.0) || !std::isfinite(sigmas[i]))
@@ -329,6 +329,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     cudaStream_t st = c->stream;
     const bool fp64 = prec == KRR_PREC_FP64;
     const bool tf32 = prec == KRR_PREC_TF32;
+    const bool bf16x3 = prec == KRR_PREC_BF16X3;
     Prof *prof = c->prof.on ? &c->prof : nullptr;
 
     // partition sizes on the host
@@ -537,20 +538,22 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));
         FIT_TRY(cudaStreamSynchronize(st));
 
-        // factor class per solve: FP64 path -> FP64; FP32 -> 3-pass; TF32 -> 1-pass
-        // unless kappa_est * 2^-11 exceeds the escalation threshold (then 3-pass)
+        // factor class per solve: FP64 path -> FP64; FP32 -> 3-pass TF32; TF32 ->
+        // 1-pass unless kappa_est * 2^-11 exceeds the escalation threshold;
+        // BF16x3 -> 3-pass BF16 unless kappa_est * 2^-16 exceeds it (then 3-pass TF32)
         CUtensorMap tmap, tmapZ;
         memset(&tmap, 0, sizeof(tmap));
         memset(&tmapZ, 0, sizeof(tmapZ));
         if (!fp64 && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles)))
             return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
-        std::vector<int> cls(nsolve, fp64 ? 0 : (tf32 ? 1 : 3));  // update class per solve
+        const int base_cls = fp64 ? 0 : (tf32 ? 1 : (bf16x3 ? 2 : 3));
+        std::vector<int> cls(nsolve, base_cls);  // update class per solve
         M.st_class.assign(nsolve, 0);
-        if (tf32 && c->escalate > 0.0)
+        if ((tf32 || bf16x3) && c->escalate > 0.0)
             for (int s = 0; s < nsolve; ++s) {
                 const double lm = M.solves[s].lambda_m;
                 const double kap = lm > 0.0 ? hs0[s].anorm / lm : INFINITY;
-                if (kap * std::ldexp(1.0, -11) > c->escalate) cls[s] = 3;
+                if (kap * std::ldexp(1.0, tf32 ? -11 : -16) > c->escalate) cls[s] = 3;
             }
         for (int s = 0; s < nsolve; ++s) M.st_class[s] = cls[s];
 
@@ -560,7 +563,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         // on these matrices (restored from K_hi between trials)
         std::vector<int> Ts(nsolve);
         for (int s = 0; s < nsolve; ++s) Ts[s] = M.solves[s].T;
-        const int tcmode = fp64 ? 0 : (tf32 ? 1 : 3);  // tensor-core mode of the factor (0: SIMT FP64)
+        const int tcmode = base_cls;  // tensor-core mode of the factor (0: SIMT FP64)
         int Wp = c->chol_W;
         const std::pair<int, int> key((int)prec, maxT);
         if (Wp <= 0 && c->tuned_W.count(key)) Wp = c->tuned_W[key];

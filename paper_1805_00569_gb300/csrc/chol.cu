@@ -24,6 +24,8 @@
 // L_ik = A_ik Z_kk^T always runs as three passes (an FP32-class product).
 #include <algorithm>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -304,18 +306,42 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 // other one back (tcgen05.ld) for the epilogue of the previous task (A_ij -= C,
 // or A_ik = C for the panel solve), so loads, MMAs and epilogues of
 // consecutive tasks overlap and the per-CTA setup is paid once per launch.
-// X3 = false: one kind::tf32 MMA per K step (the tensor core reads the top 19
-// bits of each FP32 operand).  X3 = true: warps 6..9 split each landed stage
+// TC_TF32: one kind::tf32 MMA per K step (the tensor core reads the top 19
+// bits of each FP32 operand).  TC_BF16X3: warps 6..9 convert each landed FP32
+// stage into BF16 hi = rn(x) and lo = rn(x - hi) operands and three kind::f16
+// MMAs per K step form hi*hi + hi*lo + lo*hi (~16-bit products at the BF16
+// rate).  TC_TF32X3: warps 6..9 split each landed stage
 // into hi = x with the low 13 mantissa bits cleared and lo = x - hi (exact),
 // and three MMAs per K step form hi*hi + hi*lo + lo*hi: FP32-class products on
 // the tensor cores.
 constexpr int TC_CHUNK = 32;                                       // floats of K per stage (128 bytes)
 constexpr uint32_t TC_HALF = (uint32_t)KRR_TILE * TC_CHUNK * 4;     // one operand tile chunk, 16 KB
 constexpr uint32_t TC_IDESC = make_idesc(2u /*TF32*/, 128u, 128u);
-template <bool X3> struct TcCfg {
-    static constexpr int STAGES = X3 ? 2 : 3;
-    static constexpr uint32_t STAGE_BYTES = (X3 ? 4u : 2u) * TC_HALF;  // A, B (+ A_lo, B_lo)
-    static constexpr int THREADS = X3 ? 320 : 192;
+constexpr uint32_t TC_IDESC_BF16 = make_idesc(1u /*BF16*/, 128u, 128u);
+constexpr uint32_t TC_BHALF = (uint32_t)KRR_TILE * TC_CHUNK * 2;  // one BF16 operand chunk, 8 KB
+
+// Shared-memory descriptor, K-major operand with the 64-byte swizzle (8-row x
+// 64-byte atoms, 512 bytes apart along M/N): the BF16 hi/lo operands.
+__device__ __forceinline__ uint64_t smem_desc_sw64_tc(const void *p) {
+    uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr & 0x3FFFFull) >> 4;
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+// MODE: TC_TF32 one pass; TC_TF32X3 three TF32 passes on hi/lo splits;
+// TC_BF16X3 three BF16 passes (kind::f16) on hi/lo BF16 splits
+enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
+template <int MODE> struct TcCfg {
+    static constexpr bool SPLIT = MODE != TC_TF32;
+    static constexpr int STAGES = SPLIT ? 2 : 3;
+    // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
+    // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
+    static constexpr uint32_t STAGE_BYTES = (SPLIT ? 4u : 2u) * TC_HALF;
+    static constexpr int THREADS = SPLIT ? 320 : 192;
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
 };
 
@@ -338,12 +364,13 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
     }
 }
 
-template <bool X3>
-__global__ void __launch_bounds__(TcCfg<X3>::THREADS, 1)
+template <int MODE>
+__global__ void __launch_bounds__(TcCfg<MODE>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
                 float *__restrict__ A, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
                 int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
-    using Cfg = TcCfg<X3>;
+    using Cfg = TcCfg<MODE>;
+    constexpr bool X3 = Cfg::SPLIT;
     constexpr int KCH = KRR_TILE / TC_CHUNK;  // chunks per K tile
     extern __shared__ unsigned char tc_dyn[];
     const uint32_t base = smem_u32(tc_dyn);
@@ -440,15 +467,30 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 tc_fence_after();
                 unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
                 unsigned char *sb = sa + TC_HALF;
-                const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+                if constexpr (MODE == TC_BF16X3) {
+                    // BF16 hi/lo operands after the two FP32 chunks: A_hi, A_lo, B_hi, B_lo
+                    unsigned char *sp = sa + 2 * TC_HALF;
+                    const uint64_t dah = smem_desc_sw64_tc(sp), dal = smem_desc_sw64_tc(sp + TC_BHALF);
+                    const uint64_t dbh = smem_desc_sw64_tc(sp + 2 * TC_BHALF), dbl = smem_desc_sw64_tc(sp + 3 * TC_BHALF);
 #pragma unroll
-                for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
-                    const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
-                    tc_mma_tf32(acc, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
-                    if (X3) {
-                        const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF), dbl = smem_desc_sw128(sb + 2 * TC_HALF);
-                        tc_mma_tf32(acc, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
-                        tc_mma_tf32(acc, dal + 2 * kk, db + 2 * kk, TC_IDESC, 1u);
+                    for (int kk = 0; kk < TC_CHUNK / 16; ++kk) {  // K = 16 BF16 = 32 bytes per MMA
+                        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+                        tc_mma_f16(acc, dah + 2 * kk, dbh + 2 * kk, TC_IDESC_BF16, acc0);
+                        tc_mma_f16(acc, dah + 2 * kk, dbl + 2 * kk, TC_IDESC_BF16, 1u);
+                        tc_mma_f16(acc, dal + 2 * kk, dbh + 2 * kk, TC_IDESC_BF16, 1u);
+                    }
+                } else {
+                    const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+#pragma unroll
+                    for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
+                        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+                        tc_mma_tf32(acc, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
+                        if (X3) {
+                            const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF),
+                                           dbl = smem_desc_sw128(sb + 2 * TC_HALF);
+                            tc_mma_tf32(acc, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
+                            tc_mma_tf32(acc, dal + 2 * kk, db + 2 * kk, TC_IDESC, 1u);
+                        }
                     }
                 }
                 tc_commit(&empty[st]);
@@ -471,21 +513,49 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                     ok = false;
                     break;
                 }
-                float4 *hi = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES);
-                float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
+                if constexpr (MODE == TC_BF16X3) {
+                    // FP32 chunk (128-byte swizzle: 16-byte unit q of row r at q ^ (r % 8))
+                    // -> BF16 hi = rn(x), lo = rn(x - hi) (64-byte swizzle: 16-byte unit c of
+                    // row r at c ^ ((r % 8) >> 1)); operand o = 0 (A), 1 (B)
+                    unsigned char *stage = buf + st * Cfg::STAGE_BYTES;
 #pragma unroll 4
-                for (int e = tsp; e < (int)(2 * TC_HALF / 16); e += 128) {
-                    float4 v = hi[e], h, l;
-                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                    l.x = v.x - h.x;
-                    l.y = v.y - h.y;
-                    l.z = v.z - h.z;
-                    l.w = v.w - h.w;
-                    hi[e] = h;
-                    lo[e] = l;
+                    for (int e = tsp; e < 2 * KRR_TILE * (TC_CHUNK / 4); e += 128) {
+                        const int o = e / (KRR_TILE * (TC_CHUNK / 4));
+                        const int r = (e / (TC_CHUNK / 4)) % KRR_TILE, q = e % (TC_CHUNK / 4);
+                        const float4 v = *reinterpret_cast<const float4 *>(
+                            stage + o * TC_HALF + (r >> 3) * 1024 + (r & 7) * 128 + ((q ^ (r & 7)) << 4));
+                        const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+                        const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+                        const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+                        const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+                        const __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
+                        const __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+                        const uint32_t off = (uint32_t)(r >> 3) * 512 + (r & 7) * 64 +
+                                             ((((uint32_t)q >> 1) ^ ((r & 7) >> 1)) << 4) + (q & 1) * 8;
+                        unsigned char *ph = stage + 2 * TC_HALF + (2 * o) * TC_BHALF + off;
+                        unsigned char *pl = ph + TC_BHALF;
+                        *reinterpret_cast<__nv_bfloat162 *>(ph) = __halves2bfloat162(h0, h1);
+                        *reinterpret_cast<__nv_bfloat162 *>(ph + 4) = __halves2bfloat162(h2, h3);
+                        *reinterpret_cast<__nv_bfloat162 *>(pl) = __halves2bfloat162(l0, l1);
+                        *reinterpret_cast<__nv_bfloat162 *>(pl + 4) = __halves2bfloat162(l2, l3);
+                    }
+                } else {
+                    float4 *hi = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES);
+                    float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
+#pragma unroll 4
+                    for (int e = tsp; e < (int)(2 * TC_HALF / 16); e += 128) {
+                        float4 v = hi[e], h, l;
+                        h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                        h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                        h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                        h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                        l.x = v.x - h.x;
+                        l.y = v.y - h.y;
+                        l.z = v.z - h.z;
+                        l.w = v.w - h.w;
+                        hi[e] = h;
+                        lo[e] = l;
+                    }
                 }
                 fence_proxy_async_smem();  // generic-proxy writes -> visible to the tensor core
                 __syncwarp();
@@ -655,16 +725,22 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
             // tensor cores: the panel solve always FP32-class (3 passes); the
             // trailing updates 1 pass (TF32) or 3 passes (FP32), per launch class
             if (tc != 0) {
-                const bool x3 = (L.kind == 1) || L.tc == 3;
+                // the panel solve always FP32-class; updates per class: 1 TF32, 2 BF16x3, 3 TF32x3
+                const int m = (L.kind == 1 || L.tc == 3) ? TC_TF32X3 : (L.tc == 2 ? TC_BF16X3 : TC_TF32);
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
-                if (x3)
-                    KRR_LAUNCHED(), tile_mma_kernel<true><<<pgrid, TcCfg<true>::THREADS, TcCfg<true>::SMEM, st>>>(
-                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, L.tasks, mode, L.K0, W,
-                        d_err);
+                float *Af = reinterpret_cast<float *>(A);
+                if (m == TC_TF32X3)
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
+                                                                 TcCfg<TC_TF32X3>::SMEM, st>>>(
+                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                else if (m == TC_BF16X3)
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_BF16X3><<<pgrid, TcCfg<TC_BF16X3>::THREADS,
+                                                                 TcCfg<TC_BF16X3>::SMEM, st>>>(
+                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else
-                    KRR_LAUNCHED(), tile_mma_kernel<false><<<pgrid, TcCfg<false>::THREADS, TcCfg<false>::SMEM, st>>>(
-                        *tmap, *tmapZ, reinterpret_cast<float *>(A), d_solves, p, nsolve, L.tasks, mode, L.K0, W,
-                        d_err);
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32><<<pgrid, TcCfg<TC_TF32>::THREADS,
+                                                              TcCfg<TC_TF32>::SMEM, st>>>(
+                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 continue;
             }
         }
@@ -678,8 +754,9 @@ cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, 
                           bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
                           const CUtensorMap *tmap, const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
     // set on every call: the attribute is per device
-    allow_max_dyn_smem(tile_mma_kernel<false>);
-    allow_max_dyn_smem(tile_mma_kernel<true>);
+    allow_max_dyn_smem(tile_mma_kernel<TC_TF32>);
+    allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3>);
+    allow_max_dyn_smem(tile_mma_kernel<TC_BF16X3>);
     if (fp64)
         return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, d_solves, nsolve, flags, 0, tmap,
                                        tmapZ, d_err, prof);

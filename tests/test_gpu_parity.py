@@ -132,7 +132,7 @@ def oracle_case():
     return dict(X=X, y=y, Xt=Xt, yt=yt, perm=perm, offsets=offsets, alphas=al, infos=infos, rcs=rcs, yall=yall)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
 def test_fit_predict_select_parity(ctx, oracle_case, prec):
     c = oracle_case
     G = len(SIG) * len(LAM)
@@ -215,7 +215,7 @@ def test_dkrr_fp64_full_size(ctx):
         model.free()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32"])
+@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
 def test_bkrr2_full_size_sampled(ctx, prec):
     """The BKRR2 workload at full size (n = 65536, p = 16 x 4096, 3 sigma x 2
     lambda) in the benchmark's launch configuration; the oracle recomputes two
@@ -313,7 +313,7 @@ def test_sweep_full_size_sampled(ctx):
         oa, _, rc = oracle.fit(X[rows], y[rows], w["sigmas"][0], w["lambdas"][0])
         assert rc == 0
         refs[j] = (oa, oracle.predict(X[rows], oa, Xt[sample], w["sigmas"][0]))
-    for prec in ("tf32", "fp32"):
+    for prec in ("tf32", "bf16x3", "fp32"):
         model, status, alpha = K.krr_fit_batch(ctx, dX, cuda(y), perm, offsets, w["sigmas"], w["lambdas"], prec,
                                                want_alpha=True)
         try:
