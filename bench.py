@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--requests", type=int, default=1500, help="serve: requests replayed from the stream")
     ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (one stream each)")
     ap.add_argument("--fp64-sample", type=int, default=24, help="serve: requests in the sequential FP64 sample")
+    ap.add_argument("--precisions", default="",
+                    help="comma list (fp64,fp32,tf32,bf16x3): time the workload once per factor precision and "
+                         "report each in the line's precision_sweep object")
     ap.add_argument("--n", type=int, default=0, help="training rows (0 = the workload's; smaller: profiling cases)")
     ap.add_argument("--t", type=int, default=0, help="test rows (0 = the workload's)")
     ap.add_argument("--p", type=int, default=0, help="partitions (0 = the workload's)")
@@ -506,6 +509,17 @@ def main():
         torch.cuda.set_device(local_rank)
         tdist.init_process_group("nccl")
     res = run_ours(args, rank, world, local_rank)
+    sweep = None
+    if args.precisions:
+        sweep = {}
+        for pr in [x.strip() for x in args.precisions.split(",") if x.strip()]:
+            a2 = argparse.Namespace(**vars(args))
+            a2.prec, a2.no_fp64_path = pr, True
+            a2.steps = max(1, min(args.steps, 3)) if pr == "fp64" else args.steps
+            r2 = run_ours(a2, rank, world, local_rank)
+            sweep[pr] = {"value": r2["value"], "unit": UNIT, "ms_per_step": r2["ms_per_step"],
+                         "failed_solves": r2["bad"], "tflops": r2["tflops"],
+                         "stages_ms_per_step": {k: v[0] / a2.steps for k, v in r2["prof"].items()}}
     if world > 1:
         import torch.distributed as tdist
         tdist.destroy_process_group()
@@ -538,6 +552,8 @@ def main():
         "failed_solves": res["bad"], "best_model": res["best"], "best_mse": res["best_mse"],
         "stages_ms_per_step": {k: v[0] / args.steps for k, v in res["prof"].items()},
     }
+    if sweep is not None:
+        line["precision_sweep"] = sweep
     print(json.dumps(line))
 
 

@@ -38,7 +38,7 @@ typedef enum {
     KRR_ERR_NOT_SPD = 5,      /* per solve: K + lambda m I not positive definite */
     KRR_ERR_NO_CONVERGE = 6,  /* per solve: refinement did not reach tolerance   */
     KRR_ERR_TIMEOUT = 7,      /* a bounded device-side wait expired              */
-    KRR_ERR_UNSUPPORTED = 8   /* a valid request this build does not implement   */
+    KRR_ERR_UNSUPPORTED = 8   /* a valid request the library does not implement  */
 } krr_status;
 
 typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1 } krr_part_mode;

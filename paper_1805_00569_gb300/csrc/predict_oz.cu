@@ -9,7 +9,8 @@
 // below 2^(e_a+e_b) * 96 * 2^-37).  Each S_L is an integer below 2^23, so the
 // bf16 MMAs accumulate it exactly in FP32: no rounding happens on the tensor
 // cores at all, and the distance ||a||^2 + ||b||^2 - 2 a.b is assembled in
-// double-float (~1e-10 relative, what the kernel values need: see the design doc).
+// double-float (~1e-11 relative to the norms, the size of the dropped slice
+// products; the kernel values need ~1e-10).
 //
 // Kernel layout, one CTA per (partition, 128 test rows):
 //   warp 0, one thread: TMA producer -- the 5 slices of the next 64 training
@@ -114,6 +115,28 @@ __device__ __forceinline__ bool oz_wait(uint64_t *bar, uint32_t parity, int *err
             return false;
         }
     }
+}
+
+// Squared distance ||a||^2 + ||b||^2 - 2 a.b from the five exact slice levels
+// S_L of the scaled Gram G = S0 + 2^-8 S1 + 2^-16 S2 + 2^-24 S3 + 2^-32 S4:
+// S0 + 2^-8 S1 exactly by TwoSum; the three lower levels (below 2^8 in size)
+// in FP32, folded into the low part (rounding ~2^-17 absolute in G, below the
+// size of the dropped slice products); then (na + nb) - 2^sc G with TwoSums on
+// the high parts, the low parts summed in FP32 and one Fast2Sum to normalise.
+// Clamped at 0 (rounding can leave a tiny negative for coincident rows).
+__device__ __forceinline__ df oz_distance(float s0, float s1, float s2, float s3, float s4, df na, float nbh,
+                                          float nbl, float scale) {
+    float h, l;
+    two_sum(s0, s1 * 0x1p-8f, h, l);
+    l = __fadd_rn(l, __fmaf_rn(s2, 0x1p-16f, __fmaf_rn(s3, 0x1p-24f, s4 * 0x1p-32f)));
+    float t1, e1, t2, e2;
+    two_sum(na.hi, nbh, t1, e1);
+    two_sum(t1, -h * scale, t2, e2);
+    const float lo = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(na.lo, nbl)), -l * scale);
+    df D;
+    fast_two_sum(t2, lo, D.hi, D.lo);
+    if (D.hi < 0.f) D = df_make(0.f, 0.f);
+    return D;
 }
 
 // ---------------------------------------------------------------- slicing
@@ -315,19 +338,10 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 float dm = INFINITY;
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
-                    // G_scaled = S0 + 2^-8 S1 + 2^-16 S2 + 2^-24 S3 + 2^-32 S4 (all exact integers)
-                    float th, tl;
-                    two_sum(lv[3][k] * 0x1p-24f, lv[4][k] * 0x1p-32f, th, tl);
-                    df u = df_make(th, tl);
-                    u = df_add(df_make(lv[2][k] * 0x1p-16f, 0.f), u);
-                    u = df_add(df_make(lv[1][k] * 0x1p-8f, 0.f), u);
-                    u = df_add(df_make(lv[0][k], 0.f), u);
                     const int col = (int)col0 + k;
                     const int sc = eq + cd.e[col] - 13;  // factor 2 of -2 a.b folded in
-                    const float s2 = __int_as_float((127 + sc) << 23);
-                    df D = df_add(nq, df_make(cd.nh[col], cd.nl[col]));
-                    D = df_add(D, df_make(-u.hi * s2, -u.lo * s2));
-                    if (D.hi < 0.f) D = df_make(0.f, 0.f);
+                    const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nq, cd.nh[col],
+                                             cd.nl[col], __int_as_float((127 + sc) << 23));
                     sm.dist[et][k] = make_float2(D.hi, D.lo);
                     if (c * OZ_N + col < P.m) dm = fminf(dm, D.hi);
                 }
@@ -578,18 +592,10 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
-                    float th, tl;
-                    two_sum(lv[3][k] * 0x1p-24f, lv[4][k] * 0x1p-32f, th, tl);
-                    df u = df_make(th, tl);
-                    u = df_add(df_make(lv[2][k] * 0x1p-16f, 0.f), u);
-                    u = df_add(df_make(lv[1][k] * 0x1p-8f, 0.f), u);
-                    u = df_add(df_make(lv[0][k], 0.f), u);
                     const float2 nc2 = nrm[pc];
                     const int sc = er + ex[pc] - 13;
-                    const float s2 = __int_as_float((127 + sc) << 23);
-                    df D = df_add(nr, df_make(nc2.x, nc2.y));
-                    D = df_add(D, df_make(-u.hi * s2, -u.lo * s2));
-                    if (D.hi < 0.f) D = df_make(0.f, 0.f);
+                    const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nr, nc2.x, nc2.y,
+                                             __int_as_float((127 + sc) << 23));
                     dh[k] = D.hi;
                     dl[k] = D.lo;
                 }
