@@ -357,7 +357,7 @@ def run_ours(args, rank, world, local_rank):
 # DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
 # capture of this bench's workload (profiles/launch_list_bkrr2_n65536_p16.md);
 # an entry is removed whenever its kernel changes.
-TRAFFIC = {("predict", "bkrr2_n65536_t8192_d90_p16"): 276918784 + 7724288}
+TRAFFIC = {}
 
 
 def roofline(res, steps, peaks):

@@ -178,7 +178,47 @@ __global__ void oz_slice_kernel(const double *__restrict__ X, int32_t d, int32_t
 }
 
 // ---------------------------------------------------------------- predict
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+// Prediction CTA: 18 warps -- TMA producer, MMA issuer and 16 epilogue warps
+// (4 TMEM lane quadrants x 4 column quarters of a 64-column chunk; the
+// quarters' partial sums meet at the end in the fixed order
+// (q0 + q1) + (q2 + q3)).
+constexpr int OZP_EPI_WARPS = 16;
+constexpr int OZP_EPI = OZP_EPI_WARPS * 32;                // epilogue threads
+constexpr int OZP_THREADS = (OZ_EPI_WARP0 + OZP_EPI_WARPS) * 32;
+constexpr int OZP_SUB = 8;                                 // columns per TMEM read
+struct OzPSmem {
+    unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
+    unsigned char b[OZ_B_BYTES];
+    OzChunkData cd[2];
+    float2 exptab[256];
+    float2 comb[2][OZ_NSP * OZ_NLP][OZ_M];       // quarter partial sums on their way to quarter 0
+    int combk[2][OZ_NSP][OZ_M];                  // and their range shifts
+    float2 shift[OZ_NSP][OZP_EPI];               // per epilogue thread: -K ln2 per sigma (df)
+    float2 dist[OZP_EPI][OZP_SUB + 1];           // per epilogue thread: 8 distances (padded row)
+    uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
+    uint64_t b_full, b_empty, t_full, t_empty;
+    uint32_t tmem;
+};
+static_assert(sizeof(OzPSmem) + 1024 <= 232448, "prediction CTA exceeds the opt-in shared memory");
+__device__ __forceinline__ void epi_bar_p() { asm volatile("bar.sync 1, %0;" ::"n"(OZP_EPI) : "memory"); }
+__device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+// a (shift ka) + b (shift kb) at the larger shift; *k receives it
+__device__ __forceinline__ df oz_combine(df a, int ka, df b, int kb, int *k) {
+    const int km = max(ka, kb);
+    if (ka != km) a = df_scale2(a, pow2_nonpos(ka - km));
+    if (kb != km) b = df_scale2(b, pow2_nonpos(kb - km));
+    *k = km;
+    return df_add(a, b);
+}
+
+__global__ void __launch_bounds__(OZP_THREADS, 1)
 predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
                   const double *__restrict__ alpha, const int32_t *__restrict__ ex_train,
@@ -188,7 +228,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                   double *__restrict__ out, int *__restrict__ err) {
     extern __shared__ unsigned char oz_dyn[];
     const uint32_t base = smem_u32(oz_dyn);
-    OzSmem &sm = *reinterpret_cast<OzSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
+    OzPSmem &sm = *reinterpret_cast<OzPSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int j = blockIdx.x;
     const PartDesc P = parts[j];
@@ -207,7 +247,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         mbar_init(&sm.b_full, 1);
         mbar_init(&sm.b_empty, 1);
         mbar_init(&sm.t_full, 1);
-        mbar_init(&sm.t_empty, 8);
+        mbar_init(&sm.t_empty, OZP_EPI_WARPS);
         fence_mbar_init();
     }
     exp_table_init(sm.exptab);
@@ -278,9 +318,9 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         }
     } else if (warp >= OZ_EPI_WARP0) {
         // ---------------- epilogue
-        const int ew = warp - OZ_EPI_WARP0;       // 0..7
+        const int ew = warp - OZ_EPI_WARP0;       // 0..15
         const int quad = warp & 3;                // TMEM lane quadrant of this warp
-        const int half = ew >> 2;                 // column half of the chunk
+        const int quarter = ew >> 2;              // column quarter of the chunk
         const int row = quad * 32 + lane;         // test row inside the tile
         const int64_t grow = tstart + q0 + row;   // row in the (grouped) test slice array
         const bool live = q0 + row < cnt;
@@ -290,7 +330,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         df_acc acc[OZ_NSP][OZ_NLP];
         int ksh[OZ_NSP];       // range shift of the accumulators per sigma (exp_row_shift)
         float dmin = INFINITY;  // smallest distance to a real training row so far
-        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..255
+        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..511
 #pragma unroll
         for (int a = 0; a < OZ_NSP; ++a) {
             ksh[a] = KRR_SHIFT_NONE;  // no term yet: the shift argument stays 0
@@ -301,14 +341,14 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         for (int c = 0; c < nchunks; ++c) {
             OzChunkData &cd = sm.cd[c & 1];
             // training-side data of the chunk
-            for (int e = et; e < OZ_N; e += 256) {
+            for (int e = et; e < OZ_N; e += OZP_EPI) {
                 const int64_t pr = P.prow0 + (int64_t)c * OZ_N + e;
                 const float2 v = nrm_train[pr];
                 cd.nh[e] = v.x;
                 cd.nl[e] = v.y;
                 cd.e[e] = ex_train[pr];
             }
-            for (int e = et; e < G * OZ_N; e += 256) {
+            for (int e = et; e < G * OZ_N; e += OZP_EPI) {
                 const int g = e / OZ_N, col = e % OZ_N;
                 const int is = g / pp.nlam, il = g % pp.nlam;
                 const SolveDesc S =
@@ -318,26 +358,26 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 cd.ah[is * OZ_NLP + il][col] = h;
                 cd.al[is * OZ_NLP + il][col] = __double2float_rn(av - (double)h);
             }
-            epi_bar();
+            epi_bar_p();
             if (!oz_wait(&sm.t_full, c & 1, err)) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int sub = 0; sub < 2; ++sub) {
-                float lv[OZ_SLICES][16];
-                const uint32_t col0 = (uint32_t)(half * 32 + sub * 16);
+            for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
+                float lv[OZ_SLICES][OZP_SUB];
+                const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
 #pragma unroll
                 for (int L = 0; L < OZ_SLICES; ++L)
-                    tmem_ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
+                    tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
                 tmem_wait_ld();
-                if (sub == 1) {
+                if (sub == (OZ_N / 4) / OZP_SUB - 1) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sm.t_empty);
                 }
-                // distances of the 16 columns (static register indices), parked in shared memory
+                // distances of the columns (static register indices), parked in shared memory
                 float dm = INFINITY;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < OZP_SUB; ++k) {
                     const int col = (int)col0 + k;
                     const int sc = eq + cd.e[col] - 13;  // factor 2 of -2 a.b folded in
                     const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nq, cd.nh[col],
@@ -375,7 +415,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 // chains the scheduler can interleave.  Padded training rows have
                 // alpha = 0 exactly, so they need no test.
 #pragma unroll 1
-                for (int k = 0; k < 16; k += 2) {
+                for (int k = 0; k < OZP_SUB; k += 2) {
                     const int col = (int)col0 + k;
                     const float2 dv0 = sm.dist[et][k], dv1 = sm.dist[et][k + 1];
                     const df D0 = df_make(dv0.x, dv0.y), D1 = df_make(dv1.x, dv1.y);
@@ -404,36 +444,64 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 }
             }
         }
-        // combine the two column halves in a fixed order: half 0 + half 1
-        epi_bar();
-        if (half == 1) {
+        // combine the four column quarters of a row in a fixed order:
+        // (q0 + q1) + (q2 + q3)
+        df v[OZ_NSP][OZ_NLP];
+        int kv[OZ_NSP];
+#pragma unroll
+        for (int is = 0; is < OZ_NSP; ++is) {
+            kv[is] = ksh[is];
+#pragma unroll
+            for (int il = 0; il < OZ_NLP; ++il) v[is][il] = dfa_value(acc[is][il]);
+        }
+        epi_bar_p();
+        if (quarter & 1) {  // quarters 1 and 3 hand their sums to 0 and 2
 #pragma unroll
             for (int is = 0; is < OZ_NSP; ++is) {
-                sm.combk[is][row] = ksh[is];
+                sm.combk[quarter >> 1][is][row] = kv[is];
 #pragma unroll
-                for (int il = 0; il < OZ_NLP; ++il) {
-                    const df v = dfa_value(acc[is][il]);
-                    sm.comb[is * OZ_NLP + il][row] = make_float2(v.hi, v.lo);
-                }
+                for (int il = 0; il < OZ_NLP; ++il)
+                    sm.comb[quarter >> 1][is * OZ_NLP + il][row] = make_float2(v[is][il].hi, v[is][il].lo);
             }
         }
-        epi_bar();
-        if (half == 0 && live) {
+        epi_bar_p();
+        if (!(quarter & 1)) {
+#pragma unroll
+            for (int is = 0; is < OZ_NSP; ++is) {
+                const int kb = sm.combk[quarter >> 1][is][row];
+                int km = kv[is];
+#pragma unroll
+                for (int il = 0; il < OZ_NLP; ++il) {
+                    const float2 o = sm.comb[quarter >> 1][is * OZ_NLP + il][row];
+                    v[is][il] = oz_combine(v[is][il], kv[is], df_make(o.x, o.y), kb, &km);
+                }
+                kv[is] = km;
+            }
+        }
+        epi_bar_p();
+        if (quarter == 2) {  // (q2 + q3) to quarter 0
+#pragma unroll
+            for (int is = 0; is < OZ_NSP; ++is) {
+                sm.combk[0][is][row] = kv[is];
+#pragma unroll
+                for (int il = 0; il < OZ_NLP; ++il)
+                    sm.comb[0][is * OZ_NLP + il][row] = make_float2(v[is][il].hi, v[is][il].lo);
+            }
+        }
+        epi_bar_p();
+        if (quarter == 0 && live) {
             const int64_t orow_t = toff ? (tidx ? tidx[grow] : grow) : (q0 + row);
 #pragma unroll
             for (int is = 0; is < OZ_NSP; ++is)
 #pragma unroll
                 for (int il = 0; il < OZ_NLP; ++il) {
                     if (is < pp.nsig && il < pp.nlam) {
-                        const float2 o = sm.comb[is * OZ_NLP + il][row];
-                        const int k1 = sm.combk[is][row], km = max(ksh[is], k1);
-                        df a = dfa_value(acc[is][il]), b = df_make(o.x, o.y);
-                        if (ksh[is] != km) a = df_scale2(a, pow2_nonpos(ksh[is] - km));
-                        if (k1 != km) b = df_scale2(b, pow2_nonpos(k1 - km));
-                        const df v = df_add(a, b);
+                        const float2 o = sm.comb[0][is * OZ_NLP + il][row];
+                        int km;
+                        const df r = oz_combine(v[is][il], kv[is], df_make(o.x, o.y), sm.combk[0][is][row], &km);
                         const int gm = (pp.sig0 + is) * pp.nl_total + pp.lam0 + il;
                         const int64_t orow = routed ? (int64_t)gm : (int64_t)j * pp.Gtot + gm;
-                        out[orow * t + orow_t] = km == 0 ? df_to_double(v) : ldexp(df_to_double(v), km);
+                        out[orow * t + orow_t] = km == 0 ? df_to_double(r) : ldexp(df_to_double(r), km);
                     }
                 }
         }
@@ -692,6 +760,7 @@ void launch_oz_slice(cudaStream_t st, const double *X, int d, const int64_t *map
 }
 
 size_t oz_smem_bytes() { return sizeof(OzSmem) + 1024; }
+static size_t oz_psmem_bytes() { return sizeof(OzPSmem) + 1024; }
 
 // Kernel tiles of every partition and sigma, plus the factor matrices.
 cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
@@ -744,7 +813,7 @@ cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap
             }
             // for the routed form the grouped rows start at toff[j]; the tile count bounds every partition
             dim3 grid((unsigned)M.p, (unsigned)((t + OZ_M - 1) / OZ_M));
-            KRR_LAUNCHED(), predict_oz_kernel<<<grid, OZ_THREADS, oz_smem_bytes(), st>>>(
+            KRR_LAUNCHED(), predict_oz_kernel<<<grid, OZP_THREADS, oz_psmem_bytes(), st>>>(
                 tmA, tmB, M.d_parts, M.d_solves, M.alpha, M.ozex, M.nrm, tex, tnrm, t, toff, routed ? tidx : nullptr,
                 pp, routed, M.prows, out, d_err);
         }
