@@ -19,10 +19,14 @@
 //     of 32 features;
 //   warp 1, one thread: MMA issuer -- 15 x (d/16) kind::f16 MMAs per chunk into
 //     five 64-column FP32 accumulators in tensor memory;
-//   warps 4..11: epilogue -- tcgen05.ld of the five levels, distance, every
-//     sigma's double-float exponential and every lambda's alpha contraction
-//     into double-float accumulators; the two column halves of a test row are
-//     combined in a fixed order at the end.  K(test, train) is never stored.
+//   warps 2..17: epilogue -- tcgen05.ld of the five levels (8 columns at a
+//     time), distance, every sigma's double-float exponential and every
+//     lambda's alpha contraction into double-float accumulators; each warp
+//     owns one TMEM lane quadrant and one 16-column quarter of the chunk, and
+//     the four quarter sums of a test row are combined in a fixed order at
+//     the end.  K(test, train) is never stored.
+// The kernel-tile build uses the same producer / MMA / 16-warp epilogue
+// layout on the two 64-column chunks of one 128 x 128 tile.
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -37,8 +41,7 @@ constexpr int OZ_KC = 32;          // features per K chunk (64 bytes of bf16)
 constexpr int OZ_MAXKC = 3;        // d <= 96
 constexpr int OZ_ASTAGES = 3;
 constexpr int OZ_NSP = 4, OZ_NLP = 2;  // sigmas / lambdas per pass
-constexpr int OZ_THREADS = 320;    // 10 warps: producer, MMA issuer, 8 epilogue warps
-constexpr int OZ_EPI_WARP0 = 2;
+constexpr int OZ_EPI_WARP0 = 2;    // warps 0, 1: TMA producer, MMA issuer
 
 constexpr uint32_t OZ_A_CHUNK = OZ_M * 64;                 // bytes of one K chunk of one A slice
 constexpr uint32_t OZ_B_CHUNK = OZ_N * 64;
@@ -52,19 +55,14 @@ struct OzChunkData {  // per training column of a chunk
     float ah[OZ_NSP * OZ_NLP][OZ_N], al[OZ_NSP * OZ_NLP][OZ_N];
 };
 
-struct OzSmem {
+struct OzSmem {  // kernel-tile build CTA
     unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
     unsigned char b[OZ_B_BYTES];
-    OzChunkData cd[2];
     float2 exptab[256];
-    float2 comb[OZ_NSP * OZ_NLP][OZ_M];
-    int combk[OZ_NSP][OZ_M];                     // column half 1's range shift per sigma
-    float2 shift[OZ_NSP][256];                   // per epilogue thread: -K ln2 per sigma (df)
-    float2 dist[256][17];                        // per epilogue thread: 16 distances (padded row)
     uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
     uint64_t b_full, b_empty, t_full, t_empty;
     uint32_t tmem;
-    float2 cs[8];  // -1/(2 sigma^2) as df (kernel-tile build)
+    float2 cs[8];  // -1/(2 sigma^2) as df
 };
 
 struct OzParams {
@@ -534,7 +532,7 @@ __device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64
     return lo;
 }
 
-__global__ void __launch_bounds__(OZ_THREADS, 1)
+__global__ void __launch_bounds__(OZP_THREADS, 1)
 kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
                  const int32_t *__restrict__ ex, const float2 *__restrict__ nrm, OzKParams kp, int64_t prows,
@@ -560,7 +558,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         mbar_init(&sm.b_full, 1);
         mbar_init(&sm.b_empty, 1);
         mbar_init(&sm.t_full, 1);
-        mbar_init(&sm.t_empty, 8);
+        mbar_init(&sm.t_empty, OZP_EPI_WARPS);
         fence_mbar_init();
     }
     exp_table_init(sm.exptab);
@@ -628,8 +626,8 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             tc_commit(&sm.t_full);
         }
     } else if (warp >= OZ_EPI_WARP0) {
-        const int ew = warp - OZ_EPI_WARP0;
-        const int quad = warp & 3, half = ew >> 2;
+        const int ew = warp - OZ_EPI_WARP0;    // 0..15
+        const int quad = warp & 3, quarter = ew >> 2;
         const int r = quad * 32 + lane;            // row inside the tile
         const int gr = ti * KRR_TILE + r;          // row inside the partition
         const int64_t prow = P.prow0 + gr;
@@ -641,24 +639,25 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             if (!oz_wait(&sm.t_full, c & 1, err)) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int sub = 0; sub < 2; ++sub) {
-                float lv[OZ_SLICES][16];
-                const uint32_t col0 = (uint32_t)(half * 32 + sub * 16);
+            for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
+                float lv[OZ_SLICES][OZP_SUB];
+                const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
 #pragma unroll
                 for (int L = 0; L < OZ_SLICES; ++L)
-                    tmem_ld_32x32b_x16(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
+                    tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
                 tmem_wait_ld();
-                if (sub == 1 && c == nchunks - 1) {
+                const bool last_sub = sub == (OZ_N / 4) / OZP_SUB - 1;
+                if (last_sub && c == nchunks - 1) {
                     // nothing follows the last chunk
-                } else if (sub == 1) {
+                } else if (last_sub) {
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&sm.t_empty);
                 }
                 const int cbase = c * OZ_N + (int)col0;  // column inside the tile
-                float dh[16], dl[16];
+                float dh[OZP_SUB], dl[OZP_SUB];
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
+                for (int k = 0; k < OZP_SUB; ++k) {
                     const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
                     const float2 nc2 = nrm[pc];
                     const int sc = er + ex[pc] - 13;
@@ -671,9 +670,9 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 #pragma unroll 1
                 for (int is = 0; is < kp.nsig; ++is) {
                     const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
-                    float hv[16], lw[16];
+                    float hv[OZP_SUB], lw[OZP_SUB];
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
+                    for (int k = 0; k < OZP_SUB; ++k) {
                         const int gc = tj * KRR_TILE + cbase + k;
                         df kv;
                         if (gr >= P.m || gc >= P.m) kv = df_make(gr == gc ? 1.f : 0.f, 0.f);
@@ -686,7 +685,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     float4 *oh = reinterpret_cast<float4 *>(Kh + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
                     float4 *ol = reinterpret_cast<float4 *>(Kl + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
+                    for (int q = 0; q < OZP_SUB / 4; ++q) {
                         oh[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
                         ol[q] = make_float4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
                     }
@@ -697,7 +696,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                         float4 *oa = reinterpret_cast<float4 *>(A + (S.ltile0 + lt) * KRR_TILE_ELEMS +
                                                                  (int64_t)r * KRR_TILE + cbase);
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
+                        for (int q = 0; q < OZP_SUB / 4; ++q) {
                             float4 v = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
                             if (diag_here && gr < P.m) {
                                 const int d0 = gr - (tj * KRR_TILE + cbase + 4 * q);
@@ -780,7 +779,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
         kp.c_hi[i] = (float)c;
         kp.c_lo[i] = (float)(c - (double)(float)c);
     }
-    KRR_LAUNCHED(), kbuild_oz_kernel<<<(unsigned)ktot, OZ_THREADS, oz_smem_bytes(), st>>>(
+    KRR_LAUNCHED(), kbuild_oz_kernel<<<(unsigned)ktot, OZP_THREADS, oz_smem_bytes(), st>>>(
         tmA, M.oz_tmB, M.d_parts, M.d_solves, M.ozex, M.nrm, kp, M.prows, Kh, Kl, A, d_err);
     return cudaGetLastError();
 }
