@@ -329,6 +329,12 @@ def run_ours(args, rank, world, local_rank):
     d2h = hbest.numel() * 4 + hmse.numel() * 8
 
     # ---- plain FP64 path, one step, for the comparison the metric names
+    sizes0 = np.diff(last_offsets[0].cpu().numpy())
+    Wt = ctypes_int()
+    ctx.lib.krr_ctx_get_panel_width(ctx.handle, {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3}[args.prec],
+                                    int((sizes0.max() + 127) // 128), ctypes.byref(Wt))
+    panel_width = int(Wt.value)
+
     fp64 = None
     if not args.no_fp64_path and rank == 0:
         torch.cuda.synchronize()
@@ -349,15 +355,17 @@ def run_ours(args, rank, world, local_rank):
     sizes = np.diff(last_offsets[0].cpu().numpy())
     tflops = world * G * sum(solve_flops(int(m), d) for m in sizes) * args.steps / (total_ms / 1e3) / 1e12
     return dict(w=w, sizes=sizes, value=value, ms_per_step=ms_per_step, tflops=tflops, prof=prof, clocks=clk,
+                panel_width=panel_width,
                 launches=launches + flush_launches, e2e=dict(value=world * nsolve * args.steps / e2e_s, unit=UNIT,
                                                          h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                 fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times)
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu
-# capture of this bench's workload (profiles/launch_list_bkrr2_n65536_p16.md);
+# DRAM bytes (read + write) per launch of the dominant kernel class, averaged
+# over its launches in one step, from one ncu capture of this bench's workload
+# at the panel width the autotuner picks (profiles/launch_list_bkrr2_n65536_p16.md);
 # an entry is removed whenever its kernel changes.
-TRAFFIC = {}
+TRAFFIC = {("update", "bkrr2_n65536_t8192_d90_p16", 8): 380639971}
 
 
 def roofline(res, steps, peaks):
@@ -403,7 +411,7 @@ def roofline(res, steps, peaks):
         out.update(bound="hbm", achieved=byts / (ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6797.9), unit="GB/s",
                    peak_note="measured copy bandwidth; bytes assume every solve active (upper bound)")
     out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = TRAFFIC.get((dom, w["workload"]))
+    out["traffic"] = TRAFFIC.get((dom, w["workload"], res.get("panel_width")))
     if out["traffic"] is not None:
         out["traffic_unit"] = "bytes per launch (DRAM read + write)"
     return out
@@ -546,6 +554,7 @@ def main():
         "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": args.prec,
                    "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]),
                    "parallelism": "independent workloads per GPU" if world > 1 else "single GPU",
+                   "panel_width": res["panel_width"],
                    "l2": "flushed (512 MB write) before every timed step"},
         "tflops": res["tflops"], "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"],
         "clocks": res["clocks"], "gpu_launches": res["launches"], "fp64_path": res["fp64"],
