@@ -47,13 +47,15 @@ bool make_tile_tmap(CUtensorMap *, float *, int64_t);
 size_t pcg_state_size();
 size_t precond_smem_bytes(bool, int);
 struct PcgBuffers {
-    double *x, *r, *z, *p, *q, *y, *slots;
+    double *x, *r, *z, *p, *q, *y;
+    float2 *pdf, *slots;  // the direction as double-float pairs; matvec partials
     PcgState *state;
     unsigned int *nactive;
     GroupDesc *d_groups;
     int64_t *d_gpre;
     int ng;
     int64_t gtiles;
+    int maxT;
 };
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
@@ -421,7 +423,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                          (size_t)prow * (10 * (size_t)((d + 31) / 32 * 32) + 4) +
                          sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
-                        (size_t)dtiles * tileb + 5 * (size_t)vec * 8 + (size_t)scratch * 8 +
+                        (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
                         4 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
@@ -455,8 +457,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
 
     {
         DevBuf W(c);
-        double *yg = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *yv = nullptr,
-               *slots = nullptr;
+        double *yg = nullptr, *r = nullptr, *z = nullptr, *pv = nullptr, *q = nullptr, *yv = nullptr;
+        float2 *pdf = nullptr, *slots = nullptr;
         void *Kst = nullptr, *Ast = nullptr, *Zst = nullptr;
         PcgState *state = nullptr;
         unsigned int *nactive = nullptr;
@@ -470,6 +472,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         FIT_TRY(W.get(&r, (size_t)vec * 8));
         FIT_TRY(W.get(&z, (size_t)vec * 8));
         FIT_TRY(W.get(&pv, (size_t)vec * 8));
+        FIT_TRY(W.get(&pdf, (size_t)vec * 8));
         FIT_TRY(W.get(&q, (size_t)vec * 8));
         FIT_TRY(W.get(&yv, (size_t)vec * 8));
         FIT_TRY(W.get(&slots, (size_t)scratch * 8));
@@ -526,6 +529,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.p = pv;
         B.q = q;
         B.y = yv;
+        B.pdf = pdf;
         B.slots = slots;
         B.state = state;
         B.nactive = nactive;
@@ -533,6 +537,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.d_gpre = d_gpre;
         B.ng = (int)groups.size();
         B.gtiles = gtiles;
+        B.maxT = maxT;
         FIT_TRY(run_pcg_norms(st, M, B, Kh, Kl, K64, fp64, prof));
         std::vector<PcgState> hs0(nsolve);
         FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));

@@ -15,6 +15,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "exp2_table.h"
+
 #define KRR_TILE 128            // tile edge of every kernel/factor tile
 #define KRR_TILE_ELEMS (KRR_TILE * KRR_TILE)
 
@@ -88,14 +90,12 @@ __device__ __forceinline__ df dfa_value(const df_acc &a) {
 //   exp(r) = 1 + s + q(s) + rlo (1 + s + s^2/2 + rlo/2),  q = s^2/2 + s^3/6 + s^4/24,
 // with q and the rlo term in FP32 (both below 1e-6 in size, so their rounding
 // stays below 1e-13) and 1 + s exact as a double-float.  The 256 table values
-// 2^(j/256) are double-float numbers in shared memory.  Relative error ~7e-13
-// for results above ~1e-30 (the lo part runs into FP32 subnormals below that).
+// 2^(j/256) are double-float numbers (exp2_table.h, computed to 60 digits and
+// rounded to hi + lo once), copied to shared memory by every CTA.  Relative
+// error ~7e-13 for results above ~1e-30 (the lo part runs into FP32
+// subnormals below that).
 __device__ __forceinline__ void exp_table_init(float2 *tab) {
-    for (int j = threadIdx.x; j < 256; j += blockDim.x) {
-        const double v = exp2((double)j / 256.0);
-        const float h = __double2float_rn(v);
-        tab[j] = make_float2(h, __double2float_rn(v - (double)h));
-    }
+    for (int j = threadIdx.x; j < 256; j += blockDim.x) tab[j] = krr_exp2_tab[j];
 }
 __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab) {
     if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
@@ -307,7 +307,9 @@ __host__ __device__ constexpr uint32_t make_idesc(uint32_t fmt, uint32_t M, uint
 __device__ __forceinline__ int64_t tri_index(int64_t i, int64_t j) { return i * (i + 1) / 2 + j; }
 // inverse of tri_index for idx < T(T+1)/2: row i (>= col j)
 __device__ __forceinline__ void tri_decode(int64_t idx, int &i, int &j) {
-    int r = (int)((sqrt(8.0 * (double)idx + 1.0) - 1.0) * 0.5);
+    // FP32 estimate (no FP64 instructions: GB300's FP64 pipe runs at 1/64 of
+    // the FP32 rate); the integer steps below correct it exactly
+    int r = (int)((sqrtf(8.0f * (float)idx + 1.0f) - 1.0f) * 0.5f);
     while ((int64_t)(r + 1) * (r + 2) / 2 <= idx) ++r;
     while ((int64_t)r * (r + 1) / 2 > idx) --r;
     i = r;

@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(256, 2)
 matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, const double *__restrict__ K64,
                     const GroupDesc *__restrict__ groups, const int64_t *__restrict__ gpre, int ng,
                     const SolveDesc *__restrict__ solves, const PcgState *__restrict__ state,
-                    const double *__restrict__ pv, double *__restrict__ slots) {
+                    const float2 *__restrict__ pdf, float2 *__restrict__ slots) {
     constexpr int NL = 2;  // lambdas per pass
     __shared__ float2 sp_row[NL][KRR_TILE];   // p of the column block (df)
     __shared__ float2 sp_col[NL][KRR_TILE];   // p of the row block
@@ -79,11 +79,8 @@ matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, 
         for (int e = threadIdx.x; e < nl * KRR_TILE; e += 256) {
             const int l = e >> 7, c = e & 127;
             const SolveDesc S = solves[G.solve0 + l0 + l];
-            const double a = pv[S.vec0 + (int64_t)tj * KRR_TILE + c];
-            const double b = pv[S.vec0 + (int64_t)ti * KRR_TILE + c];
-            const float ah = __double2float_rn(a), bh = __double2float_rn(b);
-            sp_row[l][c] = make_float2(ah, __double2float_rn(a - (double)ah));
-            sp_col[l][c] = make_float2(bh, __double2float_rn(b - (double)bh));
+            sp_row[l][c] = pdf[S.vec0 + (int64_t)tj * KRR_TILE + c];
+            sp_col[l][c] = pdf[S.vec0 + (int64_t)ti * KRR_TILE + c];
         }
         __syncthreads();
         constexpr int RB = 2;  // rows per step
@@ -123,7 +120,7 @@ matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, 
 #pragma unroll
             for (int l = 0; l < NL; ++l) {
                 if (l >= nl) break;
-                double *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
+                float2 *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
 #pragma unroll
                 for (int i = 0; i < RB; ++i) {
                     const int r = ty * 8 + RB * h + i;
@@ -146,7 +143,7 @@ matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, 
                         }
                         rv = df_sum16(df_from_double(a));
                     }
-                    if (tx == 0) base[((int64_t)ti * T + tj) * KRR_TILE + r] = df_to_double(rv);
+                    if (tx == 0) base[((int64_t)ti * T + tj) * KRR_TILE + r] = make_float2(rv.hi, rv.lo);
                     const float2 pr = sp_col[l][r];
 #pragma unroll
                     for (int j = 0; j < 8; ++j) {
@@ -174,32 +171,37 @@ matvec_tiles_kernel(const float *__restrict__ Kh, const float *__restrict__ Kl, 
                 if (l < nl) {
                     df s = df_make(scol[l][0][c].x, scol[l][0][c].y);
                     for (int u = 1; u < 16; ++u) s = df_add(s, df_make(scol[l][u][c].x, scol[l][u][c].y));
-                    double *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
-                    base[((int64_t)tj * T + ti) * KRR_TILE + c] = df_to_double(s);
+                    float2 *base = slots + G.scratch0 + (int64_t)(l0 + l) * T * T * KRR_TILE;
+                    base[((int64_t)tj * T + ti) * KRR_TILE + c] = make_float2(s.hi, s.lo);
                 }
             }
         }
     }
 }
 
-// q_a = sum_b slot(a, b) + lambda m p_a ; grid (solves), 128 threads
+// q_a = sum_b slot(a, b) + lambda m p_a, the slots (double-float) summed in
+// double-float in the fixed order b = 0 .. T-1; grid (solves, largest T),
+// 128 threads: CTA (s, a) finishes row block a of solve s
 __global__ void matvec_reduce_kernel(const GroupDesc *__restrict__ groups, const SolveDesc *__restrict__ solves,
                                      const PcgState *__restrict__ state, const double *__restrict__ pv,
-                                     const double *__restrict__ slots, double *__restrict__ q) {
-    const int s = blockIdx.x;
+                                     const float2 *__restrict__ slots, double *__restrict__ q) {
+    const int s = blockIdx.x, a = blockIdx.y;
     if (!state[s].active) return;
     const SolveDesc S = solves[s];
     const GroupDesc G = groups[S.grp];
-    const int l = s - (int)G.solve0;
     const int T = G.T;
-    const double *base = slots + G.scratch0 + (int64_t)l * T * T * KRR_TILE;
-    for (int64_t e = threadIdx.x; e < (int64_t)T * KRR_TILE; e += blockDim.x) {
-        const int a = (int)(e >> 7), c = (int)(e & 127);
-        double acc = 0.0;
-        for (int b = 0; b < T; ++b) acc += base[((int64_t)a * T + b) * KRR_TILE + c];
-        const bool real = e < S.m;
-        q[S.vec0 + e] = real ? acc + S.lambda_m * pv[S.vec0 + e] : pv[S.vec0 + e];
+    if (a >= T) return;
+    const int l = s - (int)G.solve0;
+    const int c = threadIdx.x;
+    const float2 *base = slots + G.scratch0 + (int64_t)l * T * T * KRR_TILE + (int64_t)a * T * KRR_TILE + c;
+    df acc = df_make(0.f, 0.f);
+    for (int b = 0; b < T; ++b) {
+        const float2 v = base[(int64_t)b * KRR_TILE];
+        acc = df_add(acc, df_make(v.x, v.y));
     }
+    const int64_t e = (int64_t)a * KRR_TILE + c;
+    const double pe = pv[S.vec0 + e];
+    q[S.vec0 + e] = (e < S.m) ? df_to_double(acc) + S.lambda_m * pe : pe;
 }
 
 // ---------------------------------------------------------------- preconditioner
@@ -416,13 +418,15 @@ __device__ __forceinline__ double block_max(double v, double *sh) {
 
 // phase 0: p = 1 on real rows (for ||A||_inf = max (A 1) since A >= 0), x = 0
 __global__ void pcg_prepare_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
-                                   const int32_t *__restrict__ flags, double *__restrict__ x, double *__restrict__ p) {
+                                   const int32_t *__restrict__ flags, double *__restrict__ x, double *__restrict__ p,
+                                   float2 *__restrict__ pdf) {
     const int s = blockIdx.x;
     const SolveDesc S = solves[s];
     const int M = S.T * KRR_TILE;
     for (int e = threadIdx.x; e < M; e += blockDim.x) {
         x[S.vec0 + e] = 0.0;
         p[S.vec0 + e] = (e < S.m) ? 1.0 : 0.0;
+        pdf[S.vec0 + e] = make_float2((e < S.m) ? 1.f : 0.f, 0.f);
     }
     if (threadIdx.x == 0) {
         PcgState st;
@@ -460,9 +464,16 @@ __global__ void pcg_norms_kernel(const SolveDesc *__restrict__ solves, PcgState 
     }
 }
 
+// the direction as a double-float pair for the matvec: hi = rn(v), lo = rn(v - hi)
+__device__ __forceinline__ float2 split_df(double v) {
+    const float h = __double2float_rn(v);
+    return make_float2(h, __double2float_rn(v - (double)h));
+}
+
 // phase 2 (after the first preconditioner application): p = z, rz = r.z
 __global__ void pcg_start_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
-                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p) {
+                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p,
+                                 float2 *__restrict__ pdf) {
     __shared__ double sh[256];
     const int s = blockIdx.x;
     if (!state[s].active) return;
@@ -472,6 +483,7 @@ __global__ void pcg_start_kernel(const SolveDesc *__restrict__ solves, PcgState 
     for (int e = threadIdx.x; e < M; e += blockDim.x) {
         const double zv = z[S.vec0 + e];
         p[S.vec0 + e] = zv;
+        pdf[S.vec0 + e] = split_df(zv);
         acc += r[S.vec0 + e] * zv;
     }
     acc = block_sum(acc, sh);
@@ -542,7 +554,8 @@ __global__ void pcg_step1_kernel(const SolveDesc *__restrict__ solves, PcgState 
 
 // step 2: rz' = r.z ; p = z + (rz'/rz) p
 __global__ void pcg_step2_kernel(const SolveDesc *__restrict__ solves, PcgState *__restrict__ state,
-                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p) {
+                                 const double *__restrict__ r, const double *__restrict__ z, double *__restrict__ p,
+                                 float2 *__restrict__ pdf) {
     __shared__ double sh[256];
     const int s = blockIdx.x;
     if (!state[s].active) return;
@@ -552,36 +565,44 @@ __global__ void pcg_step2_kernel(const SolveDesc *__restrict__ solves, PcgState 
     for (int e = threadIdx.x; e < M; e += blockDim.x) acc += r[S.vec0 + e] * z[S.vec0 + e];
     acc = block_sum(acc, sh);
     const double beta = acc / state[s].rz;
-    for (int e = threadIdx.x; e < M; e += blockDim.x) p[S.vec0 + e] = z[S.vec0 + e] + beta * p[S.vec0 + e];
+    for (int e = threadIdx.x; e < M; e += blockDim.x) {
+        const double pe = z[S.vec0 + e] + beta * p[S.vec0 + e];
+        p[S.vec0 + e] = pe;
+        pdf[S.vec0 + e] = split_df(pe);
+    }
     __syncthreads();
     if (threadIdx.x == 0) state[s].rz = acc;
 }
 
 // ---------------------------------------------------------------- host
 struct PcgBuffers {
-    double *x, *r, *z, *p, *q, *y, *slots;
+    double *x, *r, *z, *p, *q, *y;
+    float2 *pdf, *slots;  // the direction as double-float pairs; matvec partials
     PcgState *state;
     unsigned int *nactive;
     GroupDesc *d_groups;
     int64_t *d_gpre;
     int ng;
     int64_t gtiles;
+    int maxT;
 };
 
 size_t pcg_state_size() { return sizeof(PcgState); }
 
+// q = (K + lambda m I) p for every active solve; p in FP64 (B.p) and as
+// double-float pairs (B.pdf), both written by the kernel that formed p
 static void launch_matvec(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
-                          const double *K64, bool fp64, const double *p, Prof *prof) {
+                          const double *K64, bool fp64, Prof *prof) {
     if (B.gtiles == 0) return;
     ProfScope ps(prof, PROF_MATVEC, st);
     if (fp64)
         KRR_LAUNCHED(), matvec_tiles_kernel<false><<<(unsigned)B.gtiles, 256, 0, st>>>(Kh, Kl, K64, B.d_groups, B.d_gpre, B.ng,
-                                                                       M.d_solves, B.state, p, B.slots);
+                                                                       M.d_solves, B.state, B.pdf, B.slots);
     else
         KRR_LAUNCHED(), matvec_tiles_kernel<true><<<(unsigned)B.gtiles, 256, 0, st>>>(Kh, Kl, K64, B.d_groups, B.d_gpre, B.ng,
-                                                                      M.d_solves, B.state, p, B.slots);
-    KRR_LAUNCHED(), matvec_reduce_kernel<<<(unsigned)M.solves.size(), 128, 0, st>>>(B.d_groups, M.d_solves, B.state, p, B.slots,
-                                                                    B.q);
+                                                                      M.d_solves, B.state, B.pdf, B.slots);
+    const dim3 rgrid((unsigned)M.solves.size(), (unsigned)B.maxT);
+    KRR_LAUNCHED(), matvec_reduce_kernel<<<rgrid, KRR_TILE, 0, st>>>(B.d_groups, M.d_solves, B.state, B.p, B.slots, B.q);
 }
 
 static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuffers &B, const void *L, const void *Z,
@@ -610,8 +631,8 @@ size_t precond_smem_bytes(bool fp64, int maxT) {
 cudaError_t run_pcg_norms(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
                           const double *K64, bool fp64, Prof *prof) {
     const unsigned ns = (unsigned)M.solves.size();
-    KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, nullptr, B.x, B.p);
-    launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
+    KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, nullptr, B.x, B.p, B.pdf);
+    launch_matvec(st, M, B, Kh, Kl, K64, fp64, prof);
     KRR_LAUNCHED(), pcg_norms_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.y, B.q, B.r);
     return cudaGetLastError();
 }
@@ -625,15 +646,15 @@ cudaError_t run_pcg(cudaStream_t st, const Model &M, const PcgBuffers &B, const 
     KRR_LAUNCHED(), pcg_apply_flags_kernel<<<(ns + 127) / 128, 128, 0, st>>>(B.state, flags, (int)ns);
     cudaError_t e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
     if (e != cudaSuccess) return e;
-    KRR_LAUNCHED(), pcg_start_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);
+    KRR_LAUNCHED(), pcg_start_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p, B.pdf);
     for (int it = 0; it < maxit; ++it) {
         cudaMemsetAsync(B.nactive, 0, sizeof(unsigned int), st);
-        launch_matvec(st, M, B, Kh, Kl, K64, fp64, B.p, prof);
+        launch_matvec(st, M, B, Kh, Kl, K64, fp64, prof);
         KRR_LAUNCHED(), pcg_step1_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.x, B.r, B.p, B.q, tau, target, maxit,
                                                               B.nactive);
         e = launch_precond(st, M, B, L, Z, fp64, maxT, prof);
         if (e != cudaSuccess) return e;
-        KRR_LAUNCHED(), pcg_step2_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p);
+        KRR_LAUNCHED(), pcg_step2_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.r, B.z, B.p, B.pdf);
         if (it % check_every == check_every - 1) {
             cudaMemcpyAsync(h_nactive, B.nactive, sizeof(unsigned int), cudaMemcpyDeviceToHost, st);
             e = cudaStreamSynchronize(st);
