@@ -8,6 +8,8 @@
 #include <new>
 #include <set>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -41,9 +43,10 @@ struct CholLaunch {
 void build_chol_plan(const std::vector<int> &, const std::vector<int> &, int, std::vector<CholLaunch> &,
                      std::vector<int64_t> &);
 cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
-                          const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, int *,
-                          Prof *);
+                          const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, __half *,
+                          const CUtensorMap *, int *, Prof *);
 bool make_tile_tmap(CUtensorMap *, float *, int64_t);
+bool make_tile_tmap16(CUtensorMap *, __half *, int64_t);
 size_t pcg_state_size();
 size_t precond_smem_bytes(bool, int);
 struct PcgBuffers {
@@ -56,6 +59,7 @@ struct PcgBuffers {
     int ng;
     int64_t gtiles;
     int maxT;
+    const void *L16;  // FP16 factor store of class-1 solves (null without them)
 };
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
@@ -395,6 +399,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 S.T = P.T;
                 S.m = P.m;
                 S.grp = j * ns + is;
+                S.cls = 0;
+                S.pad0 = 0;
                 S.ltile0 = ltiles;
                 S.dtile0 = dtiles;
                 S.ktile0 = Gd.ktile0;
@@ -424,6 +430,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                          sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
                         (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
+                        (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
                         4 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
@@ -469,6 +476,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         FIT_TRY(W.get(&Kst, (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb));
         FIT_TRY(W.get(&Ast, (size_t)ltiles * tileb));
         FIT_TRY(W.get(&Zst, (size_t)dtiles * tileb));
+        __half *A16 = nullptr;  // FP16 copies of the L tiles of one-pass (class 1) solves
+        if (tf32) FIT_TRY(W.get(&A16, (size_t)ltiles * KRR_TILE_ELEMS * sizeof(__half)));
         FIT_TRY(W.get(&r, (size_t)vec * 8));
         FIT_TRY(W.get(&z, (size_t)vec * 8));
         FIT_TRY(W.get(&pv, (size_t)vec * 8));
@@ -538,18 +547,21 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.ng = (int)groups.size();
         B.gtiles = gtiles;
         B.maxT = maxT;
+        B.L16 = A16;
         FIT_TRY(run_pcg_norms(st, M, B, Kh, Kl, K64, fp64, prof));
         std::vector<PcgState> hs0(nsolve);
         FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));
         FIT_TRY(cudaStreamSynchronize(st));
 
         // factor class per solve: FP64 path -> FP64; FP32 -> 3-pass TF32; TF32 ->
-        // 1-pass unless kappa_est * 2^-11 exceeds the escalation threshold;
+        // one FP16 pass unless kappa_est * 2^-11 exceeds the escalation threshold;
         // BF16x3 -> 3-pass BF16 unless kappa_est * 2^-16 exceeds it (then 3-pass TF32)
-        CUtensorMap tmap, tmapZ;
+        CUtensorMap tmap, tmapZ, tmap16;
         memset(&tmap, 0, sizeof(tmap));
         memset(&tmapZ, 0, sizeof(tmapZ));
-        if (!fp64 && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles)))
+        memset(&tmap16, 0, sizeof(tmap16));
+        if (!fp64 && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles) ||
+                      (A16 && !make_tile_tmap16(&tmap16, A16, ltiles))))
             return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
         const int base_cls = fp64 ? 0 : (tf32 ? 1 : (bf16x3 ? 2 : 3));
         std::vector<int> cls(nsolve, base_cls);  // update class per solve
@@ -560,7 +572,15 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 const double kap = lm > 0.0 ? hs0[s].anorm / lm : INFINITY;
                 if (kap * std::ldexp(1.0, tf32 ? -11 : -16) > c->escalate) cls[s] = 3;
             }
-        for (int s = 0; s < nsolve; ++s) M.st_class[s] = cls[s];
+        // FP16 range: |L_ij| <= sqrt(A_jj) = sqrt(1 + lambda m) must stay far below 65504
+        if (tf32)
+            for (int s = 0; s < nsolve; ++s)
+                if (cls[s] == 1 && !(1.0 + M.solves[s].lambda_m <= 16777216.0)) cls[s] = 3;
+        for (int s = 0; s < nsolve; ++s) {
+            M.st_class[s] = cls[s];
+            M.solves[s].cls = cls[s];
+        }
+        FIT_TRY(cudaMemcpyAsync(M.d_solves, M.solves.data(), sizeof(SolveDesc) * nsolve, cudaMemcpyHostToDevice, st));
 
         // one joint schedule: shared diagonal factorisations and panel solves,
         // one update launch per class; outer panel width W explicit, cached per
@@ -603,7 +623,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                                                                                          Kh, (float *)Ast, 0.f);
                     cudaEventRecord(e0, st);
                     FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tcmode,
-                                          &tmap, &tmapZ, c->d_err, nullptr));
+                                          &tmap, &tmapZ, A16, &tmap16, c->d_err, nullptr));
                     cudaEventRecord(e1, st);
                     FIT_TRY(cudaEventSynchronize(e1));
                     float ms = 0.f;
@@ -629,7 +649,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             if (!pre.empty())
                 FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
             FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tcmode, &tmap, &tmapZ,
-                                  c->d_err, prof));
+                                  A16, &tmap16, c->d_err, prof));
             FIT_TRY(cudaMemcpyAsync(hflags.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
             FIT_TRY(cudaStreamSynchronize(st));
         }
@@ -648,6 +668,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 std::vector<int64_t> rpre(nsub + 1, 0);
                 for (int i = 0; i < nsub; ++i) {
                     sub[i] = M.solves[failed[i]];
+                    sub[i].cls = 3;  // refactored in 3 passes, L in the FP32 store
                     rpre[i + 1] = rpre[i] + tri(sub[i].T);
                 }
                 SolveDesc *d_sub = nullptr;
@@ -673,7 +694,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
                                         st));
                 FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, 3, &tmap, &tmapZ,
-                                      c->d_err, prof));
+                                      A16, &tmap16, c->d_err, prof));
                 std::vector<int32_t> hr(nsub);
                 FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
                 FIT_TRY(cudaStreamSynchronize(st));
@@ -684,6 +705,17 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             }
         }
         FIT_TRY(cudaMemcpyAsync(flags, hflags.data(), sizeof(int32_t) * nsolve, cudaMemcpyHostToDevice, st));
+        if (!fp64) {  // the preconditioner reads each solve's L where its final class left it
+            bool changed = false;
+            for (int s = 0; s < nsolve; ++s)
+                if (M.solves[s].cls != M.st_class[s]) {
+                    M.solves[s].cls = M.st_class[s];
+                    changed = true;
+                }
+            if (changed)
+                FIT_TRY(cudaMemcpyAsync(M.d_solves, M.solves.data(), sizeof(SolveDesc) * nsolve,
+                                        cudaMemcpyHostToDevice, st));
+        }
 
         // refinement: stop at the FP64-class floor, or earlier once
         // kappa_est * residual meets the context's forward-error target (refined precisions)

@@ -25,6 +25,7 @@
 #include <algorithm>
 
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "common.cuh"
 #include "internal.h"
@@ -307,7 +308,10 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 // or A_ik = C for the panel solve), so loads, MMAs and epilogues of
 // consecutive tasks overlap and the per-CTA setup is paid once per launch.
 // TC_TF32: one kind::tf32 MMA per K step (the tensor core reads the top 19
-// bits of each FP32 operand).  TC_BF16X3: warps 6..9 convert each landed FP32
+// bits of each FP32 operand).  TC_F16: one kind::f16 MMA per K step on the
+// FP16 copy of the panel (the same 11-bit significand as TF32 at twice the
+// rate and half the operand bytes); the panel solve of a class-1 solve writes
+// its L tiles in FP16 for this.  TC_BF16X3: warps 6..9 convert each landed FP32
 // stage into BF16 hi = rn(x) and lo = rn(x - hi) operands and three kind::f16
 // MMAs per K step form hi*hi + hi*lo + lo*hi (~16-bit products at the BF16
 // rate).  TC_TF32X3: warps 6..9 split each landed stage
@@ -318,6 +322,7 @@ constexpr int TC_CHUNK = 32;                                       // floats of 
 constexpr uint32_t TC_HALF = (uint32_t)KRR_TILE * TC_CHUNK * 4;     // one operand tile chunk, 16 KB
 constexpr uint32_t TC_IDESC = make_idesc(2u /*TF32*/, 128u, 128u);
 constexpr uint32_t TC_IDESC_BF16 = make_idesc(1u /*BF16*/, 128u, 128u);
+constexpr uint32_t TC_IDESC_F16 = make_idesc(0u /*F16*/, 128u, 128u);
 constexpr uint32_t TC_BHALF = (uint32_t)KRR_TILE * TC_CHUNK * 2;  // one BF16 operand chunk, 8 KB
 
 // Shared-memory descriptor, K-major operand with the 64-byte swizzle (8-row x
@@ -333,10 +338,11 @@ __device__ __forceinline__ uint64_t smem_desc_sw64_tc(const void *p) {
     return d;
 }
 // MODE: TC_TF32 one pass; TC_TF32X3 three TF32 passes on hi/lo splits;
-// TC_BF16X3 three BF16 passes (kind::f16) on hi/lo BF16 splits
-enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2 };
+// TC_BF16X3 three BF16 passes (kind::f16) on hi/lo BF16 splits; TC_F16 one
+// kind::f16 pass on FP16 operands (64 halves = 128 bytes of K per stage)
+enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3 };
 template <int MODE> struct TcCfg {
-    static constexpr bool SPLIT = MODE != TC_TF32;
+    static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;
     static constexpr int STAGES = SPLIT ? 2 : 3;
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
@@ -367,11 +373,14 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
 template <int MODE>
 __global__ void __launch_bounds__(TcCfg<MODE>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
-                float *__restrict__ A, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
-                int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
+                float *__restrict__ A, __half *__restrict__ A16, const SolveDesc *__restrict__ solves,
+                const int64_t *__restrict__ pre, int nsolve, int64_t ntasks, int mode, int K0, int W,
+                int *__restrict__ err) {
     using Cfg = TcCfg<MODE>;
     constexpr bool X3 = Cfg::SPLIT;
-    constexpr int KCH = KRR_TILE / TC_CHUNK;  // chunks per K tile
+    // elements of K per stage: 32 floats or 64 halves (128 bytes either way)
+    constexpr int KEL = MODE == TC_F16 ? 2 * TC_CHUNK : TC_CHUNK;
+    constexpr int KCH = KRR_TILE / KEL;  // chunks per K tile
     extern __shared__ unsigned char tc_dyn[];
     const uint32_t base = smem_u32(tc_dyn);
     unsigned char *buf = tc_dyn + (((base + 1023u) & ~1023u) - base);  // 1024-aligned stage ring
@@ -432,7 +441,7 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 unsigned char *sa = buf + st * Cfg::STAGE_BYTES;
                 unsigned char *sb = sa + TC_HALF;
                 const int kt = g.kb + c / KCH;
-                const int x = (c % KCH) * TC_CHUNK;
+                const int x = (c % KCH) * KEL;
                 const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
                 mbar_arrive_expect_tx(&full[st], 2 * TC_HALF);
                 tma_load_2d(sa, &tmap, x, ya, &full[st]);
@@ -478,6 +487,13 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                         tc_mma_f16(acc, dah + 2 * kk, dbh + 2 * kk, TC_IDESC_BF16, acc0);
                         tc_mma_f16(acc, dah + 2 * kk, dbl + 2 * kk, TC_IDESC_BF16, 1u);
                         tc_mma_f16(acc, dal + 2 * kk, dbh + 2 * kk, TC_IDESC_BF16, 1u);
+                    }
+                } else if constexpr (MODE == TC_F16) {
+                    const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
+#pragma unroll
+                    for (int kk = 0; kk < KEL / 16; ++kk) {  // K = 16 halves = 32 bytes per MMA
+                        const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
+                        tc_mma_f16(acc, da + 2 * kk, db + 2 * kk, TC_IDESC_F16, acc0);
                     }
                 } else {
                     const uint64_t da = smem_desc_sw128(sa), db = smem_desc_sw128(sb);
@@ -571,6 +587,9 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
             TaskGeom g;
             task(t, S, g);
             float *dst = dst_tile(S, g) + (int64_t)r * KRR_TILE;
+            // a class-1 solve's panel solve writes its L tile in FP16 (operand of the one-pass updates)
+            const bool half_out = mode == UPD_TRSM && S.cls == 1;
+            __half *dst16 = half_out ? A16 + (dst_tile(S, g) - A) + (int64_t)r * KRR_TILE : nullptr;
             const int b = lt & 1;
             if (!mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err)) break;
             tc_fence_after();
@@ -585,7 +604,23 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 float v[32];
                 tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32), v);
                 float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
-                if (mode == UPD_TRSM) {
+                if (half_out) {
+                    uint4 *h4 = reinterpret_cast<uint4 *>(dst16 + cb * 32);
+#pragma unroll
+                    for (int qq = 0; qq < 4; ++qq) {
+                        uint4 o;
+                        __half2 h;
+                        h = __floats2half2_rn(v[8 * qq + 0], v[8 * qq + 1]);
+                        o.x = *reinterpret_cast<uint32_t *>(&h);
+                        h = __floats2half2_rn(v[8 * qq + 2], v[8 * qq + 3]);
+                        o.y = *reinterpret_cast<uint32_t *>(&h);
+                        h = __floats2half2_rn(v[8 * qq + 4], v[8 * qq + 5]);
+                        o.z = *reinterpret_cast<uint32_t *>(&h);
+                        h = __floats2half2_rn(v[8 * qq + 6], v[8 * qq + 7]);
+                        o.w = *reinterpret_cast<uint32_t *>(&h);
+                        h4[qq] = o;
+                    }
+                } else if (mode == UPD_TRSM) {
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq)
                         d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
@@ -645,13 +680,28 @@ bool make_tile_tmap(CUtensorMap *map, float *store, int64_t ntiles) {
     return r == CUDA_SUCCESS;
 }
 
+// 2-D view of an FP16 tile store: rows of 128 halves, box 64 x 128, 128B swizzle
+bool make_tile_tmap16(CUtensorMap *map, __half *store, int64_t ntiles) {
+    if (ntiles <= 0) ntiles = 1;
+    PFN_encodeTiled enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)KRR_TILE, (cuuint64_t)(ntiles * KRR_TILE)};
+    cuuint64_t strides[1] = {(cuuint64_t)KRR_TILE * sizeof(__half)};
+    cuuint32_t box[2] = {(cuuint32_t)(2 * TC_CHUNK), (cuuint32_t)KRR_TILE};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, store, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // One launch of the factorisation schedule.
 struct CholLaunch {
     int kind;      // 0 potrf, 1 trsm, 2 update-trail, 3 update-column
     int K0, W;     // step parameters (see decode_task)
     int64_t pre;   // offset of this launch's prefix array in the plan buffer
     int64_t tasks; // total CTAs
-    int tc;        // update arithmetic: 0 SIMT, 1 TF32 one pass, 3 three passes
+    int tc;        // update arithmetic: 0 SIMT, 1 one FP16 pass, 2 BF16x3, 3 TF32x3
 };
 
 // Build the schedule for a batch of solves with tile counts T[s] and update
@@ -704,8 +754,9 @@ void build_chol_plan(const std::vector<int> &T, const std::vector<int> &cls, int
 
 template <typename T>
 cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, T *A, T *Z,
-                            const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc, const CUtensorMap *tmap,
-                            const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
+                            __half *A16, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
+                            const CUtensorMap *tmap, const CUtensorMap *tmapZ, const CUtensorMap *tmap16, int *d_err,
+                            Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     allow_max_dyn_smem(potrf_tile_kernel<T>);
     int dev = 0, nsm = 1;
@@ -722,25 +773,27 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
         const int mode = L.kind == 1 ? UPD_TRSM : (L.kind == 2 ? UPD_TRAIL : UPD_COLUMN);
         const int W = L.kind == 1 ? 0 : L.W;
         if constexpr (sizeof(T) == 4) {
-            // tensor cores: the panel solve always FP32-class (3 passes); the
-            // trailing updates 1 pass (TF32) or 3 passes (FP32), per launch class
+            // tensor cores: the panel solve always FP32-class (3 TF32 passes);
+            // updates per class: 1 one FP16 pass (operands from the FP16 copy
+            // of the panel), 2 BF16x3, 3 TF32x3
             if (tc != 0) {
-                // the panel solve always FP32-class; updates per class: 1 TF32, 2 BF16x3, 3 TF32x3
-                const int m = (L.kind == 1 || L.tc == 3) ? TC_TF32X3 : (L.tc == 2 ? TC_BF16X3 : TC_TF32);
+                const int m = (L.kind == 1 || L.tc == 3) ? TC_TF32X3 : (L.tc == 2 ? TC_BF16X3 : TC_F16);
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 float *Af = reinterpret_cast<float *>(A);
                 if (m == TC_TF32X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
                                                                  TcCfg<TC_TF32X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else if (m == TC_BF16X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_BF16X3><<<pgrid, TcCfg<TC_BF16X3>::THREADS,
                                                                  TcCfg<TC_BF16X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                else if (A16 != nullptr && tmap16 != nullptr)
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_F16><<<pgrid, TcCfg<TC_F16>::THREADS,
+                                                             TcCfg<TC_F16>::SMEM, st>>>(
+                        *tmap16, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32><<<pgrid, TcCfg<TC_TF32>::THREADS,
-                                                              TcCfg<TC_TF32>::SMEM, st>>>(
-                        *tmap, *tmapZ, Af, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    return cudaErrorInvalidValue;  // class 1 needs the FP16 store
                 continue;
             }
         }
@@ -749,19 +802,21 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
     return cudaGetLastError();
 }
 
-// tc: 0 = SIMT trailing updates, 1 = TF32 (1 pass), 3 = FP32-class (3 passes)
+// tc: 0 = SIMT trailing updates, else tensor cores (classes per launch).
+// A16 / tmap16: the FP16 tile store (same tile indices as A) that class-1
+// solves' panel solves write and their updates read; null without class 1.
 cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, void *A, void *Z,
                           bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
-                          const CUtensorMap *tmap, const CUtensorMap *tmapZ, int *d_err, Prof *prof) {
-    // set on every call: the attribute is per device
-    allow_max_dyn_smem(tile_mma_kernel<TC_TF32>);
+                          const CUtensorMap *tmap, const CUtensorMap *tmapZ, __half *A16, const CUtensorMap *tmap16,
+                          int *d_err, Prof *prof) {
+    allow_max_dyn_smem(tile_mma_kernel<TC_F16>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3>);
     allow_max_dyn_smem(tile_mma_kernel<TC_BF16X3>);
     if (fp64)
-        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, d_solves, nsolve, flags, 0, tmap,
-                                       tmapZ, d_err, prof);
-    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, d_solves, nsolve, flags, tc, tmap, tmapZ,
-                                  d_err, prof);
+        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, nullptr, d_solves, nsolve, flags, 0,
+                                       tmap, tmapZ, nullptr, d_err, prof);
+    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, A16, d_solves, nsolve, flags, tc, tmap,
+                                  tmapZ, tmap16, d_err, prof);
 }
 
 }  // namespace krr

@@ -42,6 +42,8 @@ struct PartDesc {
 struct SolveDesc {
     int32_t part, isig, ilam, T;
     int32_t m, grp;   // grp = partition * nsig + isig (kernel-store group)
+    int32_t cls;      // factor class: 0 FP64, 1 one pass (FP16 factor store), 2 BF16x3, 3 TF32x3
+    int32_t pad0;
     int64_t ltile0;   // first tile in the factor store (lower tiles, row-major triangle order)
     int64_t dtile0;   // first tile in the diagonal-inverse store
     int64_t ktile0;   // first tile of the (partition, sigma) kernel store

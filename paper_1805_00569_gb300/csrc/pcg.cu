@@ -20,6 +20,8 @@
 //               stopping test ||r||_inf <= tau (||A||_inf ||x||_inf + ||y||_inf).
 #include <type_traits>
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -205,15 +207,23 @@ __global__ void matvec_reduce_kernel(const GroupDesc *__restrict__ groups, const
 }
 
 // ---------------------------------------------------------------- preconditioner
-// z = L^-T L^-1 r for active solves; L tiles in Lst (type TT), inverses in Zst.
-// 512 threads (16 warps).  v: working vector in shared memory (TT type).
-// Off-diagonal tiles are processed two at a time with every load of both
-// tiles issued before the arithmetic (streaming hint, no L1 allocation): one
-// CTA per solve must keep ~100 KB in flight to approach its share of HBM.
-// four consecutive elements, loaded with one (float) or two (double) 16-byte
-// streaming loads
+// z = L^-T L^-1 r for active solves; off-diagonal L tiles in Lst (FP32 or
+// FP64) or, for one-pass (class 1) solves, in the FP16 store L16; diagonal
+// blocks through the inverses Zst.  512 threads (16 warps).  v: working vector
+// in shared memory (TT type); arithmetic in TT.  Off-diagonal tiles are
+// processed two at a time with every load of both tiles issued before the
+// arithmetic (streaming hint, no L1 allocation): one CTA per solve must keep
+// ~100 KB in flight to approach its share of HBM.
+// four consecutive elements of a tile row, loaded with one 8-byte (half), one
+// 16-byte (float) or two 16-byte (double) streaming loads
 struct V4f { float a, b, c, d; };
 struct V4d { double a, b, c, d; };
+__device__ __forceinline__ V4f ld4(const __half *p) {
+    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
+    const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return V4f{x.x, x.y, y.x, y.y};
+}
 __device__ __forceinline__ V4f ld4(const float *p) {
     const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
     return V4f{v.x, v.y, v.z, v.w};
@@ -223,26 +233,26 @@ __device__ __forceinline__ V4d ld4(const double *p) {
     const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
     return V4d{v0.x, v0.y, v1.x, v1.y};
 }
-template <typename TT> struct V4 { using type = V4f; };
+template <typename LT> struct V4 { using type = V4f; };
 template <> struct V4<double> { using type = V4d; };
 
 // acc[u] += sum over this lane's columns 4 lane .. 4 lane + 3 of row (warp + 16u)
-template <typename TT>
-__device__ __forceinline__ void rows_dot(const TT *__restrict__ t, const TT *__restrict__ y, int warp, int lane,
+template <typename TT, typename LT>
+__device__ __forceinline__ void rows_dot(const LT *__restrict__ t, const TT *__restrict__ y, int warp, int lane,
                                          TT (&acc)[8]) {
     const TT y0 = y[4 * lane], y1 = y[4 * lane + 1], y2 = y[4 * lane + 2], y3 = y[4 * lane + 3];
-    typename V4<TT>::type l[8];
+    typename V4<LT>::type l[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
 #pragma unroll
     for (int u = 0; u < 8; ++u) acc[u] += l[u].a * y0 + l[u].b * y1 + l[u].c * y2 + l[u].d * y3;
 }
 // the same for two tiles at once (all 16 wide loads issued before any use)
-template <typename TT>
-__device__ __forceinline__ void rows_dot2(const TT *__restrict__ t0, const TT *__restrict__ y0p,
-                                          const TT *__restrict__ t1, const TT *__restrict__ y1p, int warp, int lane,
+template <typename TT, typename LT>
+__device__ __forceinline__ void rows_dot2(const LT *__restrict__ t0, const TT *__restrict__ y0p,
+                                          const LT *__restrict__ t1, const TT *__restrict__ y1p, int warp, int lane,
                                           TT (&acc)[8]) {
-    typename V4<TT>::type l[16];
+    typename V4<LT>::type l[16];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
@@ -255,10 +265,10 @@ __device__ __forceinline__ void rows_dot2(const TT *__restrict__ t0, const TT *_
         acc[u] += (l[u].a * a0 + l[u].b * a1 + l[u].c * a2 + l[u].d * a3) +
                   (l[8 + u].a * b0 + l[8 + u].b * b1 + l[8 + u].c * b2 + l[8 + u].d * b3);
 }
-template <typename TT>
-__device__ __forceinline__ void cols_dot2(const TT *__restrict__ t0, const TT *__restrict__ t1,
+template <typename TT, typename LT>
+__device__ __forceinline__ void cols_dot2(const LT *__restrict__ t0, const LT *__restrict__ t1,
                                           const TT *__restrict__ w, int warp, int lane, TT (&p0)[4], TT (&p1)[4]) {
-    typename V4<TT>::type l[16];
+    typename V4<LT>::type l[16];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
@@ -278,10 +288,10 @@ __device__ __forceinline__ void cols_dot2(const TT *__restrict__ t0, const TT *_
     }
 }
 // part[q] += sum over this warp's rows rr of t[rr][4 lane + q] * w[rr]
-template <typename TT>
-__device__ __forceinline__ void cols_dot(const TT *__restrict__ t, const TT *__restrict__ w, int warp, int lane,
+template <typename TT, typename LT>
+__device__ __forceinline__ void cols_dot(const LT *__restrict__ t, const TT *__restrict__ w, int warp, int lane,
                                          TT (&part)[4]) {
-    typename V4<TT>::type l[8];
+    typename V4<LT>::type l[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
 #pragma unroll
@@ -294,27 +304,17 @@ __device__ __forceinline__ void cols_dot(const TT *__restrict__ t, const TT *__r
     }
 }
 
-template <typename TT>
-__global__ void __launch_bounds__(512, 1)
-precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const SolveDesc *__restrict__ solves,
-               const PcgState *__restrict__ state, const double *__restrict__ r, double *__restrict__ z) {
-    extern __shared__ __align__(16) unsigned char pc_dyn[];
-    const int s = blockIdx.x;
-    if (!state[s].active) return;
-    const SolveDesc S = solves[s];
-    const int T = S.T, M = T * KRR_TILE;
-    TT *v = reinterpret_cast<TT *>(pc_dyn);            // [M]
-    TT *red = v + M;                                   // [2][16][128]
-    TT *tmp = red + 32 * KRR_TILE;                     // [128]
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int e = threadIdx.x; e < M; e += blockDim.x) v[e] = (TT)r[S.vec0 + e];
-    __syncthreads();
+// v <- L^-T L^-1 v for one solve, off-diagonal tiles of type LT from Lst
+template <typename TT, typename LT>
+__device__ __forceinline__ void precond_solve(const LT *__restrict__ Lst, const TT *__restrict__ Zst,
+                                              const SolveDesc &S, TT *v, TT *red, TT *tmp, int warp, int lane) {
+    const int T = S.T;
     // forward: y_i = Z_ii (v_i - sum_{j<i} L_ij y_j); y overwrites v
     for (int i = 0; i < T; ++i) {
         TT acc[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) acc[u] = TT(0);
-        const TT *row0 = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2) * KRR_TILE_ELEMS;
+        const LT *row0 = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2) * KRR_TILE_ELEMS;
         int j = 0;
         for (; j + 1 < i; j += 2)
             rows_dot2(row0 + (int64_t)j * KRR_TILE_ELEMS, v + j * KRR_TILE, row0 + (int64_t)(j + 1) * KRR_TILE_ELEMS,
@@ -361,7 +361,7 @@ precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const Sol
             __syncthreads();
         }
         // v_i -= L_ji^T w_j for i < j  (tiles of block row j), two tiles per pass
-        const TT *row0 = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2) * KRR_TILE_ELEMS;
+        const LT *row0 = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2) * KRR_TILE_ELEMS;
         const TT *wj = v + j * KRR_TILE;
         for (int i = 0; i < j; i += 2) {
             const bool two = i + 1 < j;
@@ -387,6 +387,30 @@ precond_kernel(const TT *__restrict__ Lst, const TT *__restrict__ Zst, const Sol
             }
             __syncthreads();
         }
+    }
+}
+
+template <typename TT>
+__global__ void __launch_bounds__(512, 1)
+precond_kernel(const TT *__restrict__ Lst, const __half *__restrict__ L16, const TT *__restrict__ Zst,
+               const SolveDesc *__restrict__ solves, const PcgState *__restrict__ state, const double *__restrict__ r,
+               double *__restrict__ z) {
+    extern __shared__ __align__(16) unsigned char pc_dyn[];
+    const int s = blockIdx.x;
+    if (!state[s].active) return;
+    const SolveDesc S = solves[s];
+    const int T = S.T, M = T * KRR_TILE;
+    TT *v = reinterpret_cast<TT *>(pc_dyn);            // [M]
+    TT *red = v + M;                                   // [2][16][128]
+    TT *tmp = red + 32 * KRR_TILE;                     // [128]
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int e = threadIdx.x; e < M; e += blockDim.x) v[e] = (TT)r[S.vec0 + e];
+    __syncthreads();
+    if constexpr (std::is_same<TT, float>::value) {
+        if (S.cls == 1 && L16 != nullptr) precond_solve<float, __half>(L16, Zst, S, v, red, tmp, warp, lane);
+        else precond_solve<float, float>(Lst, Zst, S, v, red, tmp, warp, lane);
+    } else {
+        precond_solve<TT, TT>(Lst, Zst, S, v, red, tmp, warp, lane);
     }
     for (int e = threadIdx.x; e < M; e += blockDim.x) z[S.vec0 + e] = (e < S.m) ? (double)v[e] : 0.0;
 }
@@ -585,6 +609,7 @@ struct PcgBuffers {
     int ng;
     int64_t gtiles;
     int maxT;
+    const void *L16;  // FP16 factor store of class-1 solves (null without them)
 };
 
 size_t pcg_state_size() { return sizeof(PcgState); }
@@ -613,11 +638,11 @@ static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuff
     if (fp64) {
         allow_max_dyn_smem(precond_kernel<double>);
         KRR_LAUNCHED(), precond_kernel<double><<<(unsigned)M.solves.size(), 512, sm, st>>>(
-            (const double *)L, (const double *)Z, M.d_solves, B.state, B.r, B.z);
+            (const double *)L, nullptr, (const double *)Z, M.d_solves, B.state, B.r, B.z);
     } else {
         allow_max_dyn_smem(precond_kernel<float>);
-        KRR_LAUNCHED(), precond_kernel<float><<<(unsigned)M.solves.size(), 512, sm, st>>>((const float *)L, (const float *)Z,
-                                                                           M.d_solves, B.state, B.r, B.z);
+        KRR_LAUNCHED(), precond_kernel<float><<<(unsigned)M.solves.size(), 512, sm, st>>>(
+            (const float *)L, (const __half *)B.L16, (const float *)Z, M.d_solves, B.state, B.r, B.z);
     }
     return cudaGetLastError();
 }

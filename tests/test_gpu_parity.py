@@ -246,6 +246,13 @@ def test_bkrr2_full_size_sampled(ctx, prec):
             assert rel(yhat[j * G + g], oyh) <= REFINED_TOL
             gm = np.mean((yhat[j * G + g] - yt[sample]) ** 2)
             assert abs(gm - oracle.mse(oyh, yt[sample])) <= REFINED_TOL * oracle.mse(oyh, yt[sample])
+        if prec == "tf32":
+            # one-pass solves (FP16 factor store, several panels of 8 tiles):
+            # their factor must still precondition well
+            it, kap, _ = K.krr_model_stats(ctx, model)
+            one_pass = kap.numpy() * 2.0 ** -11 <= 32
+            assert one_pass.sum() >= 48, kap.numpy()
+            assert np.all(it.numpy()[one_pass] <= 10), it.numpy()[one_pass]
     finally:
         model.free()
 
