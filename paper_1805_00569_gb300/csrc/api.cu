@@ -60,6 +60,7 @@ struct PcgBuffers {
     int64_t gtiles;
     int maxT;
     const void *L16;  // FP16 factor store of class-1 solves (null without them)
+    int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
 };
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
@@ -432,7 +433,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                         (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
                         (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
-                        4 * nsolve + 64 * 1024 * 1024;
+                        8 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
         delete km;
         return fail(c, KRR_ERR_BUDGET, "krr_fit_batch: needs " + std::to_string(model_bytes + work_bytes) +
@@ -490,6 +491,16 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         FIT_TRY(W.get(&d_groups, sizeof(GroupDesc) * groups.size()));
         FIT_TRY(W.get(&d_gpre, sizeof(int64_t) * gpre.size()));
         FIT_TRY(W.get(&flags, sizeof(int32_t) * nsolve));
+        int32_t *d_order = nullptr;
+        FIT_TRY(W.get(&d_order, sizeof(int32_t) * nsolve));
+        {
+            std::vector<int32_t> order(nsolve);
+            for (int s = 0; s < nsolve; ++s) order[s] = s;
+            std::stable_sort(order.begin(), order.end(),
+                             [&](int32_t a, int32_t b) { return M.solves[a].T > M.solves[b].T; });
+            FIT_TRY(cudaMemcpyAsync(d_order, order.data(), sizeof(int32_t) * nsolve, cudaMemcpyHostToDevice, st));
+            FIT_TRY(cudaStreamSynchronize(st));  // the host vector goes out of scope
+        }
         FIT_TRY(cudaMemcpyAsync(d_groups, groups.data(), sizeof(GroupDesc) * groups.size(), cudaMemcpyHostToDevice,
                                 st));
         FIT_TRY(cudaMemcpyAsync(d_gpre, gpre.data(), sizeof(int64_t) * gpre.size(), cudaMemcpyHostToDevice, st));
@@ -548,6 +559,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.gtiles = gtiles;
         B.maxT = maxT;
         B.L16 = A16;
+        B.order = d_order;
         FIT_TRY(run_pcg_norms(st, M, B, Kh, Kl, K64, fp64, prof));
         std::vector<PcgState> hs0(nsolve);
         FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));

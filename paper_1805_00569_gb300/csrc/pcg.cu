@@ -215,93 +215,67 @@ __global__ void matvec_reduce_kernel(const GroupDesc *__restrict__ groups, const
 // arithmetic (streaming hint, no L1 allocation): one CTA per solve must keep
 // ~100 KB in flight to approach its share of HBM.
 // four consecutive elements of a tile row, loaded with one 8-byte (half), one
-// 16-byte (float) or two 16-byte (double) streaming loads
+// 16-byte (float) or two 16-byte (double) streaming loads; kept as loaded
+// (Raw) until use, so a batch of FP16 loads takes half the registers
 struct V4f { float a, b, c, d; };
 struct V4d { double a, b, c, d; };
-__device__ __forceinline__ V4f ld4(const __half *p) {
-    const uint2 u = __ldcs(reinterpret_cast<const uint2 *>(p));
-    const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
-    const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
-    return V4f{x.x, x.y, y.x, y.y};
-}
-__device__ __forceinline__ V4f ld4(const float *p) {
-    const float4 v = __ldcs(reinterpret_cast<const float4 *>(p));
-    return V4f{v.x, v.y, v.z, v.w};
-}
-__device__ __forceinline__ V4d ld4(const double *p) {
+template <typename LT> struct Raw;
+template <> struct Raw<__half> { using type = uint2; using val = V4f; };
+template <> struct Raw<float> { using type = float4; using val = V4f; };
+template <> struct Raw<double> { using type = V4d; using val = V4d; };
+__device__ __forceinline__ uint2 ldraw(const __half *p) { return __ldcs(reinterpret_cast<const uint2 *>(p)); }
+__device__ __forceinline__ float4 ldraw(const float *p) { return __ldcs(reinterpret_cast<const float4 *>(p)); }
+__device__ __forceinline__ V4d ldraw(const double *p) {
     const double2 v0 = __ldcs(reinterpret_cast<const double2 *>(p));
     const double2 v1 = __ldcs(reinterpret_cast<const double2 *>(p) + 1);
     return V4d{v0.x, v0.y, v1.x, v1.y};
 }
-template <typename LT> struct V4 { using type = V4f; };
-template <> struct V4<double> { using type = V4d; };
+__device__ __forceinline__ V4f val4(uint2 u) {
+    const float2 x = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 y = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return V4f{x.x, x.y, y.x, y.y};
+}
+__device__ __forceinline__ V4f val4(float4 v) { return V4f{v.x, v.y, v.z, v.w}; }
+__device__ __forceinline__ V4d val4(V4d v) { return v; }
 
-// acc[u] += sum over this lane's columns 4 lane .. 4 lane + 3 of row (warp + 16u)
-template <typename TT, typename LT>
-__device__ __forceinline__ void rows_dot(const LT *__restrict__ t, const TT *__restrict__ y, int warp, int lane,
-                                         TT (&acc)[8]) {
-    const TT y0 = y[4 * lane], y1 = y[4 * lane + 1], y2 = y[4 * lane + 2], y3 = y[4 * lane + 3];
-    typename V4<LT>::type l[8];
+// acc[u] += sum over tiles k and this lane's columns 4 lane .. 4 lane + 3 of
+// t_k[row warp + 16u] * y_k (all loads of the batch issued before any use)
+template <int NT, typename TT, typename LT>
+__device__ __forceinline__ void rows_acc(const LT *const *t, const TT *const *y, int warp, int lane, TT (&acc)[8]) {
+    typename Raw<LT>::type l[NT][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
+    for (int k = 0; k < NT; ++k)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc[u] += l[u].a * y0 + l[u].b * y1 + l[u].c * y2 + l[u].d * y3;
-}
-// the same for two tiles at once (all 16 wide loads issued before any use)
-template <typename TT, typename LT>
-__device__ __forceinline__ void rows_dot2(const LT *__restrict__ t0, const TT *__restrict__ y0p,
-                                          const LT *__restrict__ t1, const TT *__restrict__ y1p, int warp, int lane,
-                                          TT (&acc)[8]) {
-    typename V4<LT>::type l[16];
+        for (int u = 0; u < 8; ++u) l[k][u] = ldraw(t[k] + (warp + 16 * u) * KRR_TILE + 4 * lane);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
-        l[8 + u] = ld4(t1 + (warp + 16 * u) * KRR_TILE + 4 * lane);
-    }
-    const TT a0 = y0p[4 * lane], a1 = y0p[4 * lane + 1], a2 = y0p[4 * lane + 2], a3 = y0p[4 * lane + 3];
-    const TT b0 = y1p[4 * lane], b1 = y1p[4 * lane + 1], b2 = y1p[4 * lane + 2], b3 = y1p[4 * lane + 3];
+    for (int k = 0; k < NT; ++k) {
+        const TT a0 = y[k][4 * lane], a1 = y[k][4 * lane + 1], a2 = y[k][4 * lane + 2], a3 = y[k][4 * lane + 3];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-        acc[u] += (l[u].a * a0 + l[u].b * a1 + l[u].c * a2 + l[u].d * a3) +
-                  (l[8 + u].a * b0 + l[8 + u].b * b1 + l[8 + u].c * b2 + l[8 + u].d * b3);
-}
-template <typename TT, typename LT>
-__device__ __forceinline__ void cols_dot2(const LT *__restrict__ t0, const LT *__restrict__ t1,
-                                          const TT *__restrict__ w, int warp, int lane, TT (&p0)[4], TT (&p1)[4]) {
-    typename V4<LT>::type l[16];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        l[u] = ld4(t0 + (warp + 16 * u) * KRR_TILE + 4 * lane);
-        l[8 + u] = ld4(t1 + (warp + 16 * u) * KRR_TILE + 4 * lane);
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const TT wr = w[warp + 16 * u];
-        p0[0] += l[u].a * wr;
-        p0[1] += l[u].b * wr;
-        p0[2] += l[u].c * wr;
-        p0[3] += l[u].d * wr;
-        p1[0] += l[8 + u].a * wr;
-        p1[1] += l[8 + u].b * wr;
-        p1[2] += l[8 + u].c * wr;
-        p1[3] += l[8 + u].d * wr;
+        for (int u = 0; u < 8; ++u) {
+            const typename Raw<LT>::val e = val4(l[k][u]);
+            acc[u] += e.a * a0 + e.b * a1 + e.c * a2 + e.d * a3;
+        }
     }
 }
-// part[q] += sum over this warp's rows rr of t[rr][4 lane + q] * w[rr]
-template <typename TT, typename LT>
-__device__ __forceinline__ void cols_dot(const LT *__restrict__ t, const TT *__restrict__ w, int warp, int lane,
-                                         TT (&part)[4]) {
-    typename V4<LT>::type l[8];
+// part[q] += sum over tiles k and this warp's rows rr of t_k[rr][4 lane + q] * w_k[rr]
+template <int NT, typename TT, typename LT>
+__device__ __forceinline__ void cols_acc(const LT *const *t, const TT *const *w, int warp, int lane, TT (&part)[4]) {
+    typename Raw<LT>::type l[NT][8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u) l[u] = ld4(t + (warp + 16 * u) * KRR_TILE + 4 * lane);
+    for (int k = 0; k < NT; ++k)
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
-        const TT wr = w[warp + 16 * u];
-        part[0] += l[u].a * wr;
-        part[1] += l[u].b * wr;
-        part[2] += l[u].c * wr;
-        part[3] += l[u].d * wr;
-    }
+        for (int u = 0; u < 8; ++u) l[k][u] = ldraw(t[k] + (warp + 16 * u) * KRR_TILE + 4 * lane);
+#pragma unroll
+    for (int k = 0; k < NT; ++k)
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const TT wr = w[k][warp + 16 * u];
+            const typename Raw<LT>::val e = val4(l[k][u]);
+            part[0] += e.a * wr;
+            part[1] += e.b * wr;
+            part[2] += e.c * wr;
+            part[3] += e.d * wr;
+        }
 }
 
 // v <- L^-T L^-1 v for one solve, off-diagonal tiles of type LT from Lst
@@ -309,6 +283,7 @@ template <typename TT, typename LT>
 __device__ __forceinline__ void precond_solve(const LT *__restrict__ Lst, const TT *__restrict__ Zst,
                                               const SolveDesc &S, TT *v, TT *red, TT *tmp, int warp, int lane) {
     const int T = S.T;
+    constexpr int NB = sizeof(LT) == 2 ? 4 : 2;  // tiles per batch of loads (~128 KB in flight per CTA)
     // forward: y_i = Z_ii (v_i - sum_{j<i} L_ij y_j); y overwrites v
     for (int i = 0; i < T; ++i) {
         TT acc[8];
@@ -316,10 +291,21 @@ __device__ __forceinline__ void precond_solve(const LT *__restrict__ Lst, const 
         for (int u = 0; u < 8; ++u) acc[u] = TT(0);
         const LT *row0 = Lst + (S.ltile0 + (int64_t)i * (i + 1) / 2) * KRR_TILE_ELEMS;
         int j = 0;
-        for (; j + 1 < i; j += 2)
-            rows_dot2(row0 + (int64_t)j * KRR_TILE_ELEMS, v + j * KRR_TILE, row0 + (int64_t)(j + 1) * KRR_TILE_ELEMS,
-                      v + (j + 1) * KRR_TILE, warp, lane, acc);
-        if (j < i) rows_dot(row0 + (int64_t)j * KRR_TILE_ELEMS, v + j * KRR_TILE, warp, lane, acc);
+        for (; j + NB - 1 < i; j += NB) {
+            const LT *tt[NB];
+            const TT *yy[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                tt[k] = row0 + (int64_t)(j + k) * KRR_TILE_ELEMS;
+                yy[k] = v + (j + k) * KRR_TILE;
+            }
+            rows_acc<NB>(tt, yy, warp, lane, acc);
+        }
+        for (; j < i; ++j) {
+            const LT *tt[1] = {row0 + (int64_t)j * KRR_TILE_ELEMS};
+            const TT *yy[1] = {v + j * KRR_TILE};
+            rows_acc<1>(tt, yy, warp, lane, acc);
+        }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             TT a = acc[u];
@@ -332,7 +318,9 @@ __device__ __forceinline__ void precond_solve(const LT *__restrict__ Lst, const 
             TT zr[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u) zr[u] = TT(0);
-            rows_dot(Zst + (S.dtile0 + i) * KRR_TILE_ELEMS, tmp, warp, lane, zr);
+            const TT *zt[1] = {Zst + (S.dtile0 + i) * KRR_TILE_ELEMS};
+            const TT *zy[1] = {tmp};
+            rows_acc<1>(zt, zy, warp, lane, zr);
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 TT a = zr[u];
@@ -343,60 +331,62 @@ __device__ __forceinline__ void precond_solve(const LT *__restrict__ Lst, const 
         }
         __syncthreads();
     }
-    // backward: w_j = Z_jj^T (y_j - sum_{i>j} L_ij^T w_i), right-looking over j
-    for (int j = T - 1; j >= 0; --j) {
+    // backward, left-looking: w_i = Z_ii^T (y_i - sum_{j>i} L_ji^T w_j) for
+    // i = T-1 .. 0; the tiles of block column i below the diagonal are
+    // streamed with per-thread partial sums and one cross-warp reduction per
+    // block column; w overwrites v
+    for (int i = T - 1; i >= 0; --i) {
+        TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
+        int j = i + 1;
+        for (; j + NB - 1 < T; j += NB) {
+            const LT *tt[NB];
+            const TT *ww[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) {
+                tt[k] = Lst + (S.ltile0 + (int64_t)(j + k) * (j + k + 1) / 2 + i) * KRR_TILE_ELEMS;
+                ww[k] = v + (j + k) * KRR_TILE;
+            }
+            cols_acc<NB>(tt, ww, warp, lane, part);
+        }
+        for (; j < T; ++j) {
+            const LT *tt[1] = {Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2 + i) * KRR_TILE_ELEMS};
+            const TT *ww[1] = {v + j * KRR_TILE};
+            cols_acc<1>(tt, ww, warp, lane, part);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + 4 * lane + q] = part[q];
+        __syncthreads();
+        if (threadIdx.x < KRR_TILE) {
+            TT a = TT(0);
+            for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
+            tmp[threadIdx.x] = v[i * KRR_TILE + threadIdx.x] - a;
+        }
+        __syncthreads();
         {
-            TT part[4] = {TT(0), TT(0), TT(0), TT(0)};
-            cols_dot(Zst + (S.dtile0 + j) * KRR_TILE_ELEMS, v + j * KRR_TILE, warp, lane, part);
+            TT zp[4] = {TT(0), TT(0), TT(0), TT(0)};
+            const TT *zt[1] = {Zst + (S.dtile0 + i) * KRR_TILE_ELEMS};
+            const TT *zw[1] = {tmp};
+            cols_acc<1>(zt, zw, warp, lane, zp);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + 4 * lane + q] = part[q];
-            __syncthreads();
-            if (threadIdx.x < KRR_TILE) {
-                TT a = TT(0);
-                for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
-                tmp[threadIdx.x] = a;
-            }
-            __syncthreads();
-            if (threadIdx.x < KRR_TILE) v[j * KRR_TILE + threadIdx.x] = tmp[threadIdx.x];
-            __syncthreads();
+            for (int q = 0; q < 4; ++q) red[warp * KRR_TILE + 4 * lane + q] = zp[q];
         }
-        // v_i -= L_ji^T w_j for i < j  (tiles of block row j), two tiles per pass
-        const LT *row0 = Lst + (S.ltile0 + (int64_t)j * (j + 1) / 2) * KRR_TILE_ELEMS;
-        const TT *wj = v + j * KRR_TILE;
-        for (int i = 0; i < j; i += 2) {
-            const bool two = i + 1 < j;
-            TT p0[4] = {TT(0), TT(0), TT(0), TT(0)}, p1[4] = {TT(0), TT(0), TT(0), TT(0)};
-            if (two)
-                cols_dot2(row0 + (int64_t)i * KRR_TILE_ELEMS, row0 + (int64_t)(i + 1) * KRR_TILE_ELEMS, wj, warp, lane,
-                          p0, p1);
-            else
-                cols_dot(row0 + (int64_t)i * KRR_TILE_ELEMS, wj, warp, lane, p0);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                red[warp * KRR_TILE + 4 * lane + q] = p0[q];
-                red[16 * KRR_TILE + warp * KRR_TILE + 4 * lane + q] = p1[q];
-            }
-            __syncthreads();
-            if (threadIdx.x < 2 * KRR_TILE) {
-                const int h = threadIdx.x >> 7, c = threadIdx.x & 127;
-                if (h == 0 || two) {
-                    TT a = TT(0);
-                    for (int w = 0; w < 16; ++w) a += red[h * 16 * KRR_TILE + w * KRR_TILE + c];
-                    v[(i + h) * KRR_TILE + c] -= a;
-                }
-            }
-            __syncthreads();
+        __syncthreads();
+        if (threadIdx.x < KRR_TILE) {
+            TT a = TT(0);
+            for (int w = 0; w < 16; ++w) a += red[w * KRR_TILE + threadIdx.x];
+            v[i * KRR_TILE + threadIdx.x] = a;
         }
+        __syncthreads();
     }
 }
 
 template <typename TT>
 __global__ void __launch_bounds__(512, 1)
 precond_kernel(const TT *__restrict__ Lst, const __half *__restrict__ L16, const TT *__restrict__ Zst,
-               const SolveDesc *__restrict__ solves, const PcgState *__restrict__ state, const double *__restrict__ r,
-               double *__restrict__ z) {
+               const SolveDesc *__restrict__ solves, const int32_t *__restrict__ order,
+               const PcgState *__restrict__ state, const double *__restrict__ r, double *__restrict__ z) {
     extern __shared__ __align__(16) unsigned char pc_dyn[];
-    const int s = blockIdx.x;
+    const int s = order[blockIdx.x];  // largest solves first: they set the launch's length
     if (!state[s].active) return;
     const SolveDesc S = solves[s];
     const int T = S.T, M = T * KRR_TILE;
@@ -610,6 +600,7 @@ struct PcgBuffers {
     int64_t gtiles;
     int maxT;
     const void *L16;  // FP16 factor store of class-1 solves (null without them)
+    int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
 };
 
 size_t pcg_state_size() { return sizeof(PcgState); }
@@ -638,11 +629,11 @@ static cudaError_t launch_precond(cudaStream_t st, const Model &M, const PcgBuff
     if (fp64) {
         allow_max_dyn_smem(precond_kernel<double>);
         KRR_LAUNCHED(), precond_kernel<double><<<(unsigned)M.solves.size(), 512, sm, st>>>(
-            (const double *)L, nullptr, (const double *)Z, M.d_solves, B.state, B.r, B.z);
+            (const double *)L, nullptr, (const double *)Z, M.d_solves, B.order, B.state, B.r, B.z);
     } else {
         allow_max_dyn_smem(precond_kernel<float>);
         KRR_LAUNCHED(), precond_kernel<float><<<(unsigned)M.solves.size(), 512, sm, st>>>(
-            (const float *)L, (const __half *)B.L16, (const float *)Z, M.d_solves, B.state, B.r, B.z);
+            (const float *)L, (const __half *)B.L16, (const float *)Z, M.d_solves, B.order, B.state, B.r, B.z);
     }
     return cudaGetLastError();
 }
