@@ -44,7 +44,7 @@ void build_chol_plan(const std::vector<int> &, const std::vector<int> &, int, st
                      std::vector<int64_t> &);
 cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
                           const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, __half *,
-                          const CUtensorMap *, int *, Prof *);
+                          const CUtensorMap *, float *, const CUtensorMap *, int *, Prof *);
 bool make_tile_tmap(CUtensorMap *, float *, int64_t);
 bool make_tile_tmap16(CUtensorMap *, __half *, int64_t);
 size_t pcg_state_size();
@@ -402,6 +402,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 S.grp = j * ns + is;
                 S.cls = 0;
                 S.pad0 = 0;
+                S.lotile0 = -1;
                 S.ltile0 = ltiles;
                 S.dtile0 = dtiles;
                 S.ktile0 = Gd.ktile0;
@@ -431,7 +432,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                          sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
                         (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
-                        (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) +
+                        (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) + (fp64 ? 0 : (size_t)ltiles * tileb) +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
                         8 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
@@ -588,9 +589,23 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         if (tf32)
             for (int s = 0; s < nsolve; ++s)
                 if (cls[s] == 1 && !(1.0 + M.solves[s].lambda_m <= 16777216.0)) cls[s] = 3;
+        int64_t lotiles = 0;  // lo parts of class-3 L tiles, written by the panel solves
         for (int s = 0; s < nsolve; ++s) {
             M.st_class[s] = cls[s];
             M.solves[s].cls = cls[s];
+            M.solves[s].lotile0 = -1;
+            if (cls[s] == 3) {
+                M.solves[s].lotile0 = lotiles;
+                lotiles += tri(M.solves[s].T);
+            }
+        }
+        float *Alo = nullptr;
+        CUtensorMap tmapLo;
+        memset(&tmapLo, 0, sizeof(tmapLo));
+        if (lotiles > 0) {
+            FIT_TRY(W.get(&Alo, (size_t)lotiles * KRR_TILE_ELEMS * sizeof(float)));
+            if (!make_tile_tmap(&tmapLo, Alo, lotiles))
+                return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled failed");
         }
         FIT_TRY(cudaMemcpyAsync(M.d_solves, M.solves.data(), sizeof(SolveDesc) * nsolve, cudaMemcpyHostToDevice, st));
 
@@ -635,7 +650,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                                                                                          Kh, (float *)Ast, 0.f);
                     cudaEventRecord(e0, st);
                     FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tcmode,
-                                          &tmap, &tmapZ, A16, &tmap16, c->d_err, nullptr));
+                                          &tmap, &tmapZ, A16, &tmap16, Alo, &tmapLo, c->d_err, nullptr));
                     cudaEventRecord(e1, st);
                     FIT_TRY(cudaEventSynchronize(e1));
                     float ms = 0.f;
@@ -661,7 +676,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             if (!pre.empty())
                 FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
             FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tcmode, &tmap, &tmapZ,
-                                  A16, &tmap16, c->d_err, prof));
+                                  A16, &tmap16, Alo, &tmapLo, c->d_err, prof));
             FIT_TRY(cudaMemcpyAsync(hflags.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
             FIT_TRY(cudaStreamSynchronize(st));
         }
@@ -680,7 +695,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 std::vector<int64_t> rpre(nsub + 1, 0);
                 for (int i = 0; i < nsub; ++i) {
                     sub[i] = M.solves[failed[i]];
-                    sub[i].cls = 3;  // refactored in 3 passes, L in the FP32 store
+                    sub[i].cls = 4;  // refactored in 3 passes split in shared memory, L in the FP32 store
                     rpre[i + 1] = rpre[i] + tri(sub[i].T);
                 }
                 SolveDesc *d_sub = nullptr;
@@ -700,19 +715,19 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 for (int i = 0; i < nsub; ++i) rT[i] = sub[i].T;
                 std::vector<CholLaunch> rplan;
                 std::vector<int64_t> rp;
-                build_chol_plan(rT, std::vector<int>(nsub, 3), 1, rplan, rp);
+                build_chol_plan(rT, std::vector<int>(nsub, 4), 1, rplan, rp);
                 int64_t *d_rplan = nullptr;
                 FIT_TRY(R.get(&d_rplan, sizeof(int64_t) * std::max<size_t>(rp.size(), 1)));
                 FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
                                         st));
                 FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, 3, &tmap, &tmapZ,
-                                      A16, &tmap16, c->d_err, prof));
+                                      A16, &tmap16, Alo, &tmapLo, c->d_err, prof));
                 std::vector<int32_t> hr(nsub);
                 FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
                 FIT_TRY(cudaStreamSynchronize(st));
                 for (int i = 0; i < nsub; ++i) {
                     hflags[failed[i]] = hr[i];
-                    if (!hr[i]) M.st_class[failed[i]] = 3;
+                    if (!hr[i]) M.st_class[failed[i]] = 4;
                 }
             }
         }

@@ -314,7 +314,10 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 // its L tiles in FP16 for this.  TC_BF16X3: warps 6..9 convert each landed FP32
 // stage into BF16 hi = rn(x) and lo = rn(x - hi) operands and three kind::f16
 // MMAs per K step form hi*hi + hi*lo + lo*hi (~16-bit products at the BF16
-// rate).  TC_TF32X3: warps 6..9 split each landed stage
+// rate).  TC_TF32X3P: the three-pass form on operands split once, by the
+// panel solve that wrote them: x (FP32 store; the tensor core reads its top
+// 19 bits, hi) and lo = x - hi (FP32 side store); TMA lands x and lo, no
+// split warps.  TC_TF32X3: warps 6..9 split each landed stage
 // into hi = x with the low 13 mantissa bits cleared and lo = x - hi (exact),
 // and three MMAs per K step form hi*hi + hi*lo + lo*hi: FP32-class products on
 // the tensor cores.
@@ -340,15 +343,17 @@ __device__ __forceinline__ uint64_t smem_desc_sw64_tc(const void *p) {
 // MODE: TC_TF32 one pass; TC_TF32X3 three TF32 passes on hi/lo splits;
 // TC_BF16X3 three BF16 passes (kind::f16) on hi/lo BF16 splits; TC_F16 one
 // kind::f16 pass on FP16 operands (64 halves = 128 bytes of K per stage)
-enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3 };
+enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3, TC_TF32X3P = 4 };
 template <int MODE> struct TcCfg {
-    static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;
+    static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;  // split warps present
+    static constexpr bool PRE = MODE == TC_TF32X3P;                        // lo operands landed by TMA
     static constexpr int STAGES = SPLIT ? 2 : 3;
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
-    static constexpr uint32_t STAGE_BYTES = (SPLIT ? 4u : 2u) * TC_HALF;
+    static constexpr uint32_t STAGE_BYTES = (SPLIT || PRE ? 4u : 2u) * TC_HALF;
     static constexpr int THREADS = SPLIT ? 320 : 192;
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static_assert(SMEM <= 232448, "tile kernel shared memory");
 };
 
 __device__ __forceinline__ uint64_t global_ns() {
@@ -373,11 +378,12 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
 template <int MODE>
 __global__ void __launch_bounds__(TcCfg<MODE>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
-                float *__restrict__ A, __half *__restrict__ A16, const SolveDesc *__restrict__ solves,
-                const int64_t *__restrict__ pre, int nsolve, int64_t ntasks, int mode, int K0, int W,
-                int *__restrict__ err) {
+                const __grid_constant__ CUtensorMap tmapLo, float *__restrict__ A, __half *__restrict__ A16,
+                float *__restrict__ Alo, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
+                int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
     using Cfg = TcCfg<MODE>;
-    constexpr bool X3 = Cfg::SPLIT;
+    constexpr bool X3 = Cfg::SPLIT;                              // split warps
+    constexpr bool X3MMA = MODE == TC_TF32X3 || MODE == TC_TF32X3P;  // three TF32 passes
     // elements of K per stage: 32 floats or 64 halves (128 bytes either way)
     constexpr int KEL = MODE == TC_F16 ? 2 * TC_CHUNK : TC_CHUNK;
     constexpr int KCH = KRR_TILE / KEL;  // chunks per K tile
@@ -443,13 +449,19 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 const int kt = g.kb + c / KCH;
                 const int x = (c % KCH) * KEL;
                 const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
-                mbar_arrive_expect_tx(&full[st], 2 * TC_HALF);
+                mbar_arrive_expect_tx(&full[st], (Cfg::PRE ? 4 : 2) * TC_HALF);
                 tma_load_2d(sa, &tmap, x, ya, &full[st]);
                 if (mode == UPD_TRSM) {
                     tma_load_2d(sb, &tmapZ, x, (int)((S.dtile0 + kt) * KRR_TILE), &full[st]);
                 } else {
                     const int yb = (int)((S.ltile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE);
                     tma_load_2d(sb, &tmap, x, yb, &full[st]);
+                }
+                if constexpr (Cfg::PRE) {  // lo parts of both operands (updates only)
+                    tma_load_2d(sa + 2 * TC_HALF, &tmapLo, x,
+                                (int)((S.lotile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE), &full[st]);
+                    tma_load_2d(sa + 3 * TC_HALF, &tmapLo, x,
+                                (int)((S.lotile0 + (int64_t)g.j * (g.j + 1) / 2 + kt) * KRR_TILE), &full[st]);
                 }
             }
         }
@@ -501,7 +513,7 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                     for (int kk = 0; kk < TC_CHUNK / 8; ++kk) {  // K = 8 TF32 = 32 bytes per MMA
                         const uint32_t acc0 = (c > 0 || kk > 0) ? 1u : 0u;
                         tc_mma_tf32(acc, da + 2 * kk, db + 2 * kk, TC_IDESC, acc0);
-                        if (X3) {
+                        if (X3MMA) {
                             const uint64_t dal = smem_desc_sw128(sa + 2 * TC_HALF),
                                            dbl = smem_desc_sw128(sb + 2 * TC_HALF);
                             tc_mma_tf32(acc, da + 2 * kk, dbl + 2 * kk, TC_IDESC, 1u);
@@ -590,6 +602,12 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
             // a class-1 solve's panel solve writes its L tile in FP16 (operand of the one-pass updates)
             const bool half_out = mode == UPD_TRSM && S.cls == 1;
             __half *dst16 = half_out ? A16 + (dst_tile(S, g) - A) + (int64_t)r * KRR_TILE : nullptr;
+            // a class-3 solve's panel solve also writes lo = x - hi (hi: x with
+            // the low 13 mantissa bits cleared), the second operand of TC_TF32X3P
+            const bool lo_out = mode == UPD_TRSM && S.cls == 3 && Alo != nullptr;
+            float *dstlo = lo_out ? Alo + (S.lotile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS +
+                                        (int64_t)r * KRR_TILE
+                                  : nullptr;
             const int b = lt & 1;
             if (!mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err)) break;
             tc_fence_after();
@@ -624,6 +642,18 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq)
                         d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                    if (lo_out) {
+                        float4 *l4 = reinterpret_cast<float4 *>(dstlo + cb * 32);
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq) {
+                            float4 o;
+                            o.x = v[4 * qq + 0] - __uint_as_float(__float_as_uint(v[4 * qq + 0]) & 0xFFFFE000u);
+                            o.y = v[4 * qq + 1] - __uint_as_float(__float_as_uint(v[4 * qq + 1]) & 0xFFFFE000u);
+                            o.z = v[4 * qq + 2] - __uint_as_float(__float_as_uint(v[4 * qq + 2]) & 0xFFFFE000u);
+                            o.w = v[4 * qq + 3] - __uint_as_float(__float_as_uint(v[4 * qq + 3]) & 0xFFFFE000u);
+                            l4[qq] = o;
+                        }
+                    }
                 } else {
 #pragma unroll
                     for (int qq = 0; qq < 8; ++qq) {
@@ -705,9 +735,10 @@ struct CholLaunch {
 };
 
 // Build the schedule for a batch of solves with tile counts T[s] and update
-// classes cls[s] (0 SIMT, 1 TF32, 3 three-pass): the diagonal factorisations
-// and panel solves of all solves share their launches; each update step is
-// one launch per class present.
+// classes cls[s] (0 SIMT, 1 one FP16 pass, 2 BF16x3, 3 TF32x3 pre-split,
+// 4 TF32x3 split in shared memory): the diagonal factorisations and panel
+// solves of all solves share their launches; each update step is one launch
+// per class present.
 void build_chol_plan(const std::vector<int> &T, const std::vector<int> &cls, int W, std::vector<CholLaunch> &plan,
                      std::vector<int64_t> &pre) {
     const int ns = (int)T.size();
@@ -754,9 +785,9 @@ void build_chol_plan(const std::vector<int> &T, const std::vector<int> &cls, int
 
 template <typename T>
 cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, T *A, T *Z,
-                            __half *A16, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
-                            const CUtensorMap *tmap, const CUtensorMap *tmapZ, const CUtensorMap *tmap16, int *d_err,
-                            Prof *prof) {
+                            __half *A16, float *Alo, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
+                            const CUtensorMap *tmap, const CUtensorMap *tmapZ, const CUtensorMap *tmap16,
+                            const CUtensorMap *tmapLo, int *d_err, Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     allow_max_dyn_smem(potrf_tile_kernel<T>);
     int dev = 0, nsm = 1;
@@ -773,27 +804,39 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
         const int mode = L.kind == 1 ? UPD_TRSM : (L.kind == 2 ? UPD_TRAIL : UPD_COLUMN);
         const int W = L.kind == 1 ? 0 : L.W;
         if constexpr (sizeof(T) == 4) {
-            // tensor cores: the panel solve always FP32-class (3 TF32 passes);
-            // updates per class: 1 one FP16 pass (operands from the FP16 copy
-            // of the panel), 2 BF16x3, 3 TF32x3
+            // tensor cores: the panel solve always FP32-class (3 TF32 passes,
+            // split in shared memory); updates per class: 1 one FP16 pass
+            // (operands from the FP16 copy of the panel), 2 BF16x3, 3 TF32x3 on
+            // operands split by the panel solve, 4 TF32x3 split in shared memory
             if (tc != 0) {
-                const int m = (L.kind == 1 || L.tc == 3) ? TC_TF32X3 : (L.tc == 2 ? TC_BF16X3 : TC_F16);
+                int m = TC_TF32X3;
+                if (L.kind != 1) {
+                    if (L.tc == 1) m = TC_F16;
+                    else if (L.tc == 2) m = TC_BF16X3;
+                    else if (L.tc == 3) m = TC_TF32X3P;
+                }
+                if ((m == TC_F16 && (A16 == nullptr || tmap16 == nullptr)) ||
+                    (m == TC_TF32X3P && (Alo == nullptr || tmapLo == nullptr)))
+                    return cudaErrorInvalidValue;  // classes 1 and 3 need their side stores
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 float *Af = reinterpret_cast<float *>(A);
+                const CUtensorMap &tmLo = tmapLo ? *tmapLo : *tmap;
                 if (m == TC_TF32X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
                                                                  TcCfg<TC_TF32X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                else if (m == TC_TF32X3P)
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3P><<<pgrid, TcCfg<TC_TF32X3P>::THREADS,
+                                                                  TcCfg<TC_TF32X3P>::SMEM, st>>>(
+                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else if (m == TC_BF16X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_BF16X3><<<pgrid, TcCfg<TC_BF16X3>::THREADS,
                                                                  TcCfg<TC_BF16X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
-                else if (A16 != nullptr && tmap16 != nullptr)
+                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                else
                     KRR_LAUNCHED(), tile_mma_kernel<TC_F16><<<pgrid, TcCfg<TC_F16>::THREADS,
                                                              TcCfg<TC_F16>::SMEM, st>>>(
-                        *tmap16, *tmapZ, Af, A16, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
-                else
-                    return cudaErrorInvalidValue;  // class 1 needs the FP16 store
+                        *tmap16, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 continue;
             }
         }
@@ -805,18 +848,21 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
 // tc: 0 = SIMT trailing updates, else tensor cores (classes per launch).
 // A16 / tmap16: the FP16 tile store (same tile indices as A) that class-1
 // solves' panel solves write and their updates read; null without class 1.
+// Alo / tmapLo: the lo parts of class-3 solves' L tiles (tile index
+// S.lotile0 + i(i+1)/2 + j); null without class 3.
 cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, void *A, void *Z,
                           bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
                           const CUtensorMap *tmap, const CUtensorMap *tmapZ, __half *A16, const CUtensorMap *tmap16,
-                          int *d_err, Prof *prof) {
+                          float *Alo, const CUtensorMap *tmapLo, int *d_err, Prof *prof) {
     allow_max_dyn_smem(tile_mma_kernel<TC_F16>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3>);
+    allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3P>);
     allow_max_dyn_smem(tile_mma_kernel<TC_BF16X3>);
     if (fp64)
-        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, nullptr, d_solves, nsolve, flags, 0,
-                                       tmap, tmapZ, nullptr, d_err, prof);
-    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, A16, d_solves, nsolve, flags, tc, tmap,
-                                  tmapZ, tmap16, d_err, prof);
+        return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, nullptr, nullptr, d_solves, nsolve,
+                                       flags, 0, tmap, tmapZ, nullptr, nullptr, d_err, prof);
+    return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, A16, Alo, d_solves, nsolve, flags, tc,
+                                  tmap, tmapZ, tmap16, tmapLo, d_err, prof);
 }
 
 }  // namespace krr

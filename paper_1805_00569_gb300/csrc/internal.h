@@ -42,9 +42,11 @@ struct PartDesc {
 struct SolveDesc {
     int32_t part, isig, ilam, T;
     int32_t m, grp;   // grp = partition * nsig + isig (kernel-store group)
-    int32_t cls;      // factor class: 0 FP64, 1 one pass (FP16 factor store), 2 BF16x3, 3 TF32x3
+    int32_t cls;      // factor class: 0 FP64, 1 one pass (FP16 factor store), 2 BF16x3,
+                      // 3 TF32x3 on operands split by the panel solve, 4 TF32x3 split in shared memory
     int32_t pad0;
     int64_t ltile0;   // first tile in the factor store (lower tiles, row-major triangle order)
+    int64_t lotile0;  // class 3: first tile of its L lo parts in the lo store (else -1)
     int64_t dtile0;   // first tile in the diagonal-inverse store
     int64_t ktile0;   // first tile of the (partition, sigma) kernel store
     int64_t vec0;     // first element in the per-solve padded vectors
