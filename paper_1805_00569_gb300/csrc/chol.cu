@@ -304,9 +304,12 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 // operand tiles of all its tasks with 2-D TMA loads (128-byte swizzle) through
 // an mbarrier ring; warp 1 lane 0 issues the MMAs of task t into one of two
 // 128-column FP32 accumulators in tensor memory (t % 2); warps 2..5 read the
-// other one back (tcgen05.ld) for the epilogue of the previous task (A_ij -= C,
-// or A_ik = C for the panel solve), so loads, MMAs and epilogues of
-// consecutive tasks overlap and the per-CTA setup is paid once per launch.
+// other one back (tcgen05.ld) for the epilogue of the previous task, so loads,
+// MMAs and epilogues of consecutive tasks overlap and the per-CTA setup is
+// paid once per launch.  Update epilogue: the destination tile A_ij lands in
+// shared memory by TMA while the task's MMAs run, A_ij -= C is formed there
+// (128-byte swizzle: conflict-free row access) and the tile leaves by TMA
+// store; the panel solve (A_ik = C, no read) stores directly.
 // TC_TF32: one kind::tf32 MMA per K step (the tensor core reads the top 19
 // bits of each FP32 operand).  TC_F16: one kind::f16 MMA per K step on the
 // FP16 copy of the panel (the same 11-bit significand as TF32 at twice the
@@ -347,12 +350,13 @@ enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3, TC_TF32X3P = 4 };
 template <int MODE> struct TcCfg {
     static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;  // split warps present
     static constexpr bool PRE = MODE == TC_TF32X3P;                        // lo operands landed by TMA
-    static constexpr int STAGES = SPLIT ? 2 : 3;
+    static constexpr int STAGES = (SPLIT || PRE) ? 2 : 3;
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
     static constexpr uint32_t STAGE_BYTES = (SPLIT || PRE ? 4u : 2u) * TC_HALF;
     static constexpr int THREADS = SPLIT ? 320 : 192;
-    static constexpr size_t SMEM = STAGES * STAGE_BYTES + 1024 + 256;
+    static constexpr uint32_t CBUF = (uint32_t)KRR_TILE * KRR_TILE * 4;  // destination tile (TMA epilogue)
+    static constexpr size_t SMEM = STAGES * STAGE_BYTES + CBUF + 1024 + 256;
     static_assert(SMEM <= 232448, "tile kernel shared memory");
 };
 
@@ -378,7 +382,8 @@ __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parit
 template <int MODE>
 __global__ void __launch_bounds__(TcCfg<MODE>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
-                const __grid_constant__ CUtensorMap tmapLo, float *__restrict__ A, __half *__restrict__ A16,
+                const __grid_constant__ CUtensorMap tmapLo, const __grid_constant__ CUtensorMap tmapC,
+                float *__restrict__ A, __half *__restrict__ A16,
                 float *__restrict__ Alo, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
                 int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
     using Cfg = TcCfg<MODE>;
@@ -390,12 +395,16 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     extern __shared__ unsigned char tc_dyn[];
     const uint32_t base = smem_u32(tc_dyn);
     unsigned char *buf = tc_dyn + (((base + 1023u) & ~1023u) - base);  // 1024-aligned stage ring
-    uint64_t *full = reinterpret_cast<uint64_t *>(buf + Cfg::STAGES * Cfg::STAGE_BYTES);
+    // destination tile of the update epilogue: four 32-column boxes (16 KB,
+    // 128-byte swizzle) as the FP32 tile map lands and stores them
+    unsigned char *cbuf = buf + Cfg::STAGES * Cfg::STAGE_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(cbuf + Cfg::CBUF);
     uint64_t *empty = full + Cfg::STAGES;
     uint64_t *split = empty + Cfg::STAGES;
     uint64_t *tfull = split + Cfg::STAGES;  // accumulator b ready for the epilogue
     uint64_t *tempty = tfull + 2;           // accumulator b read back by the 4 epilogue warps
-    uint32_t *tslot = reinterpret_cast<uint32_t *>(tempty + 2);
+    uint64_t *cfull = tempty + 2;           // destination tile landed in cbuf
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(cfull + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     // task geometry: the solve by binary search, then the tile of that solve
@@ -418,6 +427,7 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
+        mbar_init(cfull, 1);
         fence_mbar_init();
     }
     if (warp == 0) {
@@ -593,7 +603,24 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     } else if (warp >= 2 && warp < 6) {  // epilogue
         const int quad = warp & 3;
         const int r = quad * 32 + lane;
+        // updates: the destination tile comes in by TMA (issued by thread 64 as
+        // soon as the previous tile's store has read cbuf), A_ij -= C is formed
+        // in shared memory and the tile goes back by TMA store; the panel
+        // solve (no read of the destination) stores directly
+        const bool tma_c = mode != UPD_TRSM;
+        auto c_tile_y = [&](int64_t tt) {
+            SolveDesc S2;
+            TaskGeom g2;
+            task(tt, S2, g2);
+            return (int)((S2.ltile0 + (int64_t)g2.i * (g2.i + 1) / 2 + g2.j) * KRR_TILE);
+        };
+        if (tma_c && threadIdx.x == 64 && (int64_t)blockIdx.x < ntasks) {
+            const int y = c_tile_y(blockIdx.x);
+            mbar_arrive_expect_tx(cfull, Cfg::CBUF);
+            for (int cb = 0; cb < KRR_TILE / 32; ++cb) tma_load_2d(cbuf + cb * (Cfg::CBUF / 4), &tmapC, cb * 32, y, cfull);
+        }
         int lt = 0;
+        bool ok = true;
         for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++lt) {
             SolveDesc S;
             TaskGeom g;
@@ -609,67 +636,91 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                                         (int64_t)r * KRR_TILE
                                   : nullptr;
             const int b = lt & 1;
-            if (!mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err)) break;
-            tc_fence_after();
-            if (t + gridDim.x < ntasks && mode != UPD_TRSM) {  // the next destination row into L2
-                SolveDesc S2;
-                TaskGeom g2;
-                task(t + gridDim.x, S2, g2);
-                bulk_prefetch_l2(dst_tile(S2, g2) + (int64_t)r * KRR_TILE, KRR_TILE * sizeof(float));
-            }
+            // after a timeout the warp keeps the loop and its barrier but skips
+            // the work (the error word is set; the results are not used)
+            bool got = ok;
+            if (got && tma_c) got = mbar_wait_deadline(cfull, (uint32_t)(lt & 1), err);
+            if (got) got = mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err);
+            ok = got;
+            if (got) {
+                tc_fence_after();
 #pragma unroll 1
-            for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
-                float v[32];
-                tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32), v);
-                float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
-                if (half_out) {
-                    uint4 *h4 = reinterpret_cast<uint4 *>(dst16 + cb * 32);
-#pragma unroll
-                    for (int qq = 0; qq < 4; ++qq) {
-                        uint4 o;
-                        __half2 h;
-                        h = __floats2half2_rn(v[8 * qq + 0], v[8 * qq + 1]);
-                        o.x = *reinterpret_cast<uint32_t *>(&h);
-                        h = __floats2half2_rn(v[8 * qq + 2], v[8 * qq + 3]);
-                        o.y = *reinterpret_cast<uint32_t *>(&h);
-                        h = __floats2half2_rn(v[8 * qq + 4], v[8 * qq + 5]);
-                        o.z = *reinterpret_cast<uint32_t *>(&h);
-                        h = __floats2half2_rn(v[8 * qq + 6], v[8 * qq + 7]);
-                        o.w = *reinterpret_cast<uint32_t *>(&h);
-                        h4[qq] = o;
-                    }
-                } else if (mode == UPD_TRSM) {
-#pragma unroll
-                    for (int qq = 0; qq < 8; ++qq)
-                        d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
-                    if (lo_out) {
-                        float4 *l4 = reinterpret_cast<float4 *>(dstlo + cb * 32);
+                for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
+                    float v[32];
+                    tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32),
+                                       v);
+                    if (tma_c) {
+                        // row r of box cb: 16-byte unit q at q ^ (r % 8)
+                        unsigned char *row = cbuf + cb * (Cfg::CBUF / 4) + r * 128;
 #pragma unroll
                         for (int qq = 0; qq < 8; ++qq) {
-                            float4 o;
-                            o.x = v[4 * qq + 0] - __uint_as_float(__float_as_uint(v[4 * qq + 0]) & 0xFFFFE000u);
-                            o.y = v[4 * qq + 1] - __uint_as_float(__float_as_uint(v[4 * qq + 1]) & 0xFFFFE000u);
-                            o.z = v[4 * qq + 2] - __uint_as_float(__float_as_uint(v[4 * qq + 2]) & 0xFFFFE000u);
-                            o.w = v[4 * qq + 3] - __uint_as_float(__float_as_uint(v[4 * qq + 3]) & 0xFFFFE000u);
-                            l4[qq] = o;
+                            float4 *p4 = reinterpret_cast<float4 *>(row + ((qq ^ (r & 7)) << 4));
+                            float4 o = *p4;
+                            o.x -= v[4 * qq + 0];
+                            o.y -= v[4 * qq + 1];
+                            o.z -= v[4 * qq + 2];
+                            o.w -= v[4 * qq + 3];
+                            *p4 = o;
                         }
-                    }
-                } else {
+                    } else if (half_out) {
+                        uint4 *h4 = reinterpret_cast<uint4 *>(dst16 + cb * 32);
 #pragma unroll
-                    for (int qq = 0; qq < 8; ++qq) {
-                        float4 o = d4[qq];
-                        o.x -= v[4 * qq + 0];
-                        o.y -= v[4 * qq + 1];
-                        o.z -= v[4 * qq + 2];
-                        o.w -= v[4 * qq + 3];
-                        d4[qq] = o;
+                        for (int qq = 0; qq < 4; ++qq) {
+                            uint4 o;
+                            __half2 h;
+                            h = __floats2half2_rn(v[8 * qq + 0], v[8 * qq + 1]);
+                            o.x = *reinterpret_cast<uint32_t *>(&h);
+                            h = __floats2half2_rn(v[8 * qq + 2], v[8 * qq + 3]);
+                            o.y = *reinterpret_cast<uint32_t *>(&h);
+                            h = __floats2half2_rn(v[8 * qq + 4], v[8 * qq + 5]);
+                            o.z = *reinterpret_cast<uint32_t *>(&h);
+                            h = __floats2half2_rn(v[8 * qq + 6], v[8 * qq + 7]);
+                            o.w = *reinterpret_cast<uint32_t *>(&h);
+                            h4[qq] = o;
+                        }
+                    } else {
+                        float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
+#pragma unroll
+                        for (int qq = 0; qq < 8; ++qq)
+                            d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                        if (lo_out) {
+                            float4 *l4 = reinterpret_cast<float4 *>(dstlo + cb * 32);
+#pragma unroll
+                            for (int qq = 0; qq < 8; ++qq) {
+                                float4 o;
+                                o.x = v[4 * qq + 0] - __uint_as_float(__float_as_uint(v[4 * qq + 0]) & 0xFFFFE000u);
+                                o.y = v[4 * qq + 1] - __uint_as_float(__float_as_uint(v[4 * qq + 1]) & 0xFFFFE000u);
+                                o.z = v[4 * qq + 2] - __uint_as_float(__float_as_uint(v[4 * qq + 2]) & 0xFFFFE000u);
+                                o.w = v[4 * qq + 3] - __uint_as_float(__float_as_uint(v[4 * qq + 3]) & 0xFFFFE000u);
+                                l4[qq] = o;
+                            }
+                        }
                     }
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&tempty[b]);
+            if (tma_c) {
+                fence_proxy_async_smem();  // cbuf writes -> visible to the TMA store
+                asm volatile("bar.sync 1, 128;" ::: "memory");
+                if (threadIdx.x == 64) {
+                    const int y = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE);
+                    if (ok)
+                        for (int cb = 0; cb < KRR_TILE / 32; ++cb)
+                            tma_store_2d(&tmapC, cb * 32, y, cbuf + cb * (Cfg::CBUF / 4));
+                    bulk_commit();
+                    bulk_wait_read_all();  // cbuf may be refilled
+                    if (ok && t + gridDim.x < ntasks) {
+                        const int yn = c_tile_y(t + gridDim.x);
+                        mbar_arrive_expect_tx(cfull, Cfg::CBUF);
+                        for (int cb = 0; cb < KRR_TILE / 32; ++cb)
+                            tma_load_2d(cbuf + cb * (Cfg::CBUF / 4), &tmapC, cb * 32, yn, cfull);
+                    }
+                }
+            }
         }
+        if (tma_c && threadIdx.x == 64) bulk_wait_all();  // the stores have completed
     }
     tc_fence_before();
     __syncthreads();
@@ -824,19 +875,19 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                 if (m == TC_TF32X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
                                                                  TcCfg<TC_TF32X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else if (m == TC_TF32X3P)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3P><<<pgrid, TcCfg<TC_TF32X3P>::THREADS,
                                                                   TcCfg<TC_TF32X3P>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else if (m == TC_BF16X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_BF16X3><<<pgrid, TcCfg<TC_BF16X3>::THREADS,
                                                                  TcCfg<TC_BF16X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 else
                     KRR_LAUNCHED(), tile_mma_kernel<TC_F16><<<pgrid, TcCfg<TC_F16>::THREADS,
                                                              TcCfg<TC_F16>::SMEM, st>>>(
-                        *tmap16, *tmapZ, tmLo, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                        *tmap16, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
                 continue;
             }
         }

@@ -26,7 +26,8 @@
 //     the four quarter sums of a test row are combined in a fixed order at
 //     the end.  K(test, train) is never stored.
 // The kernel-tile build uses the same producer / MMA / 16-warp epilogue
-// layout on the two 64-column chunks of one 128 x 128 tile.
+// layout on the two 64-column chunks of each 128 x 128 tile, persistent over
+// the tiles (one CTA per SM).
 #include <cuda_bf16.h>
 
 #include "common.cuh"
@@ -336,6 +337,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
             for (int b = 0; b < OZ_NLP; ++b) dfa_zero(acc[a][b]);
         }
+        bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             OzChunkData &cd = sm.cd[c & 1];
             // training-side data of the chunk
@@ -357,7 +359,12 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 cd.al[is * OZ_NLP + il][col] = __double2float_rn(av - (double)h);
             }
             epi_bar_p();
-            if (!oz_wait(&sm.t_full, c & 1, err)) break;
+            // after a timeout the warp keeps the loop (and its barriers) but skips the work,
+            // so no epilogue warp can be left waiting at a barrier for one that returned
+            if (!ok || !oz_wait(&sm.t_full, c & 1, err)) {
+                ok = false;
+                continue;
+            }
             tc_fence_after();
 #pragma unroll 1
             for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
@@ -511,9 +518,9 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 
 // ---------------------------------------------------------------- kernel tiles
 // Gaussian kernel tiles of the training partitions from the same exact slice
-// Gram: one CTA per lower tile (i, j) of a partition; the tile's 128 x 128
-// Gram is formed as two 64-column chunks (A = rows of block i, B = rows of
-// block j).  The epilogue writes, per sigma, K_hi + K_lo (df split) and, per
+// Gram: persistent CTAs (one per SM) walk the lower tiles (i, j) of every
+// partition; a tile's 128 x 128 Gram is formed as two 64-column chunks
+// (A = rows of block i, B = rows of block j).  The epilogue writes, per sigma, K_hi + K_lo (df split) and, per
 // lambda, K_hi + lambda m I into the factor store.  Diagonal entries are
 // exactly 1; padding rows and columns form an identity block.
 struct OzKParams {
@@ -532,6 +539,21 @@ __device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64
     return lo;
 }
 
+// the tile of one persistent iteration: partition, block row / column
+struct OzTile {
+    int pj, ti, tj;
+    int64_t lt;  // tile index inside the partition
+    PartDesc P;
+};
+__device__ __forceinline__ OzTile oz_tile_of(const PartDesc *__restrict__ parts, int np, int64_t tile) {
+    OzTile t;
+    t.pj = oz_find_part(parts, np, tile);
+    t.P = parts[t.pj];
+    t.lt = tile - t.P.ktile0;
+    tri_decode(t.lt, t.ti, t.tj);
+    return t;
+}
+
 __global__ void __launch_bounds__(OZP_THREADS, 1)
 kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
@@ -541,13 +563,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     const uint32_t base = smem_u32(oz_dyn);
     OzSmem &sm = *reinterpret_cast<OzSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t tile = blockIdx.x;
-    const int pj = oz_find_part(parts, kp.np, tile);
-    const PartDesc P = parts[pj];
-    int ti, tj;
-    tri_decode(tile - P.ktile0, ti, tj);
-    const int64_t lt = tile - P.ktile0;
-    constexpr int nchunks = KRR_TILE / OZ_N;  // 2
+    constexpr int nchunks = KRR_TILE / OZ_N;  // 2 per tile
     if (threadIdx.x < 8) sm.cs[threadIdx.x] = make_float2(kp.c_hi[threadIdx.x], kp.c_lo[threadIdx.x]);
 
     if (threadIdx.x == 0) {
@@ -571,141 +587,173 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     tc_fence_after();
     const uint32_t tmem = sm.tmem;
 
+    // Persistent: every role walks tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+    // with running chunk counters (cg) for the barrier phases, so the slices
+    // of the next tile stream in while the epilogue finishes the current one.
     if (threadIdx.x == 0) {
         const uint32_t bbytes = (uint32_t)(OZ_SLICES * kp.kc) * OZ_B_CHUNK;
         const uint32_t abytes = (uint32_t)kp.kc * OZ_A_CHUNK;
         int ait = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            if (c > 0 && !oz_wait(&sm.b_empty, (c - 1) & 1, err)) break;
-            mbar_arrive_expect_tx(&sm.b_full, bbytes);
-            const int brow = (int)(P.prow0 + (int64_t)tj * KRR_TILE + c * OZ_N);
-            for (int s = 0; s < OZ_SLICES; ++s)
-                for (int kc = 0; kc < kp.kc; ++kc)
-                    tma_load_2d(sm.b + (s * OZ_MAXKC + kc) * OZ_B_CHUNK, &tmB, kc * OZ_KC, (int)(s * prows) + brow,
-                                &sm.b_full);
-            bool ok = true;
-            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
-                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
-                if (use > 0 && !oz_wait(&sm.a_empty[st], (use - 1) & 1, err)) {
+        int64_t cg = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < kp.ktot && ok; tile += gridDim.x) {
+            const OzTile tl = oz_tile_of(parts, kp.np, tile);
+            const PartDesc &P = tl.P;
+            const int ti = tl.ti, tj = tl.tj;
+            for (int c = 0; c < nchunks && ok; ++c, ++cg) {
+                if (cg > 0 && !oz_wait(&sm.b_empty, (uint32_t)((cg - 1) & 1), err)) {
                     ok = false;
                     break;
                 }
-                mbar_arrive_expect_tx(&sm.a_full[st], abytes);
-                const int arow = (int)(s * prows + P.prow0 + (int64_t)ti * KRR_TILE);
-                for (int kc = 0; kc < kp.kc; ++kc)
-                    tma_load_2d(sm.a[st] + kc * OZ_A_CHUNK, &tmA, kc * OZ_KC, arow, &sm.a_full[st]);
+                mbar_arrive_expect_tx(&sm.b_full, bbytes);
+                const int brow = (int)(P.prow0 + (int64_t)tj * KRR_TILE + c * OZ_N);
+                for (int s = 0; s < OZ_SLICES; ++s)
+                    for (int kc = 0; kc < kp.kc; ++kc)
+                        tma_load_2d(sm.b + (s * OZ_MAXKC + kc) * OZ_B_CHUNK, &tmB, kc * OZ_KC,
+                                    (int)(s * prows) + brow, &sm.b_full);
+                for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                    const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                    if (use > 0 && !oz_wait(&sm.a_empty[st], (use - 1) & 1, err)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&sm.a_full[st], abytes);
+                    const int arow = (int)(s * prows + P.prow0 + (int64_t)ti * KRR_TILE);
+                    for (int kc = 0; kc < kp.kc; ++kc)
+                        tma_load_2d(sm.a[st] + kc * OZ_A_CHUNK, &tmA, kc * OZ_KC, arow, &sm.a_full[st]);
+                }
             }
-            if (!ok) break;
         }
     } else if (threadIdx.x == 32) {
         int ait = 0;
+        int64_t cg = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            if (c > 0 && !oz_wait(&sm.t_empty, (c - 1) & 1, err)) break;
-            if (!oz_wait(&sm.b_full, c & 1, err)) break;
-            tc_fence_after();
-            for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
-                const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
-                if (!oz_wait(&sm.a_full[st], use & 1, err)) {
+        for (int64_t tile = blockIdx.x; tile < kp.ktot && ok; tile += gridDim.x) {
+            for (int c = 0; c < nchunks && ok; ++c, ++cg) {
+                if (cg > 0 && !oz_wait(&sm.t_empty, (uint32_t)((cg - 1) & 1), err)) {
+                    ok = false;
+                    break;
+                }
+                if (!oz_wait(&sm.b_full, (uint32_t)(cg & 1), err)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                for (int tt = 0; tt + s < OZ_SLICES; ++tt) {
-                    const uint32_t dcol = tmem + (uint32_t)((s + tt) * OZ_N);
-                    for (int kk = 0; kk < 2 * kp.kc; ++kk) {
-                        const uint64_t da = smem_desc_sw64(sm.a[st] + (kk >> 1) * OZ_A_CHUNK) + 2 * (kk & 1);
-                        const uint64_t db =
-                            smem_desc_sw64(sm.b + (tt * OZ_MAXKC + (kk >> 1)) * OZ_B_CHUNK) + 2 * (kk & 1);
-                        tc_mma_f16(dcol, da, db, OZ_IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+                for (int s = 0; s < OZ_SLICES; ++s, ++ait) {
+                    const int st = ait % OZ_ASTAGES, use = ait / OZ_ASTAGES;
+                    if (!oz_wait(&sm.a_full[st], use & 1, err)) {
+                        ok = false;
+                        break;
                     }
+                    tc_fence_after();
+                    for (int tt = 0; tt + s < OZ_SLICES; ++tt) {
+                        const uint32_t dcol = tmem + (uint32_t)((s + tt) * OZ_N);
+                        for (int kk = 0; kk < 2 * kp.kc; ++kk) {
+                            const uint64_t da = smem_desc_sw64(sm.a[st] + (kk >> 1) * OZ_A_CHUNK) + 2 * (kk & 1);
+                            const uint64_t db =
+                                smem_desc_sw64(sm.b + (tt * OZ_MAXKC + (kk >> 1)) * OZ_B_CHUNK) + 2 * (kk & 1);
+                            tc_mma_f16(dcol, da, db, OZ_IDESC, (s > 0 || kk > 0) ? 1u : 0u);
+                        }
+                    }
+                    tc_commit(&sm.a_empty[st]);
                 }
-                tc_commit(&sm.a_empty[st]);
+                if (!ok) break;
+                tc_commit(&sm.b_empty);
+                tc_commit(&sm.t_full);
             }
-            tc_commit(&sm.b_empty);
-            tc_commit(&sm.t_full);
         }
     } else if (warp >= OZ_EPI_WARP0) {
         const int ew = warp - OZ_EPI_WARP0;    // 0..15
         const int quad = warp & 3, quarter = ew >> 2;
         const int r = quad * 32 + lane;            // row inside the tile
-        const int gr = ti * KRR_TILE + r;          // row inside the partition
-        const int64_t prow = P.prow0 + gr;
-        const int er = ex[prow];
-        const float2 nr2 = nrm[prow];
-        const df nr = df_make(nr2.x, nr2.y);
         const int G = kp.nsig * kp.nlam;
-        for (int c = 0; c < nchunks; ++c) {
-            if (!oz_wait(&sm.t_full, c & 1, err)) break;
-            tc_fence_after();
-#pragma unroll 1
-            for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
-                float lv[OZ_SLICES][OZP_SUB];
-                const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
-#pragma unroll
-                for (int L = 0; L < OZ_SLICES; ++L)
-                    tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0, lv[L]);
-                tmem_wait_ld();
-                const bool last_sub = sub == (OZ_N / 4) / OZP_SUB - 1;
-                if (last_sub && c == nchunks - 1) {
-                    // nothing follows the last chunk
-                } else if (last_sub) {
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&sm.t_empty);
+        int64_t cg = 0;
+        bool ok = true;
+        for (int64_t tile = blockIdx.x; tile < kp.ktot && ok; tile += gridDim.x) {
+            const OzTile tl = oz_tile_of(parts, kp.np, tile);
+            const PartDesc &P = tl.P;
+            const int pj = tl.pj, ti = tl.ti, tj = tl.tj;
+            const int64_t lt = tl.lt;
+            const int gr = ti * KRR_TILE + r;          // row inside the partition
+            const int64_t prow = P.prow0 + gr;
+            const int er = ex[prow];
+            const float2 nr2 = nrm[prow];
+            const df nr = df_make(nr2.x, nr2.y);
+            for (int c = 0; c < nchunks; ++c, ++cg) {
+                if (!oz_wait(&sm.t_full, (uint32_t)(cg & 1), err)) {
+                    ok = false;
+                    break;
                 }
-                const int cbase = c * OZ_N + (int)col0;  // column inside the tile
-                float dh[OZP_SUB], dl[OZP_SUB];
-#pragma unroll
-                for (int k = 0; k < OZP_SUB; ++k) {
-                    const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
-                    const float2 nc2 = nrm[pc];
-                    const int sc = er + ex[pc] - 13;
-                    const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nr, nc2.x, nc2.y,
-                                             __int_as_float((127 + sc) << 23));
-                    dh[k] = D.hi;
-                    dl[k] = D.lo;
-                }
-                const bool diag_here = (ti == tj);
+                tc_fence_after();
 #pragma unroll 1
-                for (int is = 0; is < kp.nsig; ++is) {
-                    const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
-                    float hv[OZP_SUB], lw[OZP_SUB];
+                for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
+                    float lv[OZ_SLICES][OZP_SUB];
+                    const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
+#pragma unroll
+                    for (int L = 0; L < OZ_SLICES; ++L)
+                        tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0,
+                                          lv[L]);
+                    tmem_wait_ld();
+                    if (sub == (OZ_N / 4) / OZP_SUB - 1) {  // the levels are in registers: release the TMEM
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.t_empty);
+                    }
+                    const int cbase = c * OZ_N + (int)col0;  // column inside the tile
+                    float dh[OZP_SUB], dl[OZP_SUB];
 #pragma unroll
                     for (int k = 0; k < OZP_SUB; ++k) {
-                        const int gc = tj * KRR_TILE + cbase + k;
-                        df kv;
-                        if (gr >= P.m || gc >= P.m) kv = df_make(gr == gc ? 1.f : 0.f, 0.f);
-                        else if (gr == gc) kv = df_make(1.f, 0.f);
-                        else kv = df_exp_nonpos(df_mul(df_make(dh[k], dl[k]), cs), sm.exptab);
-                        hv[k] = kv.hi;
-                        lw[k] = kv.lo;
+                        const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
+                        const float2 nc2 = nrm[pc];
+                        const int sc = er + ex[pc] - 13;
+                        const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nr, nc2.x,
+                                                 nc2.y, __int_as_float((127 + sc) << 23));
+                        dh[k] = D.hi;
+                        dl[k] = D.lo;
                     }
-                    const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
-                    float4 *oh = reinterpret_cast<float4 *>(Kh + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
-                    float4 *ol = reinterpret_cast<float4 *>(Kl + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
-#pragma unroll
-                    for (int q = 0; q < OZP_SUB / 4; ++q) {
-                        oh[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                        ol[q] = make_float4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
-                    }
+                    const bool diag_here = (ti == tj);
 #pragma unroll 1
-                    for (int il = 0; il < kp.nlam; ++il) {
-                        const SolveDesc S = solves[(int64_t)pj * G + is * kp.nlam + il];
-                        const float lm = (float)S.lambda_m;
-                        float4 *oa = reinterpret_cast<float4 *>(A + (S.ltile0 + lt) * KRR_TILE_ELEMS +
-                                                                 (int64_t)r * KRR_TILE + cbase);
+                    for (int is = 0; is < kp.nsig; ++is) {
+                        const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
+                        float hv[OZP_SUB], lw[OZP_SUB];
+#pragma unroll
+                        for (int k = 0; k < OZP_SUB; ++k) {
+                            const int gc = tj * KRR_TILE + cbase + k;
+                            df kv;
+                            if (gr >= P.m || gc >= P.m) kv = df_make(gr == gc ? 1.f : 0.f, 0.f);
+                            else if (gr == gc) kv = df_make(1.f, 0.f);
+                            else kv = df_exp_nonpos(df_mul(df_make(dh[k], dl[k]), cs), sm.exptab);
+                            hv[k] = kv.hi;
+                            lw[k] = kv.lo;
+                        }
+                        const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
+                        float4 *oh =
+                            reinterpret_cast<float4 *>(Kh + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
+                        float4 *ol =
+                            reinterpret_cast<float4 *>(Kl + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
 #pragma unroll
                         for (int q = 0; q < OZP_SUB / 4; ++q) {
-                            float4 v = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                            if (diag_here && gr < P.m) {
-                                const int d0 = gr - (tj * KRR_TILE + cbase + 4 * q);
-                                if (d0 == 0) v.x += lm;
-                                else if (d0 == 1) v.y += lm;
-                                else if (d0 == 2) v.z += lm;
-                                else if (d0 == 3) v.w += lm;
+                            oh[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                            ol[q] = make_float4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                        }
+#pragma unroll 1
+                        for (int il = 0; il < kp.nlam; ++il) {
+                            const SolveDesc S = solves[(int64_t)pj * G + is * kp.nlam + il];
+                            const float lm = (float)S.lambda_m;
+                            float4 *oa = reinterpret_cast<float4 *>(A + (S.ltile0 + lt) * KRR_TILE_ELEMS +
+                                                                     (int64_t)r * KRR_TILE + cbase);
+#pragma unroll
+                            for (int q = 0; q < OZP_SUB / 4; ++q) {
+                                float4 v = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
+                                if (diag_here && gr < P.m) {
+                                    const int d0 = gr - (tj * KRR_TILE + cbase + 4 * q);
+                                    if (d0 == 0) v.x += lm;
+                                    else if (d0 == 1) v.y += lm;
+                                    else if (d0 == 2) v.z += lm;
+                                    else if (d0 == 3) v.w += lm;
+                                }
+                                oa[q] = v;
                             }
-                            oa[q] = v;
                         }
                     }
                 }
@@ -779,7 +827,11 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
         kp.c_hi[i] = (float)c;
         kp.c_lo[i] = (float)(c - (double)(float)c);
     }
-    KRR_LAUNCHED(), kbuild_oz_kernel<<<(unsigned)ktot, OZP_THREADS, oz_smem_bytes(), st>>>(
+    int dev = 0, nsm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned grid = (unsigned)std::min<int64_t>(ktot, nsm);  // persistent: one CTA per SM
+    KRR_LAUNCHED(), kbuild_oz_kernel<<<grid, OZP_THREADS, oz_smem_bytes(), st>>>(
         tmA, M.oz_tmB, M.d_parts, M.d_solves, M.ozex, M.nrm, kp, M.prows, Kh, Kl, A, d_err);
     return cudaGetLastError();
 }
