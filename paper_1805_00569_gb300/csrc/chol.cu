@@ -350,7 +350,9 @@ enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3, TC_TF32X3P = 4 };
 template <int MODE> struct TcCfg {
     static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;  // split warps present
     static constexpr bool PRE = MODE == TC_TF32X3P;                        // lo operands landed by TMA
-    static constexpr int STAGES = (SPLIT || PRE) ? 2 : 3;
+    // operand ring depth: as many stages as fit beside the 64 KB destination
+    // tile (the loads come from L2 at ~1-2 us latency; bytes in flight set the pace)
+    static constexpr int STAGES = (SPLIT || PRE) ? 2 : (MODE == TC_F16 ? 5 : 3);
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
     static constexpr uint32_t STAGE_BYTES = (SPLIT || PRE ? 4u : 2u) * TC_HALF;
