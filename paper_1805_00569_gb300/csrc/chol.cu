@@ -345,19 +345,23 @@ __device__ __forceinline__ uint64_t smem_desc_sw64_tc(const void *p) {
 }
 // MODE: TC_TF32 one pass; TC_TF32X3 three TF32 passes on hi/lo splits;
 // TC_BF16X3 three BF16 passes (kind::f16) on hi/lo BF16 splits; TC_F16 one
-// kind::f16 pass on FP16 operands (64 halves = 128 bytes of K per stage)
-enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3, TC_TF32X3P = 4 };
+// kind::f16 pass on FP16 operands (64 halves = 128 bytes of K per stage);
+// TC_TF32X3P three TF32 passes on operands split by the panel solve; TC_TRSM
+// the panel solve (TC_TF32X3 arithmetic, no destination tile buffer, so a
+// deeper ring)
+enum { TC_TF32 = 0, TC_TF32X3 = 1, TC_BF16X3 = 2, TC_F16 = 3, TC_TF32X3P = 4, TC_TRSM = 5 };
 template <int MODE> struct TcCfg {
-    static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3;  // split warps present
+    static constexpr bool SPLIT = MODE == TC_TF32X3 || MODE == TC_BF16X3 || MODE == TC_TRSM;  // split warps
     static constexpr bool PRE = MODE == TC_TF32X3P;                        // lo operands landed by TMA
     // operand ring depth: as many stages as fit beside the 64 KB destination
     // tile (the loads come from L2 at ~1-2 us latency; bytes in flight set the pace)
-    static constexpr int STAGES = (SPLIT || PRE) ? 2 : (MODE == TC_F16 ? 5 : 3);
+    static constexpr int STAGES = MODE == TC_TRSM ? 3 : ((SPLIT || PRE) ? 2 : (MODE == TC_F16 ? 5 : 3));
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
     static constexpr uint32_t STAGE_BYTES = (SPLIT || PRE ? 4u : 2u) * TC_HALF;
     static constexpr int THREADS = SPLIT ? 320 : 192;
-    static constexpr uint32_t CBUF = (uint32_t)KRR_TILE * KRR_TILE * 4;  // destination tile (TMA epilogue)
+    // destination tile of the update epilogue (none for the panel solve)
+    static constexpr uint32_t CBUF = MODE == TC_TRSM ? 0u : (uint32_t)KRR_TILE * KRR_TILE * 4;
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + CBUF + 1024 + 256;
     static_assert(SMEM <= 232448, "tile kernel shared memory");
 };
@@ -390,7 +394,7 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
     using Cfg = TcCfg<MODE>;
     constexpr bool X3 = Cfg::SPLIT;                              // split warps
-    constexpr bool X3MMA = MODE == TC_TF32X3 || MODE == TC_TF32X3P;  // three TF32 passes
+    constexpr bool X3MMA = MODE == TC_TF32X3 || MODE == TC_TF32X3P || MODE == TC_TRSM;  // three TF32 passes
     // elements of K per stage: 32 floats or 64 halves (128 bytes either way)
     constexpr int KEL = MODE == TC_F16 ? 2 * TC_CHUNK : TC_CHUNK;
     constexpr int KCH = KRR_TILE / KEL;  // chunks per K tile
@@ -609,7 +613,7 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
         // soon as the previous tile's store has read cbuf), A_ij -= C is formed
         // in shared memory and the tile goes back by TMA store; the panel
         // solve (no read of the destination) stores directly
-        const bool tma_c = mode != UPD_TRSM;
+        const bool tma_c = mode != UPD_TRSM && Cfg::CBUF > 0;
         auto c_tile_y = [&](int64_t tt) {
             SolveDesc S2;
             TaskGeom g2;
@@ -862,8 +866,9 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
             // (operands from the FP16 copy of the panel), 2 BF16x3, 3 TF32x3 on
             // operands split by the panel solve, 4 TF32x3 split in shared memory
             if (tc != 0) {
-                int m = TC_TF32X3;
+                int m = TC_TRSM;
                 if (L.kind != 1) {
+                    m = TC_TF32X3;
                     if (L.tc == 1) m = TC_F16;
                     else if (L.tc == 2) m = TC_BF16X3;
                     else if (L.tc == 3) m = TC_TF32X3P;
@@ -874,7 +879,11 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 float *Af = reinterpret_cast<float *>(A);
                 const CUtensorMap &tmLo = tmapLo ? *tmapLo : *tmap;
-                if (m == TC_TF32X3)
+                if (m == TC_TRSM)
+                    KRR_LAUNCHED(), tile_mma_kernel<TC_TRSM><<<pgrid, TcCfg<TC_TRSM>::THREADS,
+                                                              TcCfg<TC_TRSM>::SMEM, st>>>(
+                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                else if (m == TC_TF32X3)
                     KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
                                                                  TcCfg<TC_TF32X3>::SMEM, st>>>(
                         *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
@@ -910,6 +919,7 @@ cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, 
     allow_max_dyn_smem(tile_mma_kernel<TC_F16>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3P>);
+    allow_max_dyn_smem(tile_mma_kernel<TC_TRSM>);
     allow_max_dyn_smem(tile_mma_kernel<TC_BF16X3>);
     if (fp64)
         return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, nullptr, nullptr, d_solves, nsolve,
