@@ -56,15 +56,21 @@ struct OzChunkData {  // per training column of a chunk
     float ah[OZ_NSP * OZ_NLP][OZ_N], al[OZ_NSP * OZ_NLP][OZ_N];
 };
 
+constexpr uint32_t OZ_SBOX = (uint32_t)KRR_TILE * 32 * 4;  // one 32-column box of a 128-row FP32 tile, 16 KB
+
 struct OzSmem {  // kernel-tile build CTA
     unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
     unsigned char b[OZ_B_BYTES];
+    // one chunk (128 rows x 64 columns) of K_hi and of K_lo for the TMA
+    // stores: [hi / lo][32-column box], 128-byte swizzle
+    unsigned char stage[2][2][OZ_SBOX];
     float2 exptab[256];
     uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
-    uint64_t b_full, b_empty, t_full, t_empty;
+    uint64_t b_full, b_empty, t_full, t_empty, s_free;
     uint32_t tmem;
     float2 cs[8];  // -1/(2 sigma^2) as df
 };
+static_assert(sizeof(OzSmem) + 1024 <= 232448, "kernel-tile build CTA exceeds the opt-in shared memory");
 
 struct OzParams {
     int nsig, nlam, sig0, lam0, Gtot, nl_total;
@@ -556,7 +562,9 @@ __device__ __forceinline__ OzTile oz_tile_of(const PartDesc *__restrict__ parts,
 
 __global__ void __launch_bounds__(OZP_THREADS, 1)
 kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-                 const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
+                 const __grid_constant__ CUtensorMap tmKh, const __grid_constant__ CUtensorMap tmKl,
+                 const __grid_constant__ CUtensorMap tmF, const PartDesc *__restrict__ parts,
+                 const SolveDesc *__restrict__ solves,
                  const int32_t *__restrict__ ex, const float2 *__restrict__ nrm, OzKParams kp, int64_t prows,
                  float *__restrict__ Kh, float *__restrict__ Kl, float *__restrict__ A, int *__restrict__ err) {
     extern __shared__ unsigned char oz_dyn[];
@@ -575,6 +583,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         mbar_init(&sm.b_empty, 1);
         mbar_init(&sm.t_full, 1);
         mbar_init(&sm.t_empty, OZP_EPI_WARPS);
+        mbar_init(&sm.s_free, 1);
         fence_mbar_init();
     }
     exp_table_init(sm.exptab);
@@ -663,13 +672,24 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             }
         }
     } else if (warp >= OZ_EPI_WARP0) {
+        // Per chunk: the five levels of both 8-column subs are read from TMEM
+        // (then the TMEM is released), distances formed; per sigma the values
+        // go to the staging chunk (row r, 16-byte unit u at u ^ (r % 8)) and
+        // one thread stores it by TMA to K_hi, K_lo and, as K_hi + lambda m I,
+        // to every lambda's factor tile (diagonal tiles: the diagonal patched
+        // in the staging copy between the stores).  Another sigma's values are
+        // formed while the stores read the staging chunk.
         const int ew = warp - OZ_EPI_WARP0;    // 0..15
         const int quad = warp & 3, quarter = ew >> 2;
         const int r = quad * 32 + lane;            // row inside the tile
+        const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..511
         const int G = kp.nsig * kp.nlam;
         int64_t cg = 0;
+        uint32_t round = 0;  // staging rounds (s_free phases)
         bool ok = true;
-        for (int64_t tile = blockIdx.x; tile < kp.ktot && ok; tile += gridDim.x) {
+        // after a timeout the warp keeps walking the tiles (and the barriers)
+        // but skips the work; the error word is set and the results unused
+        for (int64_t tile = blockIdx.x; tile < kp.ktot; tile += gridDim.x) {
             const OzTile tl = oz_tile_of(parts, kp.np, tile);
             const PartDesc &P = tl.P;
             const int pj = tl.pj, ti = tl.ti, tj = tl.tj;
@@ -680,85 +700,122 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
             const float2 nr2 = nrm[prow];
             const df nr = df_make(nr2.x, nr2.y);
             for (int c = 0; c < nchunks; ++c, ++cg) {
-                if (!oz_wait(&sm.t_full, (uint32_t)(cg & 1), err)) {
-                    ok = false;
-                    break;
-                }
-                tc_fence_after();
-#pragma unroll 1
-                for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
-                    float lv[OZ_SLICES][OZP_SUB];
-                    const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
+                const bool got = ok && oz_wait(&sm.t_full, (uint32_t)(cg & 1), err);
+                ok = got;
+                float dh[2][OZP_SUB], dl[2][OZP_SUB];
+                if (got) {
+                    tc_fence_after();
 #pragma unroll
-                    for (int L = 0; L < OZ_SLICES; ++L)
-                        tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0,
-                                          lv[L]);
-                    tmem_wait_ld();
-                    if (sub == (OZ_N / 4) / OZP_SUB - 1) {  // the levels are in registers: release the TMEM
-                        tc_fence_before();
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sm.t_empty);
-                    }
-                    const int cbase = c * OZ_N + (int)col0;  // column inside the tile
-                    float dh[OZP_SUB], dl[OZP_SUB];
+                    for (int sub = 0; sub < 2; ++sub) {
+                        float lv[OZ_SLICES][OZP_SUB];
+                        const uint32_t col0 = (uint32_t)(quarter * (OZ_N / 4) + sub * OZP_SUB);
 #pragma unroll
-                    for (int k = 0; k < OZP_SUB; ++k) {
-                        const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
-                        const float2 nc2 = nrm[pc];
-                        const int sc = er + ex[pc] - 13;
-                        const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nr, nc2.x,
-                                                 nc2.y, __int_as_float((127 + sc) << 23));
-                        dh[k] = D.hi;
-                        dl[k] = D.lo;
-                    }
-                    const bool diag_here = (ti == tj);
-#pragma unroll 1
-                    for (int is = 0; is < kp.nsig; ++is) {
-                        const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
-                        float hv[OZP_SUB], lw[OZP_SUB];
+                        for (int L = 0; L < OZ_SLICES; ++L)
+                            tmem_ld_32x32b_x8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(L * OZ_N) + col0,
+                                              lv[L]);
+                        tmem_wait_ld();
+                        const int cbase = c * OZ_N + (int)col0;  // column inside the tile
 #pragma unroll
                         for (int k = 0; k < OZP_SUB; ++k) {
-                            const int gc = tj * KRR_TILE + cbase + k;
+                            const int64_t pc = P.prow0 + (int64_t)tj * KRR_TILE + cbase + k;
+                            const float2 nc2 = nrm[pc];
+                            const int sc = er + ex[pc] - 13;
+                            const df D = oz_distance(lv[0][k], lv[1][k], lv[2][k], lv[3][k], lv[4][k], nr, nc2.x,
+                                                     nc2.y, __int_as_float((127 + sc) << 23));
+                            dh[sub][k] = D.hi;
+                            dl[sub][k] = D.lo;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int sub = 0; sub < 2; ++sub)
+#pragma unroll
+                        for (int k = 0; k < OZP_SUB; ++k) dh[sub][k] = dl[sub][k] = 0.f;
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&sm.t_empty);  // the levels are in registers
+#pragma unroll 1
+                for (int is = 0; is < kp.nsig; ++is, ++round) {
+                    const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
+                    float hv[2][OZP_SUB], lw[2][OZP_SUB];
+#pragma unroll
+                    for (int sub = 0; sub < 2; ++sub)
+#pragma unroll
+                        for (int k = 0; k < OZP_SUB; ++k) {
+                            const int gc = tj * KRR_TILE + c * OZ_N + quarter * (OZ_N / 4) + sub * OZP_SUB + k;
                             df kv;
                             if (gr >= P.m || gc >= P.m) kv = df_make(gr == gc ? 1.f : 0.f, 0.f);
                             else if (gr == gc) kv = df_make(1.f, 0.f);
-                            else kv = df_exp_nonpos(df_mul(df_make(dh[k], dl[k]), cs), sm.exptab);
-                            hv[k] = kv.hi;
-                            lw[k] = kv.lo;
+                            else kv = df_exp_nonpos(df_mul(df_make(dh[sub][k], dl[sub][k]), cs), sm.exptab);
+                            hv[sub][k] = kv.hi;
+                            lw[sub][k] = kv.lo;
                         }
-                        const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
-                        float4 *oh =
-                            reinterpret_cast<float4 *>(Kh + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
-                        float4 *ol =
-                            reinterpret_cast<float4 *>(Kl + kt * KRR_TILE_ELEMS + (int64_t)r * KRR_TILE + cbase);
+                    // the previous round's stores have read the staging chunk
+                    if (round > 0 && !oz_wait(&sm.s_free, (round - 1) & 1, err)) ok = false;
 #pragma unroll
-                        for (int q = 0; q < OZP_SUB / 4; ++q) {
-                            oh[q] = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                            ol[q] = make_float4(lw[4 * q], lw[4 * q + 1], lw[4 * q + 2], lw[4 * q + 3]);
+                    for (int sub = 0; sub < 2; ++sub) {
+                        const int col = quarter * (OZ_N / 4) + sub * OZP_SUB;  // in the chunk
+                        const int box = col >> 5, u0 = (col & 31) >> 2;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            const uint32_t off = (uint32_t)r * 128u + ((uint32_t)((u0 + h) ^ (r & 7)) << 4);
+                            *reinterpret_cast<float4 *>(sm.stage[0][box] + off) =
+                                make_float4(hv[sub][4 * h], hv[sub][4 * h + 1], hv[sub][4 * h + 2], hv[sub][4 * h + 3]);
+                            *reinterpret_cast<float4 *>(sm.stage[1][box] + off) =
+                                make_float4(lw[sub][4 * h], lw[sub][4 * h + 1], lw[sub][4 * h + 2], lw[sub][4 * h + 3]);
                         }
-#pragma unroll 1
+                    }
+                    fence_proxy_async_smem();
+                    epi_bar_p();
+                    const bool diag = ti == tj;
+                    const int y = (int)(((int64_t)is * kp.ktot + P.ktile0 + lt) * KRR_TILE);
+                    if (et == 0) {
+                        for (int bx = 0; bx < 2; ++bx) {
+                            tma_store_2d(&tmKh, c * OZ_N + 32 * bx, y, sm.stage[0][bx]);
+                            tma_store_2d(&tmKl, c * OZ_N + 32 * bx, y, sm.stage[1][bx]);
+                        }
+                        if (!diag)
+                            for (int il = 0; il < kp.nlam; ++il) {
+                                const int yf =
+                                    (int)((solves[(int64_t)pj * G + is * kp.nlam + il].ltile0 + lt) * KRR_TILE);
+                                for (int bx = 0; bx < 2; ++bx)
+                                    tma_store_2d(&tmF, c * OZ_N + 32 * bx, yf, sm.stage[0][bx]);
+                            }
+                        bulk_commit();
+                    }
+                    if (diag) {  // factor tiles: K_hi + lambda m on the real diagonal
                         for (int il = 0; il < kp.nlam; ++il) {
-                            const SolveDesc S = solves[(int64_t)pj * G + is * kp.nlam + il];
-                            const float lm = (float)S.lambda_m;
-                            float4 *oa = reinterpret_cast<float4 *>(A + (S.ltile0 + lt) * KRR_TILE_ELEMS +
-                                                                     (int64_t)r * KRR_TILE + cbase);
-#pragma unroll
-                            for (int q = 0; q < OZP_SUB / 4; ++q) {
-                                float4 v = make_float4(hv[4 * q], hv[4 * q + 1], hv[4 * q + 2], hv[4 * q + 3]);
-                                if (diag_here && gr < P.m) {
-                                    const int d0 = gr - (tj * KRR_TILE + cbase + 4 * q);
-                                    if (d0 == 0) v.x += lm;
-                                    else if (d0 == 1) v.y += lm;
-                                    else if (d0 == 2) v.z += lm;
-                                    else if (d0 == 3) v.w += lm;
-                                }
-                                oa[q] = v;
+                            if (et == 0) bulk_wait_read_all();
+                            epi_bar_p();  // the staging copy is no longer being read
+                            const int rr = c * OZ_N + et;  // diagonal entry (rr, rr) of this chunk
+                            if (et < OZ_N && ti * KRR_TILE + rr < P.m) {
+                                const float lm = (float)solves[(int64_t)pj * G + is * kp.nlam + il].lambda_m;
+                                const int box = et >> 5, u = (et & 31) >> 2;
+                                float *d = reinterpret_cast<float *>(sm.stage[0][box] + (uint32_t)rr * 128u +
+                                                                     ((uint32_t)(u ^ (rr & 7)) << 4)) +
+                                           (et & 3);
+                                *d = 1.f + lm;
+                            }
+                            fence_proxy_async_smem();
+                            epi_bar_p();
+                            if (et == 0) {
+                                const int yf =
+                                    (int)((solves[(int64_t)pj * G + is * kp.nlam + il].ltile0 + lt) * KRR_TILE);
+                                for (int bx = 0; bx < 2; ++bx)
+                                    tma_store_2d(&tmF, c * OZ_N + 32 * bx, yf, sm.stage[0][bx]);
+                                bulk_commit();
                             }
                         }
+                    }
+                    if (et == 0) {
+                        bulk_wait_read_all();
+                        mbar_arrive(&sm.s_free);
                     }
                 }
             }
         }
+        if (et == 0) bulk_wait_all();  // the stores have completed
     }
     tc_fence_before();
     __syncthreads();
@@ -766,6 +823,8 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
 }
 
 // ---------------------------------------------------------------- host
+bool make_tile_tmap(CUtensorMap *, float *, int64_t);  // chol.cu: FP32 tile store, 32 x 128 boxes, 128B swizzle
+
 typedef CUresult (*PFN_encodeTiled_t)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                       const cuuint64_t *, const cuuint32_t *, const cuuint32_t *,
                                       CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
@@ -813,8 +872,13 @@ static size_t oz_psmem_bytes() { return sizeof(OzPSmem) + 1024; }
 cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
                              int *d_err) {
     if (ktot == 0) return cudaSuccess;
-    CUtensorMap tmA;
+    CUtensorMap tmA, tmKh, tmKl, tmF;
     if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
+    int64_t ftiles = 0;  // tiles of the factor store
+    for (const SolveDesc &S : M.solves) ftiles = std::max<int64_t>(ftiles, S.ltile0 + tri(S.T));
+    if (!make_tile_tmap(&tmKh, Kh, (int64_t)M.nsig * ktot) || !make_tile_tmap(&tmKl, Kl, (int64_t)M.nsig * ktot) ||
+        !make_tile_tmap(&tmF, A, ftiles))
+        return cudaErrorInvalidValue;
     allow_max_dyn_smem(kbuild_oz_kernel);
     OzKParams kp;
     kp.nsig = M.nsig;
@@ -832,7 +896,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const unsigned grid = (unsigned)std::min<int64_t>(ktot, nsm);  // persistent: one CTA per SM
     KRR_LAUNCHED(), kbuild_oz_kernel<<<grid, OZP_THREADS, oz_smem_bytes(), st>>>(
-        tmA, M.oz_tmB, M.d_parts, M.d_solves, M.ozex, M.nrm, kp, M.prows, Kh, Kl, A, d_err);
+        tmA, M.oz_tmB, tmKh, tmKl, tmF, M.d_parts, M.d_solves, M.ozex, M.nrm, kp, M.prows, Kh, Kl, A, d_err);
     return cudaGetLastError();
 }
 
