@@ -355,13 +355,15 @@ template <int MODE> struct TcCfg {
     static constexpr bool PRE = MODE == TC_TF32X3P;                        // lo operands landed by TMA
     // operand ring depth: as many stages as fit beside the 64 KB destination
     // tile (the loads come from L2 at ~1-2 us latency; bytes in flight set the pace)
-    static constexpr int STAGES = MODE == TC_TRSM ? 3 : ((SPLIT || PRE) ? 2 : (MODE == TC_F16 ? 5 : 3));
+    static constexpr int STAGES = (MODE == TC_TRSM || PRE) ? 3 : (SPLIT ? 2 : (MODE == TC_F16 ? 5 : 3));
     // A, B as landed (FP32) + the hi/lo operands: FP32 A_lo, B_lo (TF32X3) or
     // BF16 A_hi, A_lo, B_hi, B_lo (BF16X3, 8 KB each)
     static constexpr uint32_t STAGE_BYTES = (SPLIT || PRE ? 4u : 2u) * TC_HALF;
     static constexpr int THREADS = SPLIT ? 320 : 192;
-    // destination tile of the update epilogue (none for the panel solve)
-    static constexpr uint32_t CBUF = MODE == TC_TRSM ? 0u : (uint32_t)KRR_TILE * KRR_TILE * 4;
+    // destination tile of the update epilogue, in 32-column boxes of 16 KB:
+    // the whole tile, or half of it at a time for the pre-split three-pass
+    // mode (whose 64 KB stages need the room); none for the panel solve
+    static constexpr uint32_t CBUF = MODE == TC_TRSM ? 0u : (uint32_t)KRR_TILE * KRR_TILE * 4 / (PRE ? 2 : 1);
     static constexpr size_t SMEM = STAGES * STAGE_BYTES + CBUF + 1024 + 256;
     static_assert(SMEM <= 232448, "tile kernel shared memory");
 };
@@ -614,119 +616,148 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
         // in shared memory and the tile goes back by TMA store; the panel
         // solve (no read of the destination) stores directly
         const bool tma_c = mode != UPD_TRSM && Cfg::CBUF > 0;
+        constexpr uint32_t BOX = (uint32_t)KRR_TILE * 32 * 4;       // one 32-column box, 16 KB
+        constexpr int CBOX = (int)(Cfg::CBUF / BOX);               // boxes held in cbuf
+        constexpr int NH = CBOX > 0 ? (KRR_TILE / 32) / CBOX : 1;  // cbuf rounds per tile
         auto c_tile_y = [&](int64_t tt) {
             SolveDesc S2;
             TaskGeom g2;
             task(tt, S2, g2);
             return (int)((S2.ltile0 + (int64_t)g2.i * (g2.i + 1) / 2 + g2.j) * KRR_TILE);
         };
-        if (tma_c && threadIdx.x == 64 && (int64_t)blockIdx.x < ntasks) {
-            const int y = c_tile_y(blockIdx.x);
+        // round h of task tt: boxes h CBOX .. h CBOX + CBOX - 1 of its destination tile
+        auto c_load = [&](int64_t tt, int h) {
+            const int y = c_tile_y(tt);
             mbar_arrive_expect_tx(cfull, Cfg::CBUF);
-            for (int cb = 0; cb < KRR_TILE / 32; ++cb) tma_load_2d(cbuf + cb * (Cfg::CBUF / 4), &tmapC, cb * 32, y, cfull);
-        }
-        int lt = 0;
-        bool ok = true;
-        for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++lt) {
-            SolveDesc S;
-            TaskGeom g;
-            task(t, S, g);
-            float *dst = dst_tile(S, g) + (int64_t)r * KRR_TILE;
-            // a class-1 solve's panel solve writes its L tile in FP16 (operand of the one-pass updates)
-            const bool half_out = mode == UPD_TRSM && S.cls == 1;
-            __half *dst16 = half_out ? A16 + (dst_tile(S, g) - A) + (int64_t)r * KRR_TILE : nullptr;
-            // a class-3 solve's panel solve also writes lo = x - hi (hi: x with
-            // the low 13 mantissa bits cleared), the second operand of TC_TF32X3P
-            const bool lo_out = mode == UPD_TRSM && S.cls == 3 && Alo != nullptr;
-            float *dstlo = lo_out ? Alo + (S.lotile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS +
-                                        (int64_t)r * KRR_TILE
-                                  : nullptr;
-            const int b = lt & 1;
-            // after a timeout the warp keeps the loop and its barrier but skips
-            // the work (the error word is set; the results are not used)
-            bool got = ok;
-            if (got && tma_c) got = mbar_wait_deadline(cfull, (uint32_t)(lt & 1), err);
-            if (got) got = mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err);
-            ok = got;
-            if (got) {
-                tc_fence_after();
+            for (int k = 0; k < CBOX; ++k) tma_load_2d(cbuf + k * BOX, &tmapC, (h * CBOX + k) * 32, y, cfull);
+        };
+        if (tma_c) {
+            if (threadIdx.x == 64 && (int64_t)blockIdx.x < ntasks) c_load(blockIdx.x, 0);
+            int lt = 0;
+            uint32_t nround = 0;  // cbuf rounds consumed (cfull phases)
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++lt) {
+                SolveDesc S;
+                TaskGeom g;
+                task(t, S, g);
+                const int b = lt & 1;
+                // after a timeout the warp keeps the loop and its barriers but
+                // skips the work (the error word is set; the results are not used)
+                bool got = ok && mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err);
+                if (got) tc_fence_after();
+                for (int h = 0; h < NH; ++h, ++nround) {
+                    got = got && mbar_wait_deadline(cfull, nround & 1, err);
+                    if (got) {
 #pragma unroll 1
-                for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
-                    float v[32];
-                    tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32),
-                                       v);
-                    if (tma_c) {
-                        // row r of box cb: 16-byte unit q at q ^ (r % 8)
-                        unsigned char *row = cbuf + cb * (Cfg::CBUF / 4) + r * 128;
-#pragma unroll
-                        for (int qq = 0; qq < 8; ++qq) {
-                            float4 *p4 = reinterpret_cast<float4 *>(row + ((qq ^ (r & 7)) << 4));
-                            float4 o = *p4;
-                            o.x -= v[4 * qq + 0];
-                            o.y -= v[4 * qq + 1];
-                            o.z -= v[4 * qq + 2];
-                            o.w -= v[4 * qq + 3];
-                            *p4 = o;
-                        }
-                    } else if (half_out) {
-                        uint4 *h4 = reinterpret_cast<uint4 *>(dst16 + cb * 32);
-#pragma unroll
-                        for (int qq = 0; qq < 4; ++qq) {
-                            uint4 o;
-                            __half2 h;
-                            h = __floats2half2_rn(v[8 * qq + 0], v[8 * qq + 1]);
-                            o.x = *reinterpret_cast<uint32_t *>(&h);
-                            h = __floats2half2_rn(v[8 * qq + 2], v[8 * qq + 3]);
-                            o.y = *reinterpret_cast<uint32_t *>(&h);
-                            h = __floats2half2_rn(v[8 * qq + 4], v[8 * qq + 5]);
-                            o.z = *reinterpret_cast<uint32_t *>(&h);
-                            h = __floats2half2_rn(v[8 * qq + 6], v[8 * qq + 7]);
-                            o.w = *reinterpret_cast<uint32_t *>(&h);
-                            h4[qq] = o;
-                        }
-                    } else {
-                        float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
-#pragma unroll
-                        for (int qq = 0; qq < 8; ++qq)
-                            d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
-                        if (lo_out) {
-                            float4 *l4 = reinterpret_cast<float4 *>(dstlo + cb * 32);
+                        for (int k = 0; k < CBOX; ++k) {
+                            const int cb = h * CBOX + k;
+                            float v[32];
+                            tmem_ld_32x32b_x32(
+                                tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32), v);
+                            // row r of the box: 16-byte unit q at q ^ (r % 8)
+                            unsigned char *row = cbuf + k * BOX + r * 128;
 #pragma unroll
                             for (int qq = 0; qq < 8; ++qq) {
-                                float4 o;
-                                o.x = v[4 * qq + 0] - __uint_as_float(__float_as_uint(v[4 * qq + 0]) & 0xFFFFE000u);
-                                o.y = v[4 * qq + 1] - __uint_as_float(__float_as_uint(v[4 * qq + 1]) & 0xFFFFE000u);
-                                o.z = v[4 * qq + 2] - __uint_as_float(__float_as_uint(v[4 * qq + 2]) & 0xFFFFE000u);
-                                o.w = v[4 * qq + 3] - __uint_as_float(__float_as_uint(v[4 * qq + 3]) & 0xFFFFE000u);
-                                l4[qq] = o;
+                                float4 *p4 = reinterpret_cast<float4 *>(row + ((qq ^ (r & 7)) << 4));
+                                float4 o = *p4;
+                                o.x -= v[4 * qq + 0];
+                                o.y -= v[4 * qq + 1];
+                                o.z -= v[4 * qq + 2];
+                                o.w -= v[4 * qq + 3];
+                                *p4 = o;
+                            }
+                        }
+                    }
+                    if (h == NH - 1) {  // the accumulator has been read back
+                        tc_fence_before();
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&tempty[b]);
+                    }
+                    fence_proxy_async_smem();  // cbuf writes -> visible to the TMA store
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                    if (threadIdx.x == 64) {
+                        const int y = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE);
+                        if (got)
+                            for (int k = 0; k < CBOX; ++k) tma_store_2d(&tmapC, (h * CBOX + k) * 32, y, cbuf + k * BOX);
+                        bulk_commit();
+                        bulk_wait_read_all();  // cbuf may be refilled
+                        if (got) {
+                            if (h + 1 < NH) c_load(t, h + 1);
+                            else if (t + gridDim.x < ntasks) c_load(t + gridDim.x, 0);
+                        }
+                    }
+                }
+                ok = got;
+            }
+            if (threadIdx.x == 64) bulk_wait_all();  // the stores have completed
+        } else {  // the panel solve (TC_TRSM): A_ik = C, stored directly
+            int lt = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntasks; t += gridDim.x, ++lt) {
+                SolveDesc S;
+                TaskGeom g;
+                task(t, S, g);
+                float *dst = dst_tile(S, g) + (int64_t)r * KRR_TILE;
+                // a class-1 solve's panel solve writes its L tile in FP16 (operand of the one-pass updates)
+                const bool half_out = S.cls == 1;
+                __half *dst16 = half_out ? A16 + (dst_tile(S, g) - A) + (int64_t)r * KRR_TILE : nullptr;
+                // a class-3 solve's panel solve also writes lo = x - hi (hi: x with
+                // the low 13 mantissa bits cleared), the second operand of TC_TF32X3P
+                const bool lo_out = S.cls == 3 && Alo != nullptr;
+                float *dstlo = lo_out ? Alo + (S.lotile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE_ELEMS +
+                                            (int64_t)r * KRR_TILE
+                                      : nullptr;
+                const int b = lt & 1;
+                const bool got = ok && mbar_wait_deadline(&tfull[b], (uint32_t)((lt >> 1) & 1), err);
+                ok = got;
+                if (got) {
+                    tc_fence_after();
+    #pragma unroll 1
+                    for (int cb = 0; cb < KRR_TILE / 32; ++cb) {
+                        float v[32];
+                        tmem_ld_32x32b_x32(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32),
+                                           v);
+                        if (half_out) {
+                            uint4 *h4 = reinterpret_cast<uint4 *>(dst16 + cb * 32);
+    #pragma unroll
+                            for (int qq = 0; qq < 4; ++qq) {
+                                uint4 o;
+                                __half2 hh;
+                                hh = __floats2half2_rn(v[8 * qq + 0], v[8 * qq + 1]);
+                                o.x = *reinterpret_cast<uint32_t *>(&hh);
+                                hh = __floats2half2_rn(v[8 * qq + 2], v[8 * qq + 3]);
+                                o.y = *reinterpret_cast<uint32_t *>(&hh);
+                                hh = __floats2half2_rn(v[8 * qq + 4], v[8 * qq + 5]);
+                                o.z = *reinterpret_cast<uint32_t *>(&hh);
+                                hh = __floats2half2_rn(v[8 * qq + 6], v[8 * qq + 7]);
+                                o.w = *reinterpret_cast<uint32_t *>(&hh);
+                                h4[qq] = o;
+                            }
+                        } else {
+                            float4 *d4 = reinterpret_cast<float4 *>(dst + cb * 32);
+    #pragma unroll
+                            for (int qq = 0; qq < 8; ++qq)
+                                d4[qq] = make_float4(v[4 * qq], v[4 * qq + 1], v[4 * qq + 2], v[4 * qq + 3]);
+                            if (lo_out) {
+                                float4 *l4 = reinterpret_cast<float4 *>(dstlo + cb * 32);
+    #pragma unroll
+                                for (int qq = 0; qq < 8; ++qq) {
+                                    float4 o;
+                                    o.x = v[4 * qq + 0] - __uint_as_float(__float_as_uint(v[4 * qq + 0]) & 0xFFFFE000u);
+                                    o.y = v[4 * qq + 1] - __uint_as_float(__float_as_uint(v[4 * qq + 1]) & 0xFFFFE000u);
+                                    o.z = v[4 * qq + 2] - __uint_as_float(__float_as_uint(v[4 * qq + 2]) & 0xFFFFE000u);
+                                    o.w = v[4 * qq + 3] - __uint_as_float(__float_as_uint(v[4 * qq + 3]) & 0xFFFFE000u);
+                                    l4[qq] = o;
+                                }
                             }
                         }
                     }
                 }
-            }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&tempty[b]);
-            if (tma_c) {
-                fence_proxy_async_smem();  // cbuf writes -> visible to the TMA store
-                asm volatile("bar.sync 1, 128;" ::: "memory");
-                if (threadIdx.x == 64) {
-                    const int y = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + g.j) * KRR_TILE);
-                    if (ok)
-                        for (int cb = 0; cb < KRR_TILE / 32; ++cb)
-                            tma_store_2d(&tmapC, cb * 32, y, cbuf + cb * (Cfg::CBUF / 4));
-                    bulk_commit();
-                    bulk_wait_read_all();  // cbuf may be refilled
-                    if (ok && t + gridDim.x < ntasks) {
-                        const int yn = c_tile_y(t + gridDim.x);
-                        mbar_arrive_expect_tx(cfull, Cfg::CBUF);
-                        for (int cb = 0; cb < KRR_TILE / 32; ++cb)
-                            tma_load_2d(cbuf + cb * (Cfg::CBUF / 4), &tmapC, cb * 32, yn, cfull);
-                    }
-                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[b]);
             }
         }
-        if (tma_c && threadIdx.x == 64) bulk_wait_all();  // the stores have completed
     }
     tc_fence_before();
     __syncthreads();
