@@ -61,6 +61,9 @@ struct PcgBuffers {
     int maxT;
     const void *L16;  // FP16 factor store of class-1 solves (null without them)
     int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
+    const float *rsR, *rsC;  // row sums of K from the kernel-tile build (null: none)
+    const int64_t *rsoff;
+    int64_t rstot;
 };
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
@@ -74,7 +77,8 @@ int oz_dpz(int d);
 bool oz_supported(int d);
 void launch_oz_slice(cudaStream_t, const double *, int, const int64_t *, int64_t, int64_t, void *, int32_t *, float2 *);
 bool make_slice_tmap(CUtensorMap *, void *, int64_t, int, int);
-cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, float *, float *, int *);
+cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, float *, float *, float *, float *,
+                             const int64_t *, int64_t, int *);
 cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
                               const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
                               int *);
@@ -426,6 +430,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     }
 
     // ---- budget check before any allocation
+    int64_t rs_slots = 0;  // row-sum slots of the exact-Gram tile build: sum of T^2
+    for (const PartDesc &P : M.parts) rs_slots += (int64_t)P.T * P.T;
     const size_t tileb = (size_t)KRR_TILE_ELEMS * esz;
     size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 8 +
                          (size_t)prow * (10 * (size_t)((d + 31) / 32 * 32) + 4) +
@@ -433,6 +439,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
                         (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
                         (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) + (fp64 ? 0 : (size_t)ltiles * tileb) +
+                        (fp64 ? 0 : (size_t)ns * rs_slots * 3 * KRR_TILE * sizeof(float)) +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
                         8 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
@@ -523,6 +530,23 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         }
         float *Kh = nullptr, *Kl = nullptr;
         double *K64 = nullptr;
+        // row sums of K left by the exact-Gram tile build, for ||A||_inf
+        float *rsR = nullptr, *rsC = nullptr;
+        int64_t *d_rsoff = nullptr, rstot = 0;
+        if (!fp64 && M.ozS) {
+            std::vector<int64_t> rsoff(p);
+            for (int j = 0; j < p; ++j) {
+                rsoff[j] = rstot;
+                rstot += (int64_t)M.parts[j].T * M.parts[j].T;
+            }
+            if (rstot > 0) {
+                FIT_TRY(W.get(&rsR, (size_t)ns * rstot * 2 * KRR_TILE * sizeof(float)));
+                FIT_TRY(W.get(&rsC, (size_t)ns * rstot * KRR_TILE * sizeof(float)));
+                FIT_TRY(W.get(&d_rsoff, sizeof(int64_t) * p));
+                FIT_TRY(cudaMemcpyAsync(d_rsoff, rsoff.data(), sizeof(int64_t) * p, cudaMemcpyHostToDevice, st));
+                FIT_TRY(cudaStreamSynchronize(st));  // the host vector goes out of scope
+            }
+        }
         {
             ProfScope ps(prof, PROF_KBUILD, st);
             if (fp64) {
@@ -532,7 +556,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 Kh = (float *)Kst;
                 Kl = Kh + (size_t)ns * ktot * KRR_TILE_ELEMS;
                 if (M.ozS) {
-                    FIT_TRY(launch_kbuild_oz(st, M, ktot, Kh, Kl, (float *)Ast, c->d_err));
+                    FIT_TRY(launch_kbuild_oz(st, M, ktot, Kh, Kl, (float *)Ast, rsR, rsC, d_rsoff, rstot,
+                                             c->d_err));
                 } else {
                     launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
                 }
@@ -561,6 +586,10 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         B.maxT = maxT;
         B.L16 = A16;
         B.order = d_order;
+        B.rsR = rsR;
+        B.rsC = rsC;
+        B.rsoff = d_rsoff;
+        B.rstot = rstot;
         FIT_TRY(run_pcg_norms(st, M, B, Kh, Kl, K64, fp64, prof));
         std::vector<PcgState> hs0(nsolve);
         FIT_TRY(cudaMemcpyAsync(hs0.data(), state, sizeof(PcgState) * nsolve, cudaMemcpyDeviceToHost, st));

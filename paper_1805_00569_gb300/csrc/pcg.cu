@@ -601,6 +601,9 @@ struct PcgBuffers {
     int maxT;
     const void *L16;  // FP16 factor store of class-1 solves (null without them)
     int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
+    const float *rsR, *rsC;  // row sums of K from the kernel-tile build (null: none)
+    const int64_t *rsoff;
+    int64_t rstot;
 };
 
 size_t pcg_state_size() { return sizeof(PcgState); }
@@ -642,13 +645,45 @@ size_t precond_smem_bytes(bool fp64, int maxT) {
     return (fp64 ? 8 : 4) * ((size_t)maxT * KRR_TILE + 33 * KRR_TILE);
 }
 
+// q = (K + lambda m I) 1 for every solve from the row sums the kernel-tile
+// build left (FP32 partials, summed in FP64 in a fixed order: tiles b <= a of
+// block row a per 64-column chunk, then the column sums of tiles (b > a, a));
+// grid (groups, largest T), 128 threads
+__global__ void rowsum_reduce_kernel(const GroupDesc *__restrict__ groups, const SolveDesc *__restrict__ solves,
+                                     const float *__restrict__ rsR, const float *__restrict__ rsC,
+                                     const int64_t *__restrict__ rsoff, int64_t rstot, double *__restrict__ q) {
+    const GroupDesc G = groups[blockIdx.x];
+    const int a = blockIdx.y, T = G.T, c = threadIdx.x;
+    if (a >= T) return;
+    const int64_t g0 = (int64_t)G.isig * rstot + rsoff[G.part];
+    double sum = 0.0;
+    for (int b = 0; b <= a; ++b) {
+        const int64_t sl = (g0 + (int64_t)a * T + b) * 2;
+        sum += (double)rsR[sl * KRR_TILE + c] + (double)rsR[(sl + 1) * KRR_TILE + c];
+    }
+    for (int b = a + 1; b < T; ++b) sum += (double)rsC[(g0 + (int64_t)a * T + b) * KRR_TILE + c];
+    const int e = a * KRR_TILE + c;
+    for (int l = 0; l < G.nlam; ++l) {
+        const SolveDesc S = solves[G.solve0 + l];
+        q[S.vec0 + e] = (e < S.m) ? sum + S.lambda_m : 0.0;
+    }
+}
+
 // Phase 1 of the refinement, also used before the factorisation: x = 0 and
-// ||A||_inf = max(A 1) (A >= 0 entrywise), ||y||_inf, r = y per solve.
+// ||A||_inf = max(A 1) (A >= 0 entrywise), ||y||_inf, r = y per solve.  A 1
+// comes from the kernel-tile build's row sums when it left them (B.rsR), else
+// from one matrix-vector product.
 cudaError_t run_pcg_norms(cudaStream_t st, const Model &M, const PcgBuffers &B, const float *Kh, const float *Kl,
                           const double *K64, bool fp64, Prof *prof) {
     const unsigned ns = (unsigned)M.solves.size();
     KRR_LAUNCHED(), pcg_prepare_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, nullptr, B.x, B.p, B.pdf);
-    launch_matvec(st, M, B, Kh, Kl, K64, fp64, prof);
+    if (B.rsR && B.ng > 0) {
+        ProfScope ps(prof, PROF_MATVEC, st);
+        KRR_LAUNCHED(), rowsum_reduce_kernel<<<dim3((unsigned)B.ng, (unsigned)B.maxT), KRR_TILE, 0, st>>>(
+            B.d_groups, M.d_solves, B.rsR, B.rsC, B.rsoff, B.rstot, B.q);
+    } else {
+        launch_matvec(st, M, B, Kh, Kl, K64, fp64, prof);
+    }
     KRR_LAUNCHED(), pcg_norms_kernel<<<ns, 256, 0, st>>>(M.d_solves, B.state, B.y, B.q, B.r);
     return cudaGetLastError();
 }

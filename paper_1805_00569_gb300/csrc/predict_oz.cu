@@ -534,6 +534,12 @@ struct OzKParams {
     float c_hi[8], c_lo[8];
     int kc;
     int64_t ktot;
+    // row sums of K (for ||K + lambda m I||_inf): per (sigma, partition) a
+    // T x T grid of 128-float slots; R holds tile (a, b <= a)'s row sums per
+    // 64-column chunk, C holds tile (b > a, a)'s column sums (null: skipped)
+    float *rsR, *rsC;
+    const int64_t *rsoff;  // per partition: first slot of its grid (sigma 0)
+    int64_t rstot;         // slots per sigma (sum of T^2)
 };
 
 __device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64_t tile) {
@@ -572,7 +578,10 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
     OzSmem &sm = *reinterpret_cast<OzSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int nchunks = KRR_TILE / OZ_N;  // 2 per tile
-    if (threadIdx.x < 8) sm.cs[threadIdx.x] = make_float2(kp.c_hi[threadIdx.x], kp.c_lo[threadIdx.x]);
+    if (threadIdx.x == 0) {  // static indices: the parameter block stays in the constant bank
+#pragma unroll
+        for (int i = 0; i < 8; ++i) sm.cs[i] = make_float2(kp.c_hi[i], kp.c_lo[i]);
+    }
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < OZ_ASTAGES; ++i) {
@@ -583,7 +592,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         mbar_init(&sm.b_empty, 1);
         mbar_init(&sm.t_full, 1);
         mbar_init(&sm.t_empty, OZP_EPI_WARPS);
-        mbar_init(&sm.s_free, 1);
+        mbar_init(&sm.s_free, 1 + (kp.rsR ? 6 : 0));  // the store thread, and the row/column-sum warps
         fence_mbar_init();
     }
     exp_table_init(sm.exptab);
@@ -769,6 +778,35 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     fence_proxy_async_smem();
                     epi_bar_p();
                     const bool diag = ti == tj;
+                    if (kp.rsR && et < 3 * KRR_TILE / 2) {
+                        // row sums of this chunk (threads 0..127, row et) and
+                        // column sums of off-diagonal tiles (threads 128..191,
+                        // column et - 128 of the chunk), from the staged K_hi
+                        const int64_t g0 = (int64_t)is * kp.rstot + kp.rsoff[pj];
+                        if (et < KRR_TILE) {
+                            const int rr = et;
+                            float rs = 0.f;
+#pragma unroll
+                            for (int u = 0; u < 16; ++u) {
+                                const float4 w = *reinterpret_cast<const float4 *>(
+                                    sm.stage[0][u >> 3] + (uint32_t)rr * 128u + ((uint32_t)((u & 7) ^ (rr & 7)) << 4));
+                                rs += (w.x + w.y) + (w.z + w.w);
+                            }
+                            kp.rsR[((g0 + (int64_t)ti * P.T + tj) * 2 + c) * KRR_TILE + rr] = rs;
+                        } else if (!diag) {
+                            const int cc = et - KRR_TILE;  // column of the chunk
+                            const uint32_t cu = (uint32_t)((cc & 31) >> 2), ce = (uint32_t)(cc & 3);
+                            const unsigned char *bx = sm.stage[0][cc >> 5];
+                            float cs = 0.f;
+#pragma unroll 8
+                            for (int rr = 0; rr < KRR_TILE; ++rr)
+                                cs += *reinterpret_cast<const float *>(bx + (uint32_t)rr * 128u +
+                                                                      ((cu ^ (uint32_t)(rr & 7)) << 4) + 4u * ce);
+                            kp.rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c * OZ_N + cc] = cs;
+                        }
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&sm.s_free);
+                    }
                     const int y = (int)(((int64_t)is * kp.ktot + P.ktile0 + lt) * KRR_TILE);
                     if (et == 0) {
                         for (int bx = 0; bx < 2; ++bx) {
@@ -870,7 +908,7 @@ static size_t oz_psmem_bytes() { return sizeof(OzPSmem) + 1024; }
 
 // Kernel tiles of every partition and sigma, plus the factor matrices.
 cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
-                             int *d_err) {
+                             float *rsR, float *rsC, const int64_t *rsoff, int64_t rstot, int *d_err) {
     if (ktot == 0) return cudaSuccess;
     CUtensorMap tmA, tmKh, tmKl, tmF;
     if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
@@ -886,6 +924,10 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
     kp.np = M.p;
     kp.kc = M.dpz / OZ_KC;
     kp.ktot = ktot;
+    kp.rsR = rsR;
+    kp.rsC = rsC;
+    kp.rsoff = rsoff;
+    kp.rstot = rstot;
     for (int i = 0; i < 8; ++i) {
         const double c = i < M.nsig ? -1.0 / (2.0 * M.sigmas[i] * M.sigmas[i]) : 0.0;
         kp.c_hi[i] = (float)c;
