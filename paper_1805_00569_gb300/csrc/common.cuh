@@ -97,6 +97,10 @@ __device__ __forceinline__ df dfa_value(const df_acc &a) {
 __device__ __forceinline__ void exp_table_init(float2 *tab) {
     for (int j = threadIdx.x; j < 256; j += blockDim.x) tab[j] = krr_exp2_tab[j];
 }
+// NORM = false returns the pair unnormalised (hi + lo with |lo| below a few
+// ulps of hi, not necessarily hi = rn(hi + lo)): enough for a product that is
+// accumulated at once, three operations cheaper.
+template <bool NORM = true>
 __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab) {
     if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
     const float C1 = 0x1.62p-9f, C2 = 0x1.c85fep-18f, C3 = -0x1.718432p-43f;
@@ -118,8 +122,8 @@ __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab
     float e = __fmaf_rn(tv.x, eh, -p);
     e = __fmaf_rn(tv.x, el, e);
     e = __fmaf_rn(tv.y, eh, e);
-    float yh, yl;
-    fast_two_sum(p, e, yh, yl);
+    float yh = p, yl = e;
+    if (NORM) fast_two_sum(p, e, yh, yl);
     const float sc = __int_as_float((127 + (n >> 8)) << 23);  // 2^(n >> 8), n >> 8 in [-126, 0]
     return df_make(yh * sc, yl * sc);
 }

@@ -440,8 +440,8 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                                 x0 = df_add(x0, df_make(sv.x, sv.y));
                                 x1 = df_add(x1, df_make(sv.x, sv.y));
                             }
-                            const df k0 = df_exp_nonpos(x0, sm.exptab);
-                            const df k1 = df_exp_nonpos(x1, sm.exptab);
+                            const df k0 = df_exp_nonpos<false>(x0, sm.exptab);
+                            const df k1 = df_exp_nonpos<false>(x1, sm.exptab);
 #pragma unroll
                             for (int il = 0; il < OZ_NLP; ++il)
                                 if (il < pp.nlam) {
@@ -797,12 +797,13 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             const int cc = et - KRR_TILE;  // column of the chunk
                             const uint32_t cu = (uint32_t)((cc & 31) >> 2), ce = (uint32_t)(cc & 3);
                             const unsigned char *bx = sm.stage[0][cc >> 5];
-                            float cs = 0.f;
+                            float cs[4] = {0.f, 0.f, 0.f, 0.f};  // four chains: rows r = 4 i + j
 #pragma unroll 8
                             for (int rr = 0; rr < KRR_TILE; ++rr)
-                                cs += *reinterpret_cast<const float *>(bx + (uint32_t)rr * 128u +
-                                                                      ((cu ^ (uint32_t)(rr & 7)) << 4) + 4u * ce);
-                            kp.rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c * OZ_N + cc] = cs;
+                                cs[rr & 3] += *reinterpret_cast<const float *>(
+                                    bx + (uint32_t)rr * 128u + ((cu ^ (uint32_t)(rr & 7)) << 4) + 4u * ce);
+                            kp.rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c * OZ_N + cc] =
+                                (cs[0] + cs[1]) + (cs[2] + cs[3]);
                         }
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&sm.s_free);
