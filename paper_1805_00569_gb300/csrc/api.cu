@@ -430,7 +430,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     }
 
     // ---- budget check before any allocation
-    int64_t rs_slots = 0;  // row-sum slots of the exact-Gram tile build: sum of T^2
+    int64_t rs_slots = 0;  // row-sum tile slots of the exact-Gram tile build: sum of T^2
     for (const PartDesc &P : M.parts) rs_slots += (int64_t)P.T * P.T;
     const size_t tileb = (size_t)KRR_TILE_ELEMS * esz;
     size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 8 +
@@ -439,7 +439,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
                         (size_t)dtiles * tileb + 6 * (size_t)vec * 8 + (size_t)scratch * 8 +
                         (tf32 ? (size_t)ltiles * KRR_TILE_ELEMS * 2 : 0) + (fp64 ? 0 : (size_t)ltiles * tileb) +
-                        (fp64 ? 0 : (size_t)ns * rs_slots * 3 * KRR_TILE * sizeof(float)) +
+                        (fp64 ? 0 : (size_t)ns * rs_slots * 9 * KRR_TILE * sizeof(float)) +
                         pcg_state_size() * nsolve + sizeof(GroupDesc) * groups.size() + 8 * gpre.size() +
                         8 * nsolve + 64 * 1024 * 1024;
     if (c->budget && c->used + model_bytes + work_bytes > c->budget) {
@@ -540,7 +540,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 rstot += (int64_t)M.parts[j].T * M.parts[j].T;
             }
             if (rstot > 0) {
-                FIT_TRY(W.get(&rsR, (size_t)ns * rstot * 2 * KRR_TILE * sizeof(float)));
+                FIT_TRY(W.get(&rsR, (size_t)ns * rstot * 8 * KRR_TILE * sizeof(float)));
                 FIT_TRY(W.get(&rsC, (size_t)ns * rstot * KRR_TILE * sizeof(float)));
                 FIT_TRY(W.get(&d_rsoff, sizeof(int64_t) * p));
                 FIT_TRY(cudaMemcpyAsync(d_rsoff, rsoff.data(), sizeof(int64_t) * p, cudaMemcpyHostToDevice, st));

@@ -647,7 +647,8 @@ size_t precond_smem_bytes(bool fp64, int maxT) {
 
 // q = (K + lambda m I) 1 for every solve from the row sums the kernel-tile
 // build left (FP32 partials, summed in FP64 in a fixed order: tiles b <= a of
-// block row a per 64-column chunk, then the column sums of tiles (b > a, a));
+// block row a, eight 16-column partials each, then the column sums of tiles
+// (b > a, a));
 // grid (groups, largest T), 128 threads
 __global__ void rowsum_reduce_kernel(const GroupDesc *__restrict__ groups, const SolveDesc *__restrict__ solves,
                                      const float *__restrict__ rsR, const float *__restrict__ rsC,
@@ -658,8 +659,9 @@ __global__ void rowsum_reduce_kernel(const GroupDesc *__restrict__ groups, const
     const int64_t g0 = (int64_t)G.isig * rstot + rsoff[G.part];
     double sum = 0.0;
     for (int b = 0; b <= a; ++b) {
-        const int64_t sl = (g0 + (int64_t)a * T + b) * 2;
-        sum += (double)rsR[sl * KRR_TILE + c] + (double)rsR[(sl + 1) * KRR_TILE + c];
+        const int64_t sl = (g0 + (int64_t)a * T + b) * 8;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) sum += (double)rsR[(sl + u) * KRR_TILE + c];
     }
     for (int b = a + 1; b < T; ++b) sum += (double)rsC[(g0 + (int64_t)a * T + b) * KRR_TILE + c];
     const int e = a * KRR_TILE + c;

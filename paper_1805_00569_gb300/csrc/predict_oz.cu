@@ -53,7 +53,9 @@ constexpr uint32_t OZ_IDESC = make_idesc(1u /*BF16*/, OZ_M, OZ_N);
 struct OzChunkData {  // per training column of a chunk
     float nh[OZ_N], nl[OZ_N];
     int e[OZ_N];
-    float ah[OZ_NSP * OZ_NLP][OZ_N], al[OZ_NSP * OZ_NLP][OZ_N];
+    // alpha of (sigma, lambda) g as double-float, two columns per entry:
+    // (hi, lo) of column 2k, then of column 2k + 1 (one 16-byte load per pair)
+    float4 a2[OZ_NSP * OZ_NLP][OZ_N / 2];
 };
 
 constexpr uint32_t OZ_SBOX = (uint32_t)KRR_TILE * 32 * 4;  // one 32-column box of a 128-row FP32 tile, 16 KB
@@ -361,8 +363,8 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     solves[(int64_t)j * pp.Gtot + (int64_t)(pp.sig0 + is) * pp.nl_total + pp.lam0 + il];
                 const double av = alpha[S.vec0 + (int64_t)c * OZ_N + col];
                 const float h = __double2float_rn(av);
-                cd.ah[is * OZ_NLP + il][col] = h;
-                cd.al[is * OZ_NLP + il][col] = __double2float_rn(av - (double)h);
+                reinterpret_cast<float2 *>(&cd.a2[is * OZ_NLP + il][col >> 1])[col & 1] =
+                    make_float2(h, __double2float_rn(av - (double)h));
             }
             epi_bar_p();
             // after a timeout the warp keeps the loop (and its barriers) but skips the work,
@@ -445,10 +447,9 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                             for (int il = 0; il < OZ_NLP; ++il)
                                 if (il < pp.nlam) {
-                                    dfa_fma(acc[is][il], k0.hi, k0.lo, cd.ah[is * OZ_NLP + il][col],
-                                            cd.al[is * OZ_NLP + il][col]);
-                                    dfa_fma(acc[is][il], k1.hi, k1.lo, cd.ah[is * OZ_NLP + il][col + 1],
-                                            cd.al[is * OZ_NLP + il][col + 1]);
+                                    const float4 a = cd.a2[is * OZ_NLP + il][col >> 1];  // col is even
+                                    dfa_fma(acc[is][il], k0.hi, k0.lo, a.x, a.y);
+                                    dfa_fma(acc[is][il], k1.hi, k1.lo, a.z, a.w);
                                 }
                         }
                     }
@@ -535,8 +536,9 @@ struct OzKParams {
     int kc;
     int64_t ktot;
     // row sums of K (for ||K + lambda m I||_inf): per (sigma, partition) a
-    // T x T grid of 128-float slots; R holds tile (a, b <= a)'s row sums per
-    // 64-column chunk, C holds tile (b > a, a)'s column sums (null: skipped)
+    // T x T grid of tile slots; R holds tile (a, b <= a)'s row sums as eight
+    // 16-column partials (2 chunks x 4 column quarters) of 128 floats, C
+    // holds tile (b > a, a)'s column sums (128 floats) (null: skipped)
     float *rsR, *rsC;
     const int64_t *rsoff;  // per partition: first slot of its grid (sigma 0)
     int64_t rstot;         // slots per sigma (sum of T^2)
@@ -592,7 +594,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
         mbar_init(&sm.b_empty, 1);
         mbar_init(&sm.t_full, 1);
         mbar_init(&sm.t_empty, OZP_EPI_WARPS);
-        mbar_init(&sm.s_free, 1 + (kp.rsR ? 6 : 0));  // the store thread, and the row/column-sum warps
+        mbar_init(&sm.s_free, 1 + (kp.rsR ? 2 : 0));  // the store thread, and the column-sum warps
         fence_mbar_init();
     }
     exp_table_init(sm.exptab);
@@ -778,35 +780,33 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                     fence_proxy_async_smem();
                     epi_bar_p();
                     const bool diag = ti == tj;
-                    if (kp.rsR && et < 3 * KRR_TILE / 2) {
-                        // row sums of this chunk (threads 0..127, row et) and
+                    if (kp.rsR) {
+                        const int64_t g0 = (int64_t)is * kp.rstot + kp.rsoff[pj];
+                        // row sums: this thread's 16 columns of row r (registers)
+                        float rs = 0.f;
+#pragma unroll
+                        for (int sub = 0; sub < 2; ++sub)
+#pragma unroll
+                            for (int k = 0; k < OZP_SUB; ++k) rs += hv[sub][k];
+                        kp.rsR[((g0 + (int64_t)ti * P.T + tj) * 8 + c * 4 + quarter) * KRR_TILE + r] = rs;
                         // column sums of off-diagonal tiles (threads 128..191,
                         // column et - 128 of the chunk), from the staged K_hi
-                        const int64_t g0 = (int64_t)is * kp.rstot + kp.rsoff[pj];
-                        if (et < KRR_TILE) {
-                            const int rr = et;
-                            float rs = 0.f;
-#pragma unroll
-                            for (int u = 0; u < 16; ++u) {
-                                const float4 w = *reinterpret_cast<const float4 *>(
-                                    sm.stage[0][u >> 3] + (uint32_t)rr * 128u + ((uint32_t)((u & 7) ^ (rr & 7)) << 4));
-                                rs += (w.x + w.y) + (w.z + w.w);
-                            }
-                            kp.rsR[((g0 + (int64_t)ti * P.T + tj) * 2 + c) * KRR_TILE + rr] = rs;
-                        } else if (!diag) {
-                            const int cc = et - KRR_TILE;  // column of the chunk
-                            const uint32_t cu = (uint32_t)((cc & 31) >> 2), ce = (uint32_t)(cc & 3);
-                            const unsigned char *bx = sm.stage[0][cc >> 5];
-                            float cs[4] = {0.f, 0.f, 0.f, 0.f};  // four chains: rows r = 4 i + j
+                        if (et >= KRR_TILE && et < 3 * KRR_TILE / 2) {
+                            if (!diag) {
+                                const int cc = et - KRR_TILE;  // column of the chunk
+                                const uint32_t cu = (uint32_t)((cc & 31) >> 2), ce = (uint32_t)(cc & 3);
+                                const unsigned char *bx = sm.stage[0][cc >> 5];
+                                float cs[4] = {0.f, 0.f, 0.f, 0.f};  // four chains: rows r = 4 i + j
 #pragma unroll 8
-                            for (int rr = 0; rr < KRR_TILE; ++rr)
-                                cs[rr & 3] += *reinterpret_cast<const float *>(
-                                    bx + (uint32_t)rr * 128u + ((cu ^ (uint32_t)(rr & 7)) << 4) + 4u * ce);
-                            kp.rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c * OZ_N + cc] =
-                                (cs[0] + cs[1]) + (cs[2] + cs[3]);
+                                for (int rr = 0; rr < KRR_TILE; ++rr)
+                                    cs[rr & 3] += *reinterpret_cast<const float *>(
+                                        bx + (uint32_t)rr * 128u + ((cu ^ (uint32_t)(rr & 7)) << 4) + 4u * ce);
+                                kp.rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c * OZ_N + cc] =
+                                    (cs[0] + cs[1]) + (cs[2] + cs[3]);
+                            }
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&sm.s_free);
                         }
-                        __syncwarp();
-                        if (lane == 0) mbar_arrive(&sm.s_free);
                     }
                     const int y = (int)(((int64_t)is * kp.ktot + P.ktile0 + lt) * KRR_TILE);
                     if (et == 0) {

@@ -71,7 +71,7 @@ def fit_footprint_bytes(n: int, d: int, t: int) -> int:
     # kernel store hi/lo, factor, FP16 factor copy, lo parts of a three-pass
     # factor, diagonal inverses, refinement vectors, matvec slots, row sums
     work = (2 * tiles * tile_b + tiles * tile_b + tiles * TILE * TILE * 2 + tiles * tile_b + T * tile_b
-            + 7 * rows * 8 + T * T * TILE * 8 + T * T * 3 * TILE * 4)
+            + 7 * rows * 8 + T * T * TILE * 8 + T * T * 9 * TILE * 4)
     model = rows * d * 8 + 2 * rows * dp * 4 + rows * 8 + rows * 8 + rows * (10 * dz + 4)
     test = t * d * 8 + (t + 256) * (10 * dz + 12) + t * 8
     return int(work + model + test + (64 << 20))
