@@ -164,6 +164,31 @@ def test_fit_predict_select_parity(ctx, oracle_case, prec):
             assert omse[b] <= omse[obest] * (1 + REFINED_TOL)
         it, kap, res = K.krr_model_stats(ctx, model)
         assert np.all(it.numpy() >= 1)
+        # ||K + lambda m I||_inf / (lambda m): FP64 matrix-vector product on
+        # the FP64 path, FP32 row sums of the stored tiles otherwise
+        okap = np.array([c["infos"][j][g][0] for j in range(3) for g in range(G)])
+        np.testing.assert_allclose(kap.numpy(), okap, rtol=1e-12 if prec == "fp64" else 1e-5)
+    finally:
+        model.free()
+
+
+@pytest.mark.parametrize("lam", [1e5, 1e8])
+def test_large_lambda_m_leaves_the_fp16_factor(ctx, lam):
+    """A one-pass solve keeps its factor in FP16 only while 1 + lambda m <=
+    2^24 (|L_ij| <= sqrt(A_jj)); beyond that (lambda m = 3e7 and 3e10 here;
+    sqrt(3e10) would overflow FP16) it is factored in the three-pass class,
+    and the result still matches the oracle."""
+    X, y, Xt, yt, perm, offsets = _case()
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(offsets, torch.int64),
+                                           [2.0], [lam], "tf32", want_alpha=True)
+    try:
+        assert np.all(status.cpu().numpy() == K.KRR_OK)
+        ga = alpha.cpu().numpy()
+        for j in range(3):
+            rows = perm[offsets[j]:offsets[j + 1]]
+            oa, info, rc = oracle.fit(X[rows], y[rows], 2.0, lam)
+            assert rc == 0
+            assert rel(split_alpha(ga, offsets, 1)[j][0], oa) <= REFINED_TOL
     finally:
         model.free()
 
