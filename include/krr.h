@@ -48,7 +48,11 @@ typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1 } krr_part_mode;
  * FP32:   FP32 factor of the double-float (~44-bit) kernel with FP32-class
  *         trailing updates (three TF32 tensor-core passes on hi/lo splits);
  *         conjugate-gradient refinement with double-float residuals.
- * TF32:   as FP32 but the trailing updates take one TF32 pass.
+ * TF32:   as FP32 but with a TF32-class factor: the panel solves store the
+ *         L tiles in FP16 (the 11-bit significand of TF32) and the updates
+ *         take one FP16 tensor-core pass; the preconditioner reads the FP16
+ *         tiles.  A solve whose 1 + lambda m exceeds 2^24, or whose condition
+ *         estimate passes the escalation threshold, is factored as FP32.
  * BF16X3: as FP32 but the trailing updates take three BF16 passes on
  *         split-BF16 operands (hi = rn(x), lo = rn(x - hi)), ~16-bit
  *         products with FP32 accumulation.                                   */
@@ -56,11 +60,12 @@ typedef enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_TF32 = 2, KRR_PREC
 
 /* Model choice (Eq. 3 scores):
  * PER_MODEL: one MSE per (partition, sigma, lambda) model; best model.
- * ROUTED:    each test point scored by its routed partition (Alg. BKRR2 lines
- *            13-19, KKRR2 Sec. 4.2); one MSE per grid point; best grid point.
- * AVERAGE:   DC-KRR (Alg. DC-KRR line 15): predictions averaged over the
+ * ROUTED:    each test point scored by its routed partition (the scoring
+ *            step of Alg. BKRR2, KKRR2 Sec. 4.2); one MSE per grid point;
+ *            best grid point.
+ * AVERAGE:   DC-KRR (the averaging step of Alg. DC-KRR): predictions averaged over the
  *            partitions; one MSE per grid point.
- * ORACLE:    BKRR3 (Alg. BKRR3 lines 14-17): each test point takes the
+ * ORACLE:    BKRR3 (the per-point choice of Alg. BKRR3): each test point takes the
  *            partition whose prediction is closest to its label.             */
 typedef enum {
     KRR_SEL_PER_MODEL = 0,
@@ -84,8 +89,9 @@ const char *krr_last_error(const krr_ctx *ctx);
 /* Bytes currently allocated through the context. */
 size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
 
-/* Partition the training rows (Alg. DC-KRR lines 1-5 for RANDOM; Alg. 2
- * plain K-means plus the KKRR2 nearest-centre rule, Sec. 4.2, for KMEANS).
+/* Partition the training rows (the shuffle and even scatter of Alg. DC-KRR
+ * for RANDOM; Alg. 2 plain K-means plus the KKRR2 nearest-centre rule,
+ * Sec. 4.2, for KMEANS).
  *   X [n x d], Xt [t x d] (Xt may be NULL when t == 0).
  *   RANDOM: a seeded bijection (Feistel network over Philox4x32-10, cycle
  *     walking) shuffles the rows; the shuffled order is cut into p parts, the

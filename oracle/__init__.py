@@ -9,16 +9,16 @@ long-double refinement residuals).  This module compiles it with gcc on first
 use and exposes thin numpy wrappers plus the paper's pipelines composed from
 them:
 
-* ``partition_random``  -- Alg. DC-KRR lines 1-5 (shuffle, even scatter).
+* ``partition_random``  -- Alg. DC-KRR, its partitioning step (shuffle, even scatter).
 * ``kmeans`` / ``assign`` -- Alg. 2 (plain K-means) and the KKRR2 routing rule.
-* ``fit``               -- Alg. 1 lines 1-4 / Alg. BKRR2 lines 9-12 for one
+* ``fit``               -- Alg. 1 / the training step of Alg. BKRR2 for one
                            partition and one (sigma, lambda): Eq. 6 solved by
                            Cholesky (Sec. 5.4) plus refinement.
 * ``predict``           -- Eq. 7.
-* ``select``            -- Eq. 3 and the model choice of Alg. BKRR2 lines 13-22
+* ``select``            -- Eq. 3 and the model choice of Alg. BKRR2
                            (routed), best-of-p per-model MSE, the DC-KRR
-                           average (Alg. DC-KRR line 15) and the BKRR3
-                           per-point choice (Alg. BKRR3 lines 14-17).
+                           average (Alg. DC-KRR) and the BKRR3
+                           per-point choice (Alg. BKRR3).
 
 Grid index g = i_sigma * |Lambda| + i_lambda; model index = partition * G + g.
 """
@@ -106,7 +106,7 @@ def perm_index(i: int, n: int, seed: int) -> int:
 
 # ---------------------------------------------------------------- partition
 def partition_random(n: int, p: int, seed: int):
-    """Alg. DC-KRR lines 1-5: returns (perm, offsets, assign)."""
+    """The partitioning step of Alg. DC-KRR: returns (perm, offsets, assign)."""
     perm = np.zeros(n, np.int64)
     offsets = np.zeros(p + 1, np.int64)
     assign = np.zeros(n, np.int32)
@@ -278,12 +278,12 @@ def select(yhat, yt, mode: int, n_partitions: int = 1, G: int = 1):
 
     SEL_PER_MODEL: yhat[model, t]; one MSE per model, best = lowest MSE.
     SEL_ROUTED:    yhat[g, t] holds each test point's routed prediction; one
-                   MSE per grid point (Alg. BKRR2 line 19), best grid point.
+                   MSE per grid point (Alg. BKRR2), best grid point.
     SEL_AVERAGE:   yhat[model, t]; per grid point the average over partitions
-                   (Alg. DC-KRR line 15) is scored.
+                   (Alg. DC-KRR) is scored.
     SEL_ORACLE:    yhat[model, t]; per grid point each test point takes the
                    partition whose prediction is closest to its label
-                   (Alg. BKRR3 line 15, lowest partition on ties).
+                   (Alg. BKRR3, lowest partition on ties).
     Ties in the best index go to the lowest index (strict <)."""
     yhat = np.asarray(yhat, np.float64)
     yt = _c(yt, np.float64)

@@ -373,8 +373,8 @@ int orc_solve_spd(const double *A, int64_t m, const double *y, double *alpha,
     return 0;
 }
 
-/* Build K + lambda m I for one partition and solve it (Alg. 1 lines 1-4 /
- * Alg. BKRR2 lines 9-12 for one (lambda, sigma)). */
+/* Build K + lambda m I for one partition and solve it (Alg. 1 / the
+ * training step of Alg. BKRR2 for one (lambda, sigma)). */
 int orc_krr_fit(const double *Xp, const double *yp, int64_t m, int32_t d,
                 int32_t kind, double sigma, double lambda, double *alpha,
                 double *info)

@@ -1,6 +1,6 @@
 // kbuild.cu -- staging of the gathered partitions and the Gaussian kernel tile
-// builder (Table 1: K_ab = exp(-||x_a - x_b||^2 / (2 sigma^2)); Alg. BKRR2
-// lines 9-11; the lambda m shift of Eq. 6 in its partitioned form).
+// builder (Table 1: K_ab = exp(-||x_a - x_b||^2 / (2 sigma^2)); the kernel
+// step of Alg. BKRR2; the lambda m shift of Eq. 6 in its partitioned form).
 //
 // Layout in HBM.  Rows of partition j occupy padded rows [prow0, prow0 + 128 T)
 // (T = ceil(m / 128)); padding rows are zero.  Every matrix is stored as its

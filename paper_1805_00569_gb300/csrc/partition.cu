@@ -1,4 +1,4 @@
-// partition.cu -- partitioning kernels (Alg. DC-KRR lines 1-5; Alg. 2 plain
+// partition.cu -- partitioning kernels (Alg. DC-KRR's partitioning; Alg. 2 plain
 // K-means; KKRR2 nearest-centre routing, Sec. 4.2).
 //
 // * random_perm: seeded bijection of [0, n) -- a balanced Feistel network over

@@ -1,6 +1,6 @@
 // predict.cu -- fused prediction (Eq. 7: yhat = sum_i alpha_i Phi(x_i, xhat))
-// and model scoring/choice (Eq. 3; Alg. BKRR2 lines 13-22; Alg. DC-KRR line 15;
-// Alg. BKRR3 lines 14-17).
+// and model scoring/choice (Eq. 3; the model choice of Alg. BKRR2; the
+// averaging of Alg. DC-KRR; the per-point choice of Alg. BKRR3).
 //
 // Prediction never stores K(test, train).  A CTA owns (partition, 64 test
 // rows) and walks the partition's training rows in chunks of 128:

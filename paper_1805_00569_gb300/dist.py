@@ -2,7 +2,7 @@
 
 Partitions are independent problems (Alg. BKRR2: no communication during
 training), so ranks shard whole units of work and exchange only the model
-scores at the end -- the single reduction of Alg. BKRR2 line 19 / the argmin of
+scores at the end -- the single reduction of Alg. BKRR2's model choice / the argmin of
 the best model.  Each rank is one process on one GPU; the exchange is one
 all-gather of a few doubles through torch.distributed (NCCL on GPUs, gloo on
 CPU).

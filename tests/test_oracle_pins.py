@@ -30,7 +30,7 @@ def test_philox_known_answers():
 
 @pytest.mark.parametrize("n,p", [(1, 1), (2, 1), (17, 4), (1000, 7), (4096, 16), (65, 64)])
 def test_random_partition_is_even_bijection(n, p):
-    """Alg. DC-KRR lines 1-5: a shuffle (a bijection) cut into p even parts,
+    """The partitioning of Alg. DC-KRR: a shuffle (a bijection) cut into p even parts,
     the larger parts first."""
     perm, offsets, assign = oracle.partition_random(n, p, 99)
     assert np.array_equal(np.sort(perm), np.arange(n))
