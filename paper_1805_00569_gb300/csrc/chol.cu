@@ -34,6 +34,16 @@ namespace krr {
 
 enum { UPD_TRAIL = 0, UPD_COLUMN = 1, UPD_TRSM = 2 };
 
+// Programmatic dependent launch: the factorisation's launches form one long
+// dependent chain, so each kernel lets the next one be scheduled early
+// (launch_dependents) and waits for its predecessor's results (wait) only
+// after its own set-up; a kernel is scheduled early only once every CTA of
+// its predecessor is resident, and the wait is a hardware dependency.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ int find_solve(const int64_t *pre, int n, int64_t b) {
     int lo = 0, hi = n - 1;  // last s with pre[s] <= b
     while (lo < hi) {
@@ -126,6 +136,8 @@ __global__ void __launch_bounds__(512, 1) potrf_tile_kernel(T *__restrict__ A, T
     __shared__ __align__(16) T bsh[2][KRR_TILE + 16];
     __shared__ T psh[2][2];  // (pivot, 1 / sqrt(pivot))
     __shared__ int bad_sh;
+    pdl_launch_dependents();
+    pdl_wait();  // the column update of this diagonal tile has completed
     const int s = find_solve(pre, nsolve, blockIdx.x);
     const SolveDesc S = solves[s];
     const int64_t tile = S.ltile0 + (int64_t)k * (k + 1) / 2 + k;
@@ -446,6 +458,8 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
+    pdl_launch_dependents();
+    pdl_wait();  // the previous launch of the factorisation has completed
 
     if (threadIdx.x == 0) {  // TMA producer
         int64_t q = 0;       // chunk counter across this CTA's tasks
@@ -871,6 +885,23 @@ void build_chol_plan(const std::vector<int> &T, const std::vector<int> &cls, int
     }
 }
 
+// launch with programmatic stream serialisation (see pdl_wait)
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, size_t smem,
+                              cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename T>
 cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, T *A, T *Z,
                             __half *A16, float *Alo, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
@@ -886,7 +917,10 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
         const int64_t *p = d_pre + L.pre;
         ProfScope ps(prof, L.kind == 0 ? PROF_POTRF : (L.kind == 1 ? PROF_TRSM : PROF_UPDATE), st);
         if (L.kind == 0) {
-            KRR_LAUNCHED(), potrf_tile_kernel<T><<<grid, 512, po_sm, st>>>(A, Z, d_solves, p, nsolve, L.K0, flags);
+            KRR_LAUNCHED();
+            const cudaError_t e = launch_pdl(potrf_tile_kernel<T>, grid, 512, po_sm, st, A, Z, d_solves, p, nsolve,
+                                             L.K0, flags);
+            if (e != cudaSuccess) return e;
             continue;
         }
         const int mode = L.kind == 1 ? UPD_TRSM : (L.kind == 2 ? UPD_TRAIL : UPD_COLUMN);
@@ -910,26 +944,23 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 float *Af = reinterpret_cast<float *>(A);
                 const CUtensorMap &tmLo = tmapLo ? *tmapLo : *tmap;
+                auto go = [&](auto kern, unsigned threads, size_t smem, const CUtensorMap &opmap) {
+                    KRR_LAUNCHED();
+                    return launch_pdl(kern, pgrid, threads, smem, st, opmap, *tmapZ, tmLo, *tmap, Af, A16, Alo,
+                                      d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                };
+                cudaError_t err;
                 if (m == TC_TRSM)
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_TRSM><<<pgrid, TcCfg<TC_TRSM>::THREADS,
-                                                              TcCfg<TC_TRSM>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    err = go(tile_mma_kernel<TC_TRSM>, TcCfg<TC_TRSM>::THREADS, TcCfg<TC_TRSM>::SMEM, *tmap);
                 else if (m == TC_TF32X3)
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3><<<pgrid, TcCfg<TC_TF32X3>::THREADS,
-                                                                 TcCfg<TC_TF32X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    err = go(tile_mma_kernel<TC_TF32X3>, TcCfg<TC_TF32X3>::THREADS, TcCfg<TC_TF32X3>::SMEM, *tmap);
                 else if (m == TC_TF32X3P)
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_TF32X3P><<<pgrid, TcCfg<TC_TF32X3P>::THREADS,
-                                                                  TcCfg<TC_TF32X3P>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    err = go(tile_mma_kernel<TC_TF32X3P>, TcCfg<TC_TF32X3P>::THREADS, TcCfg<TC_TF32X3P>::SMEM, *tmap);
                 else if (m == TC_BF16X3)
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_BF16X3><<<pgrid, TcCfg<TC_BF16X3>::THREADS,
-                                                                 TcCfg<TC_BF16X3>::SMEM, st>>>(
-                        *tmap, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    err = go(tile_mma_kernel<TC_BF16X3>, TcCfg<TC_BF16X3>::THREADS, TcCfg<TC_BF16X3>::SMEM, *tmap);
                 else
-                    KRR_LAUNCHED(), tile_mma_kernel<TC_F16><<<pgrid, TcCfg<TC_F16>::THREADS,
-                                                             TcCfg<TC_F16>::SMEM, st>>>(
-                        *tmap16, *tmapZ, tmLo, *tmap, Af, A16, Alo, d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    err = go(tile_mma_kernel<TC_F16>, TcCfg<TC_F16>::THREADS, TcCfg<TC_F16>::SMEM, *tmap16);
+                if (err != cudaSuccess) return err;
                 continue;
             }
         }
