@@ -402,14 +402,15 @@ def roofline(res, steps, peaks):
     elif dom in ("kbuild", "predict"):
         # double-float work in FP32 operations, counted from the kernels' design:
         # distance assembly from the five exact slice levels 22 per pair; per sigma
-        # a double-float product 7 and exponential 44; per (sigma, lambda) one
-        # double-float multiply-accumulate 12 (predict) or two stores (kbuild)
+        # a double-float product 7 and exponential 44 (41 unnormalised in the
+        # prediction); per (sigma, lambda) one double-float multiply-accumulate
+        # 12 (predict) or two stores (kbuild)
         ns = len(w["sigmas"])
         if dom == "kbuild":
             per_pair = 22 + ns * (7 + 44 + 4) + G * 2
             pairs = steps * sum(mm * mm / 2.0 for mm in sizes)
         else:
-            per_pair = 22 + ns * (7 + 44) + G * 12
+            per_pair = 22 + ns * (7 + 41) + G * 12
             pairs = steps * sum(t * mm for mm in sizes)
         out.update(bound="alu", achieved=pairs * per_pair / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
                    peak_note="FP32 issue peak = 152 SMs x 128 lanes x sampled SM clock (one FP32 op per lane per "
