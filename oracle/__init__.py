@@ -11,6 +11,8 @@ them:
 
 * ``partition_random``  -- Alg. DC-KRR, its partitioning step (shuffle, even scatter).
 * ``kmeans`` / ``assign`` -- Alg. 2 (plain K-means) and the KKRR2 routing rule.
+* ``kbalance_assign`` / ``partition_kbalance`` -- Alg. K-balance Clustering
+                           (the BKRR partitioner).
 * ``fit``               -- Alg. 1 / the training step of Alg. BKRR2 for one
                            partition and one (sigma, lambda): Eq. 6 solved by
                            Cholesky (Sec. 5.4) plus refinement.
@@ -69,6 +71,7 @@ def _load():
             lib.orc_kmeans.argtypes = [P, i64, i32, i32, P, i32, P, P, P]
             lib.orc_kmeans.restype = i32
             lib.orc_gather_stable.argtypes = [P, i64, i32, P, P]
+            lib.orc_kbalance_assign.argtypes = [P, i64, i32, P, i32, i64, P, P]
             lib.orc_kernel_matrix.argtypes = [P, i64, P, i64, i32, i32, f64, P]
             lib.orc_solve_spd.argtypes = [P, i64, P, P, f64, P]
             lib.orc_solve_spd.restype = ctypes.c_int
@@ -159,6 +162,35 @@ def partition_kmeans(X, Xt, k: int, init_idx, iters: int):
     perm, offsets = gather_stable(c, k)
     route = assign(Xt, C) if Xt is not None else None
     return perm, offsets, c, route, C, delta
+
+
+def kbalance_assign(X, C, cap: int):
+    """Alg. K-balance Clustering, per-sample loop: every sample in index
+    order takes its nearest centre among those holding fewer than `cap`
+    samples.  Returns (assignment, counts)."""
+    X = _c(X, np.float64)
+    C = _c(C, np.float64)
+    out = np.zeros(X.shape[0], np.int32)
+    cs = np.zeros(C.shape[0], np.int64)
+    _load().orc_kbalance_assign(_p(X), X.shape[0], X.shape[1], _p(C), C.shape[0], int(cap), _p(out), _p(cs))
+    return out, cs
+
+
+def partition_kbalance(X, Xt, p: int, init_idx, iters: int):
+    """BKRR / BKRR2 partition (Alg. K-balance Clustering): K-means centres
+    (Alg. 2, as in partition_kmeans), the balanced per-sample assignment with
+    cap = ceil(n / p), the centres recomputed as the means of the balanced
+    parts (the listing's final averaging; empty parts keep their centre),
+    stable grouping, and nearest-centre routing of the test rows with the
+    recomputed centres."""
+    X = _c(X, np.float64)
+    C, _, _ = kmeans(X, p, init_idx, iters)
+    cap = -(-X.shape[0] // p)
+    c, cs = kbalance_assign(X, C, cap)
+    C2 = update_centres(X, c, C)
+    perm, offsets = gather_stable(c, p)
+    route = assign(Xt, C2) if Xt is not None else None
+    return perm, offsets, c, route, C2, cs
 
 
 # ---------------------------------------------------------------- kernels

@@ -237,6 +237,35 @@ int32_t orc_kmeans(const double *X, int64_t n, int32_t d, int32_t k,
     return rounds;
 }
 
+/* Alg. K-balance Clustering, the per-sample loop: samples in index order,
+ * each takes the nearest centre that is not yet full (strict <, so the lowest
+ * index wins ties), with the counts starting at zero and the cap
+ * ceil(n / p) (the reading of balanced = n / p; the total capacity covers n).
+ * Distances are the squared Euclidean distances of the assignment step
+ * (sqdist).  A sample whose open centres are all at infinite distance takes
+ * the lowest open centre (the reading of the listing's minind = 0).  CS
+ * receives the final counts. */
+void orc_kbalance_assign(const double *X, int64_t n, int32_t d, const double *CT,
+                         int32_t p, int64_t cap, int32_t *c, int64_t *CS)
+{
+    for (int32_t j = 0; j < p; ++j) CS[j] = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double best = INFINITY;
+        int32_t arg = -1;
+        for (int32_t j = 0; j < p; ++j) {
+            if (CS[j] >= cap) continue;
+            if (arg < 0) arg = j;
+            double dist = sqdist(X + i * d, CT + (int64_t)j * d, d);
+            if (dist < best) {
+                best = dist;
+                arg = j;
+            }
+        }
+        c[i] = arg;
+        CS[arg] += 1;
+    }
+}
+
 /* Group rows by partition, keeping ascending row index inside a partition
  * (the scatter of the KKRR pipeline).  perm/offsets as in the random case. */
 void orc_gather_stable(const int32_t *assign, int64_t n, int32_t p,

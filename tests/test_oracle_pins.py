@@ -295,3 +295,79 @@ def test_bkrr3_lower_bound():
     m2, _ = oracle.select(yr, yt, oracle.SEL_ROUTED)
     mp, _ = oracle.select(yall, yt, oracle.SEL_PER_MODEL)
     assert m3[0] <= m2[0] and m3[0] <= mp.min()
+
+
+# ---------------------------------------------------------------- K-balance
+def _kbalance_listing(X, C, cap):
+    """The K-balance listing transcribed literally (Euclidean distances with
+    the square root, mindis / minind, the count test against the cap), for
+    brute-force comparison on small inputs."""
+    n, p = X.shape[0], C.shape[0]
+    cs = [0] * p
+    out = []
+    for i in range(n):
+        mindis, minind = math.inf, None
+        for j in range(p):
+            dist = math.sqrt(sum((float(a) - float(b)) ** 2 for a, b in zip(X[i], C[j])))
+            if dist < mindis and cs[j] < cap:
+                mindis, minind = dist, j
+        cs[minind] += 1
+        out.append(minind)
+    return np.array(out, np.int32), np.array(cs, np.int64)
+
+
+@pytest.mark.parametrize("n,p,d,seed", [(40, 3, 2, 1), (97, 7, 5, 2), (64, 8, 3, 3), (33, 1, 4, 4)])
+def test_kbalance_matches_the_listing_brute_force(n, p, d, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, d))
+    C = rng.standard_normal((p, d)) * 0.5
+    cap = -(-n // p)
+    c, cs = oracle.kbalance_assign(X, C, cap)
+    bc, bcs = _kbalance_listing(X, C, cap)
+    assert np.array_equal(c, bc) and np.array_equal(cs, bcs)
+    assert cs.sum() == n and cs.max() <= cap
+    if n % p == 0:
+        assert np.all(cs == n // p)  # p caps of n / p hold exactly n samples
+
+
+def test_kbalance_greedy_invariant():
+    """Every sample sits at its nearest centre among those still open when it
+    was placed: any strictly nearer centre had already reached the cap."""
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((500, 4))
+    C = rng.standard_normal((6, 4))
+    cap = -(-500 // 6)
+    c, _ = oracle.kbalance_assign(X, C, cap)
+    D = ((X[:, None, :] - C[None, :, :]) ** 2).sum(-1)
+    filled = np.zeros(6, np.int64)
+    for i in range(500):
+        for j in range(6):
+            if D[i, j] < D[i, c[i]]:
+                assert filled[j] == cap, (i, j)
+        filled[c[i]] += 1
+
+
+def test_kbalance_equals_nearest_centre_when_nothing_fills():
+    """Well separated clusters of at most cap samples: no centre ever fills,
+    so the balanced loop is the plain assignment step (Alg. 2)."""
+    rng = np.random.default_rng(5)
+    centres = np.array([[0.0, 0.0], [50.0, 0.0], [0.0, 50.0], [50.0, 50.0]])
+    X = np.concatenate([c + rng.standard_normal((25, 2)) for c in centres])[rng.permutation(100)]
+    c, cs = oracle.kbalance_assign(X, centres, 25)
+    assert np.array_equal(c, oracle.assign(X, centres))
+    assert np.all(cs == 25)
+
+
+def test_partition_kbalance_parts_and_routes():
+    rng = np.random.default_rng(9)
+    X = np.concatenate([rng.standard_normal((70, 3)) + 6 * k for k in range(3)])
+    Xt = rng.standard_normal((20, 3)) * 6
+    perm, offsets, c, route, C2, cs = oracle.partition_kbalance(X, Xt, 4, np.array([0, 70, 140, 5]), 5)
+    sizes = np.diff(offsets)
+    assert sizes.sum() == 210 and sizes.max() <= 53 and np.array_equal(sizes, cs)
+    for j in range(4):
+        rows = perm[offsets[j]:offsets[j + 1]]
+        assert np.all(c[rows] == j) and np.all(np.diff(rows) > 0)
+        if len(rows):
+            np.testing.assert_allclose(C2[j], X[rows].mean(0), rtol=1e-12, atol=1e-12)
+    assert np.array_equal(route, oracle.assign(Xt, C2))
