@@ -49,8 +49,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-path", action="store_true")
     ap.add_argument("--profile", action="store_true", help="print per-kernel-class times to stderr")
-    ap.add_argument("--workload", default="bkrr2", choices=["bkrr2", "kkrr2", "sweep", "dkrr", "serve"],
+    ap.add_argument("--workload", default="bkrr2", choices=["bkrr2", "kkrr2", "bkrr2kb", "sweep", "dkrr", "serve"],
                     help="bkrr2: the headline configuration; kkrr2: K-means partitions (uneven, routed); "
+                         "bkrr2kb: the bkrr2 data with K-balance partitions (routed); "
                          "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows; serve: the request "
                          "stream (Poisson 200/s, n log-uniform in [512, 16384]) through the serving loop")
     ap.add_argument("--requests", type=int, default=1500, help="serve: requests replayed from the stream")
@@ -195,6 +196,10 @@ def make_workload(args, rank):
         if args.p:
             kw["p"] = args.p
         return synth.sweep(seed=3 + rank, **kw)
+    if args.workload == "bkrr2kb":
+        if args.p:
+            kw["p"] = args.p
+        return synth.bkrr2_kbalance(seed=5 + rank, **kw)
     return synth.dkrr(seed=0 + rank, **kw)
 
 
@@ -218,7 +223,8 @@ def run_ours(args, rank, world, local_rank):
     n, d = w["X"].shape
     t = w["Xt"].shape[0]
     p = w["p"]
-    kmeans = args.workload == "kkrr2"
+    kmeans = args.workload in ("kkrr2", "bkrr2kb")  # routed prediction and selection
+    pmode = K.KRR_PART_KBALANCE if args.workload == "bkrr2kb" else K.KRR_PART_KMEANS
     S, L = w["sigmas"], w["lambdas"]
     G = len(S) * len(L)
     nsolve = p * G
@@ -238,8 +244,8 @@ def run_ours(args, rank, world, local_rank):
     last_offsets = [None]
 
     def step(Xd, yd, Xtd, ytd, prec):
-        if kmeans:  # KKRR2: K-means partitions, routed prediction, routed selection
-            _, route, perm, offsets, _ = K.krr_partition(ctx, Xd, Xtd, K.KRR_PART_KMEANS, p, iters=w["iters"],
+        if kmeans:  # KKRR2 / K-balance BKRR2: clustered partitions, routed prediction and selection
+            _, route, perm, offsets, _ = K.krr_partition(ctx, Xd, Xtd, pmode, p, iters=w["iters"],
                                                          init_idx=init_idx)
             model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
             yh = K.krr_predict(ctx, model, Xtd, route=route, out=yhat_buf)
@@ -259,7 +265,7 @@ def run_ours(args, rank, world, local_rank):
     bad = int((status != K.KRR_OK).sum().item())
     if args.profile:
         if kmeans:
-            _, _, perm, offsets, _ = K.krr_partition(ctx, X, Xt, K.KRR_PART_KMEANS, p, iters=w["iters"],
+            _, _, perm, offsets, _ = K.krr_partition(ctx, X, Xt, pmode, p, iters=w["iters"],
                                                      init_idx=init_idx)
         else:
             _, _, perm, offsets, _ = K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])

@@ -41,7 +41,7 @@ typedef enum {
     KRR_ERR_UNSUPPORTED = 8   /* a valid request the library does not implement  */
 } krr_status;
 
-typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1 } krr_part_mode;
+typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1, KRR_PART_KBALANCE = 2 } krr_part_mode;
 
 /* Arithmetic of the kernel build, the Cholesky factor and its refinement.
  * FP64:   FP64 kernel, FP64 Cholesky, FP64 refinement (the plain path).
@@ -91,7 +91,8 @@ size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
 
 /* Partition the training rows (the shuffle and even scatter of Alg. DC-KRR
  * for RANDOM; Alg. 2 plain K-means plus the KKRR2 nearest-centre rule,
- * Sec. 4.2, for KMEANS).
+ * Sec. 4.2, for KMEANS; Alg. K-balance Clustering, the BKRR partitioner, for
+ * KBALANCE).
  *   X [n x d], Xt [t x d] (Xt may be NULL when t == 0).
  *   RANDOM: a seeded bijection (Feistel network over Philox4x32-10, cycle
  *     walking) shuffles the rows; the shuffled order is cut into p parts, the
@@ -106,6 +107,14 @@ size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
  *     assignment with the final centres defines the partitions and routes
  *     the test rows.  Assignments are bit-exact with that definition (an FP64
  *     recheck decides near ties).
+ *   KBALANCE: the K-means centres as above, then the balanced assignment of
+ *     Alg. K-balance Clustering: rows in index order each take the nearest
+ *     centre (squared FP64 distance in feature order, strict <, lowest index)
+ *     among those holding fewer than ceil(n / p) rows; then every centre
+ *     becomes the mean of its part (canonical order; an empty part keeps its
+ *     centre), and the test rows are routed to the nearest such centre.
+ *     Assignments are bit-exact with that sequential definition (replayed in
+ *     at most p rounds).  Needs d <= 400; workspace n p 8 bytes.
  * Outputs: assign[n] (int32 partition of each row), perm[n] (int64 rows grouped
  * by partition; ascending row order inside a partition for KMEANS),
  * offsets[p+1] (int64), route[t] (int32, nullable), centers[p x d] (nullable;

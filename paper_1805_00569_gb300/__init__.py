@@ -19,7 +19,7 @@ from . import build as _build
 
 KRR_OK, KRR_ERR_ARG, KRR_ERR_OOM, KRR_ERR_BUDGET, KRR_ERR_CUDA = 0, 1, 2, 3, 4
 KRR_ERR_NOT_SPD, KRR_ERR_NO_CONVERGE, KRR_ERR_TIMEOUT, KRR_ERR_UNSUPPORTED = 5, 6, 7, 8
-KRR_PART_RANDOM, KRR_PART_KMEANS = 0, 1
+KRR_PART_RANDOM, KRR_PART_KMEANS, KRR_PART_KBALANCE = 0, 1, 2
 KRR_PREC_FP64, KRR_PREC_FP32, KRR_PREC_TF32, KRR_PREC_BF16X3 = 0, 1, 2, 3
 KRR_SEL_PER_MODEL, KRR_SEL_ROUTED, KRR_SEL_AVERAGE, KRR_SEL_ORACLE = 0, 1, 2, 3
 PREC_NAMES = {"fp64": KRR_PREC_FP64, "fp32": KRR_PREC_FP32, "tf32": KRR_PREC_TF32, "bf16x3": KRR_PREC_BF16X3}
@@ -192,7 +192,8 @@ def krr_partition(ctx: Context, X: torch.Tensor, Xt: torch.Tensor | None, mode: 
     route = torch.empty(t, dtype=torch.int32, device=dev) if t > 0 else None
     perm = torch.empty(n, dtype=torch.int64, device=dev)
     offsets = torch.empty(p + 1, dtype=torch.int64, device=dev)
-    centers = torch.empty((p, d), dtype=torch.float64, device=dev) if mode == KRR_PART_KMEANS else None
+    centers = (torch.empty((p, d), dtype=torch.float64, device=dev)
+               if mode in (KRR_PART_KMEANS, KRR_PART_KBALANCE) else None)
     if init_idx is not None:
         init_idx = _dev(init_idx, torch.int64, "init_idx")
     rc = ctx.lib.krr_partition(ctx.handle, _ptr(X), n, d, _ptr(Xt), t, mode, p, iters,

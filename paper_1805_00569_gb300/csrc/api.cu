@@ -28,7 +28,7 @@ std::atomic<long long> g_launch_count{0};
 krr_status run_partition_random(Ctx *, int64_t, int32_t, uint64_t, int32_t *, int64_t *, int64_t *, int32_t *,
                                 int64_t);
 krr_status run_partition_kmeans(Ctx *, const double *, int64_t, int32_t, const double *, int64_t, int32_t, int32_t,
-                                const int64_t *, int32_t *, int32_t *, int64_t *, int64_t *, double *);
+                                const int64_t *, int32_t *, int32_t *, int64_t *, int64_t *, double *, bool);
 krr_status run_gather(Ctx *, const int32_t *, int64_t, int32_t, int64_t *, int64_t *);
 void launch_stage(cudaStream_t, const double *, const double *, const int64_t *, const Model &, double *);
 void launch_kbuild_df(cudaStream_t, const Model &, int64_t, float *, float *, float *);
@@ -309,14 +309,15 @@ krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, co
     if (n < 0 || d <= 0 || p <= 0 || t < 0 || !assign || !perm || !offsets || (n > 0 && !X) ||
         (t > 0 && route && !Xt))
         return fail(c, KRR_ERR_ARG, "krr_partition: invalid argument");
-    if (p > n && n > 0 && mode == KRR_PART_KMEANS) return fail(c, KRR_ERR_ARG, "krr_partition: p > n");
+    if (p > n && n > 0 && mode != KRR_PART_RANDOM) return fail(c, KRR_ERR_ARG, "krr_partition: p > n");
     cudaSetDevice(c->device);
     ProfScope ps(&c->prof, PROF_PARTITION, c->stream);
     if (mode == KRR_PART_RANDOM) return run_partition_random(c, n, p, seed, assign, perm, offsets, route, t);
-    if (mode == KRR_PART_KMEANS) {
+    if (mode == KRR_PART_KMEANS || mode == KRR_PART_KBALANCE) {
         if (!init_idx || !centers || iters < 0)
-            return fail(c, KRR_ERR_ARG, "krr_partition: K-means needs init_idx and centers");
-        return run_partition_kmeans(c, X, n, d, Xt, t, p, iters, init_idx, assign, route, perm, offsets, centers);
+            return fail(c, KRR_ERR_ARG, "krr_partition: K-means and K-balance need init_idx and centers");
+        return run_partition_kmeans(c, X, n, d, Xt, t, p, iters, init_idx, assign, route, perm, offsets, centers,
+                                    mode == KRR_PART_KBALANCE);
     }
     return fail(c, KRR_ERR_ARG, "krr_partition: unknown mode");
 }

@@ -17,6 +17,8 @@
 //   division by the member count; an empty cluster keeps its centre.
 // * gather: stable grouping of rows by partition (ascending row inside a
 //   partition), via per-block counts, a scan and an ordered scatter.
+#include <vector>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -451,6 +453,144 @@ __global__ void gather_scatter_kernel(const int32_t *__restrict__ a, int64_t n, 
 }
 
 // ------------------------------------------------------------ host drivers
+// ------------------------------------------------------------ K-balance
+// Alg. K-balance Clustering replayed exactly in rounds.  D holds the squared
+// FP64 distance of every (row, centre) pair in the definition's order
+// (ascending feature, unfused operations, as the assignment step's FP64
+// recheck).  A round: every unplaced row takes its nearest open centre
+// (strict <, lowest index); the first row whose centre already holds its
+// remaining capacity of earlier rows of the round is the overflow row; the
+// rows before it are placed exactly as the sequential loop places them (no
+// centre overflows before it), every centre that is now full closes (the
+// overflowing one among them), and the next round starts at the overflow
+// row.  Every round but the last closes a centre, so there are at most p
+// rounds; after the first, only the rows whose choice has closed look again.
+constexpr int KB_ROWS = 64;     // rows per CTA of the distance kernel
+constexpr int KB_BLK = 1024;    // rows per counting block
+
+__global__ void __launch_bounds__(KB_ROWS)
+kb_dist_kernel(const double *__restrict__ X, int64_t n, int32_t d, const double *__restrict__ C, int32_t p,
+               double *__restrict__ D) {
+    extern __shared__ double kb_sx[];  // [d][KB_ROWS]
+    const int64_t i0 = (int64_t)blockIdx.x * KB_ROWS;
+    const int nrow = (int)((n - i0) < (int64_t)KB_ROWS ? (n - i0) : (int64_t)KB_ROWS);
+    for (int e = threadIdx.x; e < nrow * d; e += KB_ROWS) {
+        const int r = e / d, f = e % d;
+        kb_sx[f * KB_ROWS + r] = X[(i0 + r) * d + f];
+    }
+    __syncthreads();
+    const int r = threadIdx.x;
+    if (r >= nrow) return;
+    for (int j = 0; j < p; ++j) {
+        const double *c = C + (size_t)j * d;
+        double s = 0.0;
+        for (int f = 0; f < d; ++f) {
+            const double t = __dsub_rn(kb_sx[f * KB_ROWS + r], __ldg(c + f));
+            s = __dadd_rn(s, __dmul_rn(t, t));
+        }
+        D[(i0 + r) * p + j] = s;
+    }
+}
+
+// choice[i] for rows [start, n): nearest open centre; after the first round
+// only the rows whose choice has closed look again
+__global__ void kb_choose_kernel(const double *__restrict__ D, int64_t n, int32_t p, int64_t start,
+                                 const int32_t *__restrict__ open, int first, int32_t *__restrict__ choice) {
+    extern __shared__ int32_t kb_open[];  // [p]
+    for (int j = threadIdx.x; j < p; j += blockDim.x) kb_open[j] = open[j];
+    __syncthreads();
+    const int64_t i = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    if (!first && kb_open[choice[i]]) return;  // its nearest open centre is unchanged
+    int arg = -1;
+    double best = INFINITY;
+    for (int j = 0; j < p; ++j) {
+        if (!kb_open[j]) continue;
+        if (arg < 0) arg = j;
+        const double v = D[i * p + j];
+        if (v < best) {
+            best = v;
+            arg = j;
+        }
+    }
+    choice[i] = arg < 0 ? 0 : arg;  // some centre is always open while rows remain (p cap >= n)
+}
+
+// per block of KB_BLK rows of [start, n): how many rows chose each centre
+__global__ void kb_count_kernel(const int32_t *__restrict__ choice, int64_t n, int32_t p, int64_t start,
+                                int32_t *__restrict__ bcnt) {
+    extern __shared__ int32_t kb_c[];  // [p]
+    for (int j = threadIdx.x; j < p; j += blockDim.x) kb_c[j] = 0;
+    __syncthreads();
+    const int64_t i0 = start + (int64_t)blockIdx.x * KB_BLK;
+    const int64_t hi = i0 + KB_BLK < n ? i0 + KB_BLK : n;
+    for (int64_t i = i0 + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&kb_c[choice[i]], 1);
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x) bcnt[(int64_t)blockIdx.x * p + j] = kb_c[j];
+}
+
+// one warp per centre j: the row at which j's count in the round would pass
+// its remaining capacity cap - cs[j] (n when it does not)
+__global__ void kb_find_kernel(const int32_t *__restrict__ bcnt, int64_t nblk, int32_t p,
+                               const unsigned long long *__restrict__ cs, int64_t cap,
+                               const int32_t *__restrict__ choice, int64_t n, int64_t start,
+                               long long *__restrict__ ovf) {
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= p) return;
+    const int64_t rem = cap - (int64_t)cs[j];
+    int64_t cum = 0;
+    long long res = n;
+    for (int64_t b = 0; b < nblk; ++b) {
+        const int c = bcnt[b * p + j];
+        if (cum + c > rem) {
+            int64_t need = rem - cum + 1;  // the need-th row of block b that chose j
+            const int64_t i0 = start + b * KB_BLK, hi = i0 + KB_BLK < n ? i0 + KB_BLK : n;
+            for (int64_t base = i0; base < hi; base += 32) {
+                const int64_t i = base + lane;
+                unsigned mask = __ballot_sync(0xffffffffu, i < hi && choice[i] == j);
+                const int cnt = __popc(mask);
+                if (need <= cnt) {
+                    for (int64_t q = 1; q < need; ++q) mask &= mask - 1;
+                    res = base + __ffs(mask) - 1;
+                    break;
+                }
+                need -= cnt;
+            }
+            break;
+        }
+        cum += c;
+    }
+    if (lane == 0) ovf[j] = res;
+}
+
+// place rows [start, stop): assign = choice, and add them to the counts
+__global__ void kb_accept_kernel(const int32_t *__restrict__ choice, int64_t start, int64_t stop, int32_t p,
+                                 int32_t *__restrict__ assign, unsigned long long *__restrict__ cs) {
+    extern __shared__ int32_t kb_a[];  // [p]
+    for (int j = threadIdx.x; j < p; j += blockDim.x) kb_a[j] = 0;
+    __syncthreads();
+    for (int64_t i = start + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < stop;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = choice[i];
+        assign[i] = c;
+        atomicAdd(&kb_a[c], 1);
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < p; j += blockDim.x)
+        if (kb_a[j]) atomicAdd(&cs[j], (unsigned long long)kb_a[j]);
+}
+
+__global__ void kb_fill_kernel(int32_t *__restrict__ a, int32_t p, int32_t v) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x) a[j] = v;
+}
+
+// close every centre that holds cap rows
+__global__ void kb_close_kernel(int32_t *__restrict__ open, const unsigned long long *__restrict__ cs, int32_t p,
+                                int64_t cap) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < p; j += gridDim.x * blockDim.x)
+        if ((int64_t)cs[j] >= cap) open[j] = 0;
+}
+
 static inline unsigned grid_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
 
 krr_status run_gather(Ctx *ctx, const int32_t *assign, int64_t n, int32_t p, int64_t *perm, int64_t *offsets) {
@@ -561,9 +701,104 @@ krr_status run_update(Ctx *ctx, const double *X, int64_t n, int32_t d, const int
     return KRR_OK;
 }
 
+// Alg. K-balance Clustering's balanced assignment of the n rows to the p
+// centres C (cap = ceil(n / p)); see the kernels above.
+krr_status run_kbalance(Ctx *ctx, const double *X, int64_t n, int32_t d, const double *C, int32_t p,
+                        int32_t *assign) {
+    if (n == 0) return KRR_OK;
+    cudaStream_t st = ctx->stream;
+    const int64_t cap = (n + p - 1) / p;
+    const int64_t nblk_max = (n + KB_BLK - 1) / KB_BLK;
+    const size_t b_d = (size_t)n * p * sizeof(double), b_ch = (size_t)n * sizeof(int32_t),
+                 b_open = (size_t)p * sizeof(int32_t), b_cs = (size_t)p * sizeof(unsigned long long),
+                 b_bc = (size_t)nblk_max * p * sizeof(int32_t), b_ovf = (size_t)p * sizeof(long long);
+    const size_t sm_d = (size_t)d * KB_ROWS * sizeof(double);
+    if (sm_d > 200 * 1024) {
+        ctx->last_error = "kbalance: more than 400 features";
+        return KRR_ERR_UNSUPPORTED;
+    }
+    double *D = nullptr;
+    int32_t *choice = nullptr, *open = nullptr, *bcnt = nullptr;
+    unsigned long long *cs = nullptr;
+    long long *ovf = nullptr;
+    std::vector<long long> hovf(p);
+    krr_status rc = KRR_OK;
+    int64_t start = 0;
+#define KB_ALLOC(ptr, bytes)                                                  \
+    do {                                                                      \
+        cudaError_t _e = ctx_malloc(ctx, (void **)&(ptr), (bytes));           \
+        if (_e != cudaSuccess) {                                              \
+            ctx->last_error = std::string("kbalance workspace: ") + cudaGetErrorString(_e); \
+            rc = (_e == cudaErrorMemoryAllocation) ? KRR_ERR_OOM : KRR_ERR_BUDGET; \
+            goto done;                                                        \
+        }                                                                     \
+    } while (0)
+    KB_ALLOC(D, b_d);
+    KB_ALLOC(choice, b_ch);
+    KB_ALLOC(open, b_open);
+    KB_ALLOC(cs, b_cs);
+    KB_ALLOC(bcnt, b_bc);
+    KB_ALLOC(ovf, b_ovf);
+    if (sm_d > 48 * 1024 && allow_max_dyn_smem(kb_dist_kernel) != cudaSuccess) {
+        rc = KRR_ERR_CUDA;
+        goto done;
+    }
+    KRR_LAUNCHED(), kb_dist_kernel<<<grid_for(n, KB_ROWS), KB_ROWS, sm_d, st>>>(X, n, d, C, p, D);
+    KRR_LAUNCHED(), kb_fill_kernel<<<grid_for(p, 256), 256, 0, st>>>(open, p, 1);
+    cudaMemsetAsync(cs, 0, b_cs, st);
+    for (int round = 0; round <= p && start < n; ++round) {
+        KRR_LAUNCHED(), kb_choose_kernel<<<grid_for(n - start, 256), 256, b_open, st>>>(D, n, p, start, open,
+                                                                                       round == 0, choice);
+        const int64_t nblk = (n - start + KB_BLK - 1) / KB_BLK;
+        KRR_LAUNCHED(), kb_count_kernel<<<(unsigned)nblk, 256, b_open, st>>>(choice, n, p, start, bcnt);
+        KRR_LAUNCHED(), kb_find_kernel<<<grid_for((int64_t)p * 32, 256), 256, 0, st>>>(bcnt, nblk, p, cs, cap, choice,
+                                                                                      n, start, ovf);
+        cudaError_t e = cudaMemcpyAsync(hovf.data(), ovf, b_ovf, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            ctx->last_error = std::string("kbalance: ") + cudaGetErrorString(e);
+            rc = KRR_ERR_CUDA;
+            goto done;
+        }
+        int64_t stop = n;
+        for (int32_t j = 0; j < p; ++j) stop = std::min<int64_t>(stop, hovf[j]);
+        if (stop <= start) {  // cannot happen: every open centre has room for at least one row
+            ctx->last_error = "kbalance: no progress in a round";
+            rc = KRR_ERR_CUDA;
+            goto done;
+        }
+        KRR_LAUNCHED(), kb_accept_kernel<<<std::min<unsigned>(grid_for(stop - start, 256), 1024u), 256, b_open, st>>>(
+            choice, start, stop, p, assign, cs);
+        start = stop;
+        KRR_LAUNCHED(), kb_close_kernel<<<grid_for(p, 256), 256, 0, st>>>(open, cs, p, cap);
+    }
+    if (start < n) {
+        ctx->last_error = "kbalance: rows left after p rounds";
+        rc = KRR_ERR_CUDA;
+        goto done;
+    }
+    {
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // workspace is freed below
+        if (e != cudaSuccess) {
+            ctx->last_error = std::string("kbalance: ") + cudaGetErrorString(e);
+            rc = KRR_ERR_CUDA;
+        }
+    }
+done:
+#undef KB_ALLOC
+    if (ovf) ctx_free(ctx, ovf, b_ovf);
+    if (bcnt) ctx_free(ctx, bcnt, b_bc);
+    if (cs) ctx_free(ctx, cs, b_cs);
+    if (open) ctx_free(ctx, open, b_open);
+    if (choice) ctx_free(ctx, choice, b_ch);
+    if (D) ctx_free(ctx, D, b_d);
+    return rc;
+}
+
 krr_status run_partition_kmeans(Ctx *ctx, const double *X, int64_t n, int32_t d, const double *Xt, int64_t t,
                                 int32_t k, int32_t iters, const int64_t *init_idx, int32_t *assign, int32_t *route,
-                                int64_t *perm, int64_t *offsets, double *C) {
+                                int64_t *perm, int64_t *offsets, double *C, bool kbalance) {
     cudaStream_t st = ctx->stream;
     int64_t nblk = (n + CANON - 1) / CANON;
     float *C32 = nullptr;
@@ -609,9 +844,19 @@ krr_status run_partition_kmeans(Ctx *ctx, const double *X, int64_t n, int32_t d,
             if (rc != KRR_OK) goto done;
             cudaMemcpyAsync(prev, assign, (size_t)n * sizeof(int32_t), cudaMemcpyDeviceToDevice, st);
         }
-        KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
-        rc = run_assign(ctx, X32, X, n, d, C, C32, k, nullptr, assign, nullptr);
-        if (rc != KRR_OK) goto done;
+        if (kbalance) {
+            // Alg. K-balance Clustering: the balanced assignment to the K-means
+            // centres, then the centres as the means of the balanced parts
+            rc = run_kbalance(ctx, X, n, d, C, k, assign);
+            if (rc != KRR_OK) goto done;
+            rc = run_update(ctx, X, n, d, assign, k, C, partial, counts);
+            if (rc != KRR_OK) goto done;
+            KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
+        } else {
+            KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
+            rc = run_assign(ctx, X32, X, n, d, C, C32, k, nullptr, assign, nullptr);
+            if (rc != KRR_OK) goto done;
+        }
         if (route && t > 0) {
             rc = run_assign(ctx, Xt32, Xt, t, d, C, C32, k, nullptr, route, nullptr);
             if (rc != KRR_OK) goto done;

@@ -14,6 +14,7 @@ kkrr2_262144        262144   16384   90  64-component Gaussian mixture, centres 
                                          Dirichlet(0.5) weights clipped to [500, 16000] rows;
                                          y = w_c.x/sqrt d + b_c + sin||x|| + 0.05 e
 sweep_520000        520000   51630   90  Student-t(5) features, standardised; tanh target as above
+bkrr2kb_65536       65536    8192    90  the bkrr2 data; K-balance partitions (K-means from p random rows, 20 rounds)
 serve stream        10000 requests, Poisson 200/s; n log-U[512, 16384], d in {8, 32, 90},
                     sigma log-U[0.5, 16], lambda log-U[1e-7, 1e-3], 256 test rows, mixture features
 
@@ -54,6 +55,17 @@ def bkrr2(seed: int = 1, n: int = 65536, t: int = 8192, d: int = 90, p: int = 16
     return dict(X=X, y=y, Xt=Xt, yt=yt, sigmas=list(sigmas), lambdas=list(lambdas), p=p,
                 part_seed=int(rng.integers(0, 2**63)),
                 workload="bkrr2_n%d_t%d_d%d_p%d" % (n, t, d, p))
+
+
+def bkrr2_kbalance(seed: int = 5, n: int = 65536, t: int = 8192, d: int = 90, p: int = 16, iters: int = 20,
+                   sigmas=(1.0, 4.0, 16.0), lambdas=(1e-6, 1e-4)):
+    """The BKRR2 shapes with the paper's own partitioner: K-balance over
+    K-means centres that start at p random training rows."""
+    w = bkrr2(seed=seed, n=n, t=t, d=d, p=p, sigmas=sigmas, lambdas=lambdas)
+    rng = np.random.default_rng(seed + 1000)
+    w.update(init_idx=rng.choice(n, size=p, replace=False).astype(np.int64), iters=iters,
+             workload="bkrr2kb_n%d_t%d_d%d_p%d" % (n, t, d, p))
+    return w
 
 
 def _mixture_sizes(rng, n: int, k: int, lo: int, hi: int):

@@ -85,6 +85,42 @@ def test_kmeans_partition_bit_exact(ctx, n, t, d, k, iters):
     assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
 
 
+@pytest.mark.parametrize("n,t,d,k,iters", [(5000, 700, 12, 8, 10), (3333, 129, 90, 16, 5), (2500, 1, 3, 5, 0),
+                                           (4096, 64, 7, 32, 3), (70000, 300, 90, 16, 4)])
+def test_kbalance_partition_bit_exact(ctx, n, t, d, k, iters):
+    """Alg. K-balance Clustering (the BKRR partitioner): K-means centres, the
+    balanced sequential assignment replayed on the GPU in rounds, the means
+    of the balanced parts and the routes, all bit-exact with the oracle."""
+    X, Xt, init = _mixture(n, t, d, k, n)
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KBALANCE, k,
+                                                            iters=iters, init_idx=cuda(init, torch.int64))
+    operm, ooff, oassign, oroute, oC, ocs = oracle.partition_kbalance(X, Xt, k, init, iters)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+    assert np.array_equal(route.cpu().numpy(), oroute)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+    sizes = np.diff(offsets.cpu().numpy())
+    assert sizes.max() <= -(-n // k)
+    if n % k == 0:
+        assert np.all(sizes == n // k)
+
+
+def test_kbalance_exact_ties(ctx):
+    """Integer points and duplicated centres: equal distances go to the lower
+    open index, and a centre that fills passes its later ties to the next one."""
+    X = np.array([[float(i % 5), float(i % 3)] for i in range(60)])
+    init = np.array([0, 15, 0, 7], np.int64)  # centres 0 and 2 coincide
+    for iters in (0, 2):
+        assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), None, K.KRR_PART_KBALANCE, 4,
+                                                                iters=iters, init_idx=cuda(init, torch.int64))
+        operm, ooff, oassign, _, oC, _ = oracle.partition_kbalance(X, None, 4, init, iters)
+        assert np.array_equal(assign.cpu().numpy(), oassign)
+        assert np.array_equal(offsets.cpu().numpy(), ooff)
+        assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+        assert np.diff(ooff).max() <= 15
+
+
 def test_kmeans_exact_ties_and_empty_cluster(ctx):
     """Integer points equidistant from two centres go to the lower index; a
     duplicated initial centre loses every tie, so with no update round it owns
