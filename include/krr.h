@@ -58,6 +58,14 @@ typedef enum { KRR_PART_RANDOM = 0, KRR_PART_KMEANS = 1, KRR_PART_KBALANCE = 2 }
  *         products with FP32 accumulation.                                   */
 typedef enum { KRR_PREC_FP64 = 0, KRR_PREC_FP32 = 1, KRR_PREC_TF32 = 2, KRR_PREC_BF16X3 = 3 } krr_prec;
 
+/* Table 1 kernel of the fits (Eq. 6) and predictions (Eq. 7).
+ * GAUSSIAN: Phi(x, y) = exp(-||x - y||^2 / (2 sigma^2)) (the default).
+ * LINEAR:   Phi(x, y) = x . y; sigma plays no part (every sigma of a fit
+ *           gives the same model).  Kernel ridge regression with it is
+ *           primal ridge regression (Eq. 2).  Needs KRR_PREC_FP64; the other
+ *           precisions return KRR_ERR_UNSUPPORTED.                            */
+typedef enum { KRR_KERNEL_GAUSSIAN = 0, KRR_KERNEL_LINEAR = 1 } krr_kernel;
+
 /* Model choice (Eq. 3 scores):
  * PER_MODEL: one MSE per (partition, sigma, lambda) model; best model.
  * ROUTED:    each test point scored by its routed partition (the scoring
@@ -231,6 +239,11 @@ krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
 krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);
 krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel);
 krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u);
+
+/* krr_ctx_set_kernel: the Table 1 kernel of this context's subsequent
+ * krr_fit_batch calls (default GAUSSIAN); a model keeps the kernel it was
+ * fitted with for krr_predict.  Errors: KRR_ERR_ARG (unknown kernel). */
+krr_status krr_ctx_set_kernel(krr_ctx *ctx, krr_kernel kind);
 long long krr_launch_count(void);
 
 #ifdef __cplusplus

@@ -20,6 +20,7 @@ from . import build as _build
 KRR_OK, KRR_ERR_ARG, KRR_ERR_OOM, KRR_ERR_BUDGET, KRR_ERR_CUDA = 0, 1, 2, 3, 4
 KRR_ERR_NOT_SPD, KRR_ERR_NO_CONVERGE, KRR_ERR_TIMEOUT, KRR_ERR_UNSUPPORTED = 5, 6, 7, 8
 KRR_PART_RANDOM, KRR_PART_KMEANS, KRR_PART_KBALANCE = 0, 1, 2
+KRR_KERNEL_GAUSSIAN, KRR_KERNEL_LINEAR = 0, 1
 KRR_PREC_FP64, KRR_PREC_FP32, KRR_PREC_TF32, KRR_PREC_BF16X3 = 0, 1, 2, 3
 KRR_SEL_PER_MODEL, KRR_SEL_ROUTED, KRR_SEL_AVERAGE, KRR_SEL_ORACLE = 0, 1, 2, 3
 PREC_NAMES = {"fp64": KRR_PREC_FP64, "fp32": KRR_PREC_FP32, "tf32": KRR_PREC_TF32, "bf16x3": KRR_PREC_BF16X3}
@@ -165,6 +166,10 @@ def krr_ctx_profile(ctx: Context) -> dict:
         ctx.check(ctx.lib.krr_ctx_profile(ctx.handle, k, ctypes.byref(ms), ctypes.byref(n)), "krr_ctx_profile")
         out[name] = (ms.value, n.value)
     return out
+
+
+def krr_ctx_set_kernel(ctx: Context, kind: int):
+    ctx.check(ctx.lib.krr_ctx_set_kernel(ctx.handle, int(kind)), "krr_ctx_set_kernel")
 
 
 def krr_ctx_set_panel_width(ctx: Context, W: int):

@@ -33,6 +33,8 @@ krr_status run_gather(Ctx *, const int32_t *, int64_t, int32_t, int64_t *, int64
 void launch_stage(cudaStream_t, const double *, const double *, const int64_t *, const Model &, double *);
 void launch_kbuild_df(cudaStream_t, const Model &, int64_t, float *, float *, float *);
 void launch_kbuild_fp64(cudaStream_t, const Model &, int64_t, double *, double *);
+void launch_k64_abs_rowsums(cudaStream_t, const Model &, int64_t, const double *, float *, float *, const int64_t *,
+                            int64_t);
 struct CholLaunch {
     int kind;
     int K0, W;
@@ -295,6 +297,12 @@ krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u) {
     return KRR_OK;
 }
 
+krr_status krr_ctx_set_kernel(krr_ctx *ctx, krr_kernel kind) {
+    if (!ctx || (kind != KRR_KERNEL_GAUSSIAN && kind != KRR_KERNEL_LINEAR)) return KRR_ERR_ARG;
+    ctx->c.kernel = kind;
+    return KRR_OK;
+}
+
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W) {
     if (!ctx || W < 0 || W > 64) return KRR_ERR_ARG;
     ctx->c.chol_W = W;
@@ -352,9 +360,12 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     for (int j = 0; j < p; ++j)
         if (off[j + 1] < off[j]) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must be non-decreasing");
 
+    if (c->kernel == KRR_KERNEL_LINEAR && !fp64)
+        return fail(c, KRR_ERR_UNSUPPORTED, "krr_fit_batch: the linear kernel needs KRR_PREC_FP64");
     krr_model *km = new (std::nothrow) krr_model();
     if (!km) return KRR_ERR_OOM;
     Model &M = km->m;
+    M.kind = c->kernel;
     M.d = d;
     M.dp = ((d + 15) / 16) * 16;
     M.p = p;
@@ -534,7 +545,9 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         // row sums of K left by the exact-Gram tile build, for ||A||_inf
         float *rsR = nullptr, *rsC = nullptr;
         int64_t *d_rsoff = nullptr, rstot = 0;
-        if (!fp64 && M.ozS) {
+        // (the FP64 path takes them from the stored tiles for the linear
+        // kernel, whose entries can be negative: ||A||_inf needs |K|)
+        if ((!fp64 && M.ozS) || (fp64 && M.kind == KRR_KERNEL_LINEAR)) {
             std::vector<int64_t> rsoff(p);
             for (int j = 0; j < p; ++j) {
                 rsoff[j] = rstot;
@@ -553,6 +566,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             if (fp64) {
                 K64 = (double *)Kst;
                 launch_kbuild_fp64(st, M, ktot, K64, (double *)Ast);
+                if (rsR) launch_k64_abs_rowsums(st, M, ktot, K64, rsR, rsC, d_rsoff, rstot);
             } else {
                 Kh = (float *)Kst;
                 Kl = Kh + (size_t)ns * ktot * KRR_TILE_ELEMS;

@@ -141,11 +141,13 @@ struct Ctx {
     int chol_W = 0;            // outer panel width (0 = tuned on first use)
     double target_err = 1e-7;  // refinement stops once kappa_est * backward error <= this
     double escalate = 32.0;    // TF32: factor a solve in 3 passes when kappa_est * 2^-11 exceeds this
+    int kernel = KRR_KERNEL_GAUSSIAN;  // Table 1 kernel of the next fits
     std::map<std::pair<int, int>, int> tuned_W;  // (precision, max tiles) -> tuned panel width
 };
 
 struct Model {
     int32_t d = 0, dp = 0, p = 0, nsig = 0, nlam = 0, prec = 0;
+    int32_t kind = KRR_KERNEL_GAUSSIAN;  // Table 1 kernel
     int64_t n = 0, prows = 0, nvec = 0;
     std::vector<double> sigmas, lambdas;
     std::vector<PartDesc> parts;

@@ -73,6 +73,7 @@ __device__ __forceinline__ int find_part(const PartDesc *parts, int np, int64_t 
 
 struct KParams {
     int nsig, nlam;
+    int kind;                     // Table 1 kernel (KRR_KERNEL_*)
     int64_t ktot;                 // tiles of one sigma's store
     float inv2s2_hi[8], inv2s2_lo[8];
     double inv2s2[8];
@@ -226,8 +227,12 @@ kbuild_fp64_kernel(const double *__restrict__ X64, int32_t d, const PartDesc *__
             for (int i = 0; i < 8; ++i)
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    double t = a[i] - b[j];
-                    acc[i][j] = fma(t, t, acc[i][j]);
+                    if (kp.kind == KRR_KERNEL_LINEAR) {  // the dot product x_a . x_b
+                        acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                    } else {  // the squared distance
+                        double t = a[i] - b[j];
+                        acc[i][j] = fma(t, t, acc[i][j]);
+                    }
                 }
         }
     }
@@ -249,7 +254,8 @@ kbuild_fp64_kernel(const double *__restrict__ X64, int32_t d, const PartDesc *__
 #pragma unroll 1
         for (int is = 0; is < kp.nsig; ++is) {
             double kv;
-            if (gr >= P.m || gc >= P.m) kv = (gr == gc) ? 1.0 : 0.0;
+            if (gr >= P.m || gc >= P.m) kv = (gr == gc) ? 1.0 : 0.0;  // padding: an identity block
+            else if (kp.kind == KRR_KERNEL_LINEAR) kv = D;                // x_a . x_b
             else if (gr == gc) kv = 1.0;
             else kv = exp(-D * kp.inv2s2[is]);
             const int64_t kt = (int64_t)is * kp.ktot + P.ktile0 + lt;
@@ -263,6 +269,31 @@ kbuild_fp64_kernel(const double *__restrict__ X64, int32_t d, const PartDesc *__
     }
 }
 
+// ||K + lambda m I||_inf for a kernel with signed entries (linear): per
+// (sigma, tile) the row sums of |K| into the first of a tile's eight
+// row-partial slots (the others stay zero) and, for an off-diagonal tile, the
+// column sums of |K| -- the slots the exact-Gram tile build fills for the
+// Gaussian kernel.  grid (tiles of every sigma), 128 threads.
+__global__ void k64_abs_rowsum_kernel(const double *__restrict__ K64, const PartDesc *__restrict__ parts, int np,
+                                      int64_t ktot, float *__restrict__ rsR, float *__restrict__ rsC,
+                                      const int64_t *__restrict__ rsoff, int64_t rstot) {
+    const int64_t g = blockIdx.x;  // sigma * ktot + tile
+    const int is = (int)(g / ktot);
+    const int64_t tile = g % ktot;
+    const int pj = find_part(parts, np, tile);
+    const PartDesc P = parts[pj];
+    int ti, tj;
+    tri_decode(tile - P.ktile0, ti, tj);
+    const double *Kt = K64 + g * KRR_TILE_ELEMS;
+    const int c = threadIdx.x;
+    double cs = 0.0, rs = 0.0;
+    for (int r = 0; r < KRR_TILE; ++r) cs += fabs(Kt[r * KRR_TILE + c]);  // column c
+    for (int q = 0; q < KRR_TILE; ++q) rs += fabs(Kt[c * KRR_TILE + q]);  // row c
+    const int64_t g0 = (int64_t)is * rstot + rsoff[pj];
+    rsR[((g0 + (int64_t)ti * P.T + tj) * 8) * KRR_TILE + c] = (float)rs;
+    if (ti != tj) rsC[(g0 + (int64_t)tj * P.T + ti) * KRR_TILE + c] = (float)cs;
+}
+
 // ------------------------------------------------------------------ host
 void launch_stage(cudaStream_t st, const double *X, const double *y, const int64_t *perm, const Model &M,
                   double *yg) {
@@ -274,6 +305,7 @@ void launch_stage(cudaStream_t st, const double *X, const double *y, const int64
 }
 
 void make_kparams(const Model &M, int64_t ktot, KParams &kp) {
+    kp.kind = M.kind;
     kp.nsig = M.nsig;
     kp.nlam = M.nlam;
     kp.ktot = ktot;
@@ -295,6 +327,14 @@ void launch_kbuild_df(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, 
     allow_max_dyn_smem(kbuild_df_kernel);
     KRR_LAUNCHED(), kbuild_df_kernel<<<(unsigned)ktot, KB_THREADS, sm, st>>>(M.Xh, M.Xl, M.nrm, M.dp, M.d_parts, M.p, M.d_solves, kp,
                                                             Kh, Kl, A);
+}
+
+void launch_k64_abs_rowsums(cudaStream_t st, const Model &M, int64_t ktot, const double *K64, float *rsR, float *rsC,
+                            const int64_t *rsoff, int64_t rstot) {
+    if (ktot == 0) return;
+    cudaMemsetAsync(rsR, 0, (size_t)M.nsig * rstot * 8 * KRR_TILE * sizeof(float), st);
+    KRR_LAUNCHED(), k64_abs_rowsum_kernel<<<(unsigned)((int64_t)M.nsig * ktot), KRR_TILE, 0, st>>>(
+        K64, M.d_parts, M.p, ktot, rsR, rsC, rsoff, rstot);
 }
 
 void launch_kbuild_fp64(cudaStream_t st, const Model &M, int64_t ktot, double *K64, double *A) {

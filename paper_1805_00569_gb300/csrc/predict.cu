@@ -25,6 +25,7 @@ constexpr int PKC = 16;  // features per staging chunk
 constexpr int PG = 16;  // (sigma, lambda) models per pass
 
 struct PredParams {
+    int kind;           // Table 1 kernel (KRR_KERNEL_*)
     int nsig, nlam;     // sigmas in this pass, lambdas
     int sig0, Gtot;     // first sigma of this pass, grid size of the model
     float c_hi[PG], c_lo[PG];  // -1 / (2 sigma^2) as df, for this pass
@@ -258,12 +259,16 @@ predict_fp64_kernel(const double *__restrict__ X64, int32_t d, const PartDesc *_
             const double *xa = X64 + (P.prow0 + r) * d;
             const double *xb = Xt + row * d;
             double D = 0.0;
-            for (int f = 0; f < d; ++f) {
-                const double df_ = xa[f] - xb[f];
-                D = fma(df_, df_, D);
+            if (pp.kind == KRR_KERNEL_LINEAR) {
+                for (int f = 0; f < d; ++f) D = fma(xa[f], xb[f], D);  // x_a . x_b
+            } else {
+                for (int f = 0; f < d; ++f) {
+                    const double df_ = xa[f] - xb[f];
+                    D = fma(df_, df_, D);
+                }
             }
             for (int is = 0; is < pp.nsig; ++is) {
-                const double k = exp(D * pp.c64[is]);
+                const double k = pp.kind == KRR_KERNEL_LINEAR ? D : exp(D * pp.c64[is]);
                 for (int il = 0; il < pp.nlam; ++il) {
                     const int g = is * pp.nlam + il;
                     const SolveDesc S = solves[(int64_t)j * pp.Gtot + pp.sig0 * pp.nlam + g];
@@ -352,6 +357,7 @@ void launch_predict(cudaStream_t st, const Model &M, const double *Xt, int64_t t
     const int per_pass = std::max(1, PG / std::max(1, M.nlam));
     for (int s0 = 0; s0 < M.nsig; s0 += per_pass) {
         PredParams pp;
+        pp.kind = M.kind;
         pp.nsig = std::min(per_pass, M.nsig - s0);
         pp.nlam = M.nlam;
         pp.sig0 = s0;

@@ -229,6 +229,43 @@ def test_large_lambda_m_leaves_the_fp16_factor(ctx, lam):
         model.free()
 
 
+def test_linear_kernel_fp64_matches_oracle_and_primal_ridge(ctx):
+    """Table 1's linear kernel (FP64 path): alpha and predictions match the
+    oracle's linear fit, the predictions equal primal ridge regression
+    (Eq. 2: yhat = Xt w, w = (X^T X + lambda m I)^-1 X^T y per partition), the
+    condition estimates use |K|, and the other precisions are refused."""
+    X, y, Xt, yt, perm, offsets = _case()
+    d = X.shape[1]
+    lams = [1e-3, 1e-1]
+    K.krr_ctx_set_kernel(ctx, K.KRR_KERNEL_LINEAR)
+    try:
+        with pytest.raises(K.KrrError):
+            K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(offsets, torch.int64), [1.0], lams,
+                            "tf32")
+        model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64),
+                                               cuda(offsets, torch.int64), [1.0], lams, "fp64", want_alpha=True)
+    finally:
+        K.krr_ctx_set_kernel(ctx, K.KRR_KERNEL_GAUSSIAN)
+    try:
+        assert np.all(status.cpu().numpy() == K.KRR_OK)
+        ga = split_alpha(alpha.cpu().numpy(), offsets, 2)
+        yhat = K.krr_predict(ctx, model, cuda(Xt)).cpu().numpy()
+        _, kap, _ = K.krr_model_stats(ctx, model)
+        for j in range(3):
+            rows = perm[offsets[j]:offsets[j + 1]]
+            m = len(rows)
+            for g, lam in enumerate(lams):
+                oa, info, rc = oracle.fit(X[rows], y[rows], 1.0, lam, oracle.KIND_LINEAR)
+                assert rc == 0
+                assert rel(ga[j][g], oa) <= FP64_TOL, (j, g)
+                Xp = X[rows]
+                w = np.linalg.solve(Xp.T @ Xp + lam * m * np.eye(d), Xp.T @ y[rows])
+                assert rel(yhat[j * 2 + g], Xt @ w) <= 1e-9, (j, g)
+                assert kap.numpy()[j * 2 + g] == pytest.approx(info[0], rel=1e-6)
+    finally:
+        model.free()
+
+
 def test_routed_predict_parity(ctx):
     X, Xt, init = _mixture(1400, 300, 7, 5, 31)
     y = np.sin(X.sum(1)) + 0.05 * np.random.default_rng(1).standard_normal(1400)
