@@ -51,22 +51,6 @@ bool make_tile_tmap(CUtensorMap *, float *, int64_t);
 bool make_tile_tmap16(CUtensorMap *, __half *, int64_t);
 size_t pcg_state_size();
 size_t precond_smem_bytes(bool, int);
-struct PcgBuffers {
-    double *x, *r, *z, *p, *q, *y;
-    float2 *pdf, *slots;  // the direction as double-float pairs; matvec partials
-    PcgState *state;
-    unsigned int *nactive;
-    GroupDesc *d_groups;
-    int64_t *d_gpre;
-    int ng;
-    int64_t gtiles;
-    int maxT;
-    const void *L16;  // FP16 factor store of class-1 solves (null without them)
-    int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
-    const float *rsR, *rsC;  // row sums of K from the kernel-tile build (null: none)
-    const int64_t *rsoff;
-    int64_t rstot;
-};
 cudaError_t run_pcg(cudaStream_t, const Model &, const PcgBuffers &, const float *, const float *, const double *,
                     const void *, const void *, bool, int, double, double, int, const int32_t *, unsigned int *, int,
                     Prof *);

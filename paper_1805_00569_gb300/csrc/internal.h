@@ -68,6 +68,24 @@ struct PcgState {
     int32_t active, iters, status, pad;
 };
 
+// device buffers of the refinement, shared by the library and the refinement kernels
+struct PcgBuffers {
+    double *x, *r, *z, *p, *q, *y;
+    float2 *pdf, *slots;  // the direction as double-float pairs; matvec partials
+    PcgState *state;
+    unsigned int *nactive;
+    GroupDesc *d_groups;
+    int64_t *d_gpre;
+    int ng;
+    int64_t gtiles;
+    int maxT;
+    const void *L16;  // FP16 factor store of class-1 solves (null without them)
+    int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
+    const float *rsR, *rsC;  // row sums of K from the kernel-tile build (null: none)
+    const int64_t *rsoff;
+    int64_t rstot;
+};
+
 // Optional per-kernel timing with CUDA events on the launching stream.
 enum ProfKind {
     PROF_PARTITION = 0, PROF_STAGE, PROF_KBUILD, PROF_POTRF, PROF_TRSM, PROF_UPDATE, PROF_MATVEC,

@@ -589,22 +589,6 @@ __global__ void pcg_step2_kernel(const SolveDesc *__restrict__ solves, PcgState 
 }
 
 // ---------------------------------------------------------------- host
-struct PcgBuffers {
-    double *x, *r, *z, *p, *q, *y;
-    float2 *pdf, *slots;  // the direction as double-float pairs; matvec partials
-    PcgState *state;
-    unsigned int *nactive;
-    GroupDesc *d_groups;
-    int64_t *d_gpre;
-    int ng;
-    int64_t gtiles;
-    int maxT;
-    const void *L16;  // FP16 factor store of class-1 solves (null without them)
-    int32_t *order;   // solve indices by tile count, largest first (preconditioner CTA order)
-    const float *rsR, *rsC;  // row sums of K from the kernel-tile build (null: none)
-    const int64_t *rsoff;
-    int64_t rstot;
-};
 
 size_t pcg_state_size() { return sizeof(PcgState); }
 

@@ -51,3 +51,18 @@ def test_no_oracle_in_the_product():
 def test_library_targets_sm103a_only():
     from paper_1805_00569_gb300 import build
     assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_no_device_fails_loudly(lib):
+    """Without a CUDA device the C ABI refuses a context (status, no handle)
+    and the binding raises: nothing falls back to the host."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    h = ctypes.c_void_p(1)
+    lib.krr_ctx_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t]
+    rc = lib.krr_ctx_create(ctypes.byref(h), 0, None, 0)
+    assert rc != 0 and h.value is None
+    import paper_1805_00569_gb300 as krr
+    with pytest.raises(krr.KrrError):
+        krr.krr_ctx_create()
