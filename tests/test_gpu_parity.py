@@ -142,6 +142,29 @@ def test_kmeans_exact_ties_and_empty_cluster(ctx):
             assert ooff[4] - ooff[3] == 0  # the duplicate centre owns no rows
 
 
+def test_kmeans_centre_sum_order_bit_exact(ctx):
+    """A centre whose value depends on the summation order: 2^53 absorbs the
+    ones of its own 1024-row block, the next block's ones survive, and -2^53
+    in the third block cancels; the canonical block-tree order gives 1024 / 3000
+    (the exact mean would be 2047 / 3000, one ascending pass 0)."""
+    n = 3000
+    X = np.zeros((n, 2))
+    X[0, 0] = 2.0**53
+    X[1:2048, 0] = 1.0
+    X[2048, 0] = -(2.0**53)
+    X[:, 1] = np.arange(n) % 7
+    Xt = np.array([[0.0, 0.0], [5.0, 1.0]])
+    init = np.array([5], np.int64)
+    for iters in (1, 3):
+        assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, 1,
+                                                                iters=iters, init_idx=cuda(init, torch.int64))
+        operm, ooff, oassign, oroute, oC, _ = oracle.partition_kmeans(X, Xt, 1, init, iters)
+        got = centers.cpu().numpy()
+        assert got[0, 0] == 1024.0 / 3000.0
+        assert np.array_equal(got.view(np.uint64), oC.view(np.uint64))
+        assert np.array_equal(assign.cpu().numpy(), oassign) and np.array_equal(perm.cpu().numpy(), operm)
+
+
 # ------------------------------------------------------------------ fit / predict / select
 def _case(seed=7, n=950, d=13, t=333):
     rng = np.random.default_rng(seed)

@@ -230,6 +230,35 @@ def test_kmeans_single_cluster_is_mean():
     assert np.all(c == 0) and list(delta) == [3000, 0]
 
 
+def test_centre_sum_order_is_the_canonical_block_tree():
+    """The centre step's summation order decides bit-exactness (the order the
+    paper leaves open, Alg. 2 centre step): rows in blocks of 1024, each block
+    summed in ascending row order, block sums combined pairwise in block order.
+    Hand-worked case, one cluster, 3000 rows, feature 0:
+      block 0 = [2^53, 1 x 1023]: 2^53 + 1 ties to even, so s0 = 2^53;
+      block 1 = [1 x 1024]: s1 = 1024;  block 2 = [-2^53, 0 x 951]: s2 = -2^53;
+      (s0 + s1) + s2 = 1024, while the exact sum is 2047 and a single
+      ascending pass gives 0.  Feature 1 (rows of cluster 1 only, every
+      other row) checks that a block sums only its own cluster's rows."""
+    n = 3000
+    X = np.zeros((n, 2))
+    X[0, 0] = 2.0**53
+    X[1:2048, 0] = 1.0
+    X[2048, 0] = -(2.0**53)
+    c = np.zeros(n, np.int32)
+    c[1::2] = 1
+    X[1::2, 1] = 3.0  # cluster 1: 1500 rows of 3 in feature 1
+    C = oracle.update_centres(X, c, np.zeros((2, 2)))
+    # cluster 0 (even rows): block 0 = 2^53 + 511 ones -> 2^53; block 1: 512 ones;
+    # block 2: -2^53 (row 2048 is even) -> (2^53 + 512) - 2^53 = 512, over 1500 rows
+    assert C[0, 0] == 512.0 / 1500.0
+    # cluster 1 (odd rows): 512 + 512 ones in blocks 0 and 1, row 2049 onwards zeros
+    assert C[1, 0] == 1024.0 / 1500.0
+    assert C[1, 1] == 3.0 and C[0, 1] == 0.0
+    C1 = oracle.update_centres(X, np.zeros(n, np.int32), np.zeros((1, 2)))
+    assert C1[0, 0] == 1024.0 / 3000.0
+
+
 def test_kmeans_empty_cluster_keeps_centre():
     X = np.array([[0.0], [0.1], [0.2], [10.0]])
     C0 = np.array([[0.0], [10.0], [100.0]])
