@@ -42,3 +42,31 @@ def test_exp2_table_values():
         assert lo == round_f32(v - Decimal(hi))
         err = abs(Decimal(hi) + Decimal(lo) - v) / v
         assert err < Decimal(2) ** -47, (j, err)
+
+
+def _bits(x: float) -> int:
+    """Significant bits of a binary float."""
+    m, _ = math.frexp(abs(x))
+    n = 0
+    while m:
+        m = m * 2 - int(m * 2)
+        n += 1
+    return n
+
+
+def test_range_reduction_constants():
+    """The exponential splits ln2/256 = C1 + C2 + C3 with C1 short enough that
+    n C1 is exact for |n| < 2^15 (arguments down to -87), C2 and C3 float32,
+    and the three together within 2^-56 relative of ln2/256: for |x| <= 87
+    the reduced argument is then off by at most 87 * 2^-56 ~ 1.2e-15, far
+    below the exponential's ~7e-13 relative error."""
+    getcontext().prec = 50
+    src = open(os.path.join(ROOT, "paper_1805_00569_gb300", "csrc", "common.cuh")).read()
+    m = re.search(r"C1 = (\S+)f, C2 = (\S+)f, C3 = (\S+)f;", src)
+    c1, c2, c3 = (float.fromhex(v) for v in m.groups())
+    assert all(f32(c) == c for c in (c1, c2, c3))
+    assert _bits(c1) + 15 <= 24  # n C1 exact in float32
+    ln2_256 = Decimal(2).ln() / 256
+    assert abs(Decimal(c1) + Decimal(c2) + Decimal(c3) - ln2_256) / ln2_256 < Decimal(2) ** -56
+    inv = float(re.search(r"rintf\(x\.hi \* (\S+)f\)", src).group(1))
+    assert abs(Decimal(f32(inv)) - 256 / Decimal(2).ln()) / (256 / Decimal(2).ln()) < Decimal(2) ** -24
