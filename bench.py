@@ -22,6 +22,7 @@ import ctypes
 import json
 import multiprocessing as mp
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -91,6 +92,27 @@ def _oracle_jobs(w, perm, offsets, count):
     return jobs
 
 
+def host_cpu(cpuinfo: str = "/proc/cpuinfo") -> dict:
+    """nproc and the CPU model of the host that runs the oracle (the model
+    name on x86, implementer and part codes on Arm)."""
+    info = {"nproc": os.cpu_count(), "machine": platform.machine()}
+    try:
+        keys = {}
+        with open(cpuinfo) as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                k, v = k.strip(), v.strip()
+                if k in ("model name", "CPU implementer", "CPU part") and k not in keys:
+                    keys[k] = v
+        if "model name" in keys:
+            info["model"] = keys["model name"]
+        elif "CPU part" in keys:
+            info["model"] = "implementer %s part %s" % (keys.get("CPU implementer", "?"), keys["CPU part"])
+    except (OSError, UnicodeDecodeError):
+        pass
+    return info
+
+
 def cpu_baseline(w, sample: int):
     import oracle
     oracle.build()
@@ -101,7 +123,7 @@ def cpu_baseline(w, sample: int):
     with ctx.Pool(processes=sample) as pool:
         res = pool.map(_oracle_solve, jobs)
     wall = time.perf_counter() - t0
-    return dict(value=sample / wall, unit=UNIT, cores=sample, kind="oracle",
+    return dict(value=sample / wall, unit=UNIT, cores=sample, kind="oracle", host=host_cpu(),
                 sample="%d of the %d (partition, sigma, lambda) solves of %s, one process each: kernel build + "
                        "Cholesky + long-double refinement + prediction of all %d test rows + MSE; %.1f s wall"
                        % (sample, w["p"] * len(w["sigmas"]) * len(w["lambdas"]), w["workload"],
@@ -596,7 +618,7 @@ def run_reference(args, rank, world):
             vals.append(sample / r["value"])
     wall = sum(vals)
     value = sample * args.steps / wall
-    cpu = dict(value=value, unit=UNIT, cores=sample, kind="oracle",
+    cpu = dict(value=value, unit=UNIT, cores=sample, kind="oracle", host=host_cpu(),
                sample="per step %d of the 96 solves of %s (kernel build + Cholesky + refinement + predict + MSE), "
                       "one process each" % (sample, w["workload"]))
     print(json.dumps({

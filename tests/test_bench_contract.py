@@ -47,3 +47,15 @@ def test_roofline_hbm_for_a_memory_bound_class():
     r = bench.roofline(_res("precond", ms=2.7), 5, PEAKS)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == pytest.approx(6797.9)
     assert 0 < r["frac"] and r["traffic"] is None
+
+
+def test_host_cpu_reads_x86_and_arm_cpuinfo(tmp_path):
+    import bench
+    x86 = tmp_path / "x86"
+    x86.write_text("processor\t: 0\nmodel name\t: Some CPU @ 2.0GHz\nprocessor\t: 1\nmodel name\t: Some CPU @ 2.0GHz\n")
+    arm = tmp_path / "arm"
+    arm.write_text("processor\t: 0\nCPU implementer\t: 0x41\nCPU architecture: 8\nCPU part\t: 0xd4f\n")
+    assert bench.host_cpu(str(x86))["model"] == "Some CPU @ 2.0GHz"
+    assert bench.host_cpu(str(arm))["model"] == "implementer 0x41 part 0xd4f"
+    h = bench.host_cpu(str(tmp_path / "missing"))
+    assert "model" not in h and h["nproc"] >= 1
