@@ -158,7 +158,9 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
  *   Xt [t x d].  route == NULL: every model predicts every test row and
  *   yhat is [p*ns*nl x t] (model-major).  route [t] given: row q is predicted
  *   only by partition route[q]'s models and yhat is [ns*nl x t].  A partition
- *   with no rows predicts 0.  Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */
+ *   with no rows predicts 0, and so does a row whose route lies outside
+ *   [0, p) (the route is read on the device only; such a value is skipped,
+ *   never followed).  Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */
 krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, int64_t t, const int32_t *route,
                        double *yhat);
 
@@ -192,13 +194,19 @@ krr_status krr_model_free(krr_ctx *ctx, krr_model *model);
  *   cuda_stream: the stream to enqueue on (a cudaStream_t; NULL = legacy
  *   default stream).  assign [n] (device int32, every value in [0, p)),
  *   perm [n] (device int64, output), offsets [p+1] (device int64, output);
- *   all caller-owned.  No context is needed and nothing is allocated: the
+ *   all caller-owned.  assign is read on the device only, so it cannot be
+ *   validated before the call returns: a value outside [0, p) is skipped
+ *   (its row is placed in no partition), which leaves offsets[p] < n and
+ *   perm[offsets[p] .. n) unwritten -- check offsets[p] == n after the
+ *   stream has run when assign is not trusted.  No context is needed and nothing is allocated: the
  *   per-block counts live in a fixed 4 MiB device array inside the library
  *   (held on every GPU that loads it until the process exits), so
  *   ceil(n / 1024) * p must not exceed 524288 and p must not exceed 12288;
  *   larger requests return KRR_ERR_ARG before anything is enqueued.
  *   The first call on a device looks up that array's device address (once
- *   per device); make that first call before any stream capture.  Calls share
+ *   per device) and keeps it; make that first call before any stream
+ *   capture.  The kept address is stale after cudaDeviceReset on that
+ *   device: do not call this entry point again in such a process.  Calls share
  *   the array and keep the last call's contents (every entry read is written
  *   first); calls that overlap on the GPU race on it and must be serialised.
  * Errors: KRR_ERR_ARG, KRR_ERR_CUDA. */

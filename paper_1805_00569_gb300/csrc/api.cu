@@ -824,7 +824,10 @@ krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, i
             ctx_free(c, tperm, (size_t)t * 8);
             API_TRY(c, e);
         }
-        krr_status rc = run_gather(c, route, t, M.p, tperm, toff);
+        // a route value outside [0, p) places its row nowhere: zeroed positions
+        // keep every grouped index a valid row, and such rows predict 0
+        cudaError_t ez = cudaMemsetAsync(tperm, 0, (size_t)t * 8, st);
+        krr_status rc = ez == cudaSuccess ? run_gather(c, route, t, M.p, tperm, toff) : KRR_ERR_CUDA;
         if (rc != KRR_OK) {
             ctx_free(c, toff, (size_t)(M.p + 1) * 8);
             ctx_free(c, tperm, (size_t)t * 8);

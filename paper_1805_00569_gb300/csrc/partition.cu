@@ -70,14 +70,30 @@ __global__ void random_offsets_kernel(int64_t n, int32_t p, int64_t *offsets, in
 // ------------------------------------------------------------ K-means assign
 constexpr int ASSIGN_THREADS = 128;
 
+// (4 d + 64) 2^-149: the subnormal with that integer significand (exact)
+__device__ __forceinline__ float assign_abs_bound(int d) { return __int_as_float(4 * d + 64); }
+// Centre with FP32 distance acc and error bound bnd may be the nearest given
+// the best upper bound best_hi; an overflowed or NaN distance always may.
+__device__ __forceinline__ bool assign_candidate(float acc, float bnd, float best_hi) {
+    const float ub = acc + bnd;
+    return acc - bnd <= best_hi || !(fabsf(ub) < INFINITY);
+}
+
 // One thread per point.  X32: FP32 copy of the rows (converted once per
 // K-means run: on GB300 the FP64 -> FP32 conversion runs on the slow FP64
 // pipe); C32 / C64: FP32 and FP64 centres.  The FP32 distance of every centre
-// carries the bound |d32 - d64| <= (d + 16) 2^-24 1.27 * 2 (||x||^2 + ||c||^2)
-// (rounding of the inputs, the differences, the squares and the sum; the
-// factor 2 bounds sum (|x|+|c|)^2).  Centres within the bound of the best
-// upper bound are candidates; with two or more, the FP64 distances in the
-// definition's order decide (strict <, lowest index).
+// carries the bound
+//   |d32 - d64| <= (d + 16) 2^-24 1.27 * 2 (||x||^2 + ||c||^2) + (4 d + 64) 2^-149
+// The relative part covers the rounding of the inputs, the differences, the
+// squares and the sum in the normal range (the factor 2 bounds
+// sum (|x|+|c|)^2); the absolute part covers FP32 subnormals, where rounding
+// is absolute (at most 2^-150 per input conversion and per accumulation step;
+// subnormal differences are exact), so tiny features keep a valid bound.
+// An overflowed or NaN distance (huge features) is always a candidate, and
+// with no finite upper bound every centre is one.  Centres within the bound
+// of the best upper bound are candidates; with two or more, the FP64
+// distances in the definition's order decide (strict <, lowest index; index 0
+// when no FP64 distance is finite, as the definition's loop leaves it).
 __global__ void __launch_bounds__(ASSIGN_THREADS)
 kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X, int64_t n, int32_t d,
                      const double *__restrict__ C64, const float *__restrict__ C32, int32_t k,
@@ -106,6 +122,7 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
     float xn = 0.f;
     for (int f = 0; f < d; ++f) xn = fmaf(sX[f * ASSIGN_THREADS + r], sX[f * ASSIGN_THREADS + r], xn);
     const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
+    const float babs = assign_abs_bound(d);
     float best_hi = INFINITY;
 #pragma unroll 1
     for (int j = 0; j < k; ++j) {
@@ -115,7 +132,7 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
             const float t = sX[f * ASSIGN_THREADS + r] - c[f];
             acc = fmaf(t, t, acc);
         }
-        best_hi = fminf(best_hi, acc + bscale * (xn + sCn[j]));
+        best_hi = fminf(best_hi, acc + (bscale * (xn + sCn[j]) + babs));
     }
     int ncand = 0, first = -1;
 #pragma unroll 1
@@ -126,7 +143,7 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
             const float t = sX[f * ASSIGN_THREADS + r] - c[f];
             acc = fmaf(t, t, acc);
         }
-        if (acc - bscale * (xn + sCn[j]) <= best_hi) {
+        if (assign_candidate(acc, bscale * (xn + sCn[j]) + babs, best_hi)) {
             if (ncand == 0) first = j;
             ++ncand;
         }
@@ -143,7 +160,7 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
                 const float t = sX[f * ASSIGN_THREADS + r] - c[f];
                 acc = fmaf(t, t, acc);
             }
-            if (acc - bscale * (xn + sCn[j]) > best_hi) continue;
+            if (!assign_candidate(acc, bscale * (xn + sCn[j]) + babs, best_hi)) continue;
             const double *c64 = C64 + (size_t)j * d;
             double s = 0.0;
             for (int f = 0; f < d; ++f) {
@@ -155,6 +172,7 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
                 arg = j;
             }
         }
+        if (!(best < INFINITY)) arg = 0;
     }
     out[i] = arg;
     if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
@@ -198,6 +216,7 @@ kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict
 #pragma unroll
     for (int f = 0; f < DP; ++f) xn = fmaf(x[f], x[f], xn);
     const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
+    const float babs = assign_abs_bound(d);
     float best_hi = INFINITY;
     const float4 *cT4 = reinterpret_cast<const float4 *>(cT);
 #pragma unroll 1
@@ -216,13 +235,14 @@ kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             dist[(size_t)(j4 + u) * ASSIGN2_THREADS + threadIdx.x] = av[u];
-            if (j4 + u < k) best_hi = fminf(best_hi, av[u] + bscale * (xn + cn[j4 + u]));
+            if (j4 + u < k) best_hi = fminf(best_hi, av[u] + (bscale * (xn + cn[j4 + u]) + babs));
         }
     }
     int ncand = 0, first = -1;
 #pragma unroll 1
     for (int j = 0; j < k; ++j)
-        if (dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x] - bscale * (xn + cn[j]) <= best_hi) {
+        if (assign_candidate(dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x], bscale * (xn + cn[j]) + babs,
+                             best_hi)) {
             if (ncand == 0) first = j;
             ++ncand;
         }
@@ -232,7 +252,9 @@ kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict
         double best = INFINITY;
 #pragma unroll 1
         for (int j = 0; j < k; ++j) {
-            if (dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x] - bscale * (xn + cn[j]) > best_hi) continue;
+            if (!assign_candidate(dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x], bscale * (xn + cn[j]) + babs,
+                                  best_hi))
+                continue;
             const double *c64 = C64 + (size_t)j * d;
             double sd = 0.0;
             for (int f = 0; f < d; ++f) {
@@ -244,6 +266,7 @@ kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict
                 arg = j;
             }
         }
+        if (!(best < INFINITY)) arg = 0;
     }
     out[i] = arg;
     if (delta) {  // one atomic per warp: the counter is a single address
@@ -398,7 +421,12 @@ __global__ void gather_count_kernel(const int32_t *__restrict__ a, int64_t n, in
     for (int j = threadIdx.x; j < p; j += blockDim.x) h[j] = 0;
     __syncthreads();
     int64_t lo = (int64_t)blockIdx.x * CANON, hi = min(n, lo + CANON);
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) atomicAdd(&h[a[i]], 1);
+    // a partition index outside [0, p) is counted nowhere (the scatter places
+    // only rows with an index in range, so offsets[p] then falls short of n)
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const int32_t v = a[i];
+        if ((uint32_t)v < (uint32_t)p) atomicAdd(&h[v], 1);
+    }
     __syncthreads();
     for (int j = threadIdx.x; j < p; j += blockDim.x) bcount[(int64_t)blockIdx.x * p + j] = h[j];
 }

@@ -85,6 +85,29 @@ def test_kmeans_partition_bit_exact(ctx, n, t, d, k, iters):
     assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
 
 
+@pytest.mark.parametrize("scale", [1e-40, 1e-20, 1e18, 1e25, 1e40])
+@pytest.mark.parametrize("mode", ["kmeans", "kbalance"])
+def test_partition_bit_exact_at_extreme_feature_scales(ctx, scale, mode):
+    """Alg. 2 assignments stay the FP64 argmin when the FP32 screen leaves its
+    normal range: squared features in FP32 subnormals (1e-20), features that
+    are FP32 subnormals themselves (1e-40), squared distances that overflow
+    FP32 (1e18, 1e25) and features beyond the FP32 range (1e40).  Assignments,
+    routes, groupings and centres bit-exact with the oracle."""
+    n, t, d, k, iters = 3000, 200, 90, 16, 4
+    X, Xt, init = _mixture(n, t, d, k, 77)
+    X, Xt = X * scale, Xt * scale
+    pm = K.KRR_PART_KMEANS if mode == "kmeans" else K.KRR_PART_KBALANCE
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), pm, k, iters=iters,
+                                                            init_idx=cuda(init, torch.int64))
+    fn = oracle.partition_kmeans if mode == "kmeans" else oracle.partition_kbalance
+    operm, ooff, oassign, oroute, oC, _ = fn(X, Xt, k, init, iters)
+    assert np.array_equal(assign.cpu().numpy(), oassign)
+    assert np.array_equal(route.cpu().numpy(), oroute)
+    assert np.array_equal(perm.cpu().numpy(), operm)
+    assert np.array_equal(offsets.cpu().numpy(), ooff)
+    assert np.array_equal(centers.cpu().numpy().view(np.uint64), oC.view(np.uint64))
+
+
 @pytest.mark.parametrize("n,t,d,k,iters", [(5000, 700, 12, 8, 10), (3333, 129, 90, 16, 5), (2500, 1, 3, 5, 0),
                                            (4096, 64, 7, 32, 3), (70000, 300, 90, 16, 4)])
 def test_kbalance_partition_bit_exact(ctx, n, t, d, k, iters):
@@ -309,8 +332,30 @@ def test_routed_predict_parity(ctx):
         mse, best = K.krr_select(ctx, cuda(yr), cuda(yt), 5, 2, K.KRR_SEL_ROUTED)
         omse, _ = oracle.select(oyr, yt, oracle.SEL_ROUTED)
         np.testing.assert_allclose(mse.cpu().numpy(), omse, rtol=REFINED_TOL)
+        # a route outside [0, p) is skipped on the device: that row predicts 0,
+        # every other row exactly as before
+        bad = route.clone()
+        bad[[0, 7, 299]] = torch.tensor([-1, 5, 2**31 - 1], dtype=torch.int32, device="cuda")
+        yb = K.krr_predict(ctx, model, cuda(Xt), route=bad).cpu().numpy()
+        keep = np.ones(300, bool)
+        keep[[0, 7, 299]] = False
+        assert np.all(yb[:, ~keep] == 0.0)
+        assert np.array_equal(yb[:, keep], yr[:, keep])
     finally:
         model.free()
+
+
+def test_select_hand_values_two_partitions_two_grid_points(ctx):
+    """krr_select on the hand-worked p = 2, G = 2 case of the oracle pins
+    (tests/golden/select_p2_g2_hand.txt): DC-KRR averaging over partitions
+    and the BKRR3 per-point choice, model index j*G + g."""
+    from test_oracle_pins import _select_hand_fixture
+    yhat, yt, want = _select_hand_fixture()
+    for name, mode in (("per_model", K.KRR_SEL_PER_MODEL), ("average", K.KRR_SEL_AVERAGE),
+                       ("oracle", K.KRR_SEL_ORACLE)):
+        mse, best = K.krr_select(ctx, cuda(yhat), cuda(yt), 2, 2, mode)
+        np.testing.assert_allclose(mse.cpu().numpy(), want[name][0], rtol=1e-15, atol=0)
+        assert int(best.cpu()[0]) == want[name][1], name
 
 
 def test_dkrr_fp64_full_size(ctx):

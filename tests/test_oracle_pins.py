@@ -283,6 +283,37 @@ def test_select_hand_values_and_ties():
     assert list(mses) == [1.0, 0.5, 0.5, 2.0] and best == 1
 
 
+def _select_hand_fixture():
+    """tests/golden/select_p2_g2_hand.txt: yhat rows, labels, and the
+    hand-worked MSEs (as fractions) and best index of each mode."""
+    from fractions import Fraction
+    rows, yt, want = [], None, {}
+    with open(os.path.join(GOLDEN, "select_p2_g2_hand.txt")) as f:
+        for line in f:
+            if not line.strip() or line.startswith("#"):
+                continue
+            parts = [x.strip() for x in line.split("|")]
+            if parts[0] == "yt":
+                yt = np.array([float(v) for v in parts[1].split(",")])
+            elif parts[0].startswith("model"):
+                rows.append([float(v) for v in parts[1].split(",")])
+            else:
+                vals = [float(Fraction(v)) for v in parts[1].split(",")]
+                want[parts[0]] = (np.array(vals), int(parts[2].split()[1]))
+    return np.array(rows), yt, want
+
+
+def test_select_hand_values_two_partitions_two_grid_points():
+    """p = 2, G = 2: the DC-KRR average (Alg. DC-KRR) divides by p and the
+    BKRR3 choice (Alg. BKRR3) takes models j*G + g; hand-worked values."""
+    yhat, yt, want = _select_hand_fixture()
+    for name, mode in (("per_model", oracle.SEL_PER_MODEL), ("average", oracle.SEL_AVERAGE),
+                       ("oracle", oracle.SEL_ORACLE)):
+        mses, best = oracle.select(yhat, yt, mode, 2, 2)
+        np.testing.assert_allclose(mses, want[name][0], rtol=1e-15, atol=0)
+        assert best == want[name][1], name
+
+
 def test_single_partition_modes_agree_with_dkrr():
     """p = 1: random, K-means, routed, per-model and averaged selection all
     reduce to Alg. 1 (DKRR)."""
