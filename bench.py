@@ -36,6 +36,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "KRR partition-solves/s & TFLOP/s vs plain FP64 at ≤1e-6 rel err; serve p50/p99"
 UNIT = "partition-solves/s"
+# arithmetic the path computes in, per factor precision: the factor's tensor-core
+# passes, then refinement with double-float (~44-bit) kernel entries and FP64 vectors
+DTYPE_LABEL = {"tf32": "fp16 1-pass / tf32x3 factor + df64 refinement",
+               "bf16x3": "bf16x3 / tf32x3 factor + df64 refinement",
+               "fp32": "tf32x3 factor + df64 refinement", "fp64": "f64"}
 
 
 def parse():
@@ -55,7 +60,11 @@ def parse():
                          "bkrr2kb: the bkrr2 data with K-balance partitions (routed); "
                          "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows; serve: the request "
                          "stream (Poisson 200/s, n log-uniform in [512, 16384]) through the serving loop")
-    ap.add_argument("--requests", type=int, default=1500, help="serve: requests replayed from the stream")
+    ap.add_argument("--requests", type=int, default=10000, help="serve: requests replayed from the stream")
+    ap.add_argument("--no-serve", action="store_true",
+                    help="bkrr2 line without its serve object (the request stream through the serving loop)")
+    ap.add_argument("--serve-bank", type=int, default=32,
+                    help="serve: mixtures drawn per feature count; requests take row prefixes (0 = one per request)")
     ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (one stream each)")
     ap.add_argument("--fp64-sample", type=int, default=24, help="serve: requests in the sequential FP64 sample")
     ap.add_argument("--precisions", default="",
@@ -77,15 +86,19 @@ def _oracle_solve(args):
     a, info, rc = oracle.fit(Xp, yp, sigma, lam)
     yh = oracle.predict(Xp, a, Xt, sigma)
     m = oracle.mse(yh, yt)
-    return time.perf_counter() - t0, m
+    return time.perf_counter() - t0, m, a, yh, float(info[0])
+
+
+def sample_models(p: int, G: int, count: int):
+    """(partition, grid point) of the solves the oracle recomputes: every
+    partition in turn, grid points spread over the sigma x lambda grid."""
+    return [(k % p, (k * 5 + 2) % G) for k in range(count)]
 
 
 def _oracle_jobs(w, perm, offsets, count):
     jobs = []
     G = len(w["sigmas"]) * len(w["lambdas"])
-    for k in range(count):
-        j = k % (len(offsets) - 1)
-        g = (k * 5 + 2) % G
+    for j, g in sample_models(len(offsets) - 1, G, count):
         si, li = divmod(g, len(w["lambdas"]))
         rows = perm[offsets[j]:offsets[j + 1]]
         jobs.append((w["X"][rows], w["y"][rows], w["Xt"], w["yt"], w["sigmas"][si], w["lambdas"][li]))
@@ -123,11 +136,41 @@ def cpu_baseline(w, sample: int):
     with ctx.Pool(processes=sample) as pool:
         res = pool.map(_oracle_solve, jobs)
     wall = time.perf_counter() - t0
-    return dict(value=sample / wall, unit=UNIT, cores=sample, kind="oracle", host=host_cpu(),
-                sample="%d of the %d (partition, sigma, lambda) solves of %s, one process each: kernel build + "
-                       "Cholesky + long-double refinement + prediction of all %d test rows + MSE; %.1f s wall"
-                       % (sample, w["p"] * len(w["sigmas"]) * len(w["lambdas"]), w["workload"],
-                          w["Xt"].shape[0], wall))
+    out = dict(value=sample / wall, unit=UNIT, cores=sample, kind="oracle", host=host_cpu(),
+               sample="%d of the %d (partition, sigma, lambda) solves of %s, one process each: kernel build + "
+                      "Cholesky + long-double refinement + prediction of all %d test rows + MSE; %.1f s wall"
+                      % (sample, w["p"] * len(w["sigmas"]) * len(w["lambdas"]), w["workload"],
+                         w["Xt"].shape[0], wall))
+    refs = [dict(alpha=r[2], yhat=r[3], mse=r[1], kappa=r[4]) for r in res]
+    return out, refs
+
+
+def rel_err(a, b) -> float:
+    """Max-norm relative error of a result vector against the oracle's."""
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    den = float(np.max(np.abs(b))) if b.size else 0.0
+    num = float(np.max(np.abs(a - b))) if b.size else 0.0
+    return num / den if den > 0 else num
+
+
+def accuracy_vs_oracle(gpu: dict, refs: list, pairs: list) -> dict:
+    """Per factor precision: the largest relative error of alpha, of the
+    predictions of every test row and of the MSE over the sampled solves."""
+    out = {}
+    for prec, got in gpu.items():
+        ea, ep, em = [], [], []
+        for (jg, ref) in zip(pairs, refs):
+            a, yh, m = got[jg]
+            ea.append(rel_err(a, ref["alpha"]))
+            ep.append(rel_err(yh, ref["yhat"]))
+            em.append(abs(m - ref["mse"]) / ref["mse"])
+        worst = int(np.argmax(ea))
+        out[prec] = {"max_rel_err_alpha": max(ea), "max_rel_err_pred": max(ep), "max_rel_err_mse": max(em),
+                     "worst_alpha_model": list(pairs[worst]),
+                     "worst_alpha_kappa": refs[worst]["kappa"],
+                     "failed_solves": got["failed"]}
+    return out
 
 
 # ---------------------------------------------------------------- clocks
@@ -225,6 +268,11 @@ def make_workload(args, rank):
     return synth.dkrr(seed=0 + rank, **kw)
 
 
+def oracle_sample_size(args) -> int:
+    """Solves the oracle recomputes in the CPU baseline (one process each)."""
+    return args.cpu_sample or max(1, min(16, os.cpu_count() or 1))
+
+
 def ctypes_int():
     return ctypes.c_int(0)
 
@@ -264,11 +312,13 @@ def run_ours(args, rank, world, local_rank):
         yhat_buf = torch.empty((G, t), dtype=torch.float64, device="cuda")
 
     last_offsets = [None]
+    last_route = [None]
 
     def step(Xd, yd, Xtd, ytd, prec):
         if kmeans:  # KKRR2 / K-balance BKRR2: clustered partitions, routed prediction and selection
             _, route, perm, offsets, _ = K.krr_partition(ctx, Xd, Xtd, pmode, p, iters=w["iters"],
                                                          init_idx=init_idx)
+            last_route[0] = route
             model, status, _ = K.krr_fit_batch(ctx, Xd, yd, perm, offsets, S, L, prec)
             yh = K.krr_predict(ctx, model, Xtd, route=route, out=yhat_buf)
             mse, best = K.krr_select(ctx, yh, ytd, p, G, K.KRR_SEL_ROUTED)
@@ -384,6 +434,33 @@ def run_ours(args, rank, world, local_rank):
         ms64 = e0.elapsed_time(e1)
         fp64 = {"value": nsolve / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                 "ok_solves": int((st64 == K.KRR_OK).sum().item())}
+
+    # ---- untimed fits: factor class of every solve (roofline), and the
+    # sampled models' alpha, predictions and MSE per precision (accuracy)
+    pairs = sample_models(p, G, oracle_sample_size(args)) if (rank == 0 and not kmeans) else []
+    precs = [args.prec] + ([q for q in ("fp64", "fp32", "tf32", "bf16x3") if q != args.prec]
+                           if (pairs and not args.no_cpu_baseline and world == 1) else [])
+    gpu_acc, classes = {}, None
+    for pr in precs:
+        if kmeans:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, X, Xt, pmode, p, iters=w["iters"], init_idx=init_idx)
+        else:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+        model, st, alpha = K.krr_fit_batch(ctx, X, y, perm, offsets, S, L, pr, want_alpha=bool(pairs))
+        if pr == args.prec:
+            classes = K.krr_model_factor_class(ctx, model).numpy()
+        if pairs and world == 1 and not args.no_cpu_baseline:
+            yh = K.krr_predict(ctx, model, Xt, out=yhat_buf)
+            mse_g, _ = K.krr_select(ctx, yh, yt, p, G, K.KRR_SEL_PER_MODEL)
+            al, off, yhn, msen = (alpha.cpu().numpy(), offsets.cpu().numpy(), yh.cpu().numpy(),
+                                  mse_g.cpu().numpy())
+            got = {"failed": int((st != K.KRR_OK).sum().item())}
+            for j, g in pairs:
+                mj = int(off[j + 1] - off[j])
+                a0 = int(off[j]) * G + g * mj
+                got[(j, g)] = (al[a0:a0 + mj].copy(), yhn[j * G + g].copy(), float(msen[j * G + g]))
+            gpu_acc[pr] = got
+        model.free()
     ctx.close()
 
     ms_per_step = total_ms / args.steps
@@ -395,62 +472,192 @@ def run_ours(args, rank, world, local_rank):
                 panel_width=panel_width,
                 launches=launches + flush_launches, e2e=dict(value=world * nsolve * args.steps / e2e_s, unit=UNIT,
                                                          h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
-                fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times)
+                fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times, classes=classes,
+                gpu_acc=gpu_acc, pairs=pairs,
+                route_counts=(np.bincount(last_route[0].cpu().numpy(), minlength=p) if kmeans else None))
 
 
-# DRAM bytes (read + write) per launch of the dominant kernel class, averaged
-# over its launches in one step, from one ncu capture of this bench's workload
-# at the panel width the autotuner picks (profiles/launch_list_bkrr2_n65536_p16.md);
-# an entry is removed whenever its kernel changes.
-TRAFFIC = {("update", "bkrr2_n65536_t8192_d90_p16", 8): 317845136,
-           ("predict", "bkrr2_n65536_t8192_d90_p16", 8): 303708416}
+# DRAM bytes (read + write) per launch from one ncu capture, keyed by kernel
+# class, workload and the SHA-256 (first 16 hex digits) of the source file
+# that defines the kernel: a figure whose kernel source has changed since the
+# capture is dropped (null), never reused.
+TRAFFIC = {}
+KERNEL_SOURCE = {"predict": "predict_oz.cu", "kbuild": "predict_oz.cu", "update": "chol.cu", "potrf": "chol.cu",
+                 "trsm": "chol.cu", "matvec": "pcg.cu", "precond": "pcg.cu", "partition": "partition.cu"}
+MUFU_PER_CLK_SM = 16      # nominal ex2 results per clock per SM
+FP64_PEAK_TFLOPS = 1.25   # nominal FP64 rate of GB300 (no FP64 tensor path)
 
 
-def roofline(res, steps, peaks):
-    """Roofline of the kernel class with the largest share of device time."""
-    prof = res["prof"]
+def _source_sha(kind: str) -> str | None:
+    import hashlib
+    f = KERNEL_SOURCE.get(kind)
+    if f is None:
+        return None
+    try:
+        with open(os.path.join(ROOT, "paper_1805_00569_gb300", "csrc", f), "rb") as fh:
+            return hashlib.sha256(fh.read()).hexdigest()[:16]
+    except OSError:
+        return None
+
+
+def _class_peak(cls: int, peaks: dict) -> float:
+    """Tensor-core peak (TFLOP/s) of the precision a factor class runs at:
+    one FP16 pass and three BF16 passes at the BF16 rate, three TF32 passes
+    at the TF32 rate (measured BF16 x nominal 1.1/2.25), FP64 at the nominal
+    FP64 rate (the algorithmic m^3/3 flops are charged against it, so
+    three-pass classes pay for their extra passes)."""
+    bf16 = peaks.get("bf16_tflops", 1885.0)
+    if cls in (1, 2):
+        return bf16
+    if cls in (3, 4):
+        return bf16 * 1.1 / 2.25
+    return FP64_PEAK_TFLOPS
+
+
+def factor_flops(m: int):
+    """Algorithmic flops of the blocked Cholesky of one m x m solve (128-wide
+    tiles): total m^3/3, split into the diagonal-tile factorisations, the
+    panel solves and the trailing updates."""
+    T = (m + 127) // 128
+    tot = m ** 3 / 3.0
+    potrf = T * 128 ** 3 / 3.0
+    trsm = T * (T - 1) / 2.0 * 128 ** 3
+    return tot, potrf, trsm, max(tot - potrf - trsm, 0.0)
+
+
+def stage_rooflines(res, peaks) -> dict:
+    """Each stage's measured time per step against the section 8(d) work of
+    the method (not of its implementation) and the roofline that bounds it."""
+    prof, nprof = res["prof"], max(res["nprof"], 1)
     w = res["w"]
     n, d = w["X"].shape
-    p = w["p"]
-    sizes = [int(v) for v in res["sizes"]]
-    m = n // p
-    G = len(w["sigmas"]) * len(w["lambdas"])
     t = w["Xt"].shape[0]
+    ns, nl = len(w["sigmas"]), len(w["lambdas"])
+    G = ns * nl
+    sizes = [int(v) for v in res["sizes"]]
+    clock = (res["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    hbm = peaks.get("hbm_gbs", 6779.4)
+    bf16 = peaks.get("bf16_tflops", 1885.0)
+    mufu = 152 * MUFU_PER_CLK_SM * clock * 1e6 / 1e9  # G exp / s
+    ms = {k: v[0] / nprof for k, v in prof.items()}
+    out = {}
+    routed = w["workload"].startswith(("kkrr2", "bkrr2kb"))
+    # a10 prediction: distances 2d flops per pair (tensor), one exponential per
+    # pair and sigma (MUFU), 2 flops per pair and model (contraction); bytes:
+    # the test and training rows once, (t + m) d 8 per partition
+    if ms.get("predict", 0) > 0:
+        if routed and res.get("route_counts") is not None:
+            pairs = float(sum(int(c) * m for c, m in zip(res["route_counts"], sizes)))
+        else:
+            pairs = float(t) * sum(sizes)
+        sec = ms["predict"] / 1e3
+        f_t = pairs * 2 * d / sec / 1e12 / bf16
+        f_m = pairs * ns / sec / 1e9 / mufu
+        byts = (len(sizes) * t + n) * d * 8.0
+        f_h = byts / sec / 1e9 / hbm
+        fr = {"tensor": f_t, "mufu": f_m, "hbm": f_h}
+        out["predict"] = {"ms": ms["predict"], "pairs": pairs, "tensor_frac": f_t, "mufu_frac": f_m, "hbm_frac": f_h,
+                          "binding": max(fr, key=fr.get), "frac": max(fr.values()),
+                          # the implementation's own work: double-float FP32 operations per pair
+                          "impl_fp32_ops_per_pair": 22 + ns * (7 + 41) + G * 12,
+                          "impl_alu_frac": pairs * (22 + ns * (7 + 41) + G * 12) / sec / 1e12
+                          / (152 * 128 * clock * 1e6 / 1e12)}
+    # a7 Cholesky: m^3/3 per solve at the rate of the precision each solve used
+    fk = [k for k in ("potrf", "trsm", "update") if ms.get(k, 0) > 0]
+    cls = res.get("classes")
+    if fk and cls is not None:
+        need = 0.0
+        upd_need = 0.0
+        for s_i, c in enumerate(cls):
+            m = sizes[s_i // G]
+            tot, _, _, upd = factor_flops(m)
+            need += tot / (_class_peak(int(c), peaks) * 1e12)
+            upd_need += upd / (_class_peak(int(c), peaks) * 1e12)
+        sec = sum(ms[k] for k in fk) / 1e3
+        out["factor"] = {"ms": sec * 1e3, "flops": float(sum(factor_flops(sizes[i // G])[0] for i in range(len(cls)))),
+                         "classes": {str(c): int((cls == c).sum()) for c in sorted(set(int(x) for x in cls))},
+                         "frac": need / sec, "ms_at_peak": need * 1e3,
+                         "update_frac": upd_need / (ms["update"] / 1e3) if ms.get("update", 0) > 0 else None}
+    # a6 kernel build: tensor (m^2 d flops per partition, distances once), MUFU
+    # (m^2/2 exponentials per partition and sigma), HBM (4 bytes per stored
+    # kernel entry: m^2/2 per partition and sigma)
+    if ms.get("kbuild", 0) > 0:
+        sec = ms["kbuild"] / 1e3
+        ent = sum(m * m / 2.0 for m in sizes) * ns
+        f_t = sum(m * m * d for m in sizes) / sec / 1e12 / bf16
+        f_m = ent / sec / 1e9 / mufu
+        f_h = ent * 4 / sec / 1e9 / hbm
+        fr = {"tensor": f_t, "mufu": f_m, "hbm": f_h}
+        out["kbuild"] = {"ms": ms["kbuild"], "tensor_frac": f_t, "mufu_frac": f_m, "hbm_frac": f_h,
+                         "binding": max(fr, key=fr.get), "frac": max(fr.values())}
+    # a3/a4 K-means: per round the FP32 copy of X read and the assignment
+    # written, the FP64 rows read by the centre update, plus the final pass
+    if routed and ms.get("partition", 0) > 0:
+        iters = int(w.get("iters", 0))
+        dpad = (d + 7) // 8 * 8
+        byts = (iters + 1) * (n * dpad * 4 + 4 * n) + iters * n * d * 8
+        sec = ms["partition"] / 1e3
+        out["kmeans"] = {"ms": ms["partition"], "bytes": byts, "hbm_frac": byts / sec / 1e9 / hbm,
+                         "frac": byts / sec / 1e9 / hbm, "binding": "hbm"}
+    return out
+
+
+def roofline(res, stages, peaks):
+    """Roofline object of the kernel class with the largest share of device
+    time, from its section 8(d) stage figures."""
+    prof, nprof = res["prof"], max(res["nprof"], 1)
     dom = max(prof, key=lambda k: prof[k][0])
     ms, launches = prof[dom]
-    clock = (res["clocks"] or {}).get("sm_mhz") or 1455.0
-    fp32_peak = 152 * 128 * clock * 1e6 / 1e12  # FP32 operations per second at the sampled clock
-    tf32_peak = peaks.get("bf16_tflops_sustained", 1715.4) * (1.1 / 2.25)
+    w = res["w"]
+    hbm = peaks.get("hbm_gbs", 6779.4)
+    bf16 = peaks.get("bf16_tflops", 1885.0)
+    clock = (res["clocks"] or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     out = {"kernel": dom, "launches": launches, "avg_launch_ms": ms / max(launches, 1),
            "share": ms / sum(v[0] for v in prof.values())}
-    if dom == "update":
-        flops = steps * G * sum(mm ** 3 / 3.0 for mm in sizes)
-        out.update(bound="tensor", achieved=flops / (ms / 1e3) / 1e12, peak=tf32_peak, unit="TFLOP/s",
-                   peak_note="TF32 = measured bf16 sustained x nominal TF32/BF16 ratio (1.1/2.25), of measured")
-    elif dom in ("kbuild", "predict"):
-        # double-float work in FP32 operations, counted from the kernels' design:
-        # distance assembly from the five exact slice levels 22 per pair; per sigma
-        # a double-float product 7 and exponential 44 (41 unnormalised in the
-        # prediction); per (sigma, lambda) one double-float multiply-accumulate
-        # 12 (predict) or two stores (kbuild)
-        ns = len(w["sigmas"])
-        if dom == "kbuild":
-            per_pair = 22 + ns * (7 + 44 + 4) + G * 2
-            pairs = steps * sum(mm * mm / 2.0 for mm in sizes)
+    per = ms / nprof / 1e3  # seconds per step
+    if dom == "predict" and "predict" in stages:
+        st = stages["predict"]
+        b = st["binding"]
+        if b == "tensor":
+            out.update(bound="tensor", achieved=st["tensor_frac"] * bf16, peak=bf16, unit="TFLOP/s",
+                       peak_note="BF16 dense burst, of measured; 2d flops per (test, training) pair")
+        elif b == "hbm":
+            out.update(bound="hbm", achieved=st["hbm_frac"] * hbm, peak=hbm, unit="GB/s",
+                       peak_note="copy bandwidth, of measured; (t + m) d 8 bytes per partition")
         else:
-            per_pair = 22 + ns * (7 + 41) + G * 12
-            pairs = steps * sum(t * mm for mm in sizes)
-        out.update(bound="alu", achieved=pairs * per_pair / (ms / 1e3) / 1e12, peak=fp32_peak, unit="TFLOP/s",
-                   peak_note="FP32 issue peak = 152 SMs x 128 lanes x sampled SM clock (one FP32 op per lane per "
-                             "cycle); achieved = designed FP32 operations of the double-float arithmetic "
-                             "(%d per pair) x pairs / kernel time" % per_pair)
+            mufu = 152 * MUFU_PER_CLK_SM * clock * 1e6 / 1e9
+            out.update(bound="alu", achieved=st["mufu_frac"] * mufu, peak=mufu, unit="Gexp/s",
+                       peak_note="MUFU ex2 rate, nominal 16 per clock per SM x 152 SMs x sampled SM clock; one "
+                                 "exponential per (test, training) pair and sigma")
+        out.update(stage_fracs={"tensor": st["tensor_frac"], "mufu": st["mufu_frac"], "hbm": st["hbm_frac"]},
+                   impl_alu_frac=st["impl_alu_frac"],
+                   impl_note="impl_alu_frac: the kernel's designed double-float FP32 operations "
+                             "(%d per pair) against 152 x 128 FP32 lanes x clock" % st["impl_fp32_ops_per_pair"])
+    elif dom in ("update", "potrf", "trsm") and "factor" in stages:
+        st = stages["factor"]
+        cls = res["classes"]
+        G = len(w["sigmas"]) * len(w["lambdas"])
+        sizes = [int(v) for v in res["sizes"]]
+        idx = {"potrf": 1, "trsm": 2, "update": 3}[dom]
+        flops = sum(factor_flops(sizes[i // G])[idx] for i in range(len(cls)))
+        need = sum(factor_flops(sizes[i // G])[idx] / (_class_peak(int(c), peaks) * 1e12) for i, c in enumerate(cls))
+        achieved = flops / per / 1e12
+        out.update(bound="tensor", achieved=achieved, peak=achieved / (need / per), unit="TFLOP/s",
+                   peak_note="per solve the tensor peak of its factor class (FP16/BF16 = BF16 burst, of measured; "
+                             "three-pass TF32 = BF16 x 1.1/2.25); peak = the flop-weighted harmonic mean")
+    elif dom == "kbuild" and "kbuild" in stages:
+        st = stages["kbuild"]
+        out.update(bound="hbm", achieved=st["hbm_frac"] * hbm, peak=hbm, unit="GB/s",
+                   peak_note="copy bandwidth, of measured; 4 bytes per stored kernel entry (m^2/2 per sigma)",
+                   stage_fracs={"tensor": st["tensor_frac"], "mufu": st["mufu_frac"], "hbm": st["hbm_frac"]})
+    elif dom == "partition" and "kmeans" in stages:
+        st = stages["kmeans"]
+        out.update(bound="hbm", achieved=st["hbm_frac"] * hbm, peak=hbm, unit="GB/s",
+                   peak_note="copy bandwidth, of measured")
     else:
-        tiles = (m // 128) * (m // 128 + 1) // 2 + m // 128
-        byts = steps * p * G * tiles * 128 * 128 * 4 * 2 * max(1, launches // max(steps, 1)) / max(1, G)
-        out.update(bound="hbm", achieved=byts / (ms / 1e3) / 1e9, peak=peaks.get("hbm_gbs", 6797.9), unit="GB/s",
-                   peak_note="measured copy bandwidth; bytes assume every solve active (upper bound)")
-    out["frac"] = out["achieved"] / out["peak"]
-    out["traffic"] = TRAFFIC.get((dom, w["workload"], res.get("panel_width")))
+        out.update(bound="hbm", achieved=None, peak=hbm, unit="GB/s", peak_note="no section 8(d) figure")
+    out["frac"] = (out["achieved"] / out["peak"]) if out.get("achieved") is not None else None
+    out["traffic"] = TRAFFIC.get((dom, w["workload"], _source_sha(dom)))
     if out["traffic"] is not None:
         out["traffic_unit"] = "bytes per launch (DRAM read + write)"
     return out
@@ -471,7 +678,7 @@ def run_serve(args, rank, world, local_rank):
     data = lambda seed, n, d, t: synth.serve_request_data(seed, n, d, t)
     st = synth.serve_stream(seed=4 + rank, requests=args.requests)
     t = int(st["t"])
-    reqs = make_stream_requests(st, args.requests, data, t=t)
+    reqs = make_stream_requests(st, args.requests, data, t=t, bank=args.serve_bank)
     warm = make_stream_requests(synth.serve_stream(seed=1000 + rank, requests=max(args.warmup, 1) * 8),
                                 max(args.warmup, 1) * 8, data, t=t)
     budget = 120 << 30
@@ -523,7 +730,7 @@ def main_serve(args, rank, world, local_rank):
     print(json.dumps({
         "metric": METRIC, "value": res["value"], "unit": "requests/s", "n_gpus": world, "steps": args.requests,
         "warmup": args.warmup, "ms_per_step": 1e3 * res["span"] / args.requests, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "tf32+f64" if args.prec == "tf32" else args.prec,
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_LABEL.get(args.prec, args.prec),
         "data": "synthetic",
         "config": {"workload": "serve: %d requests, Poisson %.0f/s, n log-uniform [512, 16384], d in {8, 32, 90}, "
                                "256 test rows each, repeat predicts 20%%" % (args.requests, res["offered"]),
@@ -576,11 +783,13 @@ def main():
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         peaks = {}
-    roof = roofline(res, res["nprof"], peaks)
-    cpu = None
+    stages = stage_rooflines(res, peaks)
+    roof = roofline(res, stages, peaks)
+    cpu, accuracy = None, None
     if world == 1 and not args.no_cpu_baseline:
-        sample = args.cpu_sample or max(1, min(16, os.cpu_count() or 1))
-        cpu = cpu_baseline(res["w"], sample)
+        cpu, refs = cpu_baseline(res["w"], oracle_sample_size(args))
+        if res["gpu_acc"]:
+            accuracy = accuracy_vs_oracle(res["gpu_acc"], refs, res["pairs"])
     if args.profile:
         sys.stderr.write(json.dumps({k: [round(v[0], 3), v[1]] for k, v in res["prof"].items()}) + "\n")
         sys.stderr.write("step ms: %s\n" % [round(x, 2) for x in res["times"]])
@@ -588,7 +797,7 @@ def main():
     line = {
         "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"tf32": "tf32+f64", "bf16x3": "bf16x3+f64", "fp32": "f32+f64"}.get(args.prec, "f64"),
+        "vs_baseline": None, "dtype": DTYPE_LABEL.get(args.prec, "f64"),
         "data": "synthetic",
         "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": args.prec,
                    "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]),
@@ -599,10 +808,40 @@ def main():
         "clocks": res["clocks"], "gpu_launches": res["launches"], "fp64_path": res["fp64"],
         "failed_solves": res["bad"], "best_model": res["best"], "best_mse": res["best_mse"],
         "stages_ms_per_step": {k: v[0] / res["nprof"] for k, v in res["prof"].items()},
+        "stage_roofline": stages,
+        "accuracy_vs_oracle": accuracy,
     }
+    if accuracy is not None:
+        line["accuracy_note"] = ("max-norm relative errors against the FP64 oracle on the %d sampled solves of the "
+                                 "CPU baseline (alpha, predictions of all %d test rows, MSE), per factor precision; "
+                                 "the plain FP64 path's 1e-10 bar applies where kappa * 2^-53 <= 1e-11"
+                                 % (len(res["pairs"]), w["Xt"].shape[0]))
     if sweep is not None:
         line["precision_sweep"] = sweep
+    if world == 1 and args.workload == "bkrr2" and not args.no_serve:
+        sv = run_serve(args, rank, world, local_rank)
+        line["serve"] = serve_object(args, sv)
+        line["serve"]["fp64_sequential"] = sv["seq"]
+        line["serve"]["clocks"] = sv["clocks"]
+        line["serve"]["gpu_launches"] = sv["launches"]
     print(json.dumps(line))
+
+
+def serve_object(args, res) -> dict:
+    """The request stream's figures: latency at the offered load, capacity
+    with every request queued at once, completions and admission peaks."""
+    return {"workload": "serve: %d requests, Poisson %.0f/s offered, n log-uniform [512, 16384], d in {8, 32, 90}, "
+                        "sigma log-uniform [0.5, 16], lambda log-uniform [1e-7, 1e-3], 256 test rows each, repeat "
+                        "predicts 20%%, %s" % (args.requests, res["offered"],
+                                               "row prefixes of %d mixtures per d" % args.serve_bank
+                                               if args.serve_bank else "one mixture per request"),
+            "slots": args.slots, "hbm_budget_gb": 120, "prec": args.prec,
+            "offered_rps": res["offered"], "p50_ms": res["live"]["p50_ms"], "p99_ms": res["live"]["p99_ms"],
+            "completed": res["live"]["completed"], "requests": args.requests,
+            "at_offered_load": res["live"], "saturated": res["cap"], "saturated_rps": res["value"],
+            "peak_concurrency": res["peak_conc"], "peak_admitted_bytes": res["peak_bytes"], "fits": res["fits"],
+            "e2e_note": "every request's latency includes its host-to-device copies and the read-back of its "
+                        "predictions"}
 
 
 def run_reference(args, rank, world):
@@ -613,7 +852,7 @@ def run_reference(args, rank, world):
     sample = args.cpu_sample or max(1, min(16, os.cpu_count() or 1))
     vals = []
     for i in range(args.warmup + args.steps):
-        r = cpu_baseline(w, sample)
+        r, _ = cpu_baseline(w, sample)
         if i >= args.warmup:
             vals.append(sample / r["value"])
     wall = sum(vals)

@@ -181,6 +181,15 @@ krr_status krr_select(krr_ctx *ctx, const double *yhat, const double *yt, int64_
 krr_status krr_model_stats(krr_ctx *ctx, const krr_model *model, int32_t *iters, double *kappa_est,
                            double *resid);
 
+/* Factor class of every solve of a fitted model (HOST output, p*ns*nl
+ * entries): 0 FP64 (plain path), 1 one FP16 tensor-core pass (TF32-class),
+ * 2 three BF16 passes on split operands, 3 three TF32 passes on operands
+ * split by the panel solve (FP32-class), 4 three TF32 passes split in shared
+ * memory (the refactorisation after a low-precision breakdown).  No
+ * counterpart in the paper; used to attribute factor time to the tensor-core
+ * rate each solve ran at.  Errors: KRR_ERR_ARG. */
+krr_status krr_model_factor_class(krr_ctx *ctx, const krr_model *model, int32_t *cls);
+
 /* Release a model's device memory. */
 krr_status krr_model_free(krr_ctx *ctx, krr_model *model);
 
@@ -242,6 +251,18 @@ krr_status krr_gather_noalloc(void *cuda_stream, const int32_t *assign, int64_t 
  *   0 escalates every solve.  Errors: KRR_ERR_ARG (negative).
  * krr_launch_count: kernels launched by this process through libkrr. */
 krr_status krr_ctx_set_profiling(krr_ctx *ctx, int on);
+/* krr_ctx_wait_probe: self-check of the bounded device waits that every
+ *   pipelined kernel of the library uses (no counterpart in the paper).  A
+ *   one-CTA kernel starts a 4 KB bulk copy into shared memory, then waits on
+ *   an mbarrier that nothing ever completes; the wait gives up after
+ *   `seconds`, records KRR_ERR_TIMEOUT in the context's device error word,
+ *   waits (bounded) for its own copy to land and exits, as the pipelined
+ *   kernels do when a producer never delivers.  Returns KRR_ERR_TIMEOUT when
+ *   all of that happened (the context stays usable; the error word is
+ *   cleared), KRR_ERR_CUDA when the wait or the copy misbehaved or a CUDA
+ *   call failed, KRR_ERR_ARG for seconds outside [1e-6, 10].  Synchronises
+ *   the stream. */
+krr_status krr_ctx_wait_probe(krr_ctx *ctx, double seconds);
 krr_status krr_ctx_profile(krr_ctx *ctx, int kind, double *total_ms, long long *launches);
 krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
 krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);

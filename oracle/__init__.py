@@ -68,6 +68,8 @@ def _load():
             lib.orc_partition_random.argtypes = [i64, i32, u64, P, P, P]
             lib.orc_assign.argtypes = [P, i64, i32, P, i32, P]
             lib.orc_update_centres.argtypes = [P, i64, i32, P, i32, P]
+            lib.orc_block_sums.argtypes = [P, i64, i32, P, i32, P, P]
+            lib.orc_tree_combine.argtypes = [P, P, i64, i32, i32, P]
             lib.orc_kmeans.argtypes = [P, i64, i32, i32, P, i32, P, P, P]
             lib.orc_kmeans.restype = i32
             lib.orc_gather_stable.argtypes = [P, i64, i32, P, P]
@@ -133,6 +135,31 @@ def update_centres(X, c, C_prev):
     c = _c(c, np.int32)
     C = np.array(C_prev, dtype=np.float64, copy=True, order="C")
     _load().orc_update_centres(_p(X), X.shape[0], X.shape[1], _p(c), C.shape[0], _p(C))
+    return C
+
+
+def block_sums(X, c, k: int):
+    """First half of Alg. 2 step 6 in the canonical order: per block of 1024
+    consecutive rows (from row 0 of X), every centre's member sum in
+    ascending row order and its member count.  Returns (sums [nblk, k, d],
+    counts [nblk, k])."""
+    X = _c(X, np.float64)
+    c = _c(c, np.int32)
+    nblk = -(-X.shape[0] // 1024)
+    part = np.zeros((nblk, k, X.shape[1]), np.float64)
+    cnt = np.zeros((nblk, k), np.int64)
+    _load().orc_block_sums(_p(X), X.shape[0], X.shape[1], _p(c), k, _p(part), _p(cnt))
+    return part, cnt
+
+
+def tree_combine(sums, counts, C_prev):
+    """Second half of Alg. 2 step 6: the pairwise tree over the block sums in
+    block order, one division by the member count; empty clusters keep
+    their previous centre."""
+    part = np.array(sums, dtype=np.float64, copy=True, order="C")
+    cnt = _c(counts, np.int64)
+    C = np.array(C_prev, dtype=np.float64, copy=True, order="C")
+    _load().orc_tree_combine(_p(part), _p(cnt), part.shape[0], C.shape[0], C.shape[1], _p(C))
     return C
 
 

@@ -166,25 +166,34 @@ void orc_assign(const double *X, int64_t n, int32_t d, const double *CT,
 
 #define CANON_BLOCK 1024
 
-/* Alg. 2 step 6 with R4 and R6: CT_j = (sum of members) / (member count). */
-void orc_update_centres(const double *X, int64_t n, int32_t d,
-                        const int32_t *c, int32_t k, double *CT)
+/* Alg. 2 step 6, first half (R6): per block of CANON_BLOCK consecutive rows
+ * starting at row 0 of X, each centre's member sum taken in ascending row
+ * order from 0, and its member count.  part [nblk][k][d], cnt [nblk][k]. */
+void orc_block_sums(const double *X, int64_t n, int32_t d, const int32_t *c, int32_t k,
+                    double *part, int64_t *cnt)
 {
     int64_t nblk = (n + CANON_BLOCK - 1) / CANON_BLOCK;
-    if (nblk == 0) return;
-    double *part = (double *)calloc((size_t)nblk * k * d, sizeof(double));
-    int64_t *cnt = (int64_t *)calloc((size_t)k, sizeof(int64_t));
+    for (int64_t e = 0; e < nblk * (int64_t)k * d; ++e) part[e] = 0.0;
+    for (int64_t e = 0; e < nblk * (int64_t)k; ++e) cnt[e] = 0;
     for (int64_t b = 0; b < nblk; ++b) {
         double *S = part + b * (int64_t)k * d;
         int64_t hi = (b + 1) * CANON_BLOCK < n ? (b + 1) * CANON_BLOCK : n;
         for (int64_t i = b * CANON_BLOCK; i < hi; ++i) {
             int32_t j = c[i];
-            cnt[j] += 1;
+            cnt[b * k + j] += 1;
             for (int32_t f = 0; f < d; ++f)
                 S[(int64_t)j * d + f] = S[(int64_t)j * d + f] + X[i * d + f];
         }
     }
-    /* Pairwise tree over blocks, level by level, in block order. */
+}
+
+/* Alg. 2 step 6, second half (R4, R6): the block sums combined by a pairwise
+ * tree over blocks, level by level in block order (an odd last block carried
+ * up), then one division by the centre's member count; a centre with no
+ * members keeps its entry of CT.  part is overwritten. */
+void orc_tree_combine(double *part, const int64_t *cnt, int64_t nblk, int32_t k, int32_t d, double *CT)
+{
+    if (nblk == 0) return;
     int64_t len = nblk;
     while (len > 1) {
         int64_t half = (len + 1) / 2;
@@ -201,10 +210,24 @@ void orc_update_centres(const double *X, int64_t n, int32_t d,
         len = half;
     }
     for (int32_t j = 0; j < k; ++j) {
-        if (cnt[j] == 0) continue; /* R4 */
+        int64_t m = 0;
+        for (int64_t b = 0; b < nblk; ++b) m += cnt[b * k + j];
+        if (m == 0) continue; /* R4 */
         for (int32_t f = 0; f < d; ++f)
-            CT[(int64_t)j * d + f] = part[(int64_t)j * d + f] / (double)cnt[j];
+            CT[(int64_t)j * d + f] = part[(int64_t)j * d + f] / (double)m;
     }
+}
+
+/* Alg. 2 step 6 with R4 and R6: CT_j = (sum of members) / (member count). */
+void orc_update_centres(const double *X, int64_t n, int32_t d,
+                        const int32_t *c, int32_t k, double *CT)
+{
+    int64_t nblk = (n + CANON_BLOCK - 1) / CANON_BLOCK;
+    if (nblk == 0) return;
+    double *part = (double *)calloc((size_t)nblk * k * d, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)nblk * k, sizeof(int64_t));
+    orc_block_sums(X, n, d, c, k, part, cnt);
+    orc_tree_combine(part, cnt, nblk, k, d, CT);
     free(part);
     free(cnt);
 }

@@ -68,6 +68,7 @@ def load(build_if_missing: bool = True):
     L.krr_ctx_get_panel_width.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.krr_ctx_set_target_error.argtypes = [P, ctypes.c_double]
     L.krr_ctx_set_escalation.argtypes = [P, ctypes.c_double]
+    L.krr_ctx_wait_probe.argtypes = [P, ctypes.c_double]
     L.krr_launch_count.restype = ctypes.c_longlong
     L.krr_partition.argtypes = [P, P, i64, i32, P, i64, ctypes.c_int, i32, i32, u64, P, P, P, P, P, P]
     L.krr_fit_batch.argtypes = [P, P, P, i64, i32, P, P, i32, P, i32, P, i32, ctypes.c_int,
@@ -76,10 +77,11 @@ def load(build_if_missing: bool = True):
     L.krr_select.argtypes = [P, P, P, i64, i32, i32, ctypes.c_int, P, P]
     L.krr_model_stats.argtypes = [P, P, P, P, P]
     L.krr_model_free.argtypes = [P, P]
+    L.krr_model_factor_class.argtypes = [P, P, P]
     for name in ("krr_ctx_create", "krr_ctx_destroy", "krr_ctx_set_profiling", "krr_ctx_profile",
                  "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error",
-                 "krr_ctx_set_escalation", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
-                 "krr_model_stats", "krr_model_free"):
+                 "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
+                 "krr_model_stats", "krr_model_free", "krr_model_factor_class"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -184,6 +186,12 @@ def krr_ctx_set_escalation(ctx: Context, kappa_u: float):
     ctx.check(ctx.lib.krr_ctx_set_escalation(ctx.handle, float(kappa_u)), "krr_ctx_set_escalation")
 
 
+def krr_ctx_wait_probe(ctx: Context, seconds: float) -> int:
+    """Runs the bounded-wait self-check; returns its status (KRR_ERR_TIMEOUT
+    when the wait expired as designed and the context stays usable)."""
+    return int(ctx.lib.krr_ctx_wait_probe(ctx.handle, float(seconds)))
+
+
 def krr_partition(ctx: Context, X: torch.Tensor, Xt: torch.Tensor | None, mode: int, p: int, iters: int = 0,
                   seed: int = 0, init_idx: torch.Tensor | None = None):
     """Returns (assign, route, perm, offsets, centers) as device tensors."""
@@ -265,6 +273,14 @@ def krr_model_stats(ctx: Context, model: Model):
                                  ctypes.c_void_p(ka.data_ptr()), ctypes.c_void_p(rs.data_ptr()))
     ctx.check(rc, "krr_model_stats")
     return it, ka, rs
+
+
+def krr_model_factor_class(ctx: Context, model: Model):
+    """Factor class of every solve (host int32 tensor; see include/krr.h)."""
+    cls = torch.zeros(model.p * model.G, dtype=torch.int32)
+    ctx.check(ctx.lib.krr_model_factor_class(ctx.handle, model.handle, ctypes.c_void_p(cls.data_ptr())),
+              "krr_model_factor_class")
+    return cls
 
 
 def krr_model_free(ctx: Context, model: Model):

@@ -150,6 +150,36 @@ __global__ void reform_kernel(const SolveDesc *__restrict__ sub, const int64_t *
     }
 }
 
+// A wait that nothing completes while a bulk copy of the CTA's own is in
+// flight: the deadline path of the pipelined kernels in miniature.  Every
+// thread waits on bars[1], which never gets an arrival, until limit_ns
+// passes; then the CTA waits (bounded) for its copy on bars[0] to land before
+// it exits, and thread 0 reports the sum of the landed data (-1 if the
+// never-completed wait returned as completed).
+__global__ void wait_probe_kernel(const float4 *__restrict__ src, float *__restrict__ sum_out, int *err,
+                                  uint64_t limit_ns) {
+    __shared__ __align__(128) float4 buf[256];  // 4 KB landing zone of the copy
+    __shared__ __align__(8) uint64_t bars[2];
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bars[0], (uint32_t)sizeof(buf));
+        bulk_g2s(buf, src, (uint32_t)sizeof(buf), &bars[0]);
+    }
+    const bool got = mbar_wait_until(&bars[1], 0, err, limit_ns, KRR_ERR_TIMEOUT);
+    const bool landed = mbar_wait_until(&bars[0], 0, err, KRR_WAIT_LIMIT_NS, KRR_ERR_TIMEOUT);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.f;
+        for (int i = 0; landed && i < 256; ++i) s += (buf[i].x + buf[i].y) + (buf[i].z + buf[i].w);
+        sum_out[0] = got ? -1.f : (landed ? s : -2.f);
+    }
+}
+
 struct DevBuf {
     Ctx *c;
     std::vector<std::pair<void *, size_t>> list;
@@ -279,6 +309,37 @@ krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u) {
     if (!ctx || !(kappa_u >= 0.0)) return KRR_ERR_ARG;
     ctx->c.escalate = kappa_u;
     return KRR_OK;
+}
+
+krr_status krr_ctx_wait_probe(krr_ctx *ctx, double seconds) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (!(seconds >= 1e-6 && seconds <= 10.0)) return fail(c, KRR_ERR_ARG, "krr_ctx_wait_probe: seconds outside [1e-6, 10]");
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    const size_t bytes = 4096 + 256;
+    void *buf = nullptr;
+    API_TRY(c, ctx_malloc(c, &buf, bytes));
+    float ones[1024];
+    for (int i = 0; i < 1024; ++i) ones[i] = 1.0f;
+    float sum = 0.f;
+    int herr = 0;
+    cudaError_t e = cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf, ones, sizeof(ones), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) {
+        KRR_LAUNCHED(), wait_probe_kernel<<<1, 128, 0, st>>>((const float4 *)buf, (float *)((char *)buf + 4096),
+                                                              c->d_err, (uint64_t)(seconds * 1e9));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&sum, (char *)buf + 4096, sizeof(float), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_err, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    ctx_free(c, buf, bytes);
+    API_TRY(c, e);
+    if (sum != 1024.0f) return fail(c, KRR_ERR_CUDA, "krr_ctx_wait_probe: the copy in flight did not land intact");
+    if (herr != KRR_ERR_TIMEOUT) return fail(c, KRR_ERR_CUDA, "krr_ctx_wait_probe: the wait did not report expiry");
+    return fail(c, KRR_ERR_TIMEOUT, "krr_ctx_wait_probe: the bounded wait expired as designed");
 }
 
 krr_status krr_ctx_set_kernel(krr_ctx *ctx, krr_kernel kind) {
@@ -885,6 +946,13 @@ krr_status krr_model_stats(krr_ctx *ctx, const krr_model *model, int32_t *iters,
     if (iters) std::copy(M.st_iters.begin(), M.st_iters.end(), iters);
     if (kappa_est) std::copy(M.st_kappa.begin(), M.st_kappa.begin() + n, kappa_est);
     if (resid) std::copy(M.st_resid.begin(), M.st_resid.begin() + n, resid);
+    return KRR_OK;
+}
+
+krr_status krr_model_factor_class(krr_ctx *ctx, const krr_model *model, int32_t *cls) {
+    if (!ctx || !model || !cls) return KRR_ERR_ARG;
+    const Model &M = model->m;
+    std::copy(M.st_class.begin(), M.st_class.end(), cls);
     return KRR_OK;
 }
 

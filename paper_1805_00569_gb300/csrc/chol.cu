@@ -380,23 +380,9 @@ template <int MODE> struct TcCfg {
     static_assert(SMEM <= 232448, "tile kernel shared memory");
 };
 
-__device__ __forceinline__ uint64_t global_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-// wait with a ~2 s deadline; on expiry set *err and return false
+// wait with the library's deadline; on expiry set *err and return false
 __device__ __forceinline__ bool mbar_wait_deadline(uint64_t *bar, uint32_t parity, int *err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = global_ns();
-    for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > 2000000000ull) {
-            atomicExch(err, KRR_ERR_TIMEOUT);
-            return false;
-        }
-    }
+    return mbar_wait_until(bar, parity, err, KRR_WAIT_LIMIT_NS, KRR_ERR_TIMEOUT);
 }
 
 template <int MODE>

@@ -204,13 +204,31 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait: gives up after ~2^26 polls (each try_wait itself blocks for a
-// hardware-defined interval), sets *err and returns false.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *err, int code) {
-    for (uint32_t it = 0; it < (1u << 26); ++it)
-        if (mbar_try_wait(bar, parity)) return true;
-    if (err) atomicExch(err, code);
-    return false;
+__device__ __forceinline__ uint64_t global_time_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+// Every spin-wait of the library's kernels on an mbarrier gives up after this
+// long (a producer that never completes must not hang the GPU).
+#define KRR_WAIT_LIMIT_NS 2000000000ull
+// Bounded wait for phase `parity` of *bar: polls until it completes or
+// limit_ns of the global timer have passed; on expiry stores `code` in *err
+// and returns false.  The caller then stops issuing work that depends on the
+// barrier, still waits (bounded) for any bulk copy it has in flight, frees
+// what it holds and returns.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns,
+                                                int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_time_ns();
+    for (;;) {
+        for (int i = 0; i < 256; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_time_ns() - t0 > limit_ns) {
+            if (err) atomicExch(err, code);
+            return false;
+        }
+    }
 }
 
 // 1-D bulk copy global -> shared, completion counted on an mbarrier.

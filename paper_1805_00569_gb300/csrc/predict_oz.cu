@@ -106,22 +106,8 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float *v) {
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 
-__device__ __forceinline__ uint64_t oz_ns() {
-    uint64_t t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
 __device__ __forceinline__ bool oz_wait(uint64_t *bar, uint32_t parity, int *err) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t t0 = oz_ns();
-    for (;;) {
-        for (int i = 0; i < 256; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if (oz_ns() - t0 > 2000000000ull) {
-            atomicExch(err, KRR_ERR_TIMEOUT);
-            return false;
-        }
-    }
+    return mbar_wait_until(bar, parity, err, KRR_WAIT_LIMIT_NS, KRR_ERR_TIMEOUT);
 }
 
 // Squared distance ||a||^2 + ||b||^2 - 2 a.b from the five exact slice levels

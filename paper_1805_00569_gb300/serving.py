@@ -299,15 +299,23 @@ class GpuExecutor:
             c.close()
 
 
-def make_stream_requests(stream: dict, count: int, data_fn, t: int = 256) -> list[Request]:
+def make_stream_requests(stream: dict, count: int, data_fn, t: int = 256, bank: int = 0) -> list[Request]:
     """Requests from a synthetic serving stream (arrival times and shapes);
     `data_fn(seed, n, d, t)` returns X, y, Xt and the mixture's parameters.  A
     repeat request predicts new test rows, drawn from the mixture of an
     earlier request, with that request's model; it carries that request's
-    training rows too, so it refits if the model has been evicted."""
+    training rows too, so it refits if the model has been evicted.
+
+    bank > 0: instead of one data set per request, `bank` mixtures per
+    feature count are drawn once at the stream's largest n, and a request
+    takes the first n (shuffled) rows of the one its data seed picks -- the
+    same shapes, sigma, lambda and arrivals, without drawing gigabytes of rows
+    for a long stream."""
     from .synth import serve_repeat_rows
     reqs = []
     fitted = []
+    n_max = int(max(stream["n"][:count])) if count else 0
+    banked: dict = {}
     for i in range(count):
         if stream["repeat"][i] and fitted:
             j = fitted[(i * 7919) % len(fitted)]
@@ -317,7 +325,14 @@ def make_stream_requests(stream: dict, count: int, data_fn, t: int = 256) -> lis
                                 True, {"X": base.payload["X"], "y": base.payload["y"], "Xt": Xt}))
             continue
         n, d = int(stream["n"][i]), int(stream["d"][i])
-        data = data_fn(int(stream["data_seed"][i]), n, d, t)
+        if bank > 0:
+            b = int(stream["data_seed"][i] % bank)
+            if (d, b) not in banked:
+                banked[(d, b)] = data_fn(1000003 * d + b, n_max, d, t)
+            src = banked[(d, b)]
+            data = dict(X=src["X"][:n], y=src["y"][:n], Xt=src["Xt"], yt=src["yt"], mix=src["mix"])
+        else:
+            data = data_fn(int(stream["data_seed"][i]), n, d, t)
         reqs.append(Request(i, float(stream["arrival"][i]), "req%d" % i, n, d, float(stream["sigma"][i]),
                             float(stream["lam"][i]), False, data))
         fitted.append(i)

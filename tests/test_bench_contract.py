@@ -12,41 +12,83 @@ import bench  # noqa: E402
 PEAKS = {"hbm_gbs": 6797.9, "bf16_tflops": 1885.0, "bf16_tflops_sustained": 1715.4}
 
 
-def _res(dominant, ms=7.2, panel=8):
-    prof = {k: (0.1, 5) for k in ("partition", "stage", "kbuild", "potrf", "trsm", "update", "matvec", "precond",
-                                  "pcgvec", "predict", "select")}
+def _res(dominant, ms=7.2, classes=None):
+    prof = {k: (0.1 * 5, 5) for k in ("partition", "stage", "kbuild", "potrf", "trsm", "update", "matvec",
+                                      "precond", "pcgvec", "predict", "select")}
     prof[dominant] = (ms * 5, 5 * (62 if dominant == "update" else 1))
     w = dict(X=np.zeros((65536, 90)), Xt=np.zeros((8192, 90)), p=16, sigmas=[1.0, 4.0, 16.0],
              lambdas=[1e-6, 1e-4], workload="bkrr2_n65536_t8192_d90_p16")
-    return dict(prof=prof, w=w, sizes=[4096] * 16, clocks={"sm_mhz": 2070.0}, panel_width=panel)
+    cls = np.array(classes if classes is not None else [1] * 96, np.int32)
+    return dict(prof=prof, nprof=5, w=w, sizes=[4096] * 16, clocks={"sm_mhz": 2070.0}, panel_width=8,
+                classes=cls)
 
 
-def test_roofline_alu_for_the_prediction():
-    r = bench.roofline(_res("predict"), 5, PEAKS)
-    assert r["kernel"] == "predict" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    peak = 152 * 128 * 2070e6 / 1e12
-    assert r["peak"] == pytest.approx(peak)
+def test_prediction_stage_against_section_8d_work():
+    res = _res("predict")
+    st = bench.stage_rooflines(res, PEAKS)["predict"]
     pairs = 8192 * 65536
-    per_pair = 22 + 3 * (7 + 41) + 6 * 12
-    assert r["achieved"] == pytest.approx(pairs * per_pair / 7.2e-3 / 1e12)
-    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
-    assert r["traffic"] == bench.TRAFFIC[("predict", "bkrr2_n65536_t8192_d90_p16", 8)]
+    sec = 7.2e-3
+    assert st["tensor_frac"] == pytest.approx(pairs * 180 / sec / 1e12 / 1885.0)
+    mufu = 152 * 16 * 2070e6 / 1e9
+    assert st["mufu_frac"] == pytest.approx(pairs * 3 / sec / 1e9 / mufu)
+    assert st["hbm_frac"] == pytest.approx((16 * 8192 + 65536) * 90 * 8 / sec / 1e9 / 6797.9)
+    assert st["binding"] == "mufu" and st["frac"] == pytest.approx(st["mufu_frac"])
+    r = bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)
+    assert r["kernel"] == "predict" and r["bound"] == "alu" and r["unit"] == "Gexp/s"
+    assert r["frac"] == pytest.approx(st["mufu_frac"])
+    assert r["impl_alu_frac"] == pytest.approx(pairs * 238 / sec / (152 * 128 * 2070e6))
+    assert r["traffic"] is None  # no capture of this kernel source
 
 
-def test_roofline_tensor_for_the_update_and_traffic_only_at_the_captured_width():
-    r = bench.roofline(_res("update", ms=5.3), 5, PEAKS)
-    assert r["bound"] == "tensor"
-    assert r["peak"] == pytest.approx(1715.4 * 1.1 / 2.25)
-    flops = 6 * 16 * 4096 ** 3 / 3.0  # per step: G x p x m^3/3
-    assert r["achieved"] == pytest.approx(flops / 5.3e-3 / 1e12)
-    assert r["traffic"] is not None
-    assert bench.roofline(_res("update", ms=5.3, panel=4), 5, PEAKS)["traffic"] is None
+def test_factor_stage_charges_each_solve_at_its_class_peak():
+    cls = [1] * 80 + [3] * 16
+    res = _res("update", ms=5.3, classes=cls)
+    st = bench.stage_rooflines(res, PEAKS)["factor"]
+    m = 4096
+    need = 80 * (m ** 3 / 3) / 1885e12 + 16 * (m ** 3 / 3) / (1885e12 * 1.1 / 2.25)
+    sec = (0.1 + 0.1 + 5.3) / 1e3
+    assert st["frac"] == pytest.approx(need / sec)
+    assert st["classes"] == {"1": 80, "3": 16}
+    r = bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)
+    assert r["bound"] == "tensor" and r["kernel"] == "update"
+    tot, potrf, trsm, upd = bench.factor_flops(m)
+    assert tot == pytest.approx(potrf + trsm + upd)
+    assert r["achieved"] == pytest.approx(96 * upd / 5.3e-3 / 1e12)
+    upd_need = 80 * upd / 1885e12 + 16 * upd / (1885e12 * 1.1 / 2.25)
+    assert r["frac"] == pytest.approx(upd_need / 5.3e-3)
 
 
-def test_roofline_hbm_for_a_memory_bound_class():
-    r = bench.roofline(_res("precond", ms=2.7), 5, PEAKS)
-    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == pytest.approx(6797.9)
-    assert 0 < r["frac"] and r["traffic"] is None
+def test_kernel_build_stage_and_unmeasured_classes():
+    res = _res("kbuild", ms=2.2)
+    st = bench.stage_rooflines(res, PEAKS)["kbuild"]
+    ent = 16 * 4096 ** 2 / 2 * 3
+    assert st["hbm_frac"] == pytest.approx(ent * 4 / 2.2e-3 / 1e9 / 6797.9)
+    r = bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)
+    assert r["bound"] == "hbm" and r["frac"] == pytest.approx(st["hbm_frac"])
+    r2 = bench.roofline(_res("precond", ms=2.7), {}, PEAKS)
+    assert r2["frac"] is None and r2["traffic"] is None
+
+
+def test_traffic_is_dropped_when_the_kernel_source_changes(monkeypatch):
+    res = _res("predict")
+    sha = bench._source_sha("predict")
+    monkeypatch.setitem(bench.TRAFFIC, ("predict", "bkrr2_n65536_t8192_d90_p16", sha), 123)
+    assert bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)["traffic"] == 123
+    monkeypatch.setattr(bench, "_source_sha", lambda k: "0" * 16)
+    assert bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)["traffic"] is None
+
+
+def test_accuracy_vs_oracle_reports_the_worst_sampled_solve():
+    pairs = [(0, 1), (1, 0)]
+    refs = [dict(alpha=np.array([1.0, 2.0]), yhat=np.array([1.0, -1.0]), mse=0.5, kappa=10.0),
+            dict(alpha=np.array([4.0]), yhat=np.array([2.0, 2.0]), mse=0.25, kappa=1e6)]
+    gpu = {"tf32": {"failed": 0, (0, 1): (np.array([1.0, 2.0 + 2e-7]), np.array([1.0, -1.0]), 0.5),
+                    (1, 0): (np.array([4.0 + 4e-6]), np.array([2.0, 2.0 + 2e-9]), 0.25 * (1 + 3e-8))}}
+    acc = bench.accuracy_vs_oracle(gpu, refs, pairs)["tf32"]
+    assert acc["max_rel_err_alpha"] == pytest.approx(1e-6)
+    assert acc["max_rel_err_pred"] == pytest.approx(1e-9)
+    assert acc["max_rel_err_mse"] == pytest.approx(3e-8)
+    assert acc["worst_alpha_model"] == [1, 0] and acc["worst_alpha_kappa"] == 1e6
 
 
 def test_host_cpu_reads_x86_and_arm_cpuinfo(tmp_path):

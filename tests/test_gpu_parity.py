@@ -381,7 +381,7 @@ def test_dkrr_fp64_full_size(ctx):
         model.free()
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tf32", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32", "bf16x3"])
 def test_bkrr2_full_size_sampled(ctx, prec):
     """The BKRR2 workload at full size (n = 65536, p = 16 x 4096, 3 sigma x 2
     lambda) in the benchmark's launch configuration; the oracle recomputes two
@@ -407,11 +407,14 @@ def test_bkrr2_full_size_sampled(ctx, prec):
             oa, info, rc = oracle.fit(X[rows], y[rows], w["sigmas"][si], w["lambdas"][li])
             g = si * 2 + li
             assert rc == 0
-            assert rel(galpha[j][g], oa) <= REFINED_TOL, (j, g, info)
+            # the FP64 path's 1e-10 bar holds where kappa u_64 <= 1e-11; beyond
+            # it (sigma 16, lambda 1e-6: kappa ~ 1e6) the refined bar applies
+            tol = tol_for(prec, info[0]) or REFINED_TOL
+            assert rel(galpha[j][g], oa) <= tol, (j, g, info)
             oyh = oracle.predict(X[rows], oa, Xt[sample], w["sigmas"][si])
-            assert rel(yhat[j * G + g], oyh) <= REFINED_TOL
+            assert rel(yhat[j * G + g], oyh) <= tol
             gm = np.mean((yhat[j * G + g] - yt[sample]) ** 2)
-            assert abs(gm - oracle.mse(oyh, yt[sample])) <= REFINED_TOL * oracle.mse(oyh, yt[sample])
+            assert abs(gm - oracle.mse(oyh, yt[sample])) <= tol * oracle.mse(oyh, yt[sample])
         if prec == "tf32":
             # one-pass solves (FP16 factor store, several panels of 8 tiles):
             # their factor must still precondition well
@@ -419,6 +422,56 @@ def test_bkrr2_full_size_sampled(ctx, prec):
             one_pass = kap.numpy() * 2.0 ** -11 <= 32
             assert one_pass.sum() >= 48, kap.numpy()
             assert np.all(it.numpy()[one_pass] <= 10), it.numpy()[one_pass]
+    finally:
+        model.free()
+
+
+def _reference_solve_large(X, y, sigma, lam):
+    """Eq. 6 for one large partition: the oracle's FP64 kernel matrix (direct
+    differences, built in row blocks on all host cores), a LAPACK Cholesky
+    solve as the factor step, then FP64 refinement steps with residuals
+    formed from the same matrix."""
+    import concurrent.futures as cf
+    import scipy.linalg as sla
+    m = X.shape[0]
+    A = np.empty((m, m))
+    blk = 512
+    with cf.ThreadPoolExecutor(max_workers=16) as ex:
+        def fill(r0):
+            A[r0:r0 + blk] = oracle.kernel_matrix(X[r0:r0 + blk], X, sigma)
+        list(ex.map(fill, range(0, m, blk)))
+    A[np.diag_indices(m)] += lam * m
+    c = sla.cho_factor(A, lower=True, overwrite_a=False, check_finite=False)
+    a = sla.cho_solve(c, y, check_finite=False)
+    for _ in range(3):
+        a = a + sla.cho_solve(c, y - A @ a, check_finite=False)
+    return a, A
+
+
+def test_top_of_the_condition_range(ctx):
+    """One partition of n = 16384 BKRR2-shaped rows (d = 90) at sigma = 16,
+    lambda = 1e-7: kappa_est ~ 1e7, the top of the serving range.  The TF32
+    request escalates to the FP32-class factor, which preconditions the
+    refinement; alpha and the predictions stay within 1e-6 of the reference."""
+    w = synth.bkrr2(seed=31, n=16384, t=512, p=1, sigmas=(16.0,), lambdas=(1e-7,))
+    X, y, Xt = w["X"], w["y"], w["Xt"]
+    n = X.shape[0]
+    perm = np.arange(n, dtype=np.int64)
+    off = np.array([0, n], np.int64)
+    model, status, alpha = K.krr_fit_batch(ctx, cuda(X), cuda(y), cuda(perm, torch.int64), cuda(off, torch.int64),
+                                           [16.0], [1e-7], "tf32", want_alpha=True)
+    try:
+        assert int(status.cpu()[0]) == K.KRR_OK
+        it, kap, res = K.krr_model_stats(ctx, model)
+        assert kap[0] > 1e6, kap
+        yh = K.krr_predict(ctx, model, cuda(Xt)).cpu().numpy()[0]
+        ra, A = _reference_solve_large(X, y, 16.0, 1e-7)
+        assert np.max(np.abs(A @ ra - y)) <= 1e-12 * (np.max(np.abs(A).sum(1)) * np.max(np.abs(ra)) + 1.0)
+        del A
+        assert rel(alpha.cpu().numpy(), ra) <= REFINED_TOL
+        sample = np.arange(0, Xt.shape[0], 4)
+        oyh = oracle.predict(X, ra, Xt[sample], 16.0)
+        assert rel(yh[sample], oyh) <= REFINED_TOL
     finally:
         model.free()
 
