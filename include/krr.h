@@ -136,13 +136,15 @@ krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, co
  * form (K_j + lambda m_j I) alpha = y_j with the Gaussian kernel of Table 1,
  * K_ab = exp(-||x_a - x_b||^2 / (2 sigma^2)), by Cholesky factorisation
  * (Sec. 5.4) and refinement to FP64-level residuals.
- *   X [n x d], y [n], perm [n], offsets [p+1] (device; read back to the host).
+ *   X [n x d], y [n], perm [offsets[p]], offsets [p+1] (device; read back to
+ *   the host): offsets run from 0 to at most n, so a subset of the rows (the
+ *   partitions a rank owns) can be fitted against the full X.
  *   sigmas [ns], lambdas [nl]: HOST arrays.  Grid index g = i_sigma * nl +
  *   i_lambda; solve/model index = j * (ns * nl) + g.
  *   *out receives a model owning the gathered rows and every alpha until
  *   krr_model_free.  solve_status [p*ns*nl] (device int32, nullable) receives
  *   KRR_OK, KRR_ERR_NOT_SPD or KRR_ERR_NO_CONVERGE per solve.
- *   alpha (device, nullable) receives n*ns*nl doubles: partition j's block
+ *   alpha (device, nullable) receives offsets[p]*ns*nl doubles: partition j's block
  *   starts at offsets[j]*ns*nl and holds, for each g, m_j coefficients in the
  *   partition's row order.
  * This call synchronises the stream (partition sizes are needed on the host;
@@ -192,6 +194,44 @@ krr_status krr_model_factor_class(krr_ctx *ctx, const krr_model *model, int32_t 
 
 /* Release a model's device memory. */
 krr_status krr_model_free(krr_ctx *ctx, krr_model *model);
+
+/* The grouping step of krr_partition on its own (the scatter of rows to
+ * their partitions, KKRR): rows grouped by partition, ascending row order
+ * inside a partition.  assign [n] (device int32), perm [n] and offsets [p+1]
+ * (device int64) outputs.  A value of assign outside [0, p) is skipped (its
+ * row lands in no partition and offsets[p] < n).  p <= 12288.  Errors:
+ * KRR_ERR_ARG, KRR_ERR_BUDGET, KRR_ERR_OOM, KRR_ERR_CUDA. */
+krr_status krr_group_rows(krr_ctx *ctx, const int32_t *assign, int64_t n, int32_t p, int64_t *perm,
+                          int64_t *offsets);
+
+/* Alg. 2 (plain K-means) as separate steps, for ranks that each hold a
+ * contiguous range of 1024-row blocks of the training set and exchange the
+ * block sums between the two halves of the centre update (the per-round
+ * exchange of the multi-process K-means; the combined centres are the same
+ * bits at any number of ranks).  Same arithmetic as krr_partition(KMEANS).
+ * krr_kmeans_assign: the assignment step (Alg. 2, nearest centre, FP64
+ *   squared distance in feature order, strict <, lowest index; bit-exact
+ *   through the FP64 recheck of near ties) of X [n x d] to the FP64 centres
+ *   C [k x d]; assign [n] int32 output.  Workspace n d 4 bytes.
+ * krr_kmeans_block_sums: first half of the centre step: for each block of
+ *   1024 consecutive rows of X (X must start at a block boundary of the
+ *   global row numbering), every centre's member sum in ascending row order
+ *   and its member count: sums [ceil(n/1024) x k x d] FP64, counts
+ *   [ceil(n/1024) x k] int64, outputs.  assign [n] must hold values in
+ *   [0, k).
+ * krr_kmeans_combine: second half: the block sums of all nblk blocks of the
+ *   training set, in block order, combined by the pairwise tree (level by
+ *   level, an odd last block carried up), one division by the member count;
+ *   C [k x d] in/out, a centre with no members keeps its value.  Needs
+ *   2 nblk 8 bytes <= 200 KiB of shared memory per 1..32 entries.
+ * All arrays are device arrays.  Errors: KRR_ERR_ARG, KRR_ERR_UNSUPPORTED,
+ * KRR_ERR_OOM, KRR_ERR_CUDA. */
+krr_status krr_kmeans_assign(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const double *C, int32_t k,
+                             int32_t *assign);
+krr_status krr_kmeans_block_sums(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const int32_t *assign,
+                                 int32_t k, double *sums, int64_t *counts);
+krr_status krr_kmeans_combine(krr_ctx *ctx, const double *sums, const int64_t *counts, int64_t nblk, int32_t k,
+                              int32_t d, double *C);
 
 /* Group rows by partition without allocating any device memory -- the same
  * grouping krr_partition performs after its assignment (rows of partition 0

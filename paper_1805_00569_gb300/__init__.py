@@ -78,10 +78,15 @@ def load(build_if_missing: bool = True):
     L.krr_model_stats.argtypes = [P, P, P, P, P]
     L.krr_model_free.argtypes = [P, P]
     L.krr_model_factor_class.argtypes = [P, P, P]
+    L.krr_group_rows.argtypes = [P, P, i64, i32, P, P]
+    L.krr_kmeans_assign.argtypes = [P, P, i64, i32, P, i32, P]
+    L.krr_kmeans_block_sums.argtypes = [P, P, i64, i32, P, i32, P, P]
+    L.krr_kmeans_combine.argtypes = [P, P, P, i64, i32, i32, P]
     for name in ("krr_ctx_create", "krr_ctx_destroy", "krr_ctx_set_profiling", "krr_ctx_profile",
                  "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error",
                  "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
-                 "krr_model_stats", "krr_model_free", "krr_model_factor_class"):
+                 "krr_model_stats", "krr_model_free", "krr_model_factor_class", "krr_group_rows", "krr_kmeans_assign",
+                 "krr_kmeans_block_sums", "krr_kmeans_combine"):
         getattr(L, name).restype = st
     _lib = L
     return L
@@ -230,7 +235,7 @@ def krr_fit_batch(ctx: Context, X, y, perm, offsets, sigmas, lambdas, prec=KRR_P
     lam = (ctypes.c_double * len(lambdas))(*[float(v) for v in lambdas])
     G = len(sigmas) * len(lambdas)
     status = torch.empty(p * G, dtype=torch.int32, device=X.device)
-    alpha = torch.empty(n * G, dtype=torch.float64, device=X.device) if want_alpha else None
+    alpha = torch.empty(perm.shape[0] * G, dtype=torch.float64, device=X.device) if want_alpha else None
     h = ctypes.c_void_p()
     rc = ctx.lib.krr_fit_batch(ctx.handle, _ptr(X), _ptr(y), n, d, _ptr(perm), _ptr(offsets), p, sig, len(sigmas),
                                lam, len(lambdas), int(prec), ctypes.byref(h), _ptr(status), _ptr(alpha))
@@ -273,6 +278,50 @@ def krr_model_stats(ctx: Context, model: Model):
                                  ctypes.c_void_p(ka.data_ptr()), ctypes.c_void_p(rs.data_ptr()))
     ctx.check(rc, "krr_model_stats")
     return it, ka, rs
+
+
+def krr_group_rows(ctx: Context, assign, p: int):
+    """Rows grouped by partition: (perm int64 [n], offsets int64 [p+1]) device tensors."""
+    assign = _dev(assign, torch.int32, "assign")
+    n = assign.shape[0]
+    perm = torch.empty(n, dtype=torch.int64, device=assign.device)
+    offsets = torch.empty(p + 1, dtype=torch.int64, device=assign.device)
+    ctx.check(ctx.lib.krr_group_rows(ctx.handle, _ptr(assign), n, p, _ptr(perm), _ptr(offsets)), "krr_group_rows")
+    return perm, offsets
+
+
+def krr_kmeans_assign(ctx: Context, X, C):
+    """Alg. 2 assignment step of the rows of X to the centres C (int32 device tensor)."""
+    X = _dev(X, torch.float64, "X")
+    C = _dev(C, torch.float64, "C")
+    out = torch.empty(X.shape[0], dtype=torch.int32, device=X.device)
+    ctx.check(ctx.lib.krr_kmeans_assign(ctx.handle, _ptr(X), X.shape[0], X.shape[1], _ptr(C), C.shape[0], _ptr(out)),
+              "krr_kmeans_assign")
+    return out
+
+
+def krr_kmeans_block_sums(ctx: Context, X, assign, k: int):
+    """Per 1024-row block: centre member sums [nblk, k, d] and counts [nblk, k]."""
+    X = _dev(X, torch.float64, "X")
+    assign = _dev(assign, torch.int32, "assign")
+    n, d = X.shape
+    nblk = -(-n // 1024)
+    sums = torch.empty((nblk, k, d), dtype=torch.float64, device=X.device)
+    counts = torch.empty((nblk, k), dtype=torch.int64, device=X.device)
+    ctx.check(ctx.lib.krr_kmeans_block_sums(ctx.handle, _ptr(X), n, d, _ptr(assign), k, _ptr(sums), _ptr(counts)),
+              "krr_kmeans_block_sums")
+    return sums, counts
+
+
+def krr_kmeans_combine(ctx: Context, sums, counts, C):
+    """Centres from the block sums of all blocks (canonical tree); returns a new tensor."""
+    sums = _dev(sums, torch.float64, "sums")
+    counts = _dev(counts, torch.int64, "counts")
+    out = _dev(C, torch.float64, "C").clone()
+    nblk, k, d = sums.shape
+    ctx.check(ctx.lib.krr_kmeans_combine(ctx.handle, _ptr(sums), _ptr(counts), nblk, k, d, _ptr(out)),
+              "krr_kmeans_combine")
+    return out
 
 
 def krr_model_factor_class(ctx: Context, model: Model):

@@ -30,6 +30,10 @@ krr_status run_partition_random(Ctx *, int64_t, int32_t, uint64_t, int32_t *, in
 krr_status run_partition_kmeans(Ctx *, const double *, int64_t, int32_t, const double *, int64_t, int32_t, int32_t,
                                 const int64_t *, int32_t *, int32_t *, int64_t *, int64_t *, double *, bool);
 krr_status run_gather(Ctx *, const int32_t *, int64_t, int32_t, int64_t *, int64_t *);
+krr_status run_kmeans_assign_rows(Ctx *, const double *, int64_t, int32_t, const double *, int32_t, int32_t *);
+krr_status run_kmeans_block_sums(Ctx *, const double *, int64_t, int32_t, const int32_t *, int32_t, double *,
+                                 long long *);
+krr_status run_kmeans_combine(Ctx *, const double *, const long long *, int64_t, int32_t, int32_t, double *);
 void launch_stage(cudaStream_t, const double *, const double *, const int64_t *, const Model &, double *);
 void launch_kbuild_df(cudaStream_t, const Model &, int64_t, float *, float *, float *);
 void launch_kbuild_fp64(cudaStream_t, const Model &, int64_t, double *, double *);
@@ -311,6 +315,51 @@ krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u) {
     return KRR_OK;
 }
 
+krr_status krr_group_rows(krr_ctx *ctx, const int32_t *assign, int64_t n, int32_t p, int64_t *perm,
+                          int64_t *offsets) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (n < 0 || p <= 0 || !offsets || (n > 0 && (!assign || !perm)))
+        return fail(c, KRR_ERR_ARG, "krr_group_rows: invalid argument");
+    if ((int64_t)p * 4 > 48 * 1024) return fail(c, KRR_ERR_ARG, "krr_group_rows: p above 12288");
+    cudaSetDevice(c->device);
+    ProfScope ps(c->prof.on ? &c->prof : nullptr, PROF_PARTITION, c->stream);
+    return run_gather(c, assign, n, p, perm, offsets);
+}
+
+krr_status krr_kmeans_assign(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const double *C, int32_t k,
+                             int32_t *assign) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (n < 0 || d <= 0 || k <= 0 || !C || (n > 0 && (!X || !assign)))
+        return fail(c, KRR_ERR_ARG, "krr_kmeans_assign: invalid argument");
+    cudaSetDevice(c->device);
+    ProfScope ps(c->prof.on ? &c->prof : nullptr, PROF_PARTITION, c->stream);
+    return run_kmeans_assign_rows(c, X, n, d, C, k, assign);
+}
+
+krr_status krr_kmeans_block_sums(krr_ctx *ctx, const double *X, int64_t n, int32_t d, const int32_t *assign,
+                                 int32_t k, double *sums, int64_t *counts) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (n < 0 || d <= 0 || k <= 0 || (n > 0 && (!X || !assign || !sums || !counts)))
+        return fail(c, KRR_ERR_ARG, "krr_kmeans_block_sums: invalid argument");
+    cudaSetDevice(c->device);
+    ProfScope ps(c->prof.on ? &c->prof : nullptr, PROF_PARTITION, c->stream);
+    return run_kmeans_block_sums(c, X, n, d, assign, k, sums, reinterpret_cast<long long *>(counts));
+}
+
+krr_status krr_kmeans_combine(krr_ctx *ctx, const double *sums, const int64_t *counts, int64_t nblk, int32_t k,
+                              int32_t d, double *C) {
+    if (!ctx) return KRR_ERR_ARG;
+    Ctx *c = &ctx->c;
+    if (nblk < 0 || d <= 0 || k <= 0 || !C || (nblk > 0 && (!sums || !counts)))
+        return fail(c, KRR_ERR_ARG, "krr_kmeans_combine: invalid argument");
+    cudaSetDevice(c->device);
+    ProfScope ps(c->prof.on ? &c->prof : nullptr, PROF_PARTITION, c->stream);
+    return run_kmeans_combine(c, sums, reinterpret_cast<const long long *>(counts), nblk, k, d, C);
+}
+
 krr_status krr_ctx_wait_probe(krr_ctx *ctx, double seconds) {
     if (!ctx) return KRR_ERR_ARG;
     Ctx *c = &ctx->c;
@@ -401,7 +450,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     std::vector<int64_t> off(p + 1);
     API_TRY(c, cudaMemcpyAsync(off.data(), offsets, sizeof(int64_t) * (p + 1), cudaMemcpyDeviceToHost, st));
     API_TRY(c, cudaStreamSynchronize(st));
-    if (off[0] != 0 || off[p] != n) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must run from 0 to n");
+    if (off[0] != 0 || off[p] > n) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must run from 0 to at most n");
     for (int j = 0; j < p; ++j)
         if (off[j + 1] < off[j]) return fail(c, KRR_ERR_ARG, "krr_fit_batch: offsets must be non-decreasing");
 

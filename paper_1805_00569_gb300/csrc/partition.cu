@@ -729,6 +729,69 @@ krr_status run_update(Ctx *ctx, const double *X, int64_t n, int32_t d, const int
     return KRR_OK;
 }
 
+// ---- Alg. 2 steps as separate calls (ranks that hold different row blocks
+// exchange the block sums between the two halves of the centre update)
+
+// assignment step of rows X [n x d] to the FP64 centres C [k x d]
+krr_status run_kmeans_assign_rows(Ctx *ctx, const double *X, int64_t n, int32_t d, const double *C, int32_t k,
+                                  int32_t *assign) {
+    if (n == 0) return KRR_OK;
+    cudaStream_t st = ctx->stream;
+    float *X32 = nullptr, *C32 = nullptr;
+    const size_t bx = (size_t)n * d * sizeof(float), bc = (size_t)k * d * sizeof(float);
+    KRR_CUDA_TRY(ctx, ctx_malloc(ctx, (void **)&X32, bx));
+    cudaError_t e = ctx_malloc(ctx, (void **)&C32, bc);
+    if (e != cudaSuccess) {
+        ctx_free(ctx, X32, bx);
+        KRR_CUDA_TRY(ctx, e);
+    }
+    KRR_LAUNCHED(), to_float_kernel<<<grid_for(n * d, 256), 256, 0, st>>>(X, X32, n * d);
+    KRR_LAUNCHED(), to_float_kernel<<<grid_for((int64_t)k * d, 256), 256, 0, st>>>(C, C32, (int64_t)k * d);
+    krr_status rc = run_assign(ctx, X32, X, n, d, C, C32, k, nullptr, assign, nullptr);
+    ctx_free(ctx, C32, bc);
+    ctx_free(ctx, X32, bx);
+    return rc;
+}
+
+// first half of the centre update: per block of 1024 rows of X (X starts at
+// a block boundary of the row numbering), sums [nblk][k][d] and counts [nblk][k]
+krr_status run_kmeans_block_sums(Ctx *ctx, const double *X, int64_t n, int32_t d, const int32_t *c, int32_t k,
+                                 double *partial, long long *counts) {
+    int64_t nblk = (n + CANON - 1) / CANON;
+    if (nblk == 0) return KRR_OK;
+    const size_t sm = (2 * (size_t)CANON + 2 * (size_t)k + 1) * sizeof(int32_t);
+    const int fcs = (d + 31) / 32;
+    if (fcs > 32) {
+        ctx->last_error = "kmeans: more than 1024 features";
+        return KRR_ERR_UNSUPPORTED;
+    }
+    const int cgs = std::max(1, std::min(8, 32 / fcs));
+    KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_block_sums_kernel));
+    KRR_LAUNCHED(), kmeans_block_sums_kernel<<<(unsigned)nblk, 32 * fcs * cgs, sm, ctx->stream>>>(
+        X, n, d, c, k, cgs, partial, counts);
+    KRR_CUDA_TRY(ctx, cudaGetLastError());
+    return KRR_OK;
+}
+
+// second half: the pairwise tree over all nblk block sums, one division per
+// centre; empty centres keep C
+krr_status run_kmeans_combine(Ctx *ctx, const double *partial, const long long *counts, int64_t nblk, int32_t k,
+                              int32_t d, double *C) {
+    if (nblk == 0) return KRR_OK;
+    int te = 32;
+    while (te > 1 && 2 * (size_t)nblk * te * sizeof(double) > 128 * 1024) te /= 2;
+    if (2 * (size_t)nblk * te * sizeof(double) > 200 * 1024) {
+        ctx->last_error = "kmeans: too many row blocks for the shared-memory centre tree";
+        return KRR_ERR_UNSUPPORTED;
+    }
+    KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_tree_divide_kernel));
+    KRR_LAUNCHED(), kmeans_tree_divide_kernel<<<(unsigned)(((int64_t)k * d + te - 1) / te), TREE_THREADS,
+                                                2 * (size_t)nblk * te * sizeof(double), ctx->stream>>>(
+        partial, counts, nblk, k, d, te, C);
+    KRR_CUDA_TRY(ctx, cudaGetLastError());
+    return KRR_OK;
+}
+
 // Alg. K-balance Clustering's balanced assignment of the n rows to the p
 // centres C (cap = ceil(n / p)); see the kernels above.
 krr_status run_kbalance(Ctx *ctx, const double *X, int64_t n, int32_t d, const double *C, int32_t p,

@@ -654,3 +654,41 @@ def test_budget_and_argument_errors(ctx):
     with pytest.raises(K.KrrError) as e:
         K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, 0)
     assert e.value.status == K.KRR_ERR_ARG
+
+
+def test_kmeans_steps_and_partition_subset_fit(ctx):
+    """The multi-process building blocks on one GPU: Alg. 2 driven through
+    krr_kmeans_assign / krr_kmeans_block_sums / krr_kmeans_combine (the
+    per-round exchange of the sharded K-means, here with one rank) gives the
+    centres and assignments of krr_partition(KMEANS) bit for bit; and a fit of
+    a subset of the partitions against the full X (as a rank fits the ones
+    LPT gave it) gives those partitions' alphas of the full fit."""
+    from paper_1805_00569_gb300 import dist as kd
+    n, t, d, k, iters = 5000, 300, 11, 7, 6
+    X, Xt, init = _mixture(n, t, d, k, 5)
+    dX = cuda(X)
+    assign, route, perm, offsets, centers = K.krr_partition(ctx, dX, cuda(Xt), K.KRR_PART_KMEANS, k, iters=iters,
+                                                            init_idx=cuda(init, torch.int64))
+    C, a = kd.kmeans_sharded(kd.gpu_kmeans_ops(ctx), dX, dX[cuda(init, torch.int64)].clone(), iters)
+    assert torch.equal(a, assign)
+    assert np.array_equal(C.cpu().numpy().view(np.uint64), centers.cpu().numpy().view(np.uint64))
+    y = np.sin(X[:, 0]) + 0.1 * X[:, 1]
+    sig, lam = [3.0], [1e-4]
+    full, st, al_full = K.krr_fit_batch(ctx, dX, cuda(y), perm, offsets, sig, lam, "fp64", want_alpha=True)
+    owned = kd.lpt_assign(np.diff(offsets.cpu().numpy()) ** 3, 2)[1]
+    sub, soff = kd.partition_subset(perm, offsets.cpu(), owned)
+    part, st2, al_sub = K.krr_fit_batch(ctx, dX, cuda(y), sub, soff.cuda(), sig, lam, "fp64", want_alpha=True)
+    try:
+        assert np.all(st.cpu().numpy() == K.KRR_OK) and np.all(st2.cpu().numpy() == K.KRR_OK)
+        off = offsets.cpu().numpy()
+        so = soff.cpu().numpy()
+        af, asb = al_full.cpu().numpy(), al_sub.cpu().numpy()
+        for i, j in enumerate(owned):
+            assert np.array_equal(asb[so[i]:so[i + 1]], af[off[j]:off[j + 1]])
+        yf = K.krr_predict(ctx, full, cuda(Xt)).cpu().numpy()
+        ys = K.krr_predict(ctx, part, cuda(Xt)).cpu().numpy()
+        for i, j in enumerate(owned):
+            assert np.array_equal(ys[i], yf[j])
+    finally:
+        full.free()
+        part.free()
