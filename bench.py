@@ -10,10 +10,17 @@ L2 is flushed (512 MB write) before every timed step.  `e2e` repeats the
 measurement through the same public calls with the inputs copied from pinned
 host memory each step and the chosen model read back.
 
-Multi-GPU (torchrun): weak scaling -- every rank fits its own independent
-BKRR2 workload (partitions are independent problems); the one exchange is the
-global best-model choice.  `--impl reference` times the FP64 CPU oracle on a
-bounded sample of the same workload (it is the deliberately slow reference).
+The default run also replays the serving stream (10000 fit + predict
+requests, Poisson 200/s) through the serving loop and adds its latency and
+capacity as the line's `serve` object.
+
+Multi-GPU (torchrun): weak scaling -- one BKRR2 workload N times the one-GPU
+size (N x 65536 training rows, N x 16 partitions, the same 8192 test rows),
+identical on every rank; each rank fits the partitions LPT gives it and
+predicts every test row with its models, and one all-gather of the scores
+picks the global best model (kkrr2: the K-means block sums are exchanged every
+round as well).  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload (it is the deliberately slow reference).
 """
 from __future__ import annotations
 
@@ -61,6 +68,8 @@ def parse():
                          "sweep: 520000 rows, p = 128; dkrr: one partition of 2048 rows; serve: the request "
                          "stream (Poisson 200/s, n log-uniform in [512, 16384]) through the serving loop")
     ap.add_argument("--requests", type=int, default=10000, help="serve: requests replayed from the stream")
+    ap.add_argument("--shard", action="store_true",
+                    help="bkrr2/kkrr2: take the multi-GPU (LPT-sharded) step even on one GPU")
     ap.add_argument("--no-serve", action="store_true",
                     help="bkrr2 line without its serve object (the request stream through the serving loop)")
     ap.add_argument("--serve-bank", type=int, default=32,
@@ -239,24 +248,33 @@ class Clocks:
 
 
 # ---------------------------------------------------------------- our arm
-def make_workload(args, rank):
+SHARDED = ("bkrr2", "kkrr2")  # workloads whose partitions are split over ranks (weak scaling)
+
+
+def make_workload(args, rank, world=1):
+    """The synthetic workload of this rank.  bkrr2 / kkrr2 on N ranks: ONE
+    workload N times the one-GPU size (N x the training rows and partitions,
+    the same test rows), identical on every rank, whose partitions the ranks
+    split by LPT -- the paper's weak-scaling setting.  Other workloads: an
+    independent copy per rank."""
     from paper_1805_00569_gb300 import synth
     kw = {}
-    if args.n:
-        kw["n"] = args.n
     if args.t:
         kw["t"] = args.t
     if args.workload == "bkrr2":
-        if args.p:
-            kw["p"] = args.p
-        return synth.bkrr2(seed=1 + rank, **kw)
+        kw["n"] = (args.n or 65536) * world
+        kw["p"] = (args.p or 16) * world
+        return synth.bkrr2(seed=1, **kw)
     if args.workload == "kkrr2":
-        if args.p:
-            kw["k"] = args.p
-        if args.n and args.n < 262144:  # keep the mixture's size range proportional
-            kw["lo"] = max(16, int(500 * args.n / 262144))
-            kw["hi"] = max(kw["lo"] + 1, int(16000 * args.n / 262144))
-        return synth.kkrr2(seed=2 + rank, **kw)
+        n1 = args.n or 262144
+        kw["n"] = n1 * world
+        kw["k"] = (args.p or 64) * world
+        if n1 < 262144:  # keep the mixture's size range proportional
+            kw["lo"] = max(16, int(500 * n1 / 262144))
+            kw["hi"] = max(kw["lo"] + 1, int(16000 * n1 / 262144))
+        return synth.kkrr2(seed=2, **kw)
+    if args.n:
+        kw["n"] = args.n
     if args.workload == "sweep":
         if args.p:
             kw["p"] = args.p
@@ -289,7 +307,8 @@ def run_ours(args, rank, world, local_rank):
     from paper_1805_00569_gb300 import dist as kd, synth
 
     torch.cuda.set_device(local_rank)
-    w = make_workload(args, rank)
+    w = make_workload(args, rank, world)
+    sharded = (world > 1 or args.shard) and args.workload in SHARDED
     n, d = w["X"].shape
     t = w["Xt"].shape[0]
     p = w["p"]
@@ -314,7 +333,50 @@ def run_ours(args, rank, world, local_rank):
     last_offsets = [None]
     last_route = [None]
 
+    owned_sizes = [None]
+
+    def step_sharded(Xd, yd, Xtd, ytd, prec):
+        """One step of the partitions this rank owns (LPT on m^3) of the one
+        workload all ranks share; exchanges: the K-means block sums per round
+        (kkrr2), then the scores."""
+        if kmeans:
+            C, a = kd.kmeans_sharded(kd.gpu_kmeans_ops(ctx), Xd, Xd[init_idx].clone(), w["iters"])
+            perm, offsets = K.krr_group_rows(ctx, a, p)
+            route = K.krr_kmeans_assign(ctx, Xtd, C)
+            last_route[0] = route
+        else:
+            _, _, perm, offsets, _ = K.krr_partition(ctx, Xd, None, K.KRR_PART_RANDOM, p, seed=w["part_seed"])
+        off = offsets.cpu()
+        sizes = np.diff(off.numpy())
+        owned = kd.lpt_assign([float(m) ** 3 for m in sizes], world)[rank]
+        owned_sizes[0] = sizes[owned]
+        sub, soff = kd.partition_subset(perm, off, owned)
+        model, status, _ = K.krr_fit_batch(ctx, Xd, yd, sub, soff.to(Xd.device), S, L, prec)
+        if kmeans:
+            lmap = torch.full((p,), -1, dtype=torch.int32, device=Xd.device)
+            lmap[torch.as_tensor(owned, dtype=torch.int64, device=Xd.device)] = torch.arange(
+                len(owned), dtype=torch.int32, device=Xd.device)
+            lroute = lmap[route.long()]
+            rows = torch.nonzero(lroute >= 0).flatten()
+            sse = torch.zeros(G, dtype=torch.float64, device=Xd.device)
+            if rows.numel():
+                yh = K.krr_predict(ctx, model, Xtd[rows], route=lroute[rows])
+                m_loc, _ = K.krr_select(ctx, yh, ytd[rows], len(owned), G, K.KRR_SEL_ROUTED)
+                sse = m_loc * rows.numel()
+            mse = kd.sum_over_ranks(sse) / Xtd.shape[0]
+            best = torch.tensor([kd.best_of(mse.cpu())[0]], dtype=torch.int32)
+        else:
+            yh = K.krr_predict(ctx, model, Xtd, out=yhat_buf[:len(owned) * G])
+            m_loc, _ = K.krr_select(ctx, yh, ytd, len(owned), G, K.KRR_SEL_PER_MODEL)
+            mse = kd.gather_scores(m_loc, [j * G + g for j in owned for g in range(G)], p * G)
+            best = torch.tensor([kd.best_of(mse)[0]], dtype=torch.int32)
+        model.free()
+        last_offsets[0] = offsets
+        return mse, best, status
+
     def step(Xd, yd, Xtd, ytd, prec):
+        if sharded:
+            return step_sharded(Xd, yd, Xtd, ytd, prec)
         if kmeans:  # KKRR2 / K-balance BKRR2: clustered partitions, routed prediction and selection
             _, route, perm, offsets, _ = K.krr_partition(ctx, Xd, Xtd, pmode, p, iters=w["iters"],
                                                          init_idx=init_idx)
@@ -390,7 +452,10 @@ def run_ours(args, rank, world, local_rank):
     launches = ctx.lib.krr_launch_count() - launches0
     flush_launches = 0
     total_ms = kd.max_over_ranks(sum(times))
-    gbest, gmse = kd.global_best(mse, rank * nsolve)
+    if sharded:
+        gbest, gmse = int(best[0]), float(mse[int(best[0])])
+    else:
+        gbest, gmse = kd.global_best(mse, rank * nsolve)
 
     # ---- end to end through the same calls, host inputs
     hX, hy, hXt, hyt = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
@@ -422,7 +487,7 @@ def run_ours(args, rank, world, local_rank):
     panel_width = int(Wt.value)
 
     fp64 = None
-    if not args.no_fp64_path and rank == 0:
+    if not args.no_fp64_path and world == 1:
         torch.cuda.synchronize()
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -437,9 +502,9 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- untimed fits: factor class of every solve (roofline), and the
     # sampled models' alpha, predictions and MSE per precision (accuracy)
-    pairs = sample_models(p, G, oracle_sample_size(args)) if (rank == 0 and not kmeans) else []
-    precs = [args.prec] + ([q for q in ("fp64", "fp32", "tf32", "bf16x3") if q != args.prec]
-                           if (pairs and not args.no_cpu_baseline and world == 1) else [])
+    pairs = sample_models(p, G, oracle_sample_size(args)) if (rank == 0 and not kmeans and world == 1) else []
+    precs = [] if sharded else [args.prec] + ([q for q in ("fp64", "fp32", "tf32", "bf16x3") if q != args.prec]
+                                              if (pairs and not args.no_cpu_baseline) else [])
     gpu_acc, classes = {}, None
     for pr in precs:
         if kmeans:
@@ -464,13 +529,18 @@ def run_ours(args, rank, world, local_rank):
     ctx.close()
 
     ms_per_step = total_ms / args.steps
-    value = world * nsolve * args.steps / (total_ms / 1e3)
-    sizes = np.diff(last_offsets[0].cpu().numpy())
-    tflops = world * G * sum(solve_flops(int(m), d) for m in sizes) * args.steps / (total_ms / 1e3) / 1e12
+    # solves of all ranks per step: the shared workload's p G when sharded,
+    # else every rank's own p G
+    all_solves = nsolve if sharded else world * nsolve
+    value = all_solves * args.steps / (total_ms / 1e3)
+    gsizes = np.diff(last_offsets[0].cpu().numpy())
+    tflops = ((1 if sharded else world) * G * sum(solve_flops(int(m), d) for m in gsizes) * args.steps
+              / (total_ms / 1e3) / 1e12)
+    sizes = owned_sizes[0] if sharded else gsizes
     return dict(w=w, sizes=sizes, value=value, ms_per_step=ms_per_step, tflops=tflops, prof=prof, nprof=nprof,
                 clocks=clk,
                 panel_width=panel_width,
-                launches=launches + flush_launches, e2e=dict(value=world * nsolve * args.steps / e2e_s, unit=UNIT,
+                launches=launches + flush_launches, e2e=dict(value=all_solves * args.steps / e2e_s, unit=UNIT,
                                                          h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                 fp64=fp64, best=gbest, best_mse=gmse, bad=bad, times=times, classes=classes,
                 gpu_acc=gpu_acc, pairs=pairs,
@@ -700,8 +770,10 @@ def run_serve(args, rank, world, local_rank):
     launches0 = K.load().krr_launch_count()
     clocks = Clocks(local_rank)
     clocks.start()
+    t_live0 = time.perf_counter()
     live, sc_live = replay(reqs, args.slots, args.prec, True)
     cap, sc_cap = replay(reqs, args.slots, args.prec, False)
+    clocks.window(t_live0, time.perf_counter())
     clk = clocks.stop()
     launches = K.load().krr_launch_count() - launches0
     span = max(r.done for r in cap) - min(r.start for r in cap)
@@ -800,8 +872,12 @@ def main():
         "vs_baseline": None, "dtype": DTYPE_LABEL.get(args.prec, "f64"),
         "data": "synthetic",
         "config": {"workload": w["workload"], "sigmas": w["sigmas"], "lambdas": w["lambdas"], "prec": args.prec,
-                   "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]),
-                   "parallelism": "independent workloads per GPU" if world > 1 else "single GPU",
+                   "solves_per_step_per_gpu": w["p"] * len(w["sigmas"]) * len(w["lambdas"]) // (
+                       world if args.workload in SHARDED else 1),
+                   "parallelism": ("one workload, partitions split over GPUs by LPT on m^3 (weak scaling: "
+                                   "%dx the one-GPU training rows and partitions)" % world
+                                   if world > 1 and args.workload in SHARDED else
+                                   "independent workloads per GPU" if world > 1 else "single GPU"),
                    "panel_width": res["panel_width"],
                    "l2": "flushed (512 MB write) before every timed step"},
         "tflops": res["tflops"], "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"],

@@ -147,6 +147,13 @@ krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, co
  *   alpha (device, nullable) receives offsets[p]*ns*nl doubles: partition j's block
  *   starts at offsets[j]*ns*nl and holds, for each g, m_j coefficients in the
  *   partition's row order.
+ * A refined-precision solve (FP32, TF32, BF16X3) whose refinement does not
+ * converge -- its condition estimate near the reciprocal of the factor's
+ * unit roundoff, where the low-precision factor no longer preconditions --
+ * is solved again on the plain FP64 path once the batch's work buffers are
+ * released; it then reports KRR_OK and factor class 0
+ * (krr_model_factor_class).  krr_ctx_set_fp64_fallback(ctx, 0) turns this
+ * off (such solves then report KRR_ERR_NO_CONVERGE).
  * This call synchronises the stream (partition sizes are needed on the host;
  * refinement rounds poll a device flag).  Errors: KRR_ERR_ARG,
  * KRR_ERR_BUDGET, KRR_ERR_OOM, KRR_ERR_CUDA, KRR_ERR_TIMEOUT. */
@@ -308,6 +315,10 @@ krr_status krr_ctx_set_panel_width(krr_ctx *ctx, int W);
 krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, int *W);
 krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel);
 krr_status krr_ctx_set_escalation(krr_ctx *ctx, double kappa_u);
+/* krr_ctx_set_fp64_fallback: on (the default) / off -- the FP64 re-solve of
+ *   unconverged refined-precision solves described at krr_fit_batch.
+ *   Errors: KRR_ERR_ARG. */
+krr_status krr_ctx_set_fp64_fallback(krr_ctx *ctx, int on);
 
 /* krr_ctx_set_kernel: the Table 1 kernel of this context's subsequent
  * krr_fit_batch calls (default GAUSSIAN); a model keeps the kernel it was

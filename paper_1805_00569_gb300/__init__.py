@@ -69,6 +69,7 @@ def load(build_if_missing: bool = True):
     L.krr_ctx_set_target_error.argtypes = [P, ctypes.c_double]
     L.krr_ctx_set_escalation.argtypes = [P, ctypes.c_double]
     L.krr_ctx_wait_probe.argtypes = [P, ctypes.c_double]
+    L.krr_ctx_set_fp64_fallback.argtypes = [P, ctypes.c_int]
     L.krr_launch_count.restype = ctypes.c_longlong
     L.krr_partition.argtypes = [P, P, i64, i32, P, i64, ctypes.c_int, i32, i32, u64, P, P, P, P, P, P]
     L.krr_fit_batch.argtypes = [P, P, P, i64, i32, P, P, i32, P, i32, P, i32, ctypes.c_int,
@@ -84,7 +85,7 @@ def load(build_if_missing: bool = True):
     L.krr_kmeans_combine.argtypes = [P, P, P, i64, i32, i32, P]
     for name in ("krr_ctx_create", "krr_ctx_destroy", "krr_ctx_set_profiling", "krr_ctx_profile",
                  "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error",
-                 "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
+                 "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_ctx_set_fp64_fallback", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
                  "krr_model_stats", "krr_model_free", "krr_model_factor_class", "krr_group_rows", "krr_kmeans_assign",
                  "krr_kmeans_block_sums", "krr_kmeans_combine"):
         getattr(L, name).restype = st
@@ -189,6 +190,10 @@ def krr_ctx_set_target_error(ctx: Context, rel: float):
 
 def krr_ctx_set_escalation(ctx: Context, kappa_u: float):
     ctx.check(ctx.lib.krr_ctx_set_escalation(ctx.handle, float(kappa_u)), "krr_ctx_set_escalation")
+
+
+def krr_ctx_set_fp64_fallback(ctx: Context, on: bool):
+    ctx.check(ctx.lib.krr_ctx_set_fp64_fallback(ctx.handle, 1 if on else 0), "krr_ctx_set_fp64_fallback")
 
 
 def krr_ctx_wait_probe(ctx: Context, seconds: float) -> int:

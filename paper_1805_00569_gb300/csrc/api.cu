@@ -50,7 +50,8 @@ void build_chol_plan(const std::vector<int> &, const std::vector<int> &, int, st
                      std::vector<int64_t> &);
 cudaError_t run_chol_plan(cudaStream_t, const std::vector<CholLaunch> &, const int64_t *, void *, void *, bool,
                           const SolveDesc *, int, int32_t *, int, const CUtensorMap *, const CUtensorMap *, __half *,
-                          const CUtensorMap *, float *, const CUtensorMap *, int *, Prof *);
+                          const CUtensorMap *, float *, const CUtensorMap *, const float *, const CUtensorMap *, int *,
+                          Prof *);
 bool make_tile_tmap(CUtensorMap *, float *, int64_t);
 bool make_tile_tmap16(CUtensorMap *, __half *, int64_t);
 size_t pcg_state_size();
@@ -68,7 +69,7 @@ bool oz_supported(int d);
 void launch_oz_slice(cudaStream_t, const double *, int, const int64_t *, int64_t, int64_t, void *, int32_t *, float2 *);
 bool make_slice_tmap(CUtensorMap *, void *, int64_t, int, int);
 cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, float *, float *, float *, float *,
-                             const int64_t *, int64_t, int *);
+                             const int64_t *, int64_t, int *, bool);
 cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
                               const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
                               int *);
@@ -306,6 +307,12 @@ krr_status krr_ctx_get_panel_width(const krr_ctx *ctx, int prec, int max_tiles, 
 krr_status krr_ctx_set_target_error(krr_ctx *ctx, double rel) {
     if (!ctx || !(rel >= 0.0) || rel > 1e-2) return KRR_ERR_ARG;
     ctx->c.target_err = rel;
+    return KRR_OK;
+}
+
+krr_status krr_ctx_set_fp64_fallback(krr_ctx *ctx, int on) {
+    if (!ctx) return KRR_ERR_ARG;
+    ctx->c.fp64_fallback = on != 0;
     return KRR_OK;
 }
 
@@ -665,8 +672,9 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 Kh = (float *)Kst;
                 Kl = Kh + (size_t)ns * ktot * KRR_TILE_ELEMS;
                 if (M.ozS) {
+                    // no factor tiles: the factorisation's first touch reads K_hi (Kfirst below)
                     FIT_TRY(launch_kbuild_oz(st, M, ktot, Kh, Kl, (float *)Ast, rsR, rsC, d_rsoff, rstot,
-                                             c->d_err));
+                                             c->d_err, false));
                 } else {
                     launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
                 }
@@ -707,13 +715,19 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         // factor class per solve: FP64 path -> FP64; FP32 -> 3-pass TF32; TF32 ->
         // one FP16 pass unless kappa_est * 2^-11 exceeds the escalation threshold;
         // BF16x3 -> 3-pass BF16 unless kappa_est * 2^-16 exceeds it (then 3-pass TF32)
-        CUtensorMap tmap, tmapZ, tmap16;
+        CUtensorMap tmap, tmapZ, tmap16, tmapK;
         memset(&tmap, 0, sizeof(tmap));
         memset(&tmapZ, 0, sizeof(tmapZ));
         memset(&tmap16, 0, sizeof(tmap16));
+        memset(&tmapK, 0, sizeof(tmapK));
         if (!fp64 && (!make_tile_tmap(&tmap, (float *)Ast, ltiles) || !make_tile_tmap(&tmapZ, (float *)Zst, dtiles) ||
                       (A16 && !make_tile_tmap16(&tmap16, A16, ltiles))))
             return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled unavailable or failed");
+        // the exact-Gram tile build stores no factor tiles: each factor tile's
+        // first touch in the factorisation reads K_hi and adds lambda m
+        const float *Kfirst = (!fp64 && M.ozS) ? Kh : nullptr;
+        if (Kfirst && !make_tile_tmap(&tmapK, Kh, (int64_t)ns * ktot))
+            return bail(KRR_ERR_CUDA, "krr_fit_batch: cuTensorMapEncodeTiled failed");
         const int base_cls = fp64 ? 0 : (tf32 ? 1 : (bf16x3 ? 2 : 3));
         std::vector<int> cls(nsolve, base_cls);  // update class per solve
         M.st_class.assign(nsolve, 0);
@@ -788,7 +802,8 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                                                                                          Kh, (float *)Ast, 0.f);
                     cudaEventRecord(e0, st);
                     FIT_TRY(run_chol_plan(st, tplan, d_tplan, Ast, Zst, false, M.d_solves, nsolve, flags, tcmode,
-                                          &tmap, &tmapZ, A16, &tmap16, Alo, &tmapLo, c->d_err, nullptr));
+                                          &tmap, &tmapZ, A16, &tmap16, Alo, &tmapLo, Kfirst, &tmapK, c->d_err,
+                                          nullptr));
                     cudaEventRecord(e1, st);
                     FIT_TRY(cudaEventSynchronize(e1));
                     float ms = 0.f;
@@ -814,7 +829,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             if (!pre.empty())
                 FIT_TRY(cudaMemcpyAsync(d_plan, pre.data(), sizeof(int64_t) * pre.size(), cudaMemcpyHostToDevice, st));
             FIT_TRY(run_chol_plan(st, plan, d_plan, Ast, Zst, fp64, M.d_solves, nsolve, flags, tcmode, &tmap, &tmapZ,
-                                  A16, &tmap16, Alo, &tmapLo, c->d_err, prof));
+                                  A16, &tmap16, Alo, &tmapLo, Kfirst, &tmapK, c->d_err, prof));
             FIT_TRY(cudaMemcpyAsync(hflags.data(), flags, sizeof(int32_t) * nsolve, cudaMemcpyDeviceToHost, st));
             FIT_TRY(cudaStreamSynchronize(st));
         }
@@ -859,7 +874,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 FIT_TRY(cudaMemcpyAsync(d_rplan, rp.data(), sizeof(int64_t) * rp.size(), cudaMemcpyHostToDevice,
                                         st));
                 FIT_TRY(run_chol_plan(st, rplan, d_rplan, Ast, Zst, false, d_sub, nsub, rflags, 3, &tmap, &tmapZ,
-                                      A16, &tmap16, Alo, &tmapLo, c->d_err, prof));
+                                      A16, &tmap16, Alo, &tmapLo, nullptr, nullptr, c->d_err, prof));
                 std::vector<int32_t> hr(nsub);
                 FIT_TRY(cudaMemcpyAsync(hr.data(), rflags, sizeof(int32_t) * nsub, cudaMemcpyDeviceToHost, st));
                 FIT_TRY(cudaStreamSynchronize(st));
@@ -907,6 +922,58 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
         if (herr != 0) return bail(KRR_ERR_TIMEOUT, "krr_fit_batch: a bounded device wait expired");
         // kernel stores (Kh/Kl, K64) could stay for later refinement; they are released here
         (void)Zst;
+    }
+    // FP64 fallback: a refined-precision solve whose low-precision factor was
+    // too poor a preconditioner to converge (condition estimates near the
+    // reciprocal of the factor's unit roundoff) is solved again on the plain
+    // FP64 path -- FP64 kernel, FP64 Cholesky, FP64 refinement -- with the
+    // work buffers of the batch already released; its alpha replaces the
+    // unconverged one and its factor class reads 0.
+    if (!fp64 && c->fp64_fallback) {
+        for (int s = 0; s < nsolve; ++s) {
+            if (M.st_status[s] != KRR_ERR_NO_CONVERGE) continue;
+            const SolveDesc &S = M.solves[s];
+            if (S.m == 0) continue;
+            int64_t *d_off = nullptr;
+            int32_t *d_st = nullptr;
+            const int64_t hoff[2] = {0, (int64_t)S.m};
+            krr_model *sub = nullptr;
+            int32_t hst = KRR_ERR_NO_CONVERGE;
+            const double sg = M.sigmas[S.isig], lm = M.lambdas[S.ilam];
+            if (ctx_malloc(c, (void **)&d_off, 16) != cudaSuccess) break;
+            if (ctx_malloc(c, (void **)&d_st, 4) != cudaSuccess) {
+                ctx_free(c, d_off, 16);
+                break;
+            }
+            const int prev_kernel = c->kernel;
+            c->kernel = M.kind;
+            krr_status rc = cudaMemcpyAsync(d_off, hoff, 16, cudaMemcpyHostToDevice, st) == cudaSuccess
+                                ? krr_fit_batch(ctx, X, y, n, d, perm + M.parts[S.part].row0, d_off, 1, &sg, 1, &lm, 1,
+                                                KRR_PREC_FP64, &sub, d_st, nullptr)
+                                : KRR_ERR_CUDA;
+            c->kernel = prev_kernel;
+            if (rc == KRR_OK && cudaMemcpyAsync(&hst, d_st, 4, cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+                cudaStreamSynchronize(st) == cudaSuccess && hst == KRR_OK &&
+                cudaMemcpyAsync(M.alpha + S.vec0, sub->m.alpha, (size_t)S.T * KRR_TILE * 8, cudaMemcpyDeviceToDevice,
+                                st) == cudaSuccess) {
+                M.st_status[s] = KRR_OK;
+                M.st_iters[s] += sub->m.st_iters[0];
+                M.st_resid[s] = sub->m.st_resid[0];
+                M.st_class[s] = 0;
+                const int32_t ok = KRR_OK;
+                if (solve_status) cudaMemcpyAsync(solve_status + s, &ok, 4, cudaMemcpyHostToDevice, st);
+                if (alpha)
+                    cudaMemcpyAsync(alpha + M.parts[S.part].row0 * G + (int64_t)(s % G) * S.m, sub->m.alpha,
+                                    (size_t)S.m * 8, cudaMemcpyDeviceToDevice, st);
+                cudaStreamSynchronize(st);  // host sources above are on this stack frame
+            }
+            if (sub) {
+                free_model(c, sub->m);
+                delete sub;
+            }
+            ctx_free(c, d_st, 4);
+            ctx_free(c, d_off, 16);
+        }
     }
 #undef FIT_TRY
     *out = km;

@@ -248,6 +248,170 @@ __global__ void __launch_bounds__(512, 1) potrf_tile_kernel(T *__restrict__ A, T
     }
 }
 
+// ---------------------------------------------------------------- potrf, blocked (FP32)
+// The same factor L and inverse Z of one FP32 diagonal tile, blocked by 32
+// columns so that block barriers come per block, not per column.  For each
+// 32-column block kb: warp 0 factors the 32 x 32 diagonal block and inverts
+// it in registers (lane i holds row i of the block; row and column values
+// travel by shuffle, no block barrier); then all 16 warps solve the rows
+// below against the block's inverse (L_r,kb = A_r,kb Z_kb,kb^T) and apply its
+// rank-32 update to the lower part of the trailing rows and columns.  The
+// off-diagonal blocks of Z follow by the blocked triangular inverse
+//   Z_ib,jb = -Z_ib,ib sum_{m in blocks [jb, ib)} L_ib,m Z_m,jb.
+// Eighteen block barriers instead of one per column.  The tile is held in
+// shared memory (padded rows: lanes reading a column hit distinct banks).
+constexpr int PO_B = 32;               // block width
+constexpr int PO_LD = KRR_TILE + 1;    // padded row stride in shared memory
+constexpr size_t PO_BLOCKED_SMEM = (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (KRR_TILE - PO_B)) * sizeof(float);
+
+__global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
+                                                               const float *__restrict__ Kfirst,
+                                                               const SolveDesc *__restrict__ solves,
+                                                               const int64_t *__restrict__ pre, int nsolve, int k,
+                                                               int32_t *__restrict__ flags) {
+    extern __shared__ __align__(16) unsigned char po_dyn[];
+    float *Ls = reinterpret_cast<float *>(po_dyn);  // [128][PO_LD]: A, becoming L
+    float *Zs = Ls + KRR_TILE * PO_LD;              // [128][PO_LD]: Z
+    float *Ts = Zs + KRR_TILE * PO_LD;              // [32][96]: L_ib,: Z_:,jb of the blocked inverse
+    constexpr int TW = KRR_TILE - PO_B;
+    __shared__ int bad_sh;
+    pdl_launch_dependents();
+    pdl_wait();  // the column update of this diagonal tile has completed
+    const int s = find_solve(pre, nsolve, blockIdx.x);
+    const SolveDesc S = solves[s];
+    const int64_t tile = S.ltile0 + (int64_t)k * (k + 1) / 2 + k;
+    float *g = A + tile * KRR_TILE_ELEMS;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) bad_sh = 0;
+    // the first diagonal tile's first touch reads the kernel store: K_00 + lambda m I
+    const bool kf = Kfirst != nullptr && k == 0;
+    const float *src = kf ? Kfirst + S.ktile0 * KRR_TILE_ELEMS : g;
+    const float lm = (float)S.lambda_m;
+    for (int e = tid; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int r = e >> 7, c = e & 127;
+        Ls[r * PO_LD + c] = c <= r ? (kf && r == c && r < S.m ? src[e] + lm : src[e]) : 0.f;
+        Zs[r * PO_LD + c] = 0.f;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int kb = 0; kb < KRR_TILE / PO_B; ++kb) {
+        const int o = kb * PO_B;
+        if (warp == 0) {
+            // factor: step q scales column q by 1 / sqrt(pivot) and updates
+            // the columns right of it; entries right of a lane's diagonal
+            // collect values that are never read (their multiplier is 0 by
+            // the time they are)
+            float d[PO_B];
+#pragma unroll
+            for (int j = 0; j < PO_B; ++j) d[j] = j <= lane ? Ls[(o + lane) * PO_LD + o + j] : 0.f;
+            float dinv = 0.f;  // 1 / L_ii of this lane's row
+            bool bad = false;
+#pragma unroll
+            for (int q = 0; q < PO_B; ++q) {
+                float pv = __shfl_sync(0xffffffffu, d[q], q);
+                if (!(pv > 0.f)) {  // not positive: record, continue with 1 (no NaNs)
+                    bad = true;
+                    pv = 1.f;
+                }
+                const float rl = potrf_rsqrt<float>(pv);
+                const float l = lane > q ? d[q] * rl : (lane == q ? pv * rl : 0.f);
+                if (lane == q) dinv = rl;
+                d[q] = l;
+#pragma unroll
+                for (int j = q + 1; j < PO_B; ++j) d[j] = fmaf(-l, __shfl_sync(0xffffffffu, l, j), d[j]);
+            }
+            // inverse of the block: lane j forms column j, row by row
+            float z[PO_B];
+#pragma unroll
+            for (int i = 0; i < PO_B; ++i) {
+                const float inv_ii = __shfl_sync(0xffffffffu, dinv, i);
+                float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < i; ++kk) {
+                    const float lik = __shfl_sync(0xffffffffu, d[kk], i);
+                    if (kk & 1) a1 = fmaf(lik, z[kk], a1);
+                    else a0 = fmaf(lik, z[kk], a0);
+                }
+                z[i] = lane == i ? inv_ii : (lane < i ? -(a0 + a1) * inv_ii : 0.f);
+            }
+#pragma unroll
+            for (int j = 0; j < PO_B; ++j)
+                if (j <= lane) Ls[(o + lane) * PO_LD + o + j] = d[j];
+#pragma unroll
+            for (int i = 0; i < PO_B; ++i)
+                if (i >= lane) Zs[(o + i) * PO_LD + o + lane] = z[i];
+            if (bad && lane == 0) bad_sh = 1;
+        }
+        __syncthreads();
+        const int nr = KRR_TILE - o - PO_B;  // rows below the block
+        if (nr == 0) break;
+        // rows below: L_r,o+c = sum_kk A_r,o+kk Z_o+c,o+kk (Z_o+c,o+kk = 0 for kk > c)
+        float outv[TW * PO_B / 512];
+#pragma unroll
+        for (int u = 0; u < TW * PO_B / 512; ++u) {
+            const int e = tid + u * 512;
+            float acc = 0.f;
+            if (e < nr * PO_B) {
+                const float *ar = Ls + (o + PO_B + (e >> 5)) * PO_LD + o;
+                const float *zc = Zs + (o + (e & 31)) * PO_LD + o;
+#pragma unroll
+                for (int kk = 0; kk < PO_B; ++kk) acc = fmaf(ar[kk], zc[kk], acc);
+            }
+            outv[u] = acc;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < TW * PO_B / 512; ++u) {
+            const int e = tid + u * 512;
+            if (e < nr * PO_B) Ls[(o + PO_B + (e >> 5)) * PO_LD + o + (e & 31)] = outv[u];
+        }
+        __syncthreads();
+        // rank-32 update of the lower trailing part
+        const int b0 = o + PO_B;
+        for (int e = tid; e < nr * nr; e += blockDim.x) {
+            const int r = e / nr, c = e - r * nr;
+            if (c > r) continue;
+            const float *lr = Ls + (b0 + r) * PO_LD + o, *lc = Ls + (b0 + c) * PO_LD + o;
+            float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < PO_B; kk += 2) {
+                a0 = fmaf(lr[kk], lc[kk], a0);
+                a1 = fmaf(lr[kk + 1], lc[kk + 1], a1);
+            }
+            Ls[(b0 + r) * PO_LD + b0 + c] -= a0 + a1;
+        }
+        __syncthreads();
+    }
+    // off-diagonal blocks of Z, block row by block row
+#pragma unroll 1
+    for (int ib = 1; ib < KRR_TILE / PO_B; ++ib) {
+        const int w = ib * PO_B;
+        for (int e = tid; e < PO_B * w; e += blockDim.x) {  // T_i,c = sum_{m < w} L_w+i,m Z_m,c (Z_m,c = 0, m < c)
+            const int i = e / w, c = e - i * w;
+            const float *lr = Ls + (w + i) * PO_LD;
+            float acc = 0.f;
+            for (int m = c; m < w; ++m) acc = fmaf(lr[m], Zs[m * PO_LD + c], acc);
+            Ts[i * TW + c] = acc;
+        }
+        __syncthreads();
+        for (int e = tid; e < PO_B * w; e += blockDim.x) {  // Z_w+i,c = -sum_{kk <= i} Z_w+i,w+kk T_kk,c
+            const int i = e / w, c = e - i * w;
+            const float *zr = Zs + (w + i) * PO_LD + w;
+            float acc = 0.f;
+            for (int kk = 0; kk <= i; ++kk) acc = fmaf(zr[kk], Ts[kk * TW + c], acc);
+            Zs[(w + i) * PO_LD + c] = -acc;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && bad_sh) flags[s] = 1;
+    float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
+    for (int e = tid; e < KRR_TILE_ELEMS; e += blockDim.x) {
+        const int r = e >> 7, c = e & 127;
+        g[e] = c <= r ? Ls[r * PO_LD + c] : 0.f;
+        z[e] = Zs[r * PO_LD + c];
+    }
+}
+
 // ---------------------------------------------------------------- SIMT GEMM tile
 // UPD_TRAIL / UPD_COLUMN: A_ij -= sum_{k in [kb,ke)} L_ik L_jk^T
 // UPD_TRSM:               A_ik  = A_ik Z_kk^T
@@ -389,9 +553,10 @@ template <int MODE>
 __global__ void __launch_bounds__(TcCfg<MODE>::THREADS, 1)
 tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmapZ,
                 const __grid_constant__ CUtensorMap tmapLo, const __grid_constant__ CUtensorMap tmapC,
+                const __grid_constant__ CUtensorMap tmapK,
                 float *__restrict__ A, __half *__restrict__ A16,
                 float *__restrict__ Alo, const SolveDesc *__restrict__ solves, const int64_t *__restrict__ pre,
-                int nsolve, int64_t ntasks, int mode, int K0, int W, int *__restrict__ err) {
+                int nsolve, int64_t ntasks, int mode, int K0, int W, int first, int *__restrict__ err) {
     using Cfg = TcCfg<MODE>;
     constexpr bool X3 = Cfg::SPLIT;                              // split warps
     constexpr bool X3MMA = MODE == TC_TF32X3 || MODE == TC_TF32X3P || MODE == TC_TRSM;  // three TF32 passes
@@ -466,9 +631,12 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                 unsigned char *sb = sa + TC_HALF;
                 const int kt = g.kb + c / KCH;
                 const int x = (c % KCH) * KEL;
-                const int ya = (int)((S.ltile0 + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
+                // first touch of a panel tile (K0 = 0): A_i0 is K_i0 of the kernel store
+                const bool kfirst = first && mode == UPD_TRSM;
+                const int ya =
+                    (int)(((kfirst ? S.ktile0 : S.ltile0) + (int64_t)g.i * (g.i + 1) / 2 + kt) * KRR_TILE);
                 mbar_arrive_expect_tx(&full[st], (Cfg::PRE ? 4 : 2) * TC_HALF);
-                tma_load_2d(sa, &tmap, x, ya, &full[st]);
+                tma_load_2d(sa, kfirst ? &tmapK : &tmap, x, ya, &full[st]);
                 if (mode == UPD_TRSM) {
                     tma_load_2d(sb, &tmapZ, x, (int)((S.dtile0 + kt) * KRR_TILE), &full[st]);
                 } else {
@@ -619,17 +787,20 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
         constexpr uint32_t BOX = (uint32_t)KRR_TILE * 32 * 4;       // one 32-column box, 16 KB
         constexpr int CBOX = (int)(Cfg::CBUF / BOX);               // boxes held in cbuf
         constexpr int NH = CBOX > 0 ? (KRR_TILE / 32) / CBOX : 1;  // cbuf rounds per tile
+        // the destination's first touch (K0 = 0) lands the kernel-store tile
+        // instead: A_ij = K_ij + lambda m [i = j] before this update
         auto c_tile_y = [&](int64_t tt) {
             SolveDesc S2;
             TaskGeom g2;
             task(tt, S2, g2);
-            return (int)((S2.ltile0 + (int64_t)g2.i * (g2.i + 1) / 2 + g2.j) * KRR_TILE);
+            return (int)(((first ? S2.ktile0 : S2.ltile0) + (int64_t)g2.i * (g2.i + 1) / 2 + g2.j) * KRR_TILE);
         };
         // round h of task tt: boxes h CBOX .. h CBOX + CBOX - 1 of its destination tile
         auto c_load = [&](int64_t tt, int h) {
             const int y = c_tile_y(tt);
             mbar_arrive_expect_tx(cfull, Cfg::CBUF);
-            for (int k = 0; k < CBOX; ++k) tma_load_2d(cbuf + k * BOX, &tmapC, (h * CBOX + k) * 32, y, cfull);
+            for (int k = 0; k < CBOX; ++k)
+                tma_load_2d(cbuf + k * BOX, first ? &tmapK : &tmapC, (h * CBOX + k) * 32, y, cfull);
         };
         if (tma_c) {
             if (threadIdx.x == 64 && (int64_t)blockIdx.x < ntasks) c_load(blockIdx.x, 0);
@@ -656,6 +827,12 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                                 tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(b * KRR_TILE + cb * 32), v);
                             // row r of the box: 16-byte unit q at q ^ (r % 8)
                             unsigned char *row = cbuf + k * BOX + r * 128;
+                            if (first && g.i == g.j && (r >> 5) == cb && g.i * KRR_TILE + r < S.m) {
+                                // first touch of a diagonal tile: its real diagonal gets lambda m
+                                float *dd = reinterpret_cast<float *>(row + ((((r & 31) >> 2) ^ (r & 7)) << 4)) +
+                                            (r & 3);
+                                *dd += (float)S.lambda_m;
+                            }
 #pragma unroll
                             for (int qq = 0; qq < 8; ++qq) {
                                 float4 *p4 = reinterpret_cast<float4 *>(row + ((qq ^ (r & 7)) << 4));
@@ -892,9 +1069,11 @@ template <typename T>
 cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, T *A, T *Z,
                             __half *A16, float *Alo, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
                             const CUtensorMap *tmap, const CUtensorMap *tmapZ, const CUtensorMap *tmap16,
-                            const CUtensorMap *tmapLo, int *d_err, Prof *prof) {
+                            const CUtensorMap *tmapLo, const float *Kfirst, const CUtensorMap *tmapK, int *d_err,
+                            Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
     allow_max_dyn_smem(potrf_tile_kernel<T>);
+    allow_max_dyn_smem(potrf_blocked_kernel);
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -904,8 +1083,12 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
         ProfScope ps(prof, L.kind == 0 ? PROF_POTRF : (L.kind == 1 ? PROF_TRSM : PROF_UPDATE), st);
         if (L.kind == 0) {
             KRR_LAUNCHED();
-            const cudaError_t e = launch_pdl(potrf_tile_kernel<T>, grid, 512, po_sm, st, A, Z, d_solves, p, nsolve,
-                                             L.K0, flags);
+            cudaError_t e;
+            if constexpr (sizeof(T) == 4)
+                e = launch_pdl(potrf_blocked_kernel, grid, 512, PO_BLOCKED_SMEM, st, A, Z, Kfirst, d_solves, p,
+                               nsolve, L.K0, flags);
+            else
+                e = launch_pdl(potrf_tile_kernel<T>, grid, 512, po_sm, st, A, Z, d_solves, p, nsolve, L.K0, flags);
             if (e != cudaSuccess) return e;
             continue;
         }
@@ -930,10 +1113,12 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                 const unsigned pgrid = (unsigned)std::min<int64_t>(L.tasks, nsm);  // persistent: one CTA per SM
                 float *Af = reinterpret_cast<float *>(A);
                 const CUtensorMap &tmLo = tmapLo ? *tmapLo : *tmap;
+                const CUtensorMap &tmK = tmapK ? *tmapK : *tmap;
+                const int first = (Kfirst != nullptr && tmapK != nullptr && L.K0 == 0) ? 1 : 0;
                 auto go = [&](auto kern, unsigned threads, size_t smem, const CUtensorMap &opmap) {
                     KRR_LAUNCHED();
-                    return launch_pdl(kern, pgrid, threads, smem, st, opmap, *tmapZ, tmLo, *tmap, Af, A16, Alo,
-                                      d_solves, p, nsolve, L.tasks, mode, L.K0, W, d_err);
+                    return launch_pdl(kern, pgrid, threads, smem, st, opmap, *tmapZ, tmLo, *tmap, tmK, Af, A16, Alo,
+                                      d_solves, p, nsolve, L.tasks, mode, L.K0, W, first, d_err);
                 };
                 cudaError_t err;
                 if (m == TC_TRSM)
@@ -963,7 +1148,8 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
 cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, const int64_t *d_pre, void *A, void *Z,
                           bool fp64, const SolveDesc *d_solves, int nsolve, int32_t *flags, int tc,
                           const CUtensorMap *tmap, const CUtensorMap *tmapZ, __half *A16, const CUtensorMap *tmap16,
-                          float *Alo, const CUtensorMap *tmapLo, int *d_err, Prof *prof) {
+                          float *Alo, const CUtensorMap *tmapLo, const float *Kfirst, const CUtensorMap *tmapK,
+                          int *d_err, Prof *prof) {
     allow_max_dyn_smem(tile_mma_kernel<TC_F16>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3>);
     allow_max_dyn_smem(tile_mma_kernel<TC_TF32X3P>);
@@ -971,9 +1157,9 @@ cudaError_t run_chol_plan(cudaStream_t st, const std::vector<CholLaunch> &plan, 
     allow_max_dyn_smem(tile_mma_kernel<TC_BF16X3>);
     if (fp64)
         return run_chol_plan_t<double>(st, plan, d_pre, (double *)A, (double *)Z, nullptr, nullptr, d_solves, nsolve,
-                                       flags, 0, tmap, tmapZ, nullptr, nullptr, d_err, prof);
+                                       flags, 0, tmap, tmapZ, nullptr, nullptr, nullptr, nullptr, d_err, prof);
     return run_chol_plan_t<float>(st, plan, d_pre, (float *)A, (float *)Z, A16, Alo, d_solves, nsolve, flags, tc,
-                                  tmap, tmapZ, tmap16, tmapLo, d_err, prof);
+                                  tmap, tmapZ, tmap16, tmapLo, Kfirst, tmapK, d_err, prof);
 }
 
 }  // namespace krr

@@ -160,6 +160,7 @@ struct Ctx {
     double target_err = 1e-7;  // refinement stops once kappa_est * backward error <= this
     double escalate = 32.0;    // TF32: factor a solve in 3 passes when kappa_est * 2^-11 exceeds this
     int kernel = KRR_KERNEL_GAUSSIAN;  // Table 1 kernel of the next fits
+    bool fp64_fallback = true;  // re-solve unconverged refined-precision solves on the FP64 path
     std::map<std::pair<int, int>, int> tuned_W;  // (precision, max tiles) -> tuned panel width
 };
 

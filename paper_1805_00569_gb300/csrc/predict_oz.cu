@@ -528,6 +528,7 @@ struct OzKParams {
     float *rsR, *rsC;
     const int64_t *rsoff;  // per partition: first slot of its grid (sigma 0)
     int64_t rstot;         // slots per sigma (sum of T^2)
+    int store_factor;      // also store K_hi + lambda m I per lambda (0: the factorisation reads K_hi itself)
 };
 
 __device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64_t tile) {
@@ -800,7 +801,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             tma_store_2d(&tmKh, c * OZ_N + 32 * bx, y, sm.stage[0][bx]);
                             tma_store_2d(&tmKl, c * OZ_N + 32 * bx, y, sm.stage[1][bx]);
                         }
-                        if (!diag)
+                        if (!diag && kp.store_factor)
                             for (int il = 0; il < kp.nlam; ++il) {
                                 const int yf =
                                     (int)((solves[(int64_t)pj * G + is * kp.nlam + il].ltile0 + lt) * KRR_TILE);
@@ -809,7 +810,7 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                             }
                         bulk_commit();
                     }
-                    if (diag) {  // factor tiles: K_hi + lambda m on the real diagonal
+                    if (diag && kp.store_factor) {  // factor tiles: K_hi + lambda m on the real diagonal
                         for (int il = 0; il < kp.nlam; ++il) {
                             if (et == 0) bulk_wait_read_all();
                             epi_bar_p();  // the staging copy is no longer being read
@@ -893,9 +894,12 @@ void launch_oz_slice(cudaStream_t st, const double *X, int d, const int64_t *map
 size_t oz_smem_bytes() { return sizeof(OzSmem) + 1024; }
 static size_t oz_psmem_bytes() { return sizeof(OzPSmem) + 1024; }
 
-// Kernel tiles of every partition and sigma, plus the factor matrices.
+// Kernel tiles of every partition and sigma, plus (store_factor) the factor
+// matrices K_hi + lambda m I; without them the factorisation's first touch of
+// each factor tile reads K_hi and adds lambda m itself.
 cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
-                             float *rsR, float *rsC, const int64_t *rsoff, int64_t rstot, int *d_err) {
+                             float *rsR, float *rsC, const int64_t *rsoff, int64_t rstot, int *d_err,
+                             bool store_factor) {
     if (ktot == 0) return cudaSuccess;
     CUtensorMap tmA, tmKh, tmKl, tmF;
     if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
@@ -915,6 +919,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
     kp.rsC = rsC;
     kp.rsoff = rsoff;
     kp.rstot = rstot;
+    kp.store_factor = store_factor ? 1 : 0;
     for (int i = 0; i < 8; ++i) {
         const double c = i < M.nsig ? -1.0 / (2.0 * M.sigmas[i] * M.sigmas[i]) : 0.0;
         kp.c_hi[i] = (float)c;

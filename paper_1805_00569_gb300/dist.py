@@ -192,6 +192,15 @@ def global_best(local_mse: torch.Tensor, local_offset: int):
     return int(best[1]), best[0]
 
 
+def sum_over_ranks(t: torch.Tensor) -> torch.Tensor:
+    """Element-wise sum of a tensor over ranks (a copy; the input at one rank)."""
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t.clone()
+    buf = t.detach().to(_comm_device()).clone()
+    dist.all_reduce(buf)
+    return buf.to(t.device)
+
+
 def max_over_ranks(x: float) -> float:
     if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
         return x

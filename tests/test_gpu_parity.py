@@ -647,10 +647,11 @@ def test_budget_and_argument_errors(ctx):
     with pytest.raises(K.KrrError) as e:
         K.krr_fit_batch(ctx, X, y, perm, off, [0.0], [1e-3], "tf32")
     assert e.value.status == K.KRR_ERR_ARG
-    bad = cuda(np.array([0, 599]), torch.int64)
-    with pytest.raises(K.KrrError) as e:
-        K.krr_fit_batch(ctx, X, y, perm, bad, [1.0], [1e-3], "tf32")
-    assert e.value.status == K.KRR_ERR_ARG
+    for bad_off in ([0, 601], [1, 600], [0, 400, 300]):  # beyond n, not from 0, decreasing
+        bad = cuda(np.array(bad_off), torch.int64)
+        with pytest.raises(K.KrrError) as e:
+            K.krr_fit_batch(ctx, X, y, perm, bad, [1.0], [1e-3], "tf32")
+        assert e.value.status == K.KRR_ERR_ARG
     with pytest.raises(K.KrrError) as e:
         K.krr_partition(ctx, X, None, K.KRR_PART_RANDOM, 0)
     assert e.value.status == K.KRR_ERR_ARG
@@ -692,3 +693,45 @@ def test_kmeans_steps_and_partition_subset_fit(ctx):
     finally:
         full.free()
         part.free()
+
+
+def _serve_request_5943():
+    """Request 5943 of the serving stream (seed 4): n = 589, d = 8,
+    sigma ~ 12, lambda ~ 1.4e-7 (kappa_est ~ 5e6), rows as the benchmark's
+    stream draws them (row prefix of its feature count's mixture bank)."""
+    st = synth.serve_stream(seed=4, requests=10000)
+    i = 5943
+    n, d = int(st["n"][i]), int(st["d"][i])
+    b = int(st["data_seed"][i] % 32)
+    src = synth.serve_request_data(1000003 * d + b, int(max(st["n"])), d, 256)
+    return src["X"][:n], src["y"][:n], src["Xt"], float(st["sigma"][i]), float(st["lam"][i])
+
+
+def test_fp64_fallback_for_an_unconverged_solve():
+    """A served request whose FP32-class factor broke down (the shifted
+    refactorisation then preconditions too poorly for the refinement to
+    converge in 80 iterations) is solved again on the plain FP64 path: status
+    OK, factor class 0, alpha and predictions within the refined bar."""
+    X, y, Xt, sigma, lam = _serve_request_5943()
+    n = X.shape[0]
+    perm = cuda(np.arange(n, dtype=np.int64), torch.int64)
+    off = cuda(np.array([0, n], np.int64), torch.int64)
+    out = {}
+    for on in (False, True):
+        c = K.krr_ctx_create(0)
+        K.krr_ctx_set_panel_width(c, 8)
+        K.krr_ctx_set_fp64_fallback(c, on)
+        model, status, alpha = K.krr_fit_batch(c, cuda(X), cuda(y), perm, off, [sigma], [lam], "tf32",
+                                               want_alpha=True)
+        out[on] = (int(status.cpu()[0]), int(K.krr_model_factor_class(c, model)[0]), alpha.cpu().numpy(),
+                   K.krr_predict(c, model, cuda(Xt)).cpu().numpy()[0])
+        model.free()
+        c.close()
+    st_on, cls_on, a_on, y_on = out[True]
+    assert st_on == K.KRR_OK
+    if out[False][0] == K.KRR_ERR_NO_CONVERGE:
+        assert cls_on == 0
+    oa, info, rc = oracle.fit(X, y, sigma, lam)
+    assert rc == 0 and info[0] > 1e6
+    assert rel(a_on, oa) <= REFINED_TOL
+    assert rel(y_on, oracle.predict(X, oa, Xt, sigma)) <= REFINED_TOL
