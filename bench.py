@@ -72,6 +72,8 @@ def parse():
                     help="bkrr2/kkrr2: take the multi-GPU (LPT-sharded) step even on one GPU")
     ap.add_argument("--no-serve", action="store_true",
                     help="bkrr2 line without its serve object (the request stream through the serving loop)")
+    ap.add_argument("--serve-batch", type=int, default=8,
+                    help="serve: waiting fits of one feature count packed into one krr_fit_jobs call (1 = off)")
     ap.add_argument("--serve-bank", type=int, default=32,
                     help="serve: mixtures drawn per feature count; requests take row prefixes (0 = one per request)")
     ap.add_argument("--slots", type=int, default=16, help="serve: concurrent requests (one stream each)")
@@ -755,10 +757,12 @@ def run_serve(args, rank, world, local_rank):
 
     def replay(rq, slots, prec, realtime):
         ex = GpuExecutor(slots, prec=prec, device=local_rank, resident_bytes=16 << 30)
+        mb = args.serve_batch if prec != "fp64" else 1
         try:
-            Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t).run(
-                warm[:2 * slots] if prec != "fp64" else warm[:1], realtime=False)
-            sc = Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t)
+            Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t,
+                      max_batch=mb).run(warm[:2 * slots] if prec != "fp64" else warm[:1], realtime=False)
+            sc = Scheduler(ex, slots, budget, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=t,
+                           max_batch=mb)
             torch.cuda.synchronize()
             res = sc.run(rq, realtime=realtime)
             torch.cuda.synchronize()
@@ -791,6 +795,8 @@ def run_serve(args, rank, world, local_rank):
                                                    + by_id[r.rid].payload["y"].nbytes) for r in cap) / len(cap)
     return dict(value=ok / span, span=span, ok=ok, fits=fits, live=latency_summary(live),
                 cap=latency_summary(cap), peak_conc=(sc_live.peak_concurrency, sc_cap.peak_concurrency),
+                packed=({"batches": sc_live.batches, "requests": sc_live.batched_requests},
+                        {"batches": sc_cap.batches, "requests": sc_cap.batched_requests}),
                 peak_bytes=(sc_live.peak_in_use, sc_cap.peak_in_use), seq=seq, clocks=clk, launches=launches,
                 h2d=h2d, offered=float(len(reqs) / st["arrival"][len(reqs) - 1]))
 
@@ -810,7 +816,8 @@ def main_serve(args, rank, world, local_rank):
                    "l2": "inputs of concurrent requests exceed L2; no flush between requests"},
         "serve": {"offered_rps": res["offered"], "at_offered_load": res["live"], "saturated": res["cap"],
                   "peak_concurrency": res["peak_conc"], "peak_admitted_bytes": res["peak_bytes"],
-                  "fits": res["fits"]},
+                  "fits": res["fits"], "max_batch": args.serve_batch,
+                  "packed_batches": {"at_offered_load": res["packed"][0], "saturated": res["packed"][1]}},
         "fp64_sequential": res["seq"],
         "roofline": None, "roofline_note": "concurrent streams: per-kernel durations overlap; see the bkrr2 line",
         "cpu_baseline": None,
@@ -916,6 +923,8 @@ def serve_object(args, res) -> dict:
             "completed": res["live"]["completed"], "requests": args.requests,
             "at_offered_load": res["live"], "saturated": res["cap"], "saturated_rps": res["value"],
             "peak_concurrency": res["peak_conc"], "peak_admitted_bytes": res["peak_bytes"], "fits": res["fits"],
+            "max_batch": args.serve_batch,
+            "packed_batches": {"at_offered_load": res["packed"][0], "saturated": res["packed"][1]},
             "e2e_note": "every request's latency includes its host-to-device copies and the read-back of its "
                         "predictions"}
 

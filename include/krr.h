@@ -162,6 +162,26 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                          const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
                          int32_t *solve_status, double *alpha);
 
+/* Independent problems in one batched fit: partition j is its own KRR
+ * problem (Eq. 6 for X_j = X[perm[offsets[j] .. offsets[j+1])]) with its own
+ * sigmas[j] and lambdas[j] (HOST arrays of p values) -- the batching form that
+ * packs queued requests of different sizes and hyper-parameters into the same
+ * launches as uneven partitions (the paper's partitions share one grid; its
+ * independent per-partition solves are what makes the packing exact).  One
+ * model per partition: solve/model index j, alpha block j at offsets[j].
+ * Otherwise as krr_fit_batch (same precisions, refinement, FP64 re-solve of
+ * unconverged solves, status words); predict with krr_predict (route[q] = the
+ * partition of test row q; yhat [1 x t]).  Each partition's result is the
+ * same bits whatever else is in the batch (every solve runs on its own
+ * tiles, and a converged solve stops) at a fixed panel width
+ * (krr_ctx_set_panel_width).  Needs a refined precision (FP32, TF32,
+ * BF16X3), the Gaussian kernel and d <= 96, else KRR_ERR_UNSUPPORTED.
+ * Errors as krr_fit_batch. */
+krr_status krr_fit_jobs(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                        const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas,
+                        const double *lambdas, krr_prec prec, krr_model **out, int32_t *solve_status,
+                        double *alpha);
+
 /* Eq. 7 prediction, fused: kernel rows are built on the fly and contracted
  * with alpha; K(test, train) is never stored.
  *   Xt [t x d].  route == NULL: every model predicts every test row and

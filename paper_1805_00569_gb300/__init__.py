@@ -74,6 +74,7 @@ def load(build_if_missing: bool = True):
     L.krr_partition.argtypes = [P, P, i64, i32, P, i64, ctypes.c_int, i32, i32, u64, P, P, P, P, P, P]
     L.krr_fit_batch.argtypes = [P, P, P, i64, i32, P, P, i32, P, i32, P, i32, ctypes.c_int,
                                 ctypes.POINTER(P), P, P]
+    L.krr_fit_jobs.argtypes = [P, P, P, i64, i32, P, P, i32, P, P, ctypes.c_int, ctypes.POINTER(P), P, P]
     L.krr_predict.argtypes = [P, P, P, i64, P, P]
     L.krr_select.argtypes = [P, P, P, i64, i32, i32, ctypes.c_int, P, P]
     L.krr_model_stats.argtypes = [P, P, P, P, P]
@@ -85,7 +86,7 @@ def load(build_if_missing: bool = True):
     L.krr_kmeans_combine.argtypes = [P, P, P, i64, i32, i32, P]
     for name in ("krr_ctx_create", "krr_ctx_destroy", "krr_ctx_set_profiling", "krr_ctx_profile",
                  "krr_ctx_set_panel_width", "krr_ctx_get_panel_width", "krr_ctx_set_target_error",
-                 "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_ctx_set_fp64_fallback", "krr_partition", "krr_fit_batch", "krr_predict", "krr_select",
+                 "krr_ctx_set_escalation", "krr_ctx_wait_probe", "krr_ctx_set_fp64_fallback", "krr_partition", "krr_fit_batch", "krr_fit_jobs", "krr_predict", "krr_select",
                  "krr_model_stats", "krr_model_free", "krr_model_factor_class", "krr_group_rows", "krr_kmeans_assign",
                  "krr_kmeans_block_sums", "krr_kmeans_combine"):
         getattr(L, name).restype = st
@@ -246,6 +247,30 @@ def krr_fit_batch(ctx: Context, X, y, perm, offsets, sigmas, lambdas, prec=KRR_P
                                lam, len(lambdas), int(prec), ctypes.byref(h), _ptr(status), _ptr(alpha))
     ctx.check(rc, "krr_fit_batch")
     return Model(ctx, h, p, len(sigmas), len(lambdas)), status, alpha
+
+
+def krr_fit_jobs(ctx: Context, X, y, perm, offsets, sigmas, lambdas, prec=KRR_PREC_TF32, want_alpha=False):
+    """One independent problem per partition with its own sigma and lambda.
+    Returns (Model with p models, solve_status[p], alpha or None)."""
+    X = _dev(X, torch.float64, "X")
+    y = _dev(y, torch.float64, "y")
+    perm = _dev(perm, torch.int64, "perm")
+    offsets = _dev(offsets, torch.int64, "offsets")
+    if isinstance(prec, str):
+        prec = PREC_NAMES[prec]
+    n, d = X.shape
+    p = offsets.shape[0] - 1
+    if len(sigmas) != p or len(lambdas) != p:
+        raise KrrError(KRR_ERR_ARG, "krr_fit_jobs: one sigma and one lambda per partition")
+    sig = (ctypes.c_double * p)(*[float(s) for s in sigmas])
+    lam = (ctypes.c_double * p)(*[float(v) for v in lambdas])
+    status = torch.empty(p, dtype=torch.int32, device=X.device)
+    alpha = torch.empty(perm.shape[0], dtype=torch.float64, device=X.device) if want_alpha else None
+    h = ctypes.c_void_p()
+    rc = ctx.lib.krr_fit_jobs(ctx.handle, _ptr(X), _ptr(y), n, d, _ptr(perm), _ptr(offsets), p, sig, lam, int(prec),
+                              ctypes.byref(h), _ptr(status), _ptr(alpha))
+    ctx.check(rc, "krr_fit_jobs")
+    return Model(ctx, h, p, 1, 1), status, alpha
 
 
 def krr_predict(ctx: Context, model: Model, Xt, route=None, out=None):

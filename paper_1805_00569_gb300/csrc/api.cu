@@ -69,7 +69,7 @@ bool oz_supported(int d);
 void launch_oz_slice(cudaStream_t, const double *, int, const int64_t *, int64_t, int64_t, void *, int32_t *, float2 *);
 bool make_slice_tmap(CUtensorMap *, void *, int64_t, int, int);
 cudaError_t launch_kbuild_oz(cudaStream_t, const Model &, int64_t, float *, float *, float *, float *, float *,
-                             const int64_t *, int64_t, int *, bool);
+                             const int64_t *, int64_t, int *, bool, const float2 *);
 cudaError_t launch_predict_oz(cudaStream_t, const Model &, const CUtensorMap &, const double *, int64_t,
                               const int64_t *, const int64_t *, int, void *, int32_t *, float2 *, int64_t, double *,
                               int *);
@@ -431,20 +431,27 @@ krr_status krr_partition(krr_ctx *ctx, const double *X, int64_t n, int32_t d, co
     return fail(c, KRR_ERR_ARG, "krr_partition: unknown mode");
 }
 
-krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
-                         const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas, int32_t ns,
-                         const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
-                         int32_t *solve_status, double *alpha) {
+// The fit of krr_fit_batch (a sigma x lambda grid shared by all partitions)
+// and of krr_fit_jobs (per_part: one sigma and one lambda per partition, given
+// in sigmas[p] / lambdas[p], with ns = nl = 1).
+static krr_status fit_impl(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                           const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas, int32_t ns,
+                           const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
+                           int32_t *solve_status, double *alpha, bool per_part) {
     if (!ctx) return KRR_ERR_ARG;
     Ctx *c = &ctx->c;
     if (!out || !X || !y || !perm || !offsets || !sigmas || !lambdas || n <= 0 || d <= 0 || p <= 0 || ns <= 0 ||
         nl <= 0 || ns > 8 || nl > 8 || (prec != KRR_PREC_FP64 && prec != KRR_PREC_FP32 && prec != KRR_PREC_TF32 && prec != KRR_PREC_BF16X3))
         return fail(c, KRR_ERR_ARG, "krr_fit_batch: invalid argument (1 <= ns, nl <= 8)");
-    for (int i = 0; i < ns; ++i)
+    const int nsv = per_part ? p : ns, nlv = per_part ? p : nl;  // values given
+    for (int i = 0; i < nsv; ++i)
         if (!(sigmas[i] > 0.0) || !std::isfinite(sigmas[i]))
             return fail(c, KRR_ERR_ARG, "krr_fit_batch: sigma must be positive and finite");
-    for (int i = 0; i < nl; ++i)
+    for (int i = 0; i < nlv; ++i)
         if (!std::isfinite(lambdas[i])) return fail(c, KRR_ERR_ARG, "krr_fit_batch: lambda must be finite");
+    if (per_part && (prec == KRR_PREC_FP64 || !oz_supported(d) || c->kernel != KRR_KERNEL_GAUSSIAN))
+        return fail(c, KRR_ERR_UNSUPPORTED,
+                    "krr_fit_jobs: needs a refined precision, the Gaussian kernel and d <= 96");
     *out = nullptr;
     cudaSetDevice(c->device);
     cudaStream_t st = c->stream;
@@ -474,8 +481,9 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     M.nlam = nl;
     M.prec = prec;
     M.n = n;
-    M.sigmas.assign(sigmas, sigmas + ns);
-    M.lambdas.assign(lambdas, lambdas + nl);
+    M.sigmas.assign(sigmas, sigmas + nsv);
+    M.lambdas.assign(lambdas, lambdas + nlv);
+    M.per_part = per_part;
     const int G = ns * nl;
     int64_t prow = 0, ktot = 0;
     int maxT = 0;
@@ -524,7 +532,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 S.dtile0 = dtiles;
                 S.ktile0 = Gd.ktile0;
                 S.vec0 = vec;
-                S.lambda_m = lambdas[il] * (double)P.m;
+                S.lambda_m = (per_part ? lambdas[j] : lambdas[il]) * (double)P.m;
                 ltiles += tri(P.T);
                 dtiles += P.T;
                 vec += (int64_t)P.T * KRR_TILE;
@@ -581,6 +589,15 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
     FIT_TRY(model_alloc(c, M, &M.alpha, (size_t)vec * 8));
     FIT_TRY(model_alloc(c, M, &M.d_parts, sizeof(PartDesc) * p));
     FIT_TRY(model_alloc(c, M, &M.d_solves, sizeof(SolveDesc) * nsolve));
+    std::vector<float2> hcpart;  // per_part: -1 / (2 sigma_j^2) as df
+    if (per_part) {
+        for (int j = 0; j < p; ++j) {
+            const double cv = -1.0 / (2.0 * sigmas[j] * sigmas[j]);
+            hcpart.push_back(make_float2((float)cv, (float)(cv - (double)(float)cv)));
+        }
+        FIT_TRY(model_alloc(c, M, &M.d_cpart, sizeof(float2) * p));
+        FIT_TRY(cudaMemcpyAsync(M.d_cpart, hcpart.data(), sizeof(float2) * p, cudaMemcpyHostToDevice, st));
+    }
     FIT_TRY(cudaMemcpyAsync(M.d_parts, M.parts.data(), sizeof(PartDesc) * p, cudaMemcpyHostToDevice, st));
     FIT_TRY(cudaMemcpyAsync(M.d_solves, M.solves.data(), sizeof(SolveDesc) * nsolve, cudaMemcpyHostToDevice, st));
 
@@ -674,7 +691,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
                 if (M.ozS) {
                     // no factor tiles: the factorisation's first touch reads K_hi (Kfirst below)
                     FIT_TRY(launch_kbuild_oz(st, M, ktot, Kh, Kl, (float *)Ast, rsR, rsC, d_rsoff, rstot,
-                                             c->d_err, false));
+                                             c->d_err, false, M.d_cpart));
                 } else {
                     launch_kbuild_df(st, M, ktot, Kh, Kl, (float *)Ast);
                 }
@@ -939,7 +956,7 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
             const int64_t hoff[2] = {0, (int64_t)S.m};
             krr_model *sub = nullptr;
             int32_t hst = KRR_ERR_NO_CONVERGE;
-            const double sg = M.sigmas[S.isig], lm = M.lambdas[S.ilam];
+            const double sg = M.sigmas[per_part ? S.part : S.isig], lm = M.lambdas[per_part ? S.part : S.ilam];
             if (ctx_malloc(c, (void **)&d_off, 16) != cudaSuccess) break;
             if (ctx_malloc(c, (void **)&d_st, 4) != cudaSuccess) {
                 ctx_free(c, d_off, 16);
@@ -978,6 +995,21 @@ krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t
 #undef FIT_TRY
     *out = km;
     return KRR_OK;
+}
+
+krr_status krr_fit_batch(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                         const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas, int32_t ns,
+                         const double *lambdas, int32_t nl, krr_prec prec, krr_model **out,
+                         int32_t *solve_status, double *alpha) {
+    return fit_impl(ctx, X, y, n, d, perm, offsets, p, sigmas, ns, lambdas, nl, prec, out, solve_status, alpha,
+                    false);
+}
+
+krr_status krr_fit_jobs(krr_ctx *ctx, const double *X, const double *y, int64_t n, int32_t d,
+                        const int64_t *perm, const int64_t *offsets, int32_t p, const double *sigmas,
+                        const double *lambdas, krr_prec prec, krr_model **out, int32_t *solve_status,
+                        double *alpha) {
+    return fit_impl(ctx, X, y, n, d, perm, offsets, p, sigmas, 1, lambdas, 1, prec, out, solve_status, alpha, true);
 }
 
 krr_status krr_predict(krr_ctx *ctx, const krr_model *model, const double *Xt, int64_t t, const int32_t *route,

@@ -251,18 +251,37 @@ __global__ void __launch_bounds__(512, 1) potrf_tile_kernel(T *__restrict__ A, T
 // ---------------------------------------------------------------- potrf, blocked (FP32)
 // The same factor L and inverse Z of one FP32 diagonal tile, blocked by 32
 // columns so that block barriers come per block, not per column.  For each
-// 32-column block kb: warp 0 factors the 32 x 32 diagonal block and inverts
-// it in registers (lane i holds row i of the block; row and column values
-// travel by shuffle, no block barrier); then all 16 warps solve the rows
-// below against the block's inverse (L_r,kb = A_r,kb Z_kb,kb^T) and apply its
-// rank-32 update to the lower part of the trailing rows and columns.  The
-// off-diagonal blocks of Z follow by the blocked triangular inverse
-//   Z_ib,jb = -Z_ib,ib sum_{m in blocks [jb, ib)} L_ib,m Z_m,jb.
-// Eighteen block barriers instead of one per column.  The tile is held in
-// shared memory (padded rows: lanes reading a column hit distinct banks).
+// 32-column block kb (rows and columns [o, o + 32), o = 32 kb):
+//   B. warp 0 factors the 32 x 32 diagonal block and inverts it in registers
+//      (lane i holds row i; values travel by shuffle, no block barrier).
+//      Meanwhile the other warps copy the block's columns below the diagonal
+//      block, transposed, into Pt, and form T = L_kb,<o Z_<o,<o, the first
+//      half of the blocked triangular inverse
+//        Z_kb,jb = -Z_kb,kb sum_{m in blocks [jb, kb)} L_kb,m Z_m,jb.
+//   C. the rows below solve against the block's inverse,
+//      L_r,kb = A_r,kb Z_kb,kb^T, while Z_kb,<o = -Z_kb,kb T completes the
+//      inverse's block row; then the block's rank-32 update of the lower
+//      trailing part.
+// The products run as 4 x 4 register tiles from 16-byte shared loads of the
+// transposed panel (two loads per 16 fused multiply-adds).  Seventeen block
+// barriers instead of one per column.  Shared memory: the tile (padded rows:
+// lanes reading a column hit distinct banks), Z, the transposed panel Pt,
+// the diagonal block's inverse transposed (Zt) and T.
 constexpr int PO_B = 32;               // block width
-constexpr int PO_LD = KRR_TILE + 1;    // padded row stride in shared memory
-constexpr size_t PO_BLOCKED_SMEM = (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (KRR_TILE - PO_B)) * sizeof(float);
+constexpr int PO_LD = KRR_TILE + 1;    // padded row stride of the tile and of Z
+constexpr int PO_PT = KRR_TILE + 4;    // row stride of Pt (16-byte rows)
+constexpr int PO_ZT = PO_B + 4;        // row stride of Zt
+constexpr int PO_TT = KRR_TILE - PO_B + 4;  // row stride of T
+constexpr size_t PO_BLOCKED_SMEM =
+    (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (2 * PO_PT + PO_ZT + PO_TT)) * sizeof(float);
+
+__device__ __forceinline__ void po_tri_decode(int t, int &a, int &b) {  // t = a (a + 1) / 2 + b, b <= a
+    int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
+    while ((r + 1) * (r + 2) / 2 <= t) ++r;
+    while (r * (r + 1) / 2 > t) --r;
+    a = r;
+    b = t - r * (r + 1) / 2;
+}
 
 __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
                                                                const float *__restrict__ Kfirst,
@@ -272,8 +291,10 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
     extern __shared__ __align__(16) unsigned char po_dyn[];
     float *Ls = reinterpret_cast<float *>(po_dyn);  // [128][PO_LD]: A, becoming L
     float *Zs = Ls + KRR_TILE * PO_LD;              // [128][PO_LD]: Z
-    float *Ts = Zs + KRR_TILE * PO_LD;              // [32][96]: L_ib,: Z_:,jb of the blocked inverse
-    constexpr int TW = KRR_TILE - PO_B;
+    float *Pt = Zs + KRR_TILE * PO_LD;              // [32][PO_PT]: Pt[kk][r] = (A or L)_r,o+kk
+    float *Zt = Pt + PO_B * PO_PT;                  // [32][PO_ZT]: Zt[kk][c] = Z_o+c,o+kk
+    float *Ts = Zt + PO_B * PO_ZT;                  // [32][PO_TT]: T of the blocked inverse
+    float *Pn = Ts + PO_B * PO_TT;                  // [32][PO_PT]: Pn[c][r] = L_r,o+c (the solved panel)
     __shared__ int bad_sh;
     pdl_launch_dependents();
     pdl_wait();  // the column update of this diagonal tile has completed
@@ -296,6 +317,9 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
 #pragma unroll 1
     for (int kb = 0; kb < KRR_TILE / PO_B; ++kb) {
         const int o = kb * PO_B;
+        const int b0 = o + PO_B;             // first row below the block
+        const int nr = KRR_TILE - b0;        // rows below the block
+        // ---- B: the diagonal block (warp 0); Pt and T (warps 1..15)
         if (warp == 0) {
             // factor: step q scales column q by 1 / sqrt(pivot) and updates
             // the columns right of it; entries right of a lane's diagonal
@@ -320,89 +344,141 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
 #pragma unroll
                 for (int j = q + 1; j < PO_B; ++j) d[j] = fmaf(-l, __shfl_sync(0xffffffffu, l, j), d[j]);
             }
+            // the block's L rows go to shared memory first: the inverse reads
+            // row i of L there (one broadcast load per entry), not by shuffle
+#pragma unroll
+            for (int j = 0; j < PO_B; ++j)
+                if (j <= lane) Ls[(o + lane) * PO_LD + o + j] = d[j];
+            Zt[lane * PO_ZT + PO_B] = dinv;  // spare column of Zt: 1 / L_ii
+            __syncwarp();
             // inverse of the block: lane j forms column j, row by row
             float z[PO_B];
 #pragma unroll
             for (int i = 0; i < PO_B; ++i) {
-                const float inv_ii = __shfl_sync(0xffffffffu, dinv, i);
+                const float inv_ii = Zt[i * PO_ZT + PO_B];
+                const float *li = Ls + (o + i) * PO_LD + o;
                 float a0 = 0.f, a1 = 0.f;
 #pragma unroll
                 for (int kk = 0; kk < i; ++kk) {
-                    const float lik = __shfl_sync(0xffffffffu, d[kk], i);
-                    if (kk & 1) a1 = fmaf(lik, z[kk], a1);
-                    else a0 = fmaf(lik, z[kk], a0);
+                    if (kk & 1) a1 = fmaf(li[kk], z[kk], a1);
+                    else a0 = fmaf(li[kk], z[kk], a0);
                 }
                 z[i] = lane == i ? inv_ii : (lane < i ? -(a0 + a1) * inv_ii : 0.f);
             }
+            __syncwarp();
 #pragma unroll
-            for (int j = 0; j < PO_B; ++j)
-                if (j <= lane) Ls[(o + lane) * PO_LD + o + j] = d[j];
-#pragma unroll
-            for (int i = 0; i < PO_B; ++i)
-                if (i >= lane) Zs[(o + i) * PO_LD + o + lane] = z[i];
+            for (int i = 0; i < PO_B; ++i) {
+                Zs[(o + i) * PO_LD + o + lane] = i >= lane ? z[i] : 0.f;
+                Zt[lane * PO_ZT + i] = i >= lane ? z[i] : 0.f;  // Zt[kk = lane][c = i] = Z_o+i,o+lane
+            }
             if (bad && lane == 0) bad_sh = 1;
-        }
-        __syncthreads();
-        const int nr = KRR_TILE - o - PO_B;  // rows below the block
-        if (nr == 0) break;
-        // rows below: L_r,o+c = sum_kk A_r,o+kk Z_o+c,o+kk (Z_o+c,o+kk = 0 for kk > c)
-        float outv[TW * PO_B / 512];
-#pragma unroll
-        for (int u = 0; u < TW * PO_B / 512; ++u) {
-            const int e = tid + u * 512;
-            float acc = 0.f;
-            if (e < nr * PO_B) {
-                const float *ar = Ls + (o + PO_B + (e >> 5)) * PO_LD + o;
-                const float *zc = Zs + (o + (e & 31)) * PO_LD + o;
-#pragma unroll
-                for (int kk = 0; kk < PO_B; ++kk) acc = fmaf(ar[kk], zc[kk], acc);
+        } else {
+            const int t2 = tid - 32;  // 0..479
+            // Pt[kk][r] = A_r,o+kk for the rows below the block
+            for (int e = t2; e < nr * PO_B; e += blockDim.x - 32) {
+                const int kk = e / nr, r = b0 + (e - kk * nr);
+                Pt[kk * PO_PT + r] = Ls[r * PO_LD + o + kk];
             }
-            outv[u] = acc;
-        }
-        __syncthreads();
+            // T_i,c = sum_{m < o} L_o+i,m Z_m,c for c < o (Z_m,c = 0 for m < c): 4 x 4 tiles
+            const int ntt = (PO_B / 4) * (o / 4);
+            for (int t = t2; t < ntt; t += blockDim.x - 32) {
+                const int i0 = (t / (o / 4)) * 4, c0 = (t % (o / 4)) * 4;
+                float acc[4][4] = {};
+                for (int m = c0; m < o; ++m) {
+                    float lv[4], zv[4];
 #pragma unroll
-        for (int u = 0; u < TW * PO_B / 512; ++u) {
-            const int e = tid + u * 512;
-            if (e < nr * PO_B) Ls[(o + PO_B + (e >> 5)) * PO_LD + o + (e & 31)] = outv[u];
-        }
-        __syncthreads();
-        // rank-32 update of the lower trailing part
-        const int b0 = o + PO_B;
-        for (int e = tid; e < nr * nr; e += blockDim.x) {
-            const int r = e / nr, c = e - r * nr;
-            if (c > r) continue;
-            const float *lr = Ls + (b0 + r) * PO_LD + o, *lc = Ls + (b0 + c) * PO_LD + o;
-            float a0 = 0.f, a1 = 0.f;
+                    for (int u = 0; u < 4; ++u) {
+                        lv[u] = Ls[(o + i0 + u) * PO_LD + m];
+                        zv[u] = Zs[m * PO_LD + c0 + u];
+                    }
 #pragma unroll
-            for (int kk = 0; kk < PO_B; kk += 2) {
-                a0 = fmaf(lr[kk], lc[kk], a0);
-                a1 = fmaf(lr[kk + 1], lc[kk + 1], a1);
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(lv[u], zv[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    *reinterpret_cast<float4 *>(Ts + (i0 + u) * PO_TT + c0) =
+                        make_float4(acc[u][0], acc[u][1], acc[u][2], acc[u][3]);
             }
-            Ls[(b0 + r) * PO_LD + b0 + c] -= a0 + a1;
+        }
+        __syncthreads();
+        // ---- C: rows below and the inverse's block row, as one list of 4 x 4 tiles:
+        // tiles [0, np) solve rows below into Pn (transposed, like Pt), tiles
+        // [np, np + nz) form Z_kb,<o = -Z_kb,kb T
+        const int np = (nr / 4) * (PO_B / 4), nz = (PO_B / 4) * (o / 4);
+        for (int t = tid; t < np + nz; t += blockDim.x) {
+            float acc[4][4] = {};
+            if (t < np) {
+                const int r0 = b0 + (t >> 3) * 4, c0 = (t & 7) * 4;
+#pragma unroll 4
+                for (int kk = 0; kk < PO_B; ++kk) {  // Z_o+c,o+kk = 0 for kk > c
+                    const float4 a = *reinterpret_cast<const float4 *>(Pt + kk * PO_PT + r0);
+                    const float4 zz = *reinterpret_cast<const float4 *>(Zt + kk * PO_ZT + c0);
+                    const float av[4] = {a.x, a.y, a.z, a.w}, zv[4] = {zz.x, zz.y, zz.z, zz.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], zv[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    *reinterpret_cast<float4 *>(Pn + (c0 + v) * PO_PT + r0) =
+                        make_float4(acc[0][v], acc[1][v], acc[2][v], acc[3][v]);
+            } else {
+                const int tz = t - np;
+                const int i0 = (tz / (o / 4)) * 4, c0 = (tz % (o / 4)) * 4;
+#pragma unroll 4
+                for (int kk = 0; kk < PO_B; ++kk) {  // Z_o+i,o+kk = 0 for kk > i
+                    const float4 tt = *reinterpret_cast<const float4 *>(Ts + kk * PO_TT + c0);
+                    const float tv[4] = {tt.x, tt.y, tt.z, tt.w};
+                    float zv[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) zv[u] = Zs[(o + i0 + u) * PO_LD + o + kk];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(zv[u], tv[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) Zs[(o + i0 + u) * PO_LD + c0 + v] = -acc[u][v];
+            }
+        }
+        if (nr == 0) break;  // the last block has nothing below it
+        __syncthreads();
+        // the solved panel into the tile: L_r,o+c = Pn[c][r]
+        for (int e = tid; e < nr * PO_B; e += blockDim.x) {
+            const int c = e / nr, r = b0 + (e - c * nr);
+            Ls[r * PO_LD + o + c] = Pn[c * PO_PT + r];
+        }
+        // rank-32 update of the lower trailing part, 4 x 4 tiles (a, b), b <= a
+        const int RT = nr / 4;
+        for (int t = tid; t < RT * (RT + 1) / 2; t += blockDim.x) {
+            int a, b;
+            po_tri_decode(t, a, b);
+            const int r0 = b0 + 4 * a, c0 = b0 + 4 * b;
+            float acc[4][4] = {};
+#pragma unroll 4
+            for (int kk = 0; kk < PO_B; ++kk) {
+                const float4 x = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + r0);
+                const float4 y = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + c0);
+                const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v)
+                    if (a != b || v <= u) Ls[(r0 + u) * PO_LD + c0 + v] -= acc[u][v];
         }
         __syncthreads();
     }
-    // off-diagonal blocks of Z, block row by block row
-#pragma unroll 1
-    for (int ib = 1; ib < KRR_TILE / PO_B; ++ib) {
-        const int w = ib * PO_B;
-        for (int e = tid; e < PO_B * w; e += blockDim.x) {  // T_i,c = sum_{m < w} L_w+i,m Z_m,c (Z_m,c = 0, m < c)
-            const int i = e / w, c = e - i * w;
-            const float *lr = Ls + (w + i) * PO_LD;
-            float acc = 0.f;
-            for (int m = c; m < w; ++m) acc = fmaf(lr[m], Zs[m * PO_LD + c], acc);
-            Ts[i * TW + c] = acc;
-        }
-        __syncthreads();
-        for (int e = tid; e < PO_B * w; e += blockDim.x) {  // Z_w+i,c = -sum_{kk <= i} Z_w+i,w+kk T_kk,c
-            const int i = e / w, c = e - i * w;
-            const float *zr = Zs + (w + i) * PO_LD + w;
-            float acc = 0.f;
-            for (int kk = 0; kk <= i; ++kk) acc = fmaf(zr[kk], Ts[kk * TW + c], acc);
-            Zs[(w + i) * PO_LD + c] = -acc;
-        }
-        __syncthreads();
-    }
+    __syncthreads();
     if (tid == 0 && bad_sh) flags[s] = 1;
     float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
     for (int e = tid; e < KRR_TILE_ELEMS; e += blockDim.x) {

@@ -182,6 +182,8 @@ struct Model {
     int32_t *ozex = nullptr;   // per-row slice exponent [prows]
     int32_t dpz = 0;           // features padded to the slice K chunk
     CUtensorMap oz_tmB;        // TMA view of ozS for the training-row operand
+    bool per_part = false;     // one (sigma, lambda) per partition (krr_fit_jobs): sigmas/lambdas have p entries
+    float2 *d_cpart = nullptr; // per_part: -1 / (2 sigma_j^2) as df per partition
     std::vector<int32_t> st_iters, st_status, st_class;  // per-solve refinement statistics, factor class
     std::vector<double> st_kappa, st_resid;
     std::vector<std::pair<void *, size_t>> allocs;

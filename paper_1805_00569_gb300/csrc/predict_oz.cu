@@ -79,6 +79,7 @@ struct OzParams {
     float c_hi[OZ_NSP], c_lo[OZ_NSP];  // -1 / (2 sigma^2) as df
     int kc;                              // K chunks of 32 features
     int64_t t_rows;                      // rows per slice in the test slice array
+    const float2 *cpart;                 // per-partition -1 / (2 sigma_j^2) (one sigma per partition), or null
 };
 
 // Shared-memory descriptor, K-major operand with the 64-byte swizzle
@@ -324,6 +325,18 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         int ksh[OZ_NSP];       // range shift of the accumulators per sigma (exp_row_shift)
         float dmin = INFINITY;  // smallest distance to a real training row so far
         const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..511
+        // -1 / (2 sigma^2) per sigma slot: the launch's grid, or the partition's own sigma
+        float chi[OZ_NSP], clo[OZ_NSP];
+#pragma unroll
+        for (int a = 0; a < OZ_NSP; ++a) {
+            chi[a] = pp.c_hi[a];
+            clo[a] = pp.c_lo[a];
+        }
+        if (pp.cpart) {
+            const float2 cj = pp.cpart[j];
+            chi[0] = cj.x;
+            clo[0] = cj.y;
+        }
 #pragma unroll
         for (int a = 0; a < OZ_NSP; ++a) {
             ksh[a] = KRR_SHIFT_NONE;  // no term yet: the shift argument stays 0
@@ -389,7 +402,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     dmin = dm;
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
-                        const int kn = is < pp.nsig ? exp_row_shift(dmin * pp.c_hi[is]) : 0;
+                        const int kn = is < pp.nsig ? exp_row_shift(dmin * chi[is]) : 0;
                         if (is < pp.nsig && kn != ksh[is]) {
                             const float f = pow2_nonpos(ksh[is] - kn);
 #pragma unroll
@@ -421,7 +434,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
                         if (is < pp.nsig) {
-                            const df cs = df_make(pp.c_hi[is], pp.c_lo[is]);
+                            const df cs = df_make(chi[is], clo[is]);
                             df x0 = df_mul(D0, cs), x1 = df_mul(D1, cs);
                             if (wsh & (1u << is)) {
                                 const float2 sv = sm.shift[is][et];  // (0, 0) for an unshifted row
@@ -529,6 +542,7 @@ struct OzKParams {
     const int64_t *rsoff;  // per partition: first slot of its grid (sigma 0)
     int64_t rstot;         // slots per sigma (sum of T^2)
     int store_factor;      // also store K_hi + lambda m I per lambda (0: the factorisation reads K_hi itself)
+    const float2 *cpart;   // per-partition -1 / (2 sigma_j^2) (one sigma per partition), or null
 };
 
 __device__ __forceinline__ int oz_find_part(const PartDesc *parts, int np, int64_t tile) {
@@ -735,7 +749,8 @@ kbuild_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant_
                 if (lane == 0) mbar_arrive(&sm.t_empty);  // the levels are in registers
 #pragma unroll 1
                 for (int is = 0; is < kp.nsig; ++is, ++round) {
-                    const df cs = df_make(sm.cs[is].x, sm.cs[is].y);
+                    const float2 cv = kp.cpart ? kp.cpart[pj] : sm.cs[is];
+                    const df cs = df_make(cv.x, cv.y);
                     float hv[2][OZP_SUB], lw[2][OZP_SUB];
 #pragma unroll
                     for (int sub = 0; sub < 2; ++sub)
@@ -899,7 +914,7 @@ static size_t oz_psmem_bytes() { return sizeof(OzPSmem) + 1024; }
 // each factor tile reads K_hi and adds lambda m itself.
 cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, float *Kh, float *Kl, float *A,
                              float *rsR, float *rsC, const int64_t *rsoff, int64_t rstot, int *d_err,
-                             bool store_factor) {
+                             bool store_factor, const float2 *cpart) {
     if (ktot == 0) return cudaSuccess;
     CUtensorMap tmA, tmKh, tmKl, tmF;
     if (!make_slice_tmap(&tmA, M.ozS, (int64_t)OZ_SLICES * M.prows, M.dpz, OZ_M)) return cudaErrorInvalidValue;
@@ -920,6 +935,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
     kp.rsoff = rsoff;
     kp.rstot = rstot;
     kp.store_factor = store_factor ? 1 : 0;
+    kp.cpart = cpart;
     for (int i = 0; i < 8; ++i) {
         const double c = i < M.nsig ? -1.0 / (2.0 * M.sigmas[i] * M.sigmas[i]) : 0.0;
         kp.c_hi[i] = (float)c;
@@ -939,6 +955,7 @@ cudaError_t launch_kbuild_oz(cudaStream_t st, const Model &M, int64_t ktot, floa
 cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap &tmB, const double *Xt, int64_t t,
                               const int64_t *toff, const int64_t *tidx, int routed, void *tslices, int32_t *tex,
                               float2 *tnrm, int64_t t_rows, double *out, int *d_err) {
+    // a model with one sigma per partition (krr_fit_jobs) reads its c from M.d_cpart
     const int dpz = oz_dpz(M.d);
     launch_oz_slice(st, Xt, M.d, tidx, t, t_rows, tslices, tex, tnrm);
     CUtensorMap tmA;
@@ -955,6 +972,7 @@ cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap
             pp.nl_total = M.nlam;
             pp.kc = dpz / OZ_KC;
             pp.t_rows = t_rows;
+            pp.cpart = M.d_cpart;
             for (int i = 0; i < OZ_NSP; ++i) {
                 const double c = i < pp.nsig ? -1.0 / (2.0 * M.sigmas[s0 + i] * M.sigmas[s0 + i]) : 0.0;
                 pp.c_hi[i] = (float)c;

@@ -96,8 +96,14 @@ class Scheduler:
     large request is never starved by a run of small ones."""
 
     def __init__(self, execute, slots: int, budget_bytes: int, resident=None, t_rows: int = 256,
-                 clock=time.perf_counter, reserved=None):
+                 clock=time.perf_counter, reserved=None, max_batch: int = 1):
         self.execute = execute
+        # max_batch > 1: the oldest waiting fit takes later waiting fits with
+        # the same feature count into the same slot, run as one packed fit by
+        # execute.batch(slot, requests) -> [(yhat, status, resident_hit)]
+        self.max_batch = max_batch if hasattr(execute, "batch") else 1
+        self.batches = 0
+        self.batched_requests = 0
         self.reserved = reserved or (lambda: 0)
         self.slots = slots
         self.budget = budget_bytes
@@ -126,20 +132,29 @@ class Scheduler:
         waiting: list[tuple[float, int, Request]] = []
         threads = []
 
-        def worker(slot: int, req: Request, need: int, start: float):
+        def worker(slot: int, batch: list, need: int, start: float):
+            outs = None
             err = None
             try:
-                yhat, status, hit = self.execute(slot, req)
+                if len(batch) == 1 and self.max_batch == 1:
+                    outs = [self.execute(slot, batch[0])]
+                else:
+                    outs = self.execute.batch(slot, batch)
             except Exception as e:  # a failed request frees its slot and reports its status
-                yhat, status, hit, err = None, getattr(e, "status", KRR_ERR_CUDA), False, repr(e)
+                err = repr(e)
+                outs = [(None, getattr(e, "status", KRR_ERR_CUDA), False)] * len(batch)
             done = self.clock() - t0
             with self.lock:
-                self.results.append(Result(req.rid, req.arrival if realtime else 0.0, start, done, yhat, status,
-                                           hit, err))
+                for req, (yhat, status, hit) in zip(batch, outs):
+                    self.results.append(Result(req.rid, req.arrival if realtime else 0.0, start, done, yhat, status,
+                                               hit, err))
                 self.in_use -= need
-                self.active -= 1
+                self.active -= len(batch)
                 self.free_slots.append(slot)
                 self.lock.notify_all()
+
+        def batchable(r: Request) -> bool:  # a fit (a predict-only request whose model is gone refits)
+            return not (r.predict_only and self.resident(r))
 
         while pending or waiting:
             now = self.clock() - t0
@@ -158,12 +173,28 @@ class Scheduler:
                     if not self.free_slots or self.in_use + self.reserved() + need > self.budget:
                         break
                     heapq.heappop(waiting)
+                    batch = [req]
+                    if self.max_batch > 1 and batchable(req):
+                        keep = []
+                        for item in sorted(waiting):
+                            r2 = item[2]
+                            if (len(batch) < self.max_batch and r2.d == req.d and batchable(r2)
+                                    and self.footprint(r2) + need + self.in_use + self.reserved() <= self.budget):
+                                batch.append(r2)
+                                need += self.footprint(r2)
+                            else:
+                                keep.append(item)
+                        waiting[:] = keep
+                        heapq.heapify(waiting)
+                        if len(batch) > 1:
+                            self.batches += 1
+                            self.batched_requests += len(batch)
                     slot = self.free_slots.pop()
                     self.in_use += need
                     self.peak_in_use = max(self.peak_in_use, self.in_use + self.reserved())
-                    self.active += 1
+                    self.active += len(batch)
                     self.peak_concurrency = max(self.peak_concurrency, self.active)
-                    th = threading.Thread(target=worker, args=(slot, req, need, self.clock() - t0), daemon=True)
+                    th = threading.Thread(target=worker, args=(slot, batch, need, self.clock() - t0), daemon=True)
                     threads.append(th)
                     th.start()
                 if pending and realtime:
@@ -189,14 +220,27 @@ def latency_summary(results: list[Result]) -> dict:
             "failed": dict(failed), "errors": errors}
 
 
+class _Shared:
+    """A fitted model held by one or more resident-cache entries (a packed
+    fit holds every request of its batch); freed by its owning slot once the
+    last entry is evicted."""
+
+    def __init__(self, model, owner: int, refs: int):
+        self.model, self.owner, self.refs = model, owner, refs
+        self.bytes = 0  # device bytes of all its requests' models
+
+
 class GpuExecutor:
     """libkrr executor: one CUDA stream and context per slot.  The scheduler
-    runs at most one request per slot at a time, so each context is only ever
-    called from one thread at a time.  Fitted models stay resident in an LRU
-    cache bounded by `resident_bytes`; a predict-only request uses the
-    resident model from its own slot's context (a model may be read by any
-    context on its device once its fit has completed).  An evicted model is
-    freed later by its owning slot, and never while a request holds it."""
+    runs at most one request (or one packed batch) per slot at a time, so each
+    context is only ever called from one thread at a time.  Fitted models stay
+    resident in an LRU cache bounded by `resident_bytes`; a predict-only
+    request uses the resident model from its own slot's context (a model may
+    be read by any context on its device once its fit has completed).  An
+    evicted model is freed later by its owning slot, and never while a request
+    holds it.  `batch` runs several waiting fits of the same feature count as
+    one krr_fit_jobs call (one problem per partition, each with its own sigma
+    and lambda) and one routed prediction."""
 
     def __init__(self, slots: int, prec: str = "tf32", device: int = 0, resident_bytes: int = 8 << 30,
                  panel_width: int = 8):
@@ -212,10 +256,12 @@ class GpuExecutor:
         self.ctx = [K.krr_ctx_create(device, s) for s in self.streams]
         for c in self.ctx:  # a fixed panel width: the factor's bits do not depend on timing
             K.krr_ctx_set_panel_width(c, panel_width)
-        self.cache: collections.OrderedDict[str, list] = collections.OrderedDict()  # key -> [model, owner, bytes, pins]
+        # key -> [shared model, partition (None: the whole model is the request's), bytes, pins]
+        self.cache: collections.OrderedDict[str, list] = collections.OrderedDict()
         self.cache_bytes = 0
         self.resident_limit = resident_bytes
         self.to_free: list[list] = [[] for _ in range(slots)]
+        self.live: set = set()  # shared models not freed yet (cached or waiting for their owner)
         self.lock = threading.Lock()
 
     def is_resident(self, r: Request) -> bool:
@@ -224,7 +270,14 @@ class GpuExecutor:
 
     def resident_bytes(self) -> int:
         with self.lock:
-            return self.cache_bytes + sum(m[2] for lst in self.to_free for m in lst)
+            return sum(sh.bytes for sh in self.live)
+
+    def _drop_locked(self, ent):
+        self.cache_bytes -= ent[2]
+        sh = ent[0]
+        sh.refs -= 1
+        if sh.refs == 0:
+            self.to_free[sh.owner].append(sh)
 
     def _evict_locked(self):
         for key in list(self.cache.keys()):
@@ -234,14 +287,48 @@ class GpuExecutor:
             if ent[3] > 0:
                 continue
             del self.cache[key]
-            self.cache_bytes -= ent[2]
-            self.to_free[ent[1]].append(ent)
+            self._drop_locked(ent)
 
     def _free_pending(self, slot: int):
         with self.lock:
             lst, self.to_free[slot] = self.to_free[slot], []
-        for ent in lst:
-            self.K.krr_model_free(self.ctx[slot], ent[0])
+        for sh in lst:
+            self.K.krr_model_free(self.ctx[slot], sh.model)
+            with self.lock:
+                self.live.discard(sh)
+
+    def _insert(self, r: Request, sh: _Shared, part):
+        with self.lock:
+            old = self.cache.pop(r.key, None)
+            if old is not None:
+                self._drop_locked(old)
+            self.cache[r.key] = [sh, part, model_bytes(r.n, r.d), 0]
+            self.cache_bytes += model_bytes(r.n, r.d)
+            sh.bytes += model_bytes(r.n, r.d)
+            self.live.add(sh)
+            self._evict_locked()
+
+    def _predict_resident(self, slot: int, r: Request, Xt):
+        """yhat of a predict-only request from its resident model, or None."""
+        K, torch = self.K, self.torch
+        with self.lock:
+            ent = self.cache.get(r.key)
+            if ent is not None:
+                self.cache.move_to_end(r.key)
+                ent[3] += 1
+        if ent is None:
+            return None
+        try:
+            if ent[1] is None:
+                out = K.krr_predict(self.ctx[slot], ent[0].model, Xt).cpu().numpy()[0]
+            else:
+                route = torch.full((Xt.shape[0],), int(ent[1]), dtype=torch.int32, device="cuda")
+                out = K.krr_predict(self.ctx[slot], ent[0].model, Xt, route=route).cpu().numpy()[0]
+            self.streams[slot].synchronize()
+        finally:
+            with self.lock:
+                ent[3] -= 1
+        return out
 
     def __call__(self, slot: int, r: Request):
         torch, K = self.torch, self.K
@@ -251,18 +338,8 @@ class GpuExecutor:
         with torch.cuda.stream(stream):
             Xt = torch.from_numpy(np.ascontiguousarray(r.payload["Xt"])).to("cuda")
             if r.predict_only:
-                with self.lock:
-                    ent = self.cache.get(r.key)
-                    if ent is not None:
-                        self.cache.move_to_end(r.key)
-                        ent[3] += 1
-                if ent is not None:
-                    try:
-                        out = K.krr_predict(ctx, ent[0], Xt).cpu().numpy()[0]
-                        stream.synchronize()
-                    finally:
-                        with self.lock:
-                            ent[3] -= 1
+                out = self._predict_resident(slot, r, Xt)
+                if out is not None:
                     return out, KRR_OK, True
                 if "X" not in r.payload:  # evicted and no training data with the request
                     return None, KRR_ERR_BUDGET, False
@@ -275,22 +352,60 @@ class GpuExecutor:
             out = K.krr_predict(ctx, model, Xt).cpu().numpy()[0]
             st = int(status.cpu()[0])
             stream.synchronize()
-        with self.lock:
-            old = self.cache.pop(r.key, None)
-            if old is not None:
-                self.cache_bytes -= old[2]
-                self.to_free[old[1]].append(old)
-            self.cache[r.key] = [model, slot, model_bytes(r.n, r.d), 0]
-            self.cache_bytes += model_bytes(r.n, r.d)
-            self._evict_locked()
+        self._insert(r, _Shared(model, slot, 1), None)
         return out, st, False
+
+    def batch(self, slot: int, reqs: list):
+        """Several fits of one feature count in one packed fit and one routed
+        prediction; a predict-only request whose model is resident is served
+        from it (the scheduler only batches it when its model was evicted)."""
+        torch, K = self.torch, self.K
+        stream = self.streams[slot]
+        ctx = self.ctx[slot]
+        self._free_pending(slot)
+        outs = [None] * len(reqs)
+        fits = []
+        with torch.cuda.stream(stream):
+            for i, r in enumerate(reqs):
+                if r.predict_only:
+                    Xt = torch.from_numpy(np.ascontiguousarray(r.payload["Xt"])).to("cuda")
+                    out = self._predict_resident(slot, r, Xt)
+                    if out is not None:
+                        outs[i] = (out, KRR_OK, True)
+                        continue
+                    if "X" not in r.payload:
+                        outs[i] = (None, KRR_ERR_BUDGET, False)
+                        continue
+                fits.append(i)
+            if fits:
+                sizes = [reqs[i].payload["X"].shape[0] for i in fits]
+                tsz = [reqs[i].payload["Xt"].shape[0] for i in fits]
+                X = torch.from_numpy(np.ascontiguousarray(np.concatenate([reqs[i].payload["X"] for i in fits]))).to(
+                    "cuda")
+                y = torch.from_numpy(np.ascontiguousarray(np.concatenate([reqs[i].payload["y"] for i in fits]))).to(
+                    "cuda")
+                Xt = torch.from_numpy(np.ascontiguousarray(np.concatenate([reqs[i].payload["Xt"] for i in fits]))).to(
+                    "cuda")
+                off = torch.tensor(np.concatenate([[0], np.cumsum(sizes)]), dtype=torch.int64, device="cuda")
+                perm = torch.arange(X.shape[0], dtype=torch.int64, device="cuda")
+                route = torch.tensor(np.repeat(np.arange(len(fits)), tsz), dtype=torch.int32, device="cuda")
+                model, status, _ = K.krr_fit_jobs(ctx, X, y, perm, off, [reqs[i].sigma for i in fits],
+                                                  [reqs[i].lam for i in fits], self.prec)
+                yh = K.krr_predict(ctx, model, Xt, route=route).cpu().numpy()[0]
+                st = status.cpu().numpy()
+                stream.synchronize()
+                sh = _Shared(model, slot, len(fits))
+                pos = np.concatenate([[0], np.cumsum(tsz)])
+                for k, i in enumerate(fits):
+                    outs[i] = (yh[pos[k]:pos[k + 1]].copy(), int(st[k]), False)
+                    self._insert(reqs[i], sh, k)
+        return outs
 
     def close(self):
         with self.lock:
-            for ent in self.cache.values():
-                self.to_free[ent[1]].append(ent)
+            for ent in list(self.cache.values()):
+                self._drop_locked(ent)
             self.cache.clear()
-            self.cache_bytes = 0
         for s in range(len(self.ctx)):
             self._free_pending(s)
         for s in self.streams:

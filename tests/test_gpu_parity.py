@@ -735,3 +735,48 @@ def test_fp64_fallback_for_an_unconverged_solve():
     assert rc == 0 and info[0] > 1e6
     assert rel(a_on, oa) <= REFINED_TOL
     assert rel(y_on, oracle.predict(X, oa, Xt, sigma)) <= REFINED_TOL
+
+
+def test_fit_jobs_packs_independent_problems():
+    """krr_fit_jobs: five independent problems of uneven sizes (a one-row one
+    included), each with its own sigma and lambda, in one batched fit; each
+    alpha and each routed prediction within the refined bar of the oracle's
+    solve of that problem alone, and the same bits as fitting it alone."""
+    rng = np.random.default_rng(71)
+    d = 20
+    sizes = [300, 1000, 129, 2000, 1]
+    sig = [0.7, 3.0, 12.0, 5.0, 2.0]
+    lam = [1e-3, 1e-6, 1e-4, 1e-7, 1e-2]
+    Xs = [rng.standard_normal((m, d)) * 1.5 for m in sizes]
+    ys = [np.sin(Xj[:, 0]) + 0.1 * Xj[:, 1] for Xj in Xs]
+    Xts = [rng.standard_normal((37, d)) * 1.5 for _ in sizes]
+    X, y, Xt = np.concatenate(Xs), np.concatenate(ys), np.concatenate(Xts)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    route = np.repeat(np.arange(len(sizes)), 37).astype(np.int32)
+    c = K.krr_ctx_create(0)
+    K.krr_ctx_set_panel_width(c, 8)
+    try:
+        model, st, al = K.krr_fit_jobs(c, cuda(X), cuda(y), cuda(np.arange(X.shape[0]), torch.int64),
+                                       cuda(off, torch.int64), sig, lam, "tf32", want_alpha=True)
+        assert np.all(st.cpu().numpy() == K.KRR_OK)
+        yh = K.krr_predict(c, model, cuda(Xt), route=cuda(route, torch.int32)).cpu().numpy()[0]
+        al = al.cpu().numpy()
+        model.free()
+        for j, m in enumerate(sizes):
+            oa, info, rc = oracle.fit(Xs[j], ys[j], sig[j], lam[j])
+            assert rc == 0
+            assert rel(al[off[j]:off[j + 1]], oa) <= REFINED_TOL, j
+            assert rel(yh[37 * j:37 * (j + 1)], oracle.predict(Xs[j], oa, Xts[j], sig[j])) <= REFINED_TOL, j
+            alone, st1, a1 = K.krr_fit_jobs(c, cuda(Xs[j]), cuda(ys[j]), cuda(np.arange(m), torch.int64),
+                                            cuda(np.array([0, m]), torch.int64), [sig[j]], [lam[j]], "tf32",
+                                            want_alpha=True)
+            y1 = K.krr_predict(c, alone, cuda(Xts[j]), route=cuda(np.zeros(37, np.int32), torch.int32))
+            assert np.array_equal(a1.cpu().numpy(), al[off[j]:off[j + 1]]), j
+            assert np.array_equal(y1.cpu().numpy()[0], yh[37 * j:37 * (j + 1)]), j
+            alone.free()
+        with pytest.raises(K.KrrError) as e:
+            K.krr_fit_jobs(c, cuda(X), cuda(y), cuda(np.arange(X.shape[0]), torch.int64), cuda(off, torch.int64),
+                           sig, lam, "fp64")
+        assert e.value.status == K.KRR_ERR_UNSUPPORTED
+    finally:
+        c.close()

@@ -20,10 +20,11 @@ def requests(count=14):
     return make_stream_requests(st, count, lambda seed, n, d, t: synth.serve_request_data(seed, n, d, t), t=64)
 
 
-def serve(reqs, slots):
+def serve(reqs, slots, max_batch=1):
     ex = GpuExecutor(slots, prec="tf32", resident_bytes=1 << 30)
     try:
-        s = Scheduler(ex, slots, 120 << 30, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=64)
+        s = Scheduler(ex, slots, 120 << 30, resident=ex.is_resident, reserved=ex.resident_bytes, t_rows=64,
+                      max_batch=max_batch)
         return s.run(reqs, realtime=False), s
     finally:
         ex.close()
@@ -70,3 +71,15 @@ def test_mix_matches_oracle(mix):
         e = rel(out.yhat, ref)
         assert e <= TOL, "request %d (n=%d d=%d sigma=%.3g lambda=%.3g): rel err %.3e" % (
             r.rid, r.n, r.d, r.sigma, r.lam, e)
+
+
+def test_packed_batches_equal_the_unpacked_mix_bitwise(mix):
+    """Waiting fits of one feature count packed into one krr_fit_jobs call
+    (one problem per partition, each with its own sigma and lambda) give
+    every request the same bits as serving it on its own fit."""
+    rq, res, _ = mix
+    bres, s = serve(rq, slots=2, max_batch=4)
+    assert s.batches > 0
+    assert [r.status for r in bres] == [KRR_OK] * len(rq)
+    for r, a, b in zip(rq, res, bres):
+        assert np.array_equal(a.yhat, b.yhat), "request %d differs packed vs on its own" % r.rid

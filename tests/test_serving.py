@@ -144,3 +144,50 @@ def test_stream_requests_shapes_and_repeats():
             assert b.rid < r.rid and r.payload["X"] is b.payload["X"]
     assert any(r.predict_only for r in rq)
     assert np.all(np.diff([r.arrival for r in rq]) > 0)
+
+
+class FakeBatchExec(FakeExec):
+    """FakeExec with a packed-batch entry point that records each batch."""
+
+    def __init__(self, sched_ref):
+        super().__init__(sched_ref)
+        self.batches = []
+
+    def batch(self, slot, rs):
+        with self.lock:
+            self.batches.append([(r.rid, r.d) for r in rs])
+        time.sleep(0.002)
+        return [(np.full(4, float(r.rid)), KRR_OK, False) for r in rs]
+
+
+def test_batches_pack_waiting_fits_of_one_feature_count():
+    ds = [8, 32, 8, 90, 8, 32, 8, 8, 32, 90, 8, 8]
+    rq = [Request(i, 0.0, "k%d" % i, 500 + 10 * i, d, 1.0, 1e-4) for i, d in enumerate(ds)]
+    ref = [None]
+    ex = FakeBatchExec(ref)
+    s = Scheduler(ex, 1, 1 << 50, max_batch=3)
+    ref[0] = s
+    res = s.run(rq, realtime=False)
+    assert sorted(r.rid for r in res) == list(range(len(ds))) and all(r.status == KRR_OK for r in res)
+    assert all(np.array_equal(r.yhat, np.full(4, float(r.rid))) for r in res)
+    seen = []
+    for b in ex.batches:
+        assert 1 <= len(b) <= 3 and len({d for _, d in b}) == 1
+        # the oldest request not yet served leads every batch
+        assert b[0][0] == min(rid for rid in range(len(ds)) if rid not in seen)
+        seen += [rid for rid, _ in b]
+    assert sorted(seen) == list(range(len(ds)))
+    assert s.batches >= 3 and s.batched_requests >= 7
+
+
+def test_batches_respect_the_budget():
+    fp = fit_footprint_bytes(4000, 32, 256)
+    rq = [Request(i, 0.0, "k%d" % i, 4000, 32, 1.0, 1e-4) for i in range(6)]
+    ref = [None]
+    ex = FakeBatchExec(ref)
+    s = Scheduler(ex, 2, 2 * fp + fp // 2, max_batch=4)
+    ref[0] = s
+    res = s.run(rq, realtime=False)
+    assert all(r.status == KRR_OK for r in res) and len(res) == 6
+    assert all(len(b) <= 2 for b in ex.batches)
+    assert s.peak_in_use <= 2 * fp + fp // 2
