@@ -273,7 +273,7 @@ constexpr int PO_PT = KRR_TILE + 4;    // row stride of Pt (16-byte rows)
 constexpr int PO_ZT = PO_B + 4;        // row stride of Zt
 constexpr int PO_TT = KRR_TILE - PO_B + 4;  // row stride of T
 constexpr size_t PO_BLOCKED_SMEM =
-    (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (2 * PO_PT + PO_ZT + PO_TT)) * sizeof(float);
+    (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (2 * PO_PT + 2 * PO_ZT + PO_TT)) * sizeof(float);
 
 __device__ __forceinline__ void po_tri_decode(int t, int &a, int &b) {  // t = a (a + 1) / 2 + b, b <= a
     int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -295,6 +295,7 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
     float *Zt = Pt + PO_B * PO_PT;                  // [32][PO_ZT]: Zt[kk][c] = Z_o+c,o+kk
     float *Ts = Zt + PO_B * PO_ZT;                  // [32][PO_TT]: T of the blocked inverse
     float *Pn = Ts + PO_B * PO_TT;                  // [32][PO_PT]: Pn[c][r] = L_r,o+c (the solved panel)
+    float *Lb = Pn + PO_B * PO_PT;                  // [32][PO_ZT]: the diagonal block's L rows, 1 / L_ii
     __shared__ int bad_sh;
     pdl_launch_dependents();
     pdl_wait();  // the column update of this diagonal tile has completed
@@ -308,10 +309,22 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
     const bool kf = Kfirst != nullptr && k == 0;
     const float *src = kf ? Kfirst + S.ktile0 * KRR_TILE_ELEMS : g;
     const float lm = (float)S.lambda_m;
-    for (int e = tid; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int r = e >> 7, c = e & 127;
-        Ls[r * PO_LD + c] = c <= r ? (kf && r == c && r < S.m ? src[e] + lm : src[e]) : 0.f;
-        Zs[r * PO_LD + c] = 0.f;
+    {
+        // the tile in 16-byte loads, all issued before any is used
+        constexpr int NV = KRR_TILE_ELEMS / 4 / 512;  // float4 per thread
+        float4 v[NV];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) v[u] = reinterpret_cast<const float4 *>(src)[tid + u * 512];
+#pragma unroll
+        for (int u = 0; u < NV; ++u) {
+            const int e = (tid + u * 512) * 4, r = e >> 7, c = e & 127;
+            const float w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                Ls[r * PO_LD + c + q] = c + q <= r ? (kf && r == c + q && r < S.m ? w[q] + lm : w[q]) : 0.f;
+                Zs[r * PO_LD + c + q] = 0.f;
+            }
+        }
     }
     __syncthreads();
 #pragma unroll 1
@@ -344,26 +357,31 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
 #pragma unroll
                 for (int j = q + 1; j < PO_B; ++j) d[j] = fmaf(-l, __shfl_sync(0xffffffffu, l, j), d[j]);
             }
-            // the block's L rows go to shared memory first: the inverse reads
-            // row i of L there (one broadcast load per entry), not by shuffle
+            // the block's L rows go to shared memory first (16-byte rows in
+            // Lb): the inverse reads row i of L there with broadcast loads
 #pragma unroll
-            for (int j = 0; j < PO_B; ++j)
+            for (int j = 0; j < PO_B; ++j) {
                 if (j <= lane) Ls[(o + lane) * PO_LD + o + j] = d[j];
-            Zt[lane * PO_ZT + PO_B] = dinv;  // spare column of Zt: 1 / L_ii
+                Lb[lane * PO_ZT + j] = j <= lane ? d[j] : 0.f;
+            }
+            Lb[lane * PO_ZT + PO_B] = dinv;  // spare column: 1 / L_ii
             __syncwarp();
-            // inverse of the block: lane j forms column j, row by row
+            // inverse of the block: lane j forms column j, row by row (four chains)
             float z[PO_B];
 #pragma unroll
             for (int i = 0; i < PO_B; ++i) {
-                const float inv_ii = Zt[i * PO_ZT + PO_B];
-                const float *li = Ls + (o + i) * PO_LD + o;
-                float a0 = 0.f, a1 = 0.f;
+                const float *li = Lb + i * PO_ZT;
+                const float inv_ii = li[PO_B];
+                float a[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-                for (int kk = 0; kk < i; ++kk) {
-                    if (kk & 1) a1 = fmaf(li[kk], z[kk], a1);
-                    else a0 = fmaf(li[kk], z[kk], a0);
+                for (int k4 = 0; k4 < i; k4 += 4) {
+                    const float4 lv = *reinterpret_cast<const float4 *>(li + k4);
+                    a[0] = fmaf(lv.x, z[k4], a[0]);
+                    if (k4 + 1 < i) a[1] = fmaf(lv.y, z[k4 + 1], a[1]);
+                    if (k4 + 2 < i) a[2] = fmaf(lv.z, z[k4 + 2], a[2]);
+                    if (k4 + 3 < i) a[3] = fmaf(lv.w, z[k4 + 3], a[3]);
                 }
-                z[i] = lane == i ? inv_ii : (lane < i ? -(a0 + a1) * inv_ii : 0.f);
+                z[i] = lane == i ? inv_ii : (lane < i ? -((a[0] + a[1]) + (a[2] + a[3])) * inv_ii : 0.f);
             }
             __syncwarp();
 #pragma unroll
@@ -481,10 +499,13 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
     __syncthreads();
     if (tid == 0 && bad_sh) flags[s] = 1;
     float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
-    for (int e = tid; e < KRR_TILE_ELEMS; e += blockDim.x) {
-        const int r = e >> 7, c = e & 127;
-        g[e] = c <= r ? Ls[r * PO_LD + c] : 0.f;
-        z[e] = Zs[r * PO_LD + c];
+    for (int e4 = tid; e4 < KRR_TILE_ELEMS / 4; e4 += blockDim.x) {
+        const int e = e4 * 4, r = e >> 7, c = e & 127;
+        const float *lr = Ls + r * PO_LD + c, *zr = Zs + r * PO_LD + c;
+        reinterpret_cast<float4 *>(g)[e4] =
+            make_float4(c <= r ? lr[0] : 0.f, c + 1 <= r ? lr[1] : 0.f, c + 2 <= r ? lr[2] : 0.f,
+                        c + 3 <= r ? lr[3] : 0.f);
+        reinterpret_cast<float4 *>(z)[e4] = make_float4(zr[0], zr[1], zr[2], zr[3]);
     }
 }
 
@@ -573,9 +594,12 @@ __global__ void __launch_bounds__(256) gemm_tile_simt_kernel(T *__restrict__ A, 
 // panel solve that wrote them: x (FP32 store; the tensor core reads its top
 // 19 bits, hi) and lo = x - hi (FP32 side store); TMA lands x and lo, no
 // split warps.  TC_TF32X3: warps 6..9 split each landed stage
-// into hi = x with the low 13 mantissa bits cleared and lo = x - hi (exact),
-// and three MMAs per K step form hi*hi + hi*lo + lo*hi: FP32-class products on
-// the tensor cores.
+// into hi = x rounded to the nearest TF32 value and lo = x - hi (exact), and
+// three MMAs per K step form hi*hi + hi*lo + lo*hi: FP32-class products on
+// the tensor cores.  TC_TRSM (the panel solve) splits the same way and takes
+// three passes for every solve: a one-pass panel solve for the one-pass
+// (class 1) solves, whose L tiles are kept in FP16, was measured to cost
+// more refinement iterations than it saves.
 constexpr int TC_CHUNK = 32;                                       // floats of K per stage (128 bytes)
 constexpr uint32_t TC_HALF = (uint32_t)KRR_TILE * TC_CHUNK * 4;     // one operand tile chunk, 16 KB
 constexpr uint32_t TC_IDESC = make_idesc(2u /*TF32*/, 128u, 128u);
@@ -834,11 +858,13 @@ tile_mma_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant_
                     float4 *lo = reinterpret_cast<float4 *>(buf + st * Cfg::STAGE_BYTES + 2 * TC_HALF);
 #pragma unroll 4
                     for (int e = tsp; e < (int)(2 * TC_HALF / 16); e += 128) {
+                        // hi = x rounded to the nearest TF32 value (the 13 low
+                        // significand bits rounded half away from zero), lo = x - hi
                         float4 v = hi[e], h, l;
-                        h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                        h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                        h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                        h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                        h.x = __uint_as_float((__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u);
+                        h.y = __uint_as_float((__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u);
+                        h.z = __uint_as_float((__float_as_uint(v.z) + 0x1000u) & 0xFFFFE000u);
+                        h.w = __uint_as_float((__float_as_uint(v.w) + 0x1000u) & 0xFFFFE000u);
                         l.x = v.x - h.x;
                         l.y = v.y - h.y;
                         l.z = v.z - h.z;

@@ -431,18 +431,26 @@ __global__ void gather_count_kernel(const int32_t *__restrict__ a, int64_t n, in
     for (int j = threadIdx.x; j < p; j += blockDim.x) bcount[(int64_t)blockIdx.x * p + j] = h[j];
 }
 
-// one thread per partition: offsets and per-block starting positions
-// one CTA: thread j sums partition j's block counts, a scan over partitions
-// gives the partition starts, then each thread turns its counts into block
-// starts (stable: block order, then row order inside a block)
+// Offsets and per-block starting positions, one CTA (1024 threads = 32
+// warps): warp w takes partitions w, w + 32, ...; its lanes walk the
+// partition's block counts 32 blocks at a time (warp sums for the total, then
+// warp scans for the block starts), so a large block count costs nblk / 32
+// steps per partition instead of nblk.  Between the passes one scan over the
+// partitions turns the totals into the partition starts.
 __global__ void gather_scan_kernel(long long *__restrict__ bcount, int64_t nblk, int32_t p,
                                    int64_t *__restrict__ offsets) {
     extern __shared__ unsigned char smem_raw[];
     long long *tot = reinterpret_cast<long long *>(smem_raw);  // [p]
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int j = warp; j < p; j += nw) {
         long long run = 0;
-        for (int64_t b = 0; b < nblk; ++b) run += bcount[b * p + j];
-        tot[j] = run;
+        for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+            const int64_t b = b0 + lane;
+            run += b < nblk ? bcount[b * p + j] : 0;
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) run += __shfl_xor_sync(0xffffffffu, run, off);
+        if (lane == 0) tot[j] = run;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -456,12 +464,19 @@ __global__ void gather_scan_kernel(long long *__restrict__ bcount, int64_t nblk,
         offsets[p] = run;
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < p; j += blockDim.x) {
-        long long run = tot[j];
-        for (int64_t b = 0; b < nblk; ++b) {
-            const long long c = bcount[b * p + j];
-            bcount[b * p + j] = run;
-            run += c;
+    for (int j = warp; j < p; j += nw) {
+        long long base = tot[j];
+        for (int64_t b0 = 0; b0 < nblk; b0 += 32) {
+            const int64_t b = b0 + lane;
+            const long long c = b < nblk ? bcount[b * p + j] : 0;
+            long long incl = c;  // inclusive scan over the 32 blocks of this step
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long v = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += v;
+            }
+            if (b < nblk) bcount[b * p + j] = base + incl - c;
+            base += __shfl_sync(0xffffffffu, incl, 31);
         }
     }
 }
