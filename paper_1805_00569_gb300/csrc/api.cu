@@ -185,6 +185,17 @@ __global__ void wait_probe_kernel(const float4 *__restrict__ src, float *__restr
     }
 }
 
+// alpha as double-float pairs, formed once per fit: the prediction's
+// contraction then runs with no FP64 instruction (GB300's FP64 pipe runs at
+// 1/64 of the FP32 rate)
+__global__ void alpha_pairs_kernel(const double *__restrict__ a, float2 *__restrict__ a2, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = a[i];
+    const float h = __double2float_rn(v);
+    a2[i] = make_float2(h, __double2float_rn(v - (double)h));
+}
+
 struct DevBuf {
     Ctx *c;
     std::vector<std::pair<void *, size_t>> list;
@@ -554,7 +565,7 @@ static krr_status fit_impl(krr_ctx *ctx, const double *X, const double *y, int64
     int64_t rs_slots = 0;  // row-sum tile slots of the exact-Gram tile build: sum of T^2
     for (const PartDesc &P : M.parts) rs_slots += (int64_t)P.T * P.T;
     const size_t tileb = (size_t)KRR_TILE_ELEMS * esz;
-    size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 8 +
+    size_t model_bytes = (size_t)prow * d * 8 + 2 * (size_t)prow * M.dp * 4 + (size_t)prow * 8 + (size_t)vec * 16 +
                          (size_t)prow * (10 * (size_t)((d + 31) / 32 * 32) + 4) +
                          sizeof(PartDesc) * p + sizeof(SolveDesc) * nsolve + 8 * 256;
     size_t work_bytes = (size_t)prow * 8 + (fp64 ? 1 : 2) * (size_t)ns * ktot * tileb + (size_t)ltiles * tileb +
@@ -991,6 +1002,17 @@ static krr_status fit_impl(krr_ctx *ctx, const double *X, const double *y, int64
             ctx_free(c, d_st, 4);
             ctx_free(c, d_off, 16);
         }
+    }
+    if (M.ozS) {
+        cudaError_t e = model_alloc(c, M, &M.alpha2, (size_t)M.nvec * sizeof(float2));
+        if (e == cudaSuccess) {
+            KRR_LAUNCHED(), alpha_pairs_kernel<<<(unsigned)((M.nvec + 255) / 256), 256, 0, st>>>(M.alpha, M.alpha2,
+                                                                                               M.nvec);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess)
+            return bail(e == cudaErrorMemoryAllocation ? KRR_ERR_OOM : KRR_ERR_CUDA,
+                        std::string("krr_fit_batch: alpha pairs: ") + cudaGetErrorString(e));
     }
 #undef FIT_TRY
     *out = km;

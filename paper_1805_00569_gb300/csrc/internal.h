@@ -178,6 +178,7 @@ struct Model {
     float *Xl = nullptr;       // lo part FP32 [prows x dp]
     float2 *nrm = nullptr;     // squared norms as (hi, lo) [prows]
     double *alpha = nullptr;   // per-solve coefficients, padded [nvec]
+    float2 *alpha2 = nullptr;  // the same as double-float pairs (hi, lo) for the exact-Gram prediction
     void *ozS = nullptr;       // integer bf16 slices of the padded rows [5][prows][dpz] (tensor-core predict)
     int32_t *ozex = nullptr;   // per-row slice exponent [prows]
     int32_t dpz = 0;           // features padded to the slice K chunk

@@ -180,6 +180,7 @@ constexpr int OZP_EPI_WARPS = 16;
 constexpr int OZP_EPI = OZP_EPI_WARPS * 32;                // epilogue threads
 constexpr int OZP_THREADS = (OZ_EPI_WARP0 + OZP_EPI_WARPS) * 32;
 constexpr int OZP_SUB = 8;                                 // columns per TMEM read
+constexpr int OZP_COLS = 4;                                // columns whose exponentials interleave
 struct OzPSmem {
     unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
     unsigned char b[OZ_B_BYTES];
@@ -215,7 +216,7 @@ __device__ __forceinline__ df oz_combine(df a, int ka, df b, int kb, int *k) {
 __global__ void __launch_bounds__(OZP_THREADS, 1)
 predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                   const PartDesc *__restrict__ parts, const SolveDesc *__restrict__ solves,
-                  const double *__restrict__ alpha, const int32_t *__restrict__ ex_train,
+                  const float2 *__restrict__ alpha2, const int32_t *__restrict__ ex_train,
                   const float2 *__restrict__ nrm_train, const int32_t *__restrict__ ex_test,
                   const float2 *__restrict__ nrm_test, int64_t t, const int64_t *__restrict__ toff,
                   const int64_t *__restrict__ tidx, OzParams pp, int routed, int64_t prows,
@@ -360,10 +361,8 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 const int is = g / pp.nlam, il = g % pp.nlam;
                 const SolveDesc S =
                     solves[(int64_t)j * pp.Gtot + (int64_t)(pp.sig0 + is) * pp.nl_total + pp.lam0 + il];
-                const double av = alpha[S.vec0 + (int64_t)c * OZ_N + col];
-                const float h = __double2float_rn(av);
                 reinterpret_cast<float2 *>(&cd.a2[is * OZ_NLP + il][col >> 1])[col & 1] =
-                    make_float2(h, __double2float_rn(av - (double)h));
+                    alpha2[S.vec0 + (int64_t)c * OZ_N + col];
             }
             epi_bar_p();
             // after a timeout the warp keeps the loop (and its barriers) but skips the work,
@@ -423,32 +422,41 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                 for (int is = 0; is < OZ_NSP; ++is)
                     wsh |= __any_sync(0xffffffffu, ksh[is] != 0) ? (1u << is) : 0u;
-                // two columns per iteration: their exponentials are independent
-                // chains the scheduler can interleave.  Padded training rows have
+                // OZP_COLS columns per iteration: their exponentials are
+                // independent chains the scheduler can interleave.  Padded training rows have
                 // alpha = 0 exactly, so they need no test.
 #pragma unroll 1
-                for (int k = 0; k < OZP_SUB; k += 2) {
+                for (int k = 0; k < OZP_SUB; k += OZP_COLS) {
                     const int col = (int)col0 + k;
-                    const float2 dv0 = sm.dist[et][k], dv1 = sm.dist[et][k + 1];
-                    const df D0 = df_make(dv0.x, dv0.y), D1 = df_make(dv1.x, dv1.y);
+                    df D[OZP_COLS];
+#pragma unroll
+                    for (int u = 0; u < OZP_COLS; ++u) {
+                        const float2 dv = sm.dist[et][k + u];
+                        D[u] = df_make(dv.x, dv.y);
+                    }
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
                         if (is < pp.nsig) {
                             const df cs = df_make(chi[is], clo[is]);
-                            df x0 = df_mul(D0, cs), x1 = df_mul(D1, cs);
-                            if (wsh & (1u << is)) {
-                                const float2 sv = sm.shift[is][et];  // (0, 0) for an unshifted row
-                                x0 = df_add(x0, df_make(sv.x, sv.y));
-                                x1 = df_add(x1, df_make(sv.x, sv.y));
+                            df kv[OZP_COLS];
+#pragma unroll
+                            for (int u = 0; u < OZP_COLS; ++u) {
+                                df x = df_mul(D[u], cs);
+                                if (wsh & (1u << is)) {
+                                    const float2 sv = sm.shift[is][et];  // (0, 0) for an unshifted row
+                                    x = df_add(x, df_make(sv.x, sv.y));
+                                }
+                                kv[u] = df_exp_nonpos<false>(x, sm.exptab);
                             }
-                            const df k0 = df_exp_nonpos<false>(x0, sm.exptab);
-                            const df k1 = df_exp_nonpos<false>(x1, sm.exptab);
 #pragma unroll
                             for (int il = 0; il < OZ_NLP; ++il)
                                 if (il < pp.nlam) {
-                                    const float4 a = cd.a2[is * OZ_NLP + il][col >> 1];  // col is even
-                                    dfa_fma(acc[is][il], k0.hi, k0.lo, a.x, a.y);
-                                    dfa_fma(acc[is][il], k1.hi, k1.lo, a.z, a.w);
+#pragma unroll
+                                    for (int u = 0; u < OZP_COLS; u += 2) {
+                                        const float4 a = cd.a2[is * OZ_NLP + il][(col + u) >> 1];  // col is even
+                                        dfa_fma(acc[is][il], kv[u].hi, kv[u].lo, a.x, a.y);
+                                        dfa_fma(acc[is][il], kv[u + 1].hi, kv[u + 1].lo, a.z, a.w);
+                                    }
                                 }
                         }
                     }
@@ -981,7 +989,7 @@ cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap
             // for the routed form the grouped rows start at toff[j]; the tile count bounds every partition
             dim3 grid((unsigned)M.p, (unsigned)((t + OZ_M - 1) / OZ_M));
             KRR_LAUNCHED(), predict_oz_kernel<<<grid, OZP_THREADS, oz_psmem_bytes(), st>>>(
-                tmA, tmB, M.d_parts, M.d_solves, M.alpha, M.ozex, M.nrm, tex, tnrm, t, toff, routed ? tidx : nullptr,
+                tmA, tmB, M.d_parts, M.d_solves, M.alpha2, M.ozex, M.nrm, tex, tnrm, t, toff, routed ? tidx : nullptr,
                 pp, routed, M.prows, out, d_err);
         }
     return cudaGetLastError();

@@ -72,7 +72,7 @@ def fit_footprint_bytes(n: int, d: int, t: int) -> int:
     # factor, diagonal inverses, refinement vectors, matvec slots, row sums
     work = (2 * tiles * tile_b + tiles * tile_b + tiles * TILE * TILE * 2 + tiles * tile_b + T * tile_b
             + 7 * rows * 8 + T * T * TILE * 8 + T * T * 9 * TILE * 4)
-    model = rows * d * 8 + 2 * rows * dp * 4 + rows * 8 + rows * 8 + rows * (10 * dz + 4)
+    model = rows * d * 8 + 2 * rows * dp * 4 + rows * 8 + rows * 16 + rows * (10 * dz + 4)
     test = t * d * 8 + (t + 256) * (10 * dz + 12) + t * 8
     return int(work + model + test + (64 << 20))
 
@@ -82,7 +82,7 @@ def model_bytes(n: int, d: int) -> int:
     rows = T * TILE
     dp = (d + 15) // 16 * 16
     dz = (d + 31) // 32 * 32
-    return int(rows * d * 8 + 2 * rows * dp * 4 + 2 * rows * 8 + rows * (10 * dz + 4))
+    return int(rows * d * 8 + 2 * rows * dp * 4 + 3 * rows * 8 + rows * (10 * dz + 4))
 
 
 class Scheduler:
