@@ -252,28 +252,32 @@ __global__ void __launch_bounds__(512, 1) potrf_tile_kernel(T *__restrict__ A, T
 // The same factor L and inverse Z of one FP32 diagonal tile, blocked by 32
 // columns so that block barriers come per block, not per column.  For each
 // 32-column block kb (rows and columns [o, o + 32), o = 32 kb):
-//   B. warp 0 factors the 32 x 32 diagonal block and inverts it in registers
-//      (lane i holds row i; values travel by shuffle, no block barrier).
-//      Meanwhile the other warps copy the block's columns below the diagonal
-//      block, transposed, into Pt, and form T = L_kb,<o Z_<o,<o, the first
-//      half of the blocked triangular inverse
+//   A. the previous block's rank-32 update of this block's 32 x 32 diagonal
+//      block only (lookahead: the rest of that update is not needed yet).
+//   B. warp 0 factors the diagonal block and inverts it in registers (lane i
+//      holds row i; values travel by shuffle, no block barrier).  Meanwhile
+//      the warps on the other three schedulers finish the previous block's
+//      rank-32 update of the lower trailing part, copy the block's columns
+//      below the diagonal block, transposed, into Pt, and form
+//      T = L_kb,<o Z_<o,<o, the first half of the blocked triangular inverse
 //        Z_kb,jb = -Z_kb,kb sum_{m in blocks [jb, kb)} L_kb,m Z_m,jb.
 //   C. the rows below solve against the block's inverse,
-//      L_r,kb = A_r,kb Z_kb,kb^T, while Z_kb,<o = -Z_kb,kb T completes the
-//      inverse's block row; then the block's rank-32 update of the lower
-//      trailing part.
+//      L_r,kb = A_r,kb Z_kb,kb^T (into Pn, which the next block's updates
+//      read), while Z_kb,<o = -Z_kb,kb T completes the inverse's block row.
 // The products run as 4 x 4 register tiles from 16-byte shared loads of the
-// transposed panel (two loads per 16 fused multiply-adds).  Seventeen block
+// transposed panel (two loads per 16 fused multiply-adds).  Eleven block
 // barriers instead of one per column.  Shared memory: the tile (padded rows:
 // lanes reading a column hit distinct banks), Z, the transposed panel Pt,
-// the diagonal block's inverse transposed (Zt) and T.
+// the solved panel Pn, the diagonal block's inverse transposed (Zt), its L
+// rows (Lb) and T.
 constexpr int PO_B = 32;               // block width
-constexpr int PO_LD = KRR_TILE + 1;    // padded row stride of the tile and of Z
+constexpr int PO_LD = KRR_TILE + 1;    // padded row stride of the tile
+constexpr int PO_ZL = KRR_TILE + 4;    // row stride of Z (16-byte rows: T reads four Z columns at once)
 constexpr int PO_PT = KRR_TILE + 4;    // row stride of Pt (16-byte rows)
 constexpr int PO_ZT = PO_B + 4;        // row stride of Zt
 constexpr int PO_TT = KRR_TILE - PO_B + 4;  // row stride of T
 constexpr size_t PO_BLOCKED_SMEM =
-    (2 * (size_t)KRR_TILE * PO_LD + (size_t)PO_B * (2 * PO_PT + 2 * PO_ZT + PO_TT)) * sizeof(float);
+    ((size_t)KRR_TILE * (PO_LD + PO_ZL) + (size_t)PO_B * (2 * PO_PT + 2 * PO_ZT + PO_TT)) * sizeof(float);
 
 __device__ __forceinline__ void po_tri_decode(int t, int &a, int &b) {  // t = a (a + 1) / 2 + b, b <= a
     int r = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
@@ -283,6 +287,30 @@ __device__ __forceinline__ void po_tri_decode(int t, int &a, int &b) {  // t = a
     b = t - r * (r + 1) / 2;
 }
 
+// Rank-32 update of the 4 x 4 tile (a, b), b <= a, of the tile's lower part
+// from row and column `base` on, by the solved panel Pn (Pn[kk][r] = L_r,kk of
+// the previous block): A -= L L^T there (upper entries of a diagonal tile kept).
+__device__ __forceinline__ void po_rank32_tile(float *__restrict__ Ls, const float *__restrict__ Pn, int base,
+                                               int a, int b) {
+    const int r0 = base + 4 * a, c0 = base + 4 * b;
+    float acc[4][4] = {};
+#pragma unroll 4
+    for (int kk = 0; kk < PO_B; ++kk) {
+        const float4 x = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + r0);
+        const float4 y = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + c0);
+        const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            if (a != b || v <= u) Ls[(r0 + u) * PO_LD + c0 + v] -= acc[u][v];
+}
+
 __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict__ A, float *__restrict__ Z,
                                                                const float *__restrict__ Kfirst,
                                                                const SolveDesc *__restrict__ solves,
@@ -290,8 +318,8 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
                                                                int32_t *__restrict__ flags) {
     extern __shared__ __align__(16) unsigned char po_dyn[];
     float *Ls = reinterpret_cast<float *>(po_dyn);  // [128][PO_LD]: A, becoming L
-    float *Zs = Ls + KRR_TILE * PO_LD;              // [128][PO_LD]: Z
-    float *Pt = Zs + KRR_TILE * PO_LD;              // [32][PO_PT]: Pt[kk][r] = (A or L)_r,o+kk
+    float *Zs = Ls + KRR_TILE * PO_LD;              // [128][PO_ZL]: Z
+    float *Pt = Zs + KRR_TILE * PO_ZL;              // [32][PO_PT]: Pt[kk][r] = (A or L)_r,o+kk
     float *Zt = Pt + PO_B * PO_PT;                  // [32][PO_ZT]: Zt[kk][c] = Z_o+c,o+kk
     float *Ts = Zt + PO_B * PO_ZT;                  // [32][PO_TT]: T of the blocked inverse
     float *Pn = Ts + PO_B * PO_TT;                  // [32][PO_PT]: Pn[c][r] = L_r,o+c (the solved panel)
@@ -322,7 +350,7 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 Ls[r * PO_LD + c + q] = c + q <= r ? (kf && r == c + q && r < S.m ? w[q] + lm : w[q]) : 0.f;
-                Zs[r * PO_LD + c + q] = 0.f;
+                Zs[r * PO_ZL + c + q] = 0.f;
             }
         }
     }
@@ -332,7 +360,19 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
         const int o = kb * PO_B;
         const int b0 = o + PO_B;             // first row below the block
         const int nr = KRR_TILE - b0;        // rows below the block
-        // ---- B: the diagonal block (warp 0); Pt and T (warps 1..15)
+        // ---- A (lookahead): the previous block's rank-32 update of this
+        // block's diagonal block only (the 36 lower 4 x 4 tiles); the rest of
+        // that update runs beside warp 0's phase below
+        if (kb > 0) {
+            if (tid < 36) {
+                int a, b;
+                po_tri_decode(tid, a, b);
+                po_rank32_tile(Ls, Pn, o, a, b);
+            }
+            __syncthreads();
+        }
+        // ---- B: the diagonal block (warp 0); the rest of the previous
+        // block's update, then Pt and T (warps on the other schedulers)
         if (warp == 0) {
             // factor: step q scales column q by 1 / sqrt(pivot) and updates
             // the columns right of it; entries right of a lane's diagonal
@@ -350,7 +390,9 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
                     bad = true;
                     pv = 1.f;
                 }
-                const float rl = potrf_rsqrt<float>(pv);
+                // MUFU reciprocal square root (2 ulp): the pivot's rounding is
+                // far below the factor classes' own (11-bit to FP32-class) errors
+                const float rl = rsqrtf(pv);
                 const float l = lane > q ? d[q] * rl : (lane == q ? pv * rl : 0.f);
                 if (lane == q) dinv = rl;
                 d[q] = l;
@@ -366,49 +408,76 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
             }
             Lb[lane * PO_ZT + PO_B] = dinv;  // spare column: 1 / L_ii
             __syncwarp();
-            // inverse of the block: lane j forms column j, row by row (four chains)
+            // inverse of the block: lane j forms column j, four rows at a time:
+            // their sums over the columns before the group are independent of
+            // each other, then the group's own 4 x 4 triangle in row order
             float z[PO_B];
 #pragma unroll
-            for (int i = 0; i < PO_B; ++i) {
-                const float *li = Lb + i * PO_ZT;
-                const float inv_ii = li[PO_B];
-                float a[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int i0 = 0; i0 < PO_B; i0 += 4) {
+                float sg[4];
 #pragma unroll
-                for (int k4 = 0; k4 < i; k4 += 4) {
-                    const float4 lv = *reinterpret_cast<const float4 *>(li + k4);
-                    a[0] = fmaf(lv.x, z[k4], a[0]);
-                    if (k4 + 1 < i) a[1] = fmaf(lv.y, z[k4 + 1], a[1]);
-                    if (k4 + 2 < i) a[2] = fmaf(lv.z, z[k4 + 2], a[2]);
-                    if (k4 + 3 < i) a[3] = fmaf(lv.w, z[k4 + 3], a[3]);
+                for (int u = 0; u < 4; ++u) {
+                    const float *li = Lb + (i0 + u) * PO_ZT;
+                    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+                    for (int k4 = 0; k4 < i0; k4 += 4) {
+                        const float4 lv = *reinterpret_cast<const float4 *>(li + k4);
+                        a0 = fmaf(lv.x, z[k4], fmaf(lv.y, z[k4 + 1], a0));
+                        a1 = fmaf(lv.z, z[k4 + 2], fmaf(lv.w, z[k4 + 3], a1));
+                    }
+                    sg[u] = a0 + a1;
                 }
-                z[i] = lane == i ? inv_ii : (lane < i ? -((a[0] + a[1]) + (a[2] + a[3])) * inv_ii : 0.f);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int i = i0 + u;
+                    const float *li = Lb + i * PO_ZT;
+                    float acc = sg[u];
+#pragma unroll
+                    for (int v = 0; v < u; ++v) acc = fmaf(li[i0 + v], z[i0 + v], acc);
+                    const float inv_ii = li[PO_B];
+                    z[i] = lane == i ? inv_ii : (lane < i ? -acc * inv_ii : 0.f);
+                }
             }
             __syncwarp();
 #pragma unroll
             for (int i = 0; i < PO_B; ++i) {
-                Zs[(o + i) * PO_LD + o + lane] = i >= lane ? z[i] : 0.f;
+                Zs[(o + i) * PO_ZL + o + lane] = i >= lane ? z[i] : 0.f;
                 Zt[lane * PO_ZT + i] = i >= lane ? z[i] : 0.f;  // Zt[kk = lane][c = i] = Z_o+i,o+lane
             }
             if (bad && lane == 0) bad_sh = 1;
-        } else {
-            const int t2 = tid - 32;  // 0..479
+        } else if ((warp & 3) != 0) {
+            // the 12 warps on the other three schedulers (warps 4, 8, 12 share
+            // warp 0's scheduler and stay idle: its serial chain keeps the issue slots)
+            const int t2 = (warp - 1 - (warp >> 2)) * 32 + lane;  // 0..383
+            constexpr int NB = 12 * 32;
+            if (kb > 0) {
+                // the previous block's update of rows and columns >= o outside
+                // this block's diagonal block: lower 4 x 4 tiles (a, b), a >= 8
+                const int RT = (KRR_TILE - o) / 4;
+                for (int t = 36 + t2; t < RT * (RT + 1) / 2; t += NB) {
+                    int a, b;
+                    po_tri_decode(t, a, b);
+                    po_rank32_tile(Ls, Pn, o, a, b);
+                }
+                asm volatile("bar.sync 2, 384;" ::: "memory");  // these 12 warps: the panel columns are final
+            }
             // Pt[kk][r] = A_r,o+kk for the rows below the block
-            for (int e = t2; e < nr * PO_B; e += blockDim.x - 32) {
+            for (int e = t2; e < nr * PO_B; e += NB) {
                 const int kk = e / nr, r = b0 + (e - kk * nr);
                 Pt[kk * PO_PT + r] = Ls[r * PO_LD + o + kk];
             }
-            // T_i,c = sum_{m < o} L_o+i,m Z_m,c for c < o (Z_m,c = 0 for m < c): 4 x 4 tiles
+            // T_i,c = sum_{m < o} L_o+i,m Z_m,c for c < o (Z_m,c = 0 for m < c), 4 x 4
+            // tiles, one 16-byte load of Z per step: few shared loads beside warp 0's chain
             const int ntt = (PO_B / 4) * (o / 4);
-            for (int t = t2; t < ntt; t += blockDim.x - 32) {
+            for (int t = t2; t < ntt; t += NB) {
                 const int i0 = (t / (o / 4)) * 4, c0 = (t % (o / 4)) * 4;
                 float acc[4][4] = {};
                 for (int m = c0; m < o; ++m) {
-                    float lv[4], zv[4];
+                    const float4 zz = *reinterpret_cast<const float4 *>(Zs + m * PO_ZL + c0);
+                    const float zv[4] = {zz.x, zz.y, zz.z, zz.w};
+                    float lv[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) {
-                        lv[u] = Ls[(o + i0 + u) * PO_LD + m];
-                        zv[u] = Zs[m * PO_LD + c0 + u];
-                    }
+                    for (int u = 0; u < 4; ++u) lv[u] = Ls[(o + i0 + u) * PO_LD + m];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -452,7 +521,7 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
                     const float tv[4] = {tt.x, tt.y, tt.z, tt.w};
                     float zv[4];
 #pragma unroll
-                    for (int u = 0; u < 4; ++u) zv[u] = Zs[(o + i0 + u) * PO_LD + o + kk];
+                    for (int u = 0; u < 4; ++u) zv[u] = Zs[(o + i0 + u) * PO_ZL + o + kk];
 #pragma unroll
                     for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -461,7 +530,7 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) Zs[(o + i0 + u) * PO_LD + c0 + v] = -acc[u][v];
+                    for (int v = 0; v < 4; ++v) Zs[(o + i0 + u) * PO_ZL + c0 + v] = -acc[u][v];
             }
         }
         if (nr == 0) break;  // the last block has nothing below it
@@ -471,37 +540,17 @@ __global__ void __launch_bounds__(512, 1) potrf_blocked_kernel(float *__restrict
             const int c = e / nr, r = b0 + (e - c * nr);
             Ls[r * PO_LD + o + c] = Pn[c * PO_PT + r];
         }
-        // rank-32 update of the lower trailing part, 4 x 4 tiles (a, b), b <= a
-        const int RT = nr / 4;
-        for (int t = tid; t < RT * (RT + 1) / 2; t += blockDim.x) {
-            int a, b;
-            po_tri_decode(t, a, b);
-            const int r0 = b0 + 4 * a, c0 = b0 + 4 * b;
-            float acc[4][4] = {};
-#pragma unroll 4
-            for (int kk = 0; kk < PO_B; ++kk) {
-                const float4 x = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + r0);
-                const float4 y = *reinterpret_cast<const float4 *>(Pn + kk * PO_PT + c0);
-                const float xv[4] = {x.x, x.y, x.z, x.w}, yv[4] = {y.x, y.y, y.z, y.w};
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-#pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(xv[u], yv[v], acc[u][v]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v)
-                    if (a != b || v <= u) Ls[(r0 + u) * PO_LD + c0 + v] -= acc[u][v];
-        }
-        __syncthreads();
+        // (the update by this block's panel starts at the next block's step A)
     }
     __syncthreads();
-    if (tid == 0 && bad_sh) flags[s] = 1;
-    float *z = Z + (S.dtile0 + k) * KRR_TILE_ELEMS;
+    // the solve's descriptor again (not held in registers across the blocks)
+    const int s2 = find_solve(pre, nsolve, blockIdx.x);
+    if (tid == 0 && bad_sh) flags[s2] = 1;
+    g = A + (solves[s2].ltile0 + (int64_t)k * (k + 1) / 2 + k) * KRR_TILE_ELEMS;
+    float *z = Z + (solves[s2].dtile0 + k) * KRR_TILE_ELEMS;
     for (int e4 = tid; e4 < KRR_TILE_ELEMS / 4; e4 += blockDim.x) {
         const int e = e4 * 4, r = e >> 7, c = e & 127;
-        const float *lr = Ls + r * PO_LD + c, *zr = Zs + r * PO_LD + c;
+        const float *lr = Ls + r * PO_LD + c, *zr = Zs + r * PO_ZL + c;
         reinterpret_cast<float4 *>(g)[e4] =
             make_float4(c <= r ? lr[0] : 0.f, c + 1 <= r ? lr[1] : 0.f, c + 2 <= r ? lr[2] : 0.f,
                         c + 3 <= r ? lr[3] : 0.f);

@@ -180,7 +180,7 @@ constexpr int OZP_EPI_WARPS = 16;
 constexpr int OZP_EPI = OZP_EPI_WARPS * 32;                // epilogue threads
 constexpr int OZP_THREADS = (OZ_EPI_WARP0 + OZP_EPI_WARPS) * 32;
 constexpr int OZP_SUB = 8;                                 // columns per TMEM read
-constexpr int OZP_COLS = 4;                                // columns whose exponentials interleave
+constexpr int OZP_COLS = 2;                                // columns whose exponentials interleave (4 measured no faster)
 struct OzPSmem {
     unsigned char a[OZ_ASTAGES][OZ_A_STAGE];   // 1024-aligned stage ring
     unsigned char b[OZ_B_BYTES];
