@@ -104,8 +104,11 @@ template <bool NORM = true>
 __device__ __forceinline__ df df_exp_nonpos(df x, const float2 *__restrict__ tab) {
     if (!(x.hi > -87.0f)) return df_make(0.f, 0.f);
     const float C1 = 0x1.62p-9f, C2 = 0x1.c85fep-18f, C3 = -0x1.718432p-43f;
-    const float nf = rintf(x.hi * 369.329930467574632284140718f);  // 256 / ln 2
-    const int n = (int)nf;
+    // n = x.hi 256 / ln2 rounded to an integer by the FMA into 1.5 2^23 (integers
+    // there are spaced 1; |n| < 2^15), read back from the bits: no conversion
+    const float rnd = __fmaf_rn(x.hi, 369.329930467574632284140718f, 0x1.8p23f);
+    const float nf = __fsub_rn(rnd, 0x1.8p23f);
+    const int n = __float_as_int(rnd) - 0x4B400000;
     const float t1 = __fmaf_rn(-nf, C1, x.hi);  // exact
     const float p2 = __fmul_rn(nf, C2);
     const float e2 = __fmaf_rn(nf, C2, -p2);     // n C2 = p2 + e2

@@ -190,6 +190,7 @@ struct OzPSmem {
     int combk[2][OZ_NSP][OZ_M];                  // and their range shifts
     float2 shift[OZ_NSP][OZP_EPI];               // per epilogue thread: -K ln2 per sigma (df)
     float2 dist[OZP_EPI][OZP_SUB + 1];           // per epilogue thread: 8 distances (padded row)
+    float qmin[2][4][OZ_M];                      // per chunk parity and column quarter: each row's D_min so far
     uint64_t a_full[OZ_ASTAGES], a_empty[OZ_ASTAGES];
     uint64_t b_full, b_empty, t_full, t_empty;
     uint32_t tmem;
@@ -204,6 +205,29 @@ __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float *v) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
+// Far terms of a prediction row.  A term whose exponent argument lies more
+// than OZ_FAR below that of a training row already seen, x - x_max = (D -
+// D_min) c < -OZ_FAR, is below e^-20 (2e-9) of the row's largest term (a
+// nearer training row only makes it smaller).  D_min is the smallest distance
+// this thread has seen, or that the row's other three column quarters had
+// published by the end of the previous chunk (exchanged through shared
+// memory across the chunk barrier, double-buffered, so every decision is the
+// same in every run).  Such a term is formed in FP32: x + shift by
+// one FMA on the high parts and ex2.approx (argument error below
+// 2^-22 (|x| + |shift| + 1), so relative error below 2e-4 while |x| and the
+// shift stay under 800; results below 2^-126 flush to 0, as the double-float
+// exponential drops arguments below -87), and its product with alpha_hi is
+// added to the accumulator's low part.  Per term that is an error below 4e-13
+// of the largest term times |alpha|, under the double-float path's own
+// rounding of the sum.  The test is taken warp-wide (all 32 rows far), so the
+// warp never diverges.
+constexpr float OZ_FAR = 20.0f;
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // a (shift ka) + b (shift kb) at the larger shift; *k receives it
 __device__ __forceinline__ df oz_combine(df a, int ka, df b, int kb, int *k) {
     const int km = max(ka, kb);
@@ -324,6 +348,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
         const df nq = df_make(nq2.x, nq2.y);
         df_acc acc[OZ_NSP][OZ_NLP];
         int ksh[OZ_NSP];       // range shift of the accumulators per sigma (exp_row_shift)
+        float shh[OZ_NSP];     // high part of the shift argument -K ln2 (far terms)
         float dmin = INFINITY;  // smallest distance to a real training row so far
         const int et = threadIdx.x - OZ_EPI_WARP0 * 32;  // 0..511
         // -1 / (2 sigma^2) per sigma slot: the launch's grid, or the partition's own sigma
@@ -341,10 +366,13 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
         for (int a = 0; a < OZ_NSP; ++a) {
             ksh[a] = KRR_SHIFT_NONE;  // no term yet: the shift argument stays 0
+            shh[a] = 0.f;
             sm.shift[a][et] = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < OZ_NLP; ++b) dfa_zero(acc[a][b]);
         }
+        sm.qmin[0][quarter][row] = INFINITY;
+        sm.qmin[1][quarter][row] = INFINITY;
         bool ok = true;
         for (int c = 0; c < nchunks; ++c) {
             OzChunkData &cd = sm.cd[c & 1];
@@ -372,6 +400,12 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                 continue;
             }
             tc_fence_after();
+            // the row's nearest distance over all quarters as published after the previous chunk
+            float dpub = INFINITY;
+            if (c > 0) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) dpub = fminf(dpub, sm.qmin[(c - 1) & 1][q][row]);
+            }
 #pragma unroll 1
             for (int sub = 0; sub < (OZ_N / 4) / OZP_SUB; ++sub) {
                 float lv[OZ_SLICES][OZP_SUB];
@@ -386,7 +420,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     if (lane == 0) mbar_arrive(&sm.t_empty);
                 }
                 // distances of the columns (static register indices), parked in shared memory
-                float dm = INFINITY;
+                float dm = INFINITY, dM = 0.f;
 #pragma unroll
                 for (int k = 0; k < OZP_SUB; ++k) {
                     const int col = (int)col0 + k;
@@ -395,6 +429,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                                              cd.nl[col], __int_as_float((127 + sc) << 23));
                     sm.dist[et][k] = make_float2(D.hi, D.lo);
                     if (c * OZ_N + col < P.m) dm = fminf(dm, D.hi);
+                    dM = fmaxf(dM, D.hi);
                 }
                 // a closer training row raises the range shift: rescale by 2^(K_old - K_new)
                 if (dm < dmin) {
@@ -410,7 +445,9 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                                 acc[is][il].c *= f;
                             }
                             ksh[is] = kn;
-                            sm.shift[is][et] = exp_shift_arg(kn);
+                            const float2 sa = exp_shift_arg(kn);
+                            sm.shift[is][et] = sa;
+                            shh[is] = sa.x;
                         }
                     }
                 }
@@ -422,6 +459,13 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                 for (int is = 0; is < OZ_NSP; ++is)
                     wsh |= __any_sync(0xffffffffu, ksh[is] != 0) ? (1u << is) : 0u;
+                // sigmas for which some column of this group can be far for all 32 rows
+                const float dfar = fminf(dmin, dpub);
+                unsigned wfar = 0;
+#pragma unroll
+                for (int is = 0; is < OZ_NSP; ++is)
+                    wfar |= __all_sync(0xffffffffu, is < pp.nsig && (dM - dfar) * chi[is] < -OZ_FAR) ? (1u << is)
+                                                                                                       : 0u;
                 // OZP_COLS columns per iteration: their exponentials are
                 // independent chains the scheduler can interleave.  Padded training rows have
                 // alpha = 0 exactly, so they need no test.
@@ -437,6 +481,26 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
                         if (is < pp.nsig) {
+                            bool far = (wfar >> is) & 1u;  // false while the row has no real term (D_min = inf)
+#pragma unroll
+                            for (int u = 0; u < OZP_COLS; ++u) far = far && (D[u].hi - dfar) * chi[is] < -OZ_FAR;
+                            if ((wfar >> is) & 1u && __all_sync(0xffffffffu, far)) {
+                                float kf[OZP_COLS];
+#pragma unroll
+                                for (int u = 0; u < OZP_COLS; ++u)
+                                    kf[u] = ex2_approx(__fmaf_rn(D[u].hi, chi[is], shh[is]) * 1.44269504088896341f);
+#pragma unroll
+                                for (int il = 0; il < OZ_NLP; ++il)
+                                    if (il < pp.nlam) {
+#pragma unroll
+                                        for (int u = 0; u < OZP_COLS; u += 2) {
+                                            const float4 a = cd.a2[is * OZ_NLP + il][(col + u) >> 1];
+                                            acc[is][il].c = __fmaf_rn(kf[u], a.x, acc[is][il].c);
+                                            acc[is][il].c = __fmaf_rn(kf[u + 1], a.z, acc[is][il].c);
+                                        }
+                                    }
+                                continue;
+                            }
                             const df cs = df_make(chi[is], clo[is]);
                             df kv[OZP_COLS];
 #pragma unroll
@@ -462,6 +526,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     }
                 }
             }
+            sm.qmin[c & 1][quarter][row] = dmin;  // read by the row's other quarters after the next barrier
         }
         // combine the four column quarters of a row in a fixed order:
         // (q0 + q1) + (q2 + q3)
