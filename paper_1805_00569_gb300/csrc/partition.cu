@@ -178,102 +178,291 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
     if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
 }
 
-// Same assignment (the same FP32 screening with the same bound, the same FP64
-// recheck of every candidate), organised for throughput: one thread per row
-// with the row's DP features in registers (DP = d padded to a multiple of 8,
-// up to 96; padded features are 0 on both sides, so they add exact zeros);
-// the centres in shared memory as [feature][centre] so one 16-byte broadcast
-// load feeds four centres; the k screening distances parked in shared memory
-// (column per thread) for the candidate pass.
-constexpr int ASSIGN2_THREADS = 256;
+// Same assignment, organised for throughput in two kernels.
+//
+// Screen (kmeans_screen_kernel): a CTA takes 128 rows and every centre, 64
+// at a time; thread (rg, cg) forms the FP32 Gram products of 8 rows x 4
+// centres from shared copies of the rows ([feature][row]) and centres
+// ([feature][centre]), one fused multiply-add per row, centre and feature.
+// The screening distance is the Gram form
+//   d32 = rn(rn(||x||^2 + ||c||^2) - 2 x.c)
+// with ||x||^2, ||c||^2 and x.c each an FP32 sum of products (in any order:
+// a sum of d terms in any order is off by at most (d - 1) 2^-24 times the sum
+// of their magnitudes).  The bound used above also holds for it: the three sums
+// and the two final roundings contribute at most (2d + 3) 2^-24 (||x||^2 +
+// ||c||^2) in the normal range, the FP32 rounding of the inputs 4 2^-24 of
+// the same, so (2d + 7) 2^-24 (...) <= (d + 16) 2^-24 1.27 * 2 (...); in the
+// subnormal range each of the 4d + 2 roundings is off by at most 2^-150,
+// within (4d + 64) 2^-149.  Every row with one candidate takes it; a row
+// with several goes to a list.
+//
+// Recheck (kmeans_recheck_kernel): one warp per listed row.  Its lanes form
+// the same screening distances of their centres, the candidates among them,
+// and the FP64 distances of the candidates in the definition's order (feature
+// by feature, rounding each step); the nearest by FP64 distance wins (strict
+// <, lowest index; index 0 when no FP64 distance is finite).  A row's
+// candidates are a superset of the centres that can be nearest under the
+// definition, so the result is the definition's whatever the list order.
+constexpr int SCR_THREADS = 256;
+constexpr int SCR_ROWS = 128;            // rows per CTA
+constexpr int SCR_CT = 64;               // centres per tile
+constexpr int SCR_XL = SCR_ROWS + 4;     // row stride of the [feature][row] copy (16-byte rows)
+constexpr int SCR_CL = SCR_CT + 4;       // row stride of the [feature][centre] copy
+constexpr int SCR_KMAX = 256;            // centres the screen keeps in shared memory
+
+static size_t screen_smem(int dp, int kt) {
+    return ((size_t)dp * SCR_XL + (size_t)dp * SCR_CL + SCR_ROWS + kt + (size_t)SCR_ROWS * (kt + 1)) * sizeof(float);
+}
+
 template <int DP>
-__global__ void __launch_bounds__(ASSIGN2_THREADS)
-kmeans_assign_reg_kernel(const float *__restrict__ X32, const double *__restrict__ X, int64_t n, int32_t d,
-                         const double *__restrict__ C64, const float *__restrict__ C32, int32_t k, int32_t k4,
-                         const int32_t *__restrict__ prev, int32_t *__restrict__ out,
-                         unsigned long long *delta) {
+__global__ void __launch_bounds__(SCR_THREADS)
+kmeans_screen_kernel(const float *__restrict__ X32, int64_t n, int32_t d, const float *__restrict__ C32,
+                     const float *__restrict__ cn32, int32_t k, int32_t kt, const int32_t *__restrict__ prev,
+                     int32_t *__restrict__ out, int32_t *__restrict__ list, unsigned int *__restrict__ nlist,
+                     unsigned long long *delta) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *cT = reinterpret_cast<float *>(smem_raw);  // [DP][k4]
-    float *cn = cT + (size_t)DP * k4;                 // [k4] ||c||^2
-    float *dist = cn + k4;                            // [k4][ASSIGN2_THREADS]
-    for (int e = threadIdx.x; e < DP * k4; e += blockDim.x) {
-        const int f = e / k4, j = e % k4;
-        cT[e] = (f < d && j < k) ? C32[(size_t)j * d + f] : 0.f;
+    float *xs = reinterpret_cast<float *>(smem_raw);  // [DP][SCR_XL]
+    float *cs = xs + DP * SCR_XL;                      // [DP][SCR_CL]
+    float *xn = cs + DP * SCR_CL;                      // [SCR_ROWS] ||x||^2
+    float *cn = xn + SCR_ROWS;                         // [kt] ||c||^2
+    float *dist = cn + kt;                             // [SCR_ROWS][kt + 1] screening distances
+    const int tid = threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.x * SCR_ROWS;
+    const int nrow = (int)min((int64_t)SCR_ROWS, n - i0);
+    {
+        // the tile's rows, all loads issued before the first shared store
+        constexpr int NE = SCR_ROWS * DP / SCR_THREADS;
+        float v[NE];
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+            const int e = tid + u * SCR_THREADS, r = e / DP, f = e % DP;
+            v[u] = (r < nrow && f < d) ? X32[(i0 + r) * d + f] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < NE; ++u) {
+            const int e = tid + u * SCR_THREADS, r = e / DP, f = e % DP;
+            xs[f * SCR_XL + r] = v[u];
+        }
+    }
+    for (int j = tid; j < kt; j += SCR_THREADS) cn[j] = cn32[j];
+    __syncthreads();
+    {
+        // ||x||^2: warp w takes rows 16 w .. 16 w + 15, two lanes per row (the
+        // two halves of the features, then their sum)
+        const int rr = (tid >> 5) * 16 + (tid & 15), h = (tid >> 4) & 1;
+        float sx = 0.f;
+#pragma unroll 8
+        for (int f = h * (DP / 2); f < (h + 1) * (DP / 2); ++f) sx = fmaf(xs[f * SCR_XL + rr], xs[f * SCR_XL + rr], sx);
+        sx += __shfl_xor_sync(0xffffffffu, sx, 16);
+        if (h == 0) xn[rr] = sx;
+    }
+    const int rg = tid >> 4, cg = tid & 15;  // rows 8 rg .. 8 rg + 7, centres 4 cg .. 4 cg + 3 of the tile
+    const int DL = kt + 1;
+    for (int c0 = 0; c0 < kt; c0 += SCR_CT) {
+        __syncthreads();  // the previous tile's products are done with cs
+        {
+            constexpr int NC = SCR_CT * DP / SCR_THREADS;
+            float v[NC];
+#pragma unroll
+            for (int u = 0; u < NC; ++u) {
+                const int e = tid + u * SCR_THREADS, jj = e / DP, f = e % DP;
+                v[u] = (c0 + jj < k && f < d) ? C32[(size_t)(c0 + jj) * d + f] : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < NC; ++u) {
+                const int e = tid + u * SCR_THREADS, jj = e / DP, f = e % DP;
+                cs[f * SCR_CL + jj] = v[u];
+            }
+        }
+        __syncthreads();
+        float acc[8][4] = {};
+#pragma unroll 4
+        for (int f = 0; f < DP; ++f) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(xs + f * SCR_XL + rg * 8);
+            const float4 a1 = *reinterpret_cast<const float4 *>(xs + f * SCR_XL + rg * 8 + 4);
+            const float4 b = *reinterpret_cast<const float4 *>(cs + f * SCR_CL + cg * 4);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int r = rg * 8 + u, j = c0 + cg * 4 + v;
+                dist[r * DL + j] = __fmaf_rn(-2.0f, acc[u][v], __fadd_rn(xn[r], cn[j]));
+            }
     }
     __syncthreads();
-    for (int j = threadIdx.x; j < k4; j += blockDim.x) {
-        float sacc = 0.f;
-        for (int f = 0; f < d; ++f) sacc = fmaf(cT[f * k4 + j], cT[f * k4 + j], sacc);
-        cn[j] = sacc;
-    }
-    __syncthreads();
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float x[DP];
-#pragma unroll
-    for (int f = 0; f < DP; ++f) x[f] = f < d ? X32[i * d + f] : 0.f;
-    float xn = 0.f;
-#pragma unroll
-    for (int f = 0; f < DP; ++f) xn = fmaf(x[f], x[f], xn);
+    if (tid >= SCR_ROWS) return;
+    const int r = tid;
+    const bool live = r < nrow;
     const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
     const float babs = assign_abs_bound(d);
-    float best_hi = INFINITY;
-    const float4 *cT4 = reinterpret_cast<const float4 *>(cT);
-#pragma unroll 1
-    for (int j4 = 0; j4 < k4; j4 += 4) {
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int f = 0; f < DP; ++f) {
-            const float4 c = cT4[(f * k4 + j4) >> 2];
-            const float t0 = x[f] - c.x, t1 = x[f] - c.y, t2 = x[f] - c.z, t3 = x[f] - c.w;
-            a0 = fmaf(t0, t0, a0);
-            a1 = fmaf(t1, t1, a1);
-            a2 = fmaf(t2, t2, a2);
-            a3 = fmaf(t3, t3, a3);
-        }
-        const float av[4] = {a0, a1, a2, a3};
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            dist[(size_t)(j4 + u) * ASSIGN2_THREADS + threadIdx.x] = av[u];
-            if (j4 + u < k) best_hi = fminf(best_hi, av[u] + (bscale * (xn + cn[j4 + u]) + babs));
+    int arg = -1;
+    if (live) {
+        float best_hi = INFINITY;
+        for (int j = 0; j < k; ++j) best_hi = fminf(best_hi, dist[r * DL + j] + (bscale * (xn[r] + cn[j]) + babs));
+        int ncand = 0, first = -1;
+        for (int j = 0; j < k; ++j)
+            if (assign_candidate(dist[r * DL + j], bscale * (xn[r] + cn[j]) + babs, best_hi)) {
+                if (ncand == 0) first = j;
+                ++ncand;
+            }
+        if (ncand == 1) {
+            arg = first;
+            out[i0 + r] = arg;
+        } else {
+            list[atomicAdd(nlist, 1u)] = (int32_t)(i0 + r);  // decided by the recheck
         }
     }
-    int ncand = 0, first = -1;
-#pragma unroll 1
-    for (int j = 0; j < k; ++j)
-        if (assign_candidate(dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x], bscale * (xn + cn[j]) + babs,
-                             best_hi)) {
-            if (ncand == 0) first = j;
-            ++ncand;
-        }
-    int arg = first;
-    if (ncand > 1) {
-        const double *xr = X + i * d;
-        double best = INFINITY;
-#pragma unroll 1
-        for (int j = 0; j < k; ++j) {
-            if (!assign_candidate(dist[(size_t)j * ASSIGN2_THREADS + threadIdx.x], bscale * (xn + cn[j]) + babs,
-                                  best_hi))
-                continue;
-            const double *c64 = C64 + (size_t)j * d;
-            double sd = 0.0;
-            for (int f = 0; f < d; ++f) {
-                const double t = __dsub_rn(xr[f], c64[f]);
-                sd = __dadd_rn(sd, __dmul_rn(t, t));
-            }
-            if (sd < best) {
-                best = sd;
-                arg = j;
-            }
-        }
-        if (!(best < INFINITY)) arg = 0;
-    }
-    out[i] = arg;
     if (delta) {  // one atomic per warp: the counter is a single address
-        const bool changed = prev == nullptr || prev[i] != arg;
-        const unsigned active = __activemask();
-        const unsigned vote = __ballot_sync(active, changed);
-        if ((threadIdx.x & 31) == __ffs(active) - 1 && vote) atomicAdd(delta, (unsigned long long)__popc(vote));
+        const bool changed = arg >= 0 && (prev == nullptr || prev[i0 + r] != arg);
+        const unsigned vote = __ballot_sync(0xffffffffu, changed);
+        if ((tid & 31) == 0 && vote) atomicAdd(delta, (unsigned long long)__popc(vote));
+    }
+}
+
+// ||c||^2 of every centre (0 for the padding up to kt): one warp per centre
+__global__ void centre_norms_kernel(const float *__restrict__ C32, int32_t k, int32_t d, int32_t kt,
+                                    float *__restrict__ cn32) {
+    const int j = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+    if (j >= kt) return;
+    float s = 0.f;
+    if (j < k)
+        for (int f = lane; f < d; f += 32) s = fmaf(C32[(size_t)j * d + f], C32[(size_t)j * d + f], s);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) cn32[j] = s;
+}
+
+constexpr int RCK_WARPS = 8;                  // warps (rows in flight) per CTA
+constexpr int RCK_CH = SCR_KMAX / 32;         // 32-centre chunks
+__global__ void __launch_bounds__(RCK_WARPS * 32)
+kmeans_recheck_kernel(const float *__restrict__ X32, const double *__restrict__ X, int32_t d,
+                      const float *__restrict__ C32, const double *__restrict__ C64, const float *__restrict__ cn32,
+                      int32_t k, const int32_t *__restrict__ list, const unsigned int *__restrict__ nlist,
+                      const int32_t *__restrict__ prev, int32_t *__restrict__ out, unsigned long long *delta) {
+    __shared__ double xsh[RCK_WARPS][96];  // the row in FP64 (d <= 96 on this path)
+    __shared__ float dsh[RCK_WARPS][SCR_KMAX], bsh[RCK_WARPS][SCR_KMAX];  // screening distance, bound per centre
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t warps = (int64_t)gridDim.x * RCK_WARPS;
+    const int64_t cnt = *nlist;
+    const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
+    const float babs = assign_abs_bound(d);
+    for (int64_t w = (int64_t)blockIdx.x * RCK_WARPS + wid; w < cnt; w += warps) {
+        const int64_t i = list[w];
+        // the row: FP32 features f = lane + 32 q in registers, FP64 in shared memory
+        float xv[3];
+        float xn = 0.f;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const int f = lane + 32 * q;
+            xv[q] = f < d ? X32[i * d + f] : 0.f;
+            xn = fmaf(xv[q], xv[q], xn);
+            if (f < d) xsh[wid][f] = X[i * d + f];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) xn += __shfl_xor_sync(0xffffffffu, xn, o);
+        __syncwarp();
+        // screening distance and bound of every centre (lane jj writes centre ch 32 + jj)
+        float lbest = INFINITY;
+#pragma unroll 1
+        for (int ch = 0; ch * 32 < k; ++ch) {
+            for (int jj0 = 0; jj0 < 32 && ch * 32 + jj0 < k; jj0 += 8) {
+                // the features of 8 centres, all loads issued first
+                float cv[8][3];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const int j = ch * 32 + jj0 + u, f = lane + 32 * q;
+                        cv[u][q] = (j < k && f < d) ? C32[(size_t)j * d + f] : 0.f;
+                    }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int jj = jj0 + u, j = ch * 32 + jj;
+                    float p = 0.f;
+#pragma unroll
+                    for (int q = 0; q < 3; ++q)
+                        if (lane + 32 * q < d) p = fmaf(xv[q], cv[u][q], p);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                    if (j < k && lane == jj) {
+                        const float dj = __fmaf_rn(-2.0f, p, __fadd_rn(xn, cn32[j]));
+                        const float bj = bscale * (xn + cn32[j]) + babs;
+                        dsh[wid][j] = dj;
+                        bsh[wid][j] = bj;
+                        lbest = fminf(lbest, dj + bj);
+                    }
+                }
+            }
+        }
+        float best_hi = lbest;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) best_hi = fminf(best_hi, __shfl_xor_sync(0xffffffffu, best_hi, o));
+        __syncwarp();  // dsh, bsh written
+        unsigned mask[RCK_CH];
+        int ncand = 0;
+#pragma unroll
+        for (int ch = 0; ch < RCK_CH; ++ch) {
+            const int j = ch * 32 + lane;
+            mask[ch] = __ballot_sync(0xffffffffu, j < k && assign_candidate(dsh[wid][j], bsh[wid][j], best_hi));
+            ncand += __popc(mask[ch]);
+        }
+        // candidate c (ascending index) goes to lane c % 32: FP64 distance in
+        // the definition's order, the lane keeping its smallest (strict <)
+        double best = INFINITY;
+        int barg = k;
+        for (int c0 = 0; c0 < ncand; c0 += 32) {
+            const int c = c0 + lane;
+            int j = -1;
+            if (c < ncand) {
+                int rem = c;
+#pragma unroll
+                for (int ch = 0; ch < RCK_CH; ++ch) {
+                    const int pc = __popc(mask[ch]);
+                    if (j < 0 && rem < pc) {
+                        unsigned m = mask[ch];
+                        for (int u = 0; u < rem; ++u) m &= m - 1;  // drop the rem lowest candidates
+                        j = ch * 32 + __ffs(m) - 1;
+                    }
+                    if (j < 0) rem -= pc;
+                }
+            }
+            if (j >= 0) {
+                const double *c64 = C64 + (size_t)j * d;
+                double sd = 0.0;
+#pragma unroll 8
+                for (int f = 0; f < d; ++f) {
+                    const double t = __dsub_rn(xsh[wid][f], c64[f]);
+                    sd = __dadd_rn(sd, __dmul_rn(t, t));
+                }
+                if (sd < best) {
+                    best = sd;
+                    barg = j;
+                }
+            }
+        }
+        // smallest finite distance over the lanes, lowest index on equal distances
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oa = __shfl_xor_sync(0xffffffffu, barg, o);
+            if (ob < best || (ob == best && oa < barg)) {
+                best = ob;
+                barg = oa;
+            }
+        }
+        const int arg = best < INFINITY ? barg : 0;
+        if (lane == 0) {
+            out[i] = arg;
+            if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
+        }
+        __syncwarp();  // xsh is reused by the warp's next row
     }
 }
 
@@ -374,6 +563,8 @@ __global__ void kmeans_block_sums_kernel(const double *__restrict__ X, int64_t n
 // consecutive (centre, feature) entries and keeps both levels of the tree in
 // shared memory (ping-pong), so every addition reads shared memory.
 constexpr int TREE_THREADS = 256;
+constexpr int TREE_MAXTE = 32;                  // entries per CTA at most
+constexpr int TREE_MAXC = TREE_MAXTE + 1;       // centres those entries can span
 __global__ void kmeans_tree_divide_kernel(const double *__restrict__ partial, const long long *__restrict__ counts,
                                           int64_t nblk, int32_t k, int32_t d, int32_t te, double *__restrict__ C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -382,10 +573,43 @@ __global__ void kmeans_tree_divide_kernel(const double *__restrict__ partial, co
     const int64_t kd = (int64_t)k * d;
     const int64_t e0 = (int64_t)blockIdx.x * te;
     const int ne = (int)min((int64_t)te, kd - e0);
-    for (int64_t x = threadIdx.x; x < nblk * te; x += blockDim.x) {
-        const int64_t b = x / te;
-        const int c = (int)(x % te);
-        buf0[x] = c < ne ? partial[b * kd + e0 + c] : 0.0;
+    for (int64_t x0 = 0; x0 < nblk * te; x0 += 8 * (int64_t)blockDim.x) {
+        double v[8];  // eight loads in flight per thread
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t x = x0 + threadIdx.x + u * (int64_t)blockDim.x;
+            const int64_t b = x / te;
+            const int c = (int)(x % te);
+            v[u] = (x < nblk * te && c < ne) ? partial[b * kd + e0 + c] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t x = x0 + threadIdx.x + u * (int64_t)blockDim.x;
+            if (x < nblk * te) buf0[x] = v[u];
+        }
+    }
+    // the row counts of the centres this CTA's entries belong to (integer sums:
+    // any order), one warp per centre, lanes striding over the blocks
+    __shared__ long long ctot[TREE_MAXC];
+    const int j0 = (int)(e0 / d), nj = (int)((e0 + ne - 1) / d) - j0 + 1;
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int jj = warp; jj < nj; jj += (int)(blockDim.x >> 5)) {
+            long long sacc = 0;
+            for (int64_t b0 = lane; b0 < nblk; b0 += 32 * 8) {
+                long long v[8];  // eight loads in flight per lane
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int64_t b = b0 + 32 * u;
+                    v[u] = b < nblk ? counts[b * k + j0 + jj] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) sacc += v[u];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+            if (lane == 0) ctot[jj] = sacc;
+        }
     }
     __syncthreads();
     double *src = buf0, *dst = buf1;
@@ -406,9 +630,7 @@ __global__ void kmeans_tree_divide_kernel(const double *__restrict__ partial, co
     }
     for (int c = threadIdx.x; c < ne; c += blockDim.x) {
         const int64_t e = e0 + c;
-        const int j = (int)(e / d);
-        long long cnt = 0;
-        for (int64_t b = 0; b < nblk; ++b) cnt += counts[b * k + j];
+        const long long cnt = ctot[(int)(e / d) - j0];
         if (cnt > 0) C[e] = __ddiv_rn(src[c], (double)cnt);
     }
 }
@@ -678,30 +900,60 @@ krr_status run_partition_random(Ctx *ctx, int64_t n, int32_t p, uint64_t seed, i
 krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, int32_t d, const double *C64,
                       const float *C32, int32_t k, const int32_t *prev, int32_t *out, unsigned long long *delta) {
     if (n == 0) return KRR_OK;
-    const int dp = (d + 7) / 8 * 8, k4 = (k + 3) / 4 * 4;
-    const size_t sm2 = ((size_t)dp * k4 + k4 + (size_t)k4 * ASSIGN2_THREADS) * sizeof(float);
-    if (dp <= 96 && sm2 <= 200 * 1024) {
-        auto launch = [&](auto kern) -> krr_status {
-            KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kern));
-            KRR_LAUNCHED(), kern<<<grid_for(n, ASSIGN2_THREADS), ASSIGN2_THREADS, sm2, ctx->stream>>>(
-                X32, X, n, d, C64, C32, k, k4, prev, out, delta);
-            KRR_CUDA_TRY(ctx, cudaGetLastError());
-            return KRR_OK;
-        };
-        switch (dp) {
-            case 8: return launch(kmeans_assign_reg_kernel<8>);
-            case 16: return launch(kmeans_assign_reg_kernel<16>);
-            case 24: return launch(kmeans_assign_reg_kernel<24>);
-            case 32: return launch(kmeans_assign_reg_kernel<32>);
-            case 40: return launch(kmeans_assign_reg_kernel<40>);
-            case 48: return launch(kmeans_assign_reg_kernel<48>);
-            case 56: return launch(kmeans_assign_reg_kernel<56>);
-            case 64: return launch(kmeans_assign_reg_kernel<64>);
-            case 72: return launch(kmeans_assign_reg_kernel<72>);
-            case 80: return launch(kmeans_assign_reg_kernel<80>);
-            case 88: return launch(kmeans_assign_reg_kernel<88>);
-            default: return launch(kmeans_assign_reg_kernel<96>);
+    const int dp = (d + 7) / 8 * 8, kt = (k + SCR_CT - 1) / SCR_CT * SCR_CT;
+    if (dp <= 96 && k <= SCR_KMAX) {
+        // screen, then the FP64 recheck of the rows with several candidates
+        cudaStream_t st = ctx->stream;
+        int32_t *list = nullptr;
+        const int64_t nl = (n + 63) / 64 * 64;
+        // the listed rows, the count, then ||c||^2 per centre
+        const size_t bl = ((size_t)nl + 64 + (size_t)kt) * sizeof(int32_t);
+        KRR_CUDA_TRY(ctx, ctx_malloc(ctx, (void **)&list, bl));
+        unsigned int *nlist = reinterpret_cast<unsigned int *>(list + nl);
+        float *cn32 = reinterpret_cast<float *>(list + nl + 64);
+        cudaError_t e = cudaMemsetAsync(nlist, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess) {
+            KRR_LAUNCHED(), centre_norms_kernel<<<(unsigned)((kt * 32 + 255) / 256), 256, 0, st>>>(C32, k, d, kt, cn32);
+            e = cudaGetLastError();
         }
+        const size_t sm = screen_smem(dp, kt);
+        auto launch = [&](auto kern) {
+            cudaError_t r = allow_max_dyn_smem(kern);
+            if (r == cudaSuccess) {
+                KRR_LAUNCHED(), kern<<<grid_for(n, SCR_ROWS), SCR_THREADS, sm, st>>>(X32, n, d, C32, cn32, k, kt,
+                                                                                      prev, out, list, nlist, delta);
+                r = cudaGetLastError();
+            }
+            return r;
+        };
+        if (e == cudaSuccess) {
+            switch (dp) {
+                case 8: e = launch(kmeans_screen_kernel<8>); break;
+                case 16: e = launch(kmeans_screen_kernel<16>); break;
+                case 24: e = launch(kmeans_screen_kernel<24>); break;
+                case 32: e = launch(kmeans_screen_kernel<32>); break;
+                case 40: e = launch(kmeans_screen_kernel<40>); break;
+                case 48: e = launch(kmeans_screen_kernel<48>); break;
+                case 56: e = launch(kmeans_screen_kernel<56>); break;
+                case 64: e = launch(kmeans_screen_kernel<64>); break;
+                case 72: e = launch(kmeans_screen_kernel<72>); break;
+                case 80: e = launch(kmeans_screen_kernel<80>); break;
+                case 88: e = launch(kmeans_screen_kernel<88>); break;
+                default: e = launch(kmeans_screen_kernel<96>); break;
+            }
+        }
+        if (e == cudaSuccess) {
+            const int64_t g = std::min<int64_t>((n + RCK_WARPS - 1) / RCK_WARPS, 152 * 8);
+            KRR_LAUNCHED(), kmeans_recheck_kernel<<<(unsigned)std::max<int64_t>(g, 1), RCK_WARPS * 32, 0, st>>>(
+                X32, X, d, C32, C64, cn32, k, list, nlist, prev, out, delta);
+            e = cudaGetLastError();
+        }
+        ctx_free(ctx, list, bl);
+        if (e != cudaSuccess) {
+            ctx->last_error = std::string("kmeans assign: ") + cudaGetErrorString(e);
+            return KRR_ERR_CUDA;
+        }
+        return KRR_OK;
     }
     size_t sm = ((size_t)k * d + k + (size_t)d * ASSIGN_THREADS) * sizeof(float) + 16;
     if (sm > 200 * 1024) {
@@ -730,7 +982,7 @@ krr_status run_update(Ctx *ctx, const double *X, int64_t n, int32_t d, const int
     KRR_CUDA_TRY(ctx, allow_max_dyn_smem(kmeans_block_sums_kernel));
     KRR_LAUNCHED(), kmeans_block_sums_kernel<<<(unsigned)nblk, 32 * fcs * cgs, sm, ctx->stream>>>(
         X, n, d, c, k, cgs, partial, counts);
-    int te = 32;  // entries per CTA: both tree levels within ~128 KiB of shared memory
+    int te = TREE_MAXTE;  // entries per CTA: both tree levels within ~128 KiB of shared memory
     while (te > 1 && 2 * (size_t)nblk * te * sizeof(double) > 128 * 1024) te /= 2;
     if (2 * (size_t)nblk * te * sizeof(double) > 200 * 1024) {
         ctx->last_error = "kmeans: too many row blocks for the shared-memory centre tree";
