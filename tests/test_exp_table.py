@@ -68,5 +68,15 @@ def test_range_reduction_constants():
     assert _bits(c1) + 15 <= 24  # n C1 exact in float32
     ln2_256 = Decimal(2).ln() / 256
     assert abs(Decimal(c1) + Decimal(c2) + Decimal(c3) - ln2_256) / ln2_256 < Decimal(2) ** -56
-    inv = float(re.search(r"rintf\(x\.hi \* (\S+)f\)", src).group(1))
+    m = re.search(r"__fmaf_rn\(x\.hi, (\S+)f, (\S+)f\);", src)
+    inv, big = float(m.group(1)), float.fromhex(m.group(2))
     assert abs(Decimal(f32(inv)) - 256 / Decimal(2).ln()) / (256 / Decimal(2).ln()) < Decimal(2) ** -24
+    # n is rounded by adding 1.5 2^23 (float32 integers there are spaced 1) and
+    # read back from the bits: exact for |n| < 2^22 (here |n| <= 87 * 256 / ln2)
+    assert big == 1.5 * 2.0 ** 23 and f32(big) == big
+    assert re.search(r"__float_as_int\(rnd\) - 0x4B400000", src)
+    assert struct.unpack("<I", struct.pack("<f", big))[0] == 0x4B400000
+    assert 87 * 256 / math.log(2) < 2 ** 22
+    for n in (0, -1, -255, -256, -32130):  # the bit trick recovers n
+        rnd = f32(big + n)
+        assert struct.unpack("<i", struct.pack("<f", rnd))[0] - 0x4B400000 == n
