@@ -197,10 +197,16 @@ kmeans_assign_kernel(const float *__restrict__ X32, const double *__restrict__ X
 // with several goes to a list.
 //
 // Recheck (kmeans_recheck_kernel): one warp per listed row.  Its lanes form
-// the same screening distances of their centres, the candidates among them,
-// and the FP64 distances of the candidates in the definition's order (feature
-// by feature, rounding each step); the nearest by FP64 distance wins (strict
-// <, lowest index; index 0 when no FP64 distance is finite).  A row's
+// the same screening distances of their centres and the candidates among
+// them; a single candidate is the nearest.  Several go, as (row, centre)
+// pairs in ascending centre order, to kmeans_pair_dist_kernel (one thread per
+// pair: the FP64 distance in the definition's order, feature by feature,
+// rounding each step -- a divergent FP64 instruction costs the same issue
+// slot with one lane as with 32, so the pairs of many rows fill the lanes)
+// and kmeans_pair_pick_kernel (one thread per row: the nearest by FP64
+// distance, strict <, lowest index; index 0 when no FP64 distance is
+// finite).  A row whose pairs do not fit the pair buffer is decided by its
+// warp the same way.  A row's
 // candidates are a superset of the centres that can be nearest under the
 // definition, so the result is the definition's whatever the list order.
 constexpr int SCR_THREADS = 256;
@@ -345,7 +351,9 @@ __global__ void __launch_bounds__(RCK_WARPS * 32)
 kmeans_recheck_kernel(const float *__restrict__ X32, const double *__restrict__ X, int32_t d,
                       const float *__restrict__ C32, const double *__restrict__ C64, const float *__restrict__ cn32,
                       int32_t k, const int32_t *__restrict__ list, const unsigned int *__restrict__ nlist,
-                      const int32_t *__restrict__ prev, int32_t *__restrict__ out, unsigned long long *delta) {
+                      const int32_t *__restrict__ prev, int32_t *__restrict__ out, unsigned long long *delta,
+                      int32_t *__restrict__ pstart, int32_t *__restrict__ pcnt, int32_t *__restrict__ prow,
+                      int32_t *__restrict__ pj, unsigned int *__restrict__ npairs, int64_t pcap) {
     __shared__ double xsh[RCK_WARPS][96];  // the row in FP64 (d <= 96 on this path)
     __shared__ float dsh[RCK_WARPS][SCR_KMAX], bsh[RCK_WARPS][SCR_KMAX];  // screening distance, bound per centre
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -413,26 +421,58 @@ kmeans_recheck_kernel(const float *__restrict__ X32, const double *__restrict__ 
             mask[ch] = __ballot_sync(0xffffffffu, j < k && assign_candidate(dsh[wid][j], bsh[wid][j], best_hi));
             ncand += __popc(mask[ch]);
         }
-        // candidate c (ascending index) goes to lane c % 32: FP64 distance in
-        // the definition's order, the lane keeping its smallest (strict <)
+        // candidate c in ascending index order
+        auto cand_index = [&](int c) {
+            int j = -1, rem = c;
+#pragma unroll
+            for (int ch = 0; ch < RCK_CH; ++ch) {
+                const int pc = __popc(mask[ch]);
+                if (j < 0 && rem < pc) {
+                    unsigned m = mask[ch];
+                    for (int u = 0; u < rem; ++u) m &= m - 1;  // drop the rem lowest candidates
+                    j = ch * 32 + __ffs(m) - 1;
+                }
+                if (j < 0) rem -= pc;
+            }
+            return j;
+        };
+        if (ncand == 1) {  // one candidate: it is the nearest (its bound is finite)
+            if (lane == 0) {
+                const int arg = cand_index(0);
+                pcnt[w] = 0;
+                out[i] = arg;
+                if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
+            }
+            __syncwarp();
+            continue;
+        }
+        // several: the (row, candidate) pairs go to the pair kernels, one
+        // FP64 distance per thread, when the pair buffer has room
+        unsigned int pos = 0;
+        if (lane == 0) pos = atomicAdd(npairs, (unsigned int)ncand);
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if ((int64_t)pos + ncand <= pcap) {
+            for (int c = lane; c < ncand; c += 32) {
+                pj[pos + c] = cand_index(c);
+                prow[pos + c] = (int32_t)i;
+            }
+            if (lane == 0) {
+                pstart[w] = (int32_t)pos;
+                pcnt[w] = ncand;
+            }
+            __syncwarp();
+            continue;
+        }
+        // decided here; reserved slots inside the buffer are marked unused
+        for (int64_t q = (int64_t)pos + lane; q < min((int64_t)pos + ncand, pcap); q += 32) prow[q] = -1;
+        if (lane == 0) pcnt[w] = 0;
+        // candidate c goes to lane c % 32: FP64 distance in the definition's
+        // order, the lane keeping its smallest (strict <)
         double best = INFINITY;
         int barg = k;
         for (int c0 = 0; c0 < ncand; c0 += 32) {
             const int c = c0 + lane;
-            int j = -1;
-            if (c < ncand) {
-                int rem = c;
-#pragma unroll
-                for (int ch = 0; ch < RCK_CH; ++ch) {
-                    const int pc = __popc(mask[ch]);
-                    if (j < 0 && rem < pc) {
-                        unsigned m = mask[ch];
-                        for (int u = 0; u < rem; ++u) m &= m - 1;  // drop the rem lowest candidates
-                        j = ch * 32 + __ffs(m) - 1;
-                    }
-                    if (j < 0) rem -= pc;
-                }
-            }
+            const int j = c < ncand ? cand_index(c) : -1;
             if (j >= 0) {
                 const double *c64 = C64 + (size_t)j * d;
                 double sd = 0.0;
@@ -463,6 +503,51 @@ kmeans_recheck_kernel(const float *__restrict__ X32, const double *__restrict__ 
             if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
         }
         __syncwarp();  // xsh is reused by the warp's next row
+    }
+}
+
+// FP64 distance of every (row, candidate) pair in the definition's order
+__global__ void kmeans_pair_dist_kernel(const double *__restrict__ X, const double *__restrict__ C64, int32_t d,
+                                        const int32_t *__restrict__ prow, const int32_t *__restrict__ pj,
+                                        const unsigned int *__restrict__ npairs, int64_t pcap,
+                                        double *__restrict__ pd) {
+    const int64_t np = min((int64_t)*npairs, pcap);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < np; q += (int64_t)gridDim.x * blockDim.x) {
+        if (prow[q] < 0) continue;  // slot of a row decided by its recheck warp
+        const double *xr = X + (int64_t)prow[q] * d, *c64 = C64 + (int64_t)pj[q] * d;
+        double sd = 0.0;
+#pragma unroll 8
+        for (int f = 0; f < d; ++f) {
+            const double t = __dsub_rn(xr[f], c64[f]);
+            sd = __dadd_rn(sd, __dmul_rn(t, t));
+        }
+        pd[q] = sd;
+    }
+}
+
+// the nearest candidate of every listed row whose pairs were handed over:
+// smallest finite FP64 distance, the first (lowest index) on equal distances;
+// index 0 when none is finite
+__global__ void kmeans_pair_pick_kernel(const int32_t *__restrict__ list, const unsigned int *__restrict__ nlist,
+                                        const int32_t *__restrict__ pstart, const int32_t *__restrict__ pcnt,
+                                        const int32_t *__restrict__ pj, const double *__restrict__ pd,
+                                        const int32_t *__restrict__ prev, int32_t *__restrict__ out,
+                                        unsigned long long *delta) {
+    const int64_t cnt = *nlist;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < cnt; w += (int64_t)gridDim.x * blockDim.x) {
+        const int c = pcnt[w];
+        if (c == 0) continue;
+        const int64_t p0 = pstart[w];
+        double best = INFINITY;
+        int arg = 0;
+        for (int q = 0; q < c; ++q)
+            if (pd[p0 + q] < best) {
+                best = pd[p0 + q];
+                arg = pj[p0 + q];
+            }
+        const int64_t i = list[w];
+        out[i] = arg;
+        if (delta && (prev == nullptr || prev[i] != arg)) atomicAdd(delta, 1ull);
     }
 }
 
@@ -906,12 +991,20 @@ krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, in
         cudaStream_t st = ctx->stream;
         int32_t *list = nullptr;
         const int64_t nl = (n + 63) / 64 * 64;
-        // the listed rows, the count, then ||c||^2 per centre
-        const size_t bl = ((size_t)nl + 64 + (size_t)kt) * sizeof(int32_t);
+        const int64_t pcap = 4 * nl;  // (row, candidate) pairs handed to the pair kernels
+        // the listed rows; two counts; ||c||^2 per centre; per listed row the
+        // first pair and the pair count; per pair the row, the centre and the
+        // FP64 distance
+        const int64_t o_cnt = nl, o_cn = nl + 64, o_ps = o_cn + (kt + 63) / 64 * 64, o_pc = o_ps + nl,
+                      o_pr = o_pc + nl, o_pj = o_pr + pcap, o_pd = o_pj + pcap;  // in int32 units
+        const size_t bl = ((size_t)o_pd + 2 * (size_t)pcap) * sizeof(int32_t);
         KRR_CUDA_TRY(ctx, ctx_malloc(ctx, (void **)&list, bl));
-        unsigned int *nlist = reinterpret_cast<unsigned int *>(list + nl);
-        float *cn32 = reinterpret_cast<float *>(list + nl + 64);
-        cudaError_t e = cudaMemsetAsync(nlist, 0, sizeof(unsigned int), st);
+        unsigned int *nlist = reinterpret_cast<unsigned int *>(list + o_cnt);
+        unsigned int *npairs = nlist + 1;
+        float *cn32 = reinterpret_cast<float *>(list + o_cn);
+        int32_t *pstart = list + o_ps, *pcnt = list + o_pc, *prow = list + o_pr, *pj = list + o_pj;
+        double *pd = reinterpret_cast<double *>(list + o_pd);
+        cudaError_t e = cudaMemsetAsync(nlist, 0, 2 * sizeof(unsigned int), st);
         if (e == cudaSuccess) {
             KRR_LAUNCHED(), centre_norms_kernel<<<(unsigned)((kt * 32 + 255) / 256), 256, 0, st>>>(C32, k, d, kt, cn32);
             e = cudaGetLastError();
@@ -945,7 +1038,17 @@ krr_status run_assign(Ctx *ctx, const float *X32, const double *X, int64_t n, in
         if (e == cudaSuccess) {
             const int64_t g = std::min<int64_t>((n + RCK_WARPS - 1) / RCK_WARPS, 152 * 8);
             KRR_LAUNCHED(), kmeans_recheck_kernel<<<(unsigned)std::max<int64_t>(g, 1), RCK_WARPS * 32, 0, st>>>(
-                X32, X, d, C32, C64, cn32, k, list, nlist, prev, out, delta);
+                X32, X, d, C32, C64, cn32, k, list, nlist, prev, out, delta, pstart, pcnt, prow, pj, npairs, pcap);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            KRR_LAUNCHED(), kmeans_pair_dist_kernel<<<152 * 4, 256, 0, st>>>(X, C64, d, prow, pj, npairs, pcap, pd);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
+            const unsigned gp = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 4));
+            KRR_LAUNCHED(), kmeans_pair_pick_kernel<<<gp, 256, 0, st>>>(list, nlist, pstart, pcnt, pj, pd, prev, out,
+                                                                         delta);
             e = cudaGetLastError();
         }
         ctx_free(ctx, list, bl);
