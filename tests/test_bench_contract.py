@@ -23,7 +23,7 @@ def _res(dominant, ms=7.2, classes=None):
                 classes=cls)
 
 
-def test_prediction_stage_against_section_8d_work():
+def test_prediction_stage_against_section_8d_work(monkeypatch):
     res = _res("predict")
     st = bench.stage_rooflines(res, PEAKS)["predict"]
     pairs = 8192 * 65536
@@ -37,7 +37,11 @@ def test_prediction_stage_against_section_8d_work():
     assert r["kernel"] == "predict" and r["bound"] == "alu" and r["unit"] == "Gexp/s"
     assert r["frac"] == pytest.approx(st["mufu_frac"])
     assert r["impl_alu_frac"] == pytest.approx(pairs * 238 / sec / (152 * 128 * 2070e6))
-    assert r["traffic"] is None  # no capture of this kernel source
+    # the captured traffic is used only for the kernel source it was taken on
+    key = ("predict", "bkrr2_n65536_t8192_d90_p16", bench._source_sha("predict"))
+    assert r["traffic"] == bench.TRAFFIC.get(key)
+    monkeypatch.setattr(bench, "_source_sha", lambda kind: "0" * 16)
+    assert bench.roofline(res, bench.stage_rooflines(res, PEAKS), PEAKS)["traffic"] is None
 
 
 def test_factor_stage_charges_each_solve_at_its_class_peak():
