@@ -72,7 +72,11 @@ def _mixture(n, t, d, k, seed):
     return X, Xt, rng.choice(n, k, replace=False).astype(np.int64)
 
 
-@pytest.mark.parametrize("n,t,d,k,iters", [(5000, 700, 12, 8, 10), (3333, 129, 90, 16, 5), (2500, 1, 3, 5, 0)])
+@pytest.mark.parametrize("n,t,d,k,iters", [(5000, 700, 12, 8, 10), (3333, 129, 90, 16, 5), (2500, 1, 3, 5, 0),
+                                           # the screen's centre tiles: 2 and 4 tiles of 64 (k = 256 its limit)
+                                           (4000, 100, 20, 100, 3), (3000, 30, 5, 256, 2),
+                                           # the general kernel: d > 96, k > 256
+                                           (3000, 50, 100, 12, 3), (4000, 40, 8, 300, 2)])
 def test_kmeans_partition_bit_exact(ctx, n, t, d, k, iters):
     X, Xt, init = _mixture(n, t, d, k, n)
     assign, route, perm, offsets, centers = K.krr_partition(ctx, cuda(X), cuda(Xt), K.KRR_PART_KMEANS, k,
