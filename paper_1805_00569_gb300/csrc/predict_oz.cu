@@ -249,11 +249,11 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
     const uint32_t base = smem_u32(oz_dyn);
     OzPSmem &sm = *reinterpret_cast<OzPSmem *>(oz_dyn + (((base + 1023u) & ~1023u) - base));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int j = blockIdx.x;
+    const int j = blockIdx.y;
     const PartDesc P = parts[j];
     const int64_t cnt = toff ? toff[j + 1] - toff[j] : t;
     const int64_t tstart = toff ? toff[j] : 0;
-    const int64_t q0 = (int64_t)blockIdx.y * OZ_M;
+    const int64_t q0 = (int64_t)blockIdx.x * OZ_M;
     if (q0 >= cnt) return;
     const int nchunks = P.T * (KRR_TILE / OZ_N);
     const int G = pp.nsig * pp.nlam;
@@ -1051,8 +1051,10 @@ cudaError_t launch_predict_oz(cudaStream_t st, const Model &M, const CUtensorMap
                 pp.c_hi[i] = (float)c;
                 pp.c_lo[i] = (float)(c - (double)(float)c);
             }
-            // for the routed form the grouped rows start at toff[j]; the tile count bounds every partition
-            dim3 grid((unsigned)M.p, (unsigned)((t + OZ_M - 1) / OZ_M));
+            // for the routed form the grouped rows start at toff[j]; the tile count bounds every
+            // partition.  Test tiles run fastest: the CTAs in flight share two or three
+            // partitions' training slices, which L2 then serves to every test tile
+            dim3 grid((unsigned)((t + OZ_M - 1) / OZ_M), (unsigned)M.p);
             KRR_LAUNCHED(), predict_oz_kernel<<<grid, OZP_THREADS, oz_psmem_bytes(), st>>>(
                 tmA, tmB, M.d_parts, M.d_solves, M.alpha2, M.ozex, M.nrm, tex, tnrm, t, toff, routed ? tidx : nullptr,
                 pp, routed, M.prows, out, d_err);
