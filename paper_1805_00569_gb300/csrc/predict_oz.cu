@@ -136,6 +136,69 @@ __device__ __forceinline__ df oz_distance(float s0, float s1, float s2, float s3
 // ---------------------------------------------------------------- slicing
 // Row r of the output takes source row map[r] (or r); rows >= nreal are zero.
 // S: [5][nout][dpz] bf16; ex: exponent per row; nrm (optional): ||x||^2 as df.
+//
+// The slices of a feature x are the base-256 digits of v = x 2^(7 - e) (e:
+// the exponent of the row's largest magnitude, |v| < 128), each the nearest
+// integer (ties to even) to what the digits before it leave:
+//   c_0 = rint(v), c_1 = rint((v - c_0) 256), ...
+// every step exact (but the scaling, which can underflow to a signed zero).
+// They are taken here in 64-bit integers from the double's bits: F = v 2^56
+// (below 2^63), truncated towards zero with a sticky flag for the bits
+// shifted out (their sign is x's), so a remainder exactly half-way is
+// resolved as the exact value would be -- the same digits, and the same
+// signed zeros, as the FP64 steps, without FP64 instructions (GB300's FP64
+// pipe runs at 1/64 of FP32).
+
+// nearest integer to R / 2^k, ties to even; dsign: sign of the part of the
+// exact value below R's last place (0 when there is none)
+__device__ __forceinline__ long long oz_digit(long long R, int k, int dsign) {
+    const long long q = R >> k;
+    const long long rem = R - q * (1ll << k);
+    const long long half = 1ll << (k - 1);
+    const bool up = rem > half || (rem == half && (dsign > 0 || (dsign == 0 && (q & 1))));
+    return up ? q + 1 : q;
+}
+
+// the OZ_SLICES bf16 digits of a finite x for row exponent e
+__device__ __forceinline__ void oz_digits(double x, int e, uint16_t *dig) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const bool neg = (b >> 63) != 0;
+    const int E = (int)((b >> 52) & 0x7FF);
+    unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    if (E) m |= 1ull << 52;
+    const int sh = max(E, 1) - 1012 - e;  // F = m 2^sh
+    // the FP64 steps scale x by 2^(7 - e) first: a result at or below 2^-1075
+    // in magnitude rounds to a signed zero (v = m 2^(t - 1075)), whose digits
+    // are that zero and then +0
+    const int t = max(E, 1) + 7 - e;
+    const bool vzero = m == 0 || (t <= 0 && (-t >= 53 || m <= (1ull << -t)));
+    long long F = 0;
+    bool sticky = false;
+    if (!vzero) {
+        if (sh >= 0) {
+            F = (long long)(m << sh);
+        } else if (sh > -64) {
+            F = (long long)(m >> -sh);
+            sticky = (m & ((1ull << -sh) - 1)) != 0;
+        } else {
+            sticky = true;
+        }
+    }
+    const int dsign = sticky ? (neg ? -1 : 1) : 0;
+    long long R = neg ? -F : F;
+#pragma unroll
+    for (int s = 0; s < OZ_SLICES; ++s) {
+        const int k = 56 - 8 * s;
+        const long long c = oz_digit(R, k, dsign);  // |c| <= 128
+        // rint of a negative value above -1/2 is -0 (and of a negative zero at the first digit)
+        const bool negz = c == 0 && (R < 0 || (R == 0 && dsign < 0) || (s == 0 && neg && vzero));
+        uint32_t fb = __float_as_uint(__int_as_float(0x4B400000 + (int)c) - 12582912.0f);  // (float)c, exact
+        if (negz) fb |= 0x80000000u;
+        dig[s] = (uint16_t)(fb >> 16);  // bf16: at most 8 significant bits, exact
+        R -= c * (1ll << k);
+    }
+}
+
 __global__ void oz_slice_kernel(const double *__restrict__ X, int32_t d, int32_t dpz, const int64_t *__restrict__ map,
                                 int64_t nreal, int64_t nout, __nv_bfloat16 *__restrict__ S, int32_t *__restrict__ ex,
                                 float2 *__restrict__ nrm) {
@@ -143,31 +206,61 @@ __global__ void oz_slice_kernel(const double *__restrict__ X, int32_t d, int32_t
     if (r >= nout) return;
     const bool real = r < nreal;
     const double *x = X + (real ? (map ? map[r] : r) : 0) * d;
-    double mx = 0.0;
+    unsigned long long mxb = 0;  // largest magnitude's bits
+    bool finite = true;
     df_acc a;
     dfa_zero(a);
     if (real)
         for (int f = 0; f < d; ++f) {
             const double v = x[f];
-            mx = fmax(mx, fabs(v));
+            const unsigned long long ab = (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+            finite = finite && ab < 0x7FF0000000000000ull;
+            mxb = ab > mxb ? ab : mxb;
             const float h = __double2float_rn(v), l = __double2float_rn(v - (double)h);
             dfa_fma(a, h, l, h, l);
         }
-    int e = 0;
-    if (mx > 0.0) frexp(mx, &e);  // mx = m 2^e, m in [0.5, 1): |x| 2^-e < 1
-    ex[r] = e;
     if (nrm) {
         const df v = dfa_value(a);
         nrm[r] = make_float2(v.hi, v.lo);
     }
-    for (int f = 0; f < dpz; ++f) {
-        double v = (real && f < d) ? ldexp(x[f], 7 - e) : 0.0;  // |v| < 128
+    int e = 0;
+    if (!finite) {  // the FP64 steps (a row with an infinite or NaN feature)
+        double mx = 0.0;
+        for (int f = 0; f < d; ++f) mx = fmax(mx, fabs(x[f]));
+        if (mx > 0.0) frexp(mx, &e);
+        ex[r] = e;
+        for (int f = 0; f < dpz; ++f) {
+            double v = f < d ? ldexp(x[f], 7 - e) : 0.0;
 #pragma unroll
-        for (int s = 0; s < OZ_SLICES; ++s) {
-            const double c = rint(v);
-            S[((int64_t)s * nout + r) * dpz + f] = __float2bfloat16_rn((float)c);
-            v = (v - c) * 256.0;
+            for (int s = 0; s < OZ_SLICES; ++s) {
+                const double c = rint(v);
+                S[((int64_t)s * nout + r) * dpz + f] = __float2bfloat16_rn((float)c);
+                v = (v - c) * 256.0;
+            }
         }
+        return;
+    }
+    if (mxb) {  // frexp's exponent of the largest magnitude: mx = f 2^e, f in [0.5, 1)
+        const int E = (int)(mxb >> 52);
+        const unsigned long long m = (mxb & 0xFFFFFFFFFFFFFull) | (E ? 1ull << 52 : 0ull);
+        e = (64 - __clzll((long long)m)) + max(E, 1) - 1075;
+    }
+    ex[r] = e;
+    // eight features at a time: one 16-byte store per slice (dpz is a multiple of 32)
+    for (int f0 = 0; f0 < dpz; f0 += 8) {
+        uint32_t pk[OZ_SLICES][4] = {};
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int f = f0 + u;
+            uint16_t dg[OZ_SLICES];
+            oz_digits((real && f < d) ? x[f] : 0.0, e, dg);
+#pragma unroll
+            for (int s = 0; s < OZ_SLICES; ++s) pk[s][u >> 1] |= (uint32_t)dg[s] << (16 * (u & 1));
+        }
+#pragma unroll
+        for (int s = 0; s < OZ_SLICES; ++s)
+            *reinterpret_cast<uint4 *>(S + ((int64_t)s * nout + r) * dpz + f0) =
+                make_uint4(pk[s][0], pk[s][1], pk[s][2], pk[s][3]);
     }
 }
 
