@@ -641,13 +641,26 @@ __global__ void rowsum_reduce_kernel(const GroupDesc *__restrict__ groups, const
     const int a = blockIdx.y, T = G.T, c = threadIdx.x;
     if (a >= T) return;
     const int64_t g0 = (int64_t)G.isig * rstot + rsoff[G.part];
-    double sum = 0.0;
+    // the FP32 pieces (all >= 0) summed as a double-float (TwoSum into s,
+    // compensation in cs): within ~2^-47 of the exact row sum, without FP64
+    // instructions (GB300's FP64 pipe runs at 1/64 of FP32)
+    float s = 0.f, cs = 0.f;
+    auto add = [&](float v) {
+        float t, e;
+        two_sum(s, v, t, e);
+        s = t;
+        cs += e;
+    };
     for (int b = 0; b <= a; ++b) {
         const int64_t sl = (g0 + (int64_t)a * T + b) * 8;
+        float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) sum += (double)rsR[(sl + u) * KRR_TILE + c];
+        for (int u = 0; u < 8; ++u) v[u] = rsR[(sl + u) * KRR_TILE + c];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) add(v[u]);
     }
-    for (int b = a + 1; b < T; ++b) sum += (double)rsC[(g0 + (int64_t)a * T + b) * KRR_TILE + c];
+    for (int b = a + 1; b < T; ++b) add(rsC[(g0 + (int64_t)a * T + b) * KRR_TILE + c]);
+    const double sum = (double)s + (double)cs;
     const int e = a * KRR_TILE + c;
     for (int l = 0; l < G.nlam; ++l) {
         const SolveDesc S = solves[G.solve0 + l];
