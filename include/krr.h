@@ -115,7 +115,7 @@ size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
  *     assignment with the final centres defines the partitions and routes
  *     the test rows.  Assignments are bit-exact with that definition (an FP64
  *     recheck decides near ties).  Workspace per assignment pass (d <= 96,
- *     p <= 256): about 28 rows + 4 p bytes.
+ *     p <= 256): about 76 rows + 4 p bytes.
  *   KBALANCE: the K-means centres as above, then the balanced assignment of
  *     Alg. K-balance Clustering: rows in index order each take the nearest
  *     centre (squared FP64 distance in feature order, strict <, lowest index)
@@ -241,7 +241,7 @@ krr_status krr_group_rows(krr_ctx *ctx, const int32_t *assign, int64_t n, int32_
  *   squared distance in feature order, strict <, lowest index; bit-exact
  *   through the FP64 recheck of near ties) of X [n x d] to the FP64 centres
  *   C [k x d]; assign [n] int32 output.  Workspace n d 4 bytes, plus for
- *   d <= 96 and k <= 256 (the tiled screen) about 28 n + 4 k bytes for the
+ *   d <= 96 and k <= 256 (the tiled screen) about 76 n + 4 k bytes for the
  *   rows with several candidates and their (row, centre) pairs.
  * krr_kmeans_block_sums: first half of the centre step: for each block of
  *   1024 consecutive rows of X (X must start at a block boundary of the
