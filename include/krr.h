@@ -115,7 +115,7 @@ size_t krr_ctx_bytes_in_use(const krr_ctx *ctx);
  *     assignment with the final centres defines the partitions and routes
  *     the test rows.  Assignments are bit-exact with that definition (an FP64
  *     recheck decides near ties).  Workspace per assignment pass (d <= 96,
- *     p <= 256): about 76 rows + 4 p bytes.
+ *     p <= 256): about 76 bytes per row + 4 p bytes.
  *   KBALANCE: the K-means centres as above, then the balanced assignment of
  *     Alg. K-balance Clustering: rows in index order each take the nearest
  *     centre (squared FP64 distance in feature order, strict <, lowest index)
