@@ -236,19 +236,26 @@ kmeans_screen_kernel(const float *__restrict__ X32, int64_t n, int32_t d, const 
     const int64_t i0 = (int64_t)blockIdx.x * SCR_ROWS;
     const int nrow = (int)min((int64_t)SCR_ROWS, n - i0);
     {
-        // the tile's rows, all loads issued before the first shared store
-        constexpr int NE = SCR_ROWS * DP / SCR_THREADS;
-        float v[NE];
+        // the tile's rows: warp w takes rows w, w + 8, ..., its lanes the
+        // features lane, lane + 32, lane + 64; all loads issued before the
+        // first shared store
+        constexpr int NQ = (DP + 31) / 32, NR = SCR_ROWS / (SCR_THREADS / 32);
+        const int w = tid >> 5, lane = tid & 31;
+        float v[NR][NQ];
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-            const int e = tid + u * SCR_THREADS, r = e / DP, f = e % DP;
-            v[u] = (r < nrow && f < d) ? X32[(i0 + r) * d + f] : 0.f;
-        }
+        for (int u = 0; u < NR; ++u)
 #pragma unroll
-        for (int u = 0; u < NE; ++u) {
-            const int e = tid + u * SCR_THREADS, r = e / DP, f = e % DP;
-            xs[f * SCR_XL + r] = v[u];
-        }
+            for (int q = 0; q < NQ; ++q) {
+                const int r = w + u * (SCR_THREADS / 32), f = lane + 32 * q;
+                v[u][q] = (r < nrow && f < d) ? X32[(i0 + r) * d + f] : 0.f;
+            }
+#pragma unroll
+        for (int u = 0; u < NR; ++u)
+#pragma unroll
+            for (int q = 0; q < NQ; ++q) {
+                const int r = w + u * (SCR_THREADS / 32), f = lane + 32 * q;
+                if (f < DP) xs[f * SCR_XL + r] = v[u][q];
+            }
     }
     for (int j = tid; j < kt; j += SCR_THREADS) cn[j] = cn32[j];
     __syncthreads();
@@ -303,23 +310,32 @@ kmeans_screen_kernel(const float *__restrict__ X32, int64_t n, int32_t d, const 
             }
     }
     __syncthreads();
-    if (tid >= SCR_ROWS) return;
-    const int r = tid;
+    // per row: two threads (lanes l and l + 16 of a warp), each over half the
+    // centres; the best upper bound is a minimum (any order), the candidates
+    // a count and the first of them
+    const int r = (tid >> 5) * 16 + (tid & 15), h = (tid >> 4) & 1;
     const bool live = r < nrow;
     const float bscale = (float)(d + 16) * 5.9604644775390625e-8f * 1.27f * 2.0f;
     const float babs = assign_abs_bound(d);
-    int arg = -1;
-    if (live) {
-        float best_hi = INFINITY;
-        for (int j = 0; j < k; ++j) best_hi = fminf(best_hi, dist[r * DL + j] + (bscale * (xn[r] + cn[j]) + babs));
-        int ncand = 0, first = -1;
-        for (int j = 0; j < k; ++j)
+    const int kh = (k + 1) / 2, j0 = h * kh, j1 = h ? k : kh;
+    float best_hi = INFINITY;
+    if (live)
+        for (int j = j0; j < j1; ++j) best_hi = fminf(best_hi, dist[r * DL + j] + (bscale * (xn[r] + cn[j]) + babs));
+    best_hi = fminf(best_hi, __shfl_xor_sync(0xffffffffu, best_hi, 16));
+    int ncand = 0, first = -1;
+    if (live)
+        for (int j = j0; j < j1; ++j)
             if (assign_candidate(dist[r * DL + j], bscale * (xn[r] + cn[j]) + babs, best_hi)) {
                 if (ncand == 0) first = j;
                 ++ncand;
             }
-        if (ncand == 1) {
-            arg = first;
+    const int ncand_o = __shfl_xor_sync(0xffffffffu, ncand, 16);
+    const int first_o = __shfl_xor_sync(0xffffffffu, first, 16);
+    int arg = -1;
+    if (live && h == 0) {
+        const int nc = ncand + ncand_o;
+        if (nc == 1) {
+            arg = ncand == 1 ? first : first_o;
             out[i0 + r] = arg;
         } else {
             list[atomicAdd(nlist, 1u)] = (int32_t)(i0 + r);  // decided by the recheck
