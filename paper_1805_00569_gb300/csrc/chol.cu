@@ -80,7 +80,8 @@ __device__ __forceinline__ TaskGeom decode_task(int mode, int64_t local, int K0,
 
 // ---------------------------------------------------------------- potrf
 // Cholesky factor L and inverse Z = L^-1 of one 128 x 128 diagonal tile in a
-// single right-looking sweep with the tile held in registers.  512 threads:
+// single right-looking sweep with the tile held in registers (the FP64 path;
+// FP32 factors use potrf_blocked_kernel below).  512 threads:
 // thread (rg = tid / 16, cg = tid % 16) owns the 4 x 8 block of rows
 // 4 rg .. 4 rg + 3 and columns 8 cg .. 8 cg + 7, so a step reads 4 row and 8
 // column values of the broadcast vector for its 32 updates.  An entry (i, j)
@@ -1223,8 +1224,8 @@ cudaError_t run_chol_plan_t(cudaStream_t st, const std::vector<CholLaunch> &plan
                             const CUtensorMap *tmapLo, const float *Kfirst, const CUtensorMap *tmapK, int *d_err,
                             Prof *prof) {
     const size_t po_sm = (size_t)KRR_TILE * 129 * sizeof(T);
-    allow_max_dyn_smem(potrf_tile_kernel<T>);
-    allow_max_dyn_smem(potrf_blocked_kernel);
+    if constexpr (sizeof(T) == 4) allow_max_dyn_smem(potrf_blocked_kernel);  // FP32 factors: blocked
+    else allow_max_dyn_smem(potrf_tile_kernel<T>);                           // FP64 path
     int dev = 0, nsm = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
