@@ -312,8 +312,9 @@ __device__ __forceinline__ void tmem_ld_32x32b_x8(uint32_t taddr, float *v) {
 // exponential drops arguments below -87), and its product with alpha_hi is
 // added to the accumulator's low part.  Per term that is an error below 4e-13
 // of the largest term times |alpha|, under the double-float path's own
-// rounding of the sum.  The test is taken warp-wide (all 32 rows far), so the
-// warp never diverges.
+// rounding of the sum.  The test is per row (lane); a lane's other columns
+// are queued and the warp runs them through the double-float path one per
+// lane per round.
 constexpr float OZ_FAR = 20.0f;
 __device__ __forceinline__ float ex2_approx(float x) {
     float y;
@@ -552,15 +553,16 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
 #pragma unroll
                 for (int is = 0; is < OZ_NSP; ++is)
                     wsh |= __any_sync(0xffffffffu, ksh[is] != 0) ? (1u << is) : 0u;
-                // sigmas for which some column of this group can be far for all 32 rows
+                // sigmas for which some lane has a far column in this group
                 const float dfar = fminf(dmin, dpub);
                 unsigned wfar = 0;
 #pragma unroll
                 for (int is = 0; is < OZ_NSP; ++is)
-                    wfar |= __all_sync(0xffffffffu, is < pp.nsig && (dM - dfar) * chi[is] < -OZ_FAR) ? (1u << is)
+                    wfar |= __any_sync(0xffffffffu, is < pp.nsig && (dM - dfar) * chi[is] < -OZ_FAR) ? (1u << is)
                                                                                                        : 0u;
-                // OZP_COLS columns per iteration: their exponentials are
-                // independent chains the scheduler can interleave.  Padded training rows have
+                // the other sigmas: OZP_COLS columns per iteration through the
+                // double-float path (their exponentials are independent chains
+                // the scheduler can interleave).  Padded training rows have
                 // alpha = 0 exactly, so they need no test.
 #pragma unroll 1
                 for (int k = 0; k < OZP_SUB; k += OZP_COLS) {
@@ -573,27 +575,7 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                     }
 #pragma unroll
                     for (int is = 0; is < OZ_NSP; ++is) {
-                        if (is < pp.nsig) {
-                            bool far = (wfar >> is) & 1u;  // false while the row has no real term (D_min = inf)
-#pragma unroll
-                            for (int u = 0; u < OZP_COLS; ++u) far = far && (D[u].hi - dfar) * chi[is] < -OZ_FAR;
-                            if ((wfar >> is) & 1u && __all_sync(0xffffffffu, far)) {
-                                float kf[OZP_COLS];
-#pragma unroll
-                                for (int u = 0; u < OZP_COLS; ++u)
-                                    kf[u] = ex2_approx(__fmaf_rn(D[u].hi, chi[is], shh[is]) * 1.44269504088896341f);
-#pragma unroll
-                                for (int il = 0; il < OZ_NLP; ++il)
-                                    if (il < pp.nlam) {
-#pragma unroll
-                                        for (int u = 0; u < OZP_COLS; u += 2) {
-                                            const float4 a = cd.a2[is * OZ_NLP + il][(col + u) >> 1];
-                                            acc[is][il].c = __fmaf_rn(kf[u], a.x, acc[is][il].c);
-                                            acc[is][il].c = __fmaf_rn(kf[u + 1], a.z, acc[is][il].c);
-                                        }
-                                    }
-                                continue;
-                            }
+                        if (is < pp.nsig && !((wfar >> is) & 1u)) {
                             const df cs = df_make(chi[is], clo[is]);
                             df kv[OZP_COLS];
 #pragma unroll
@@ -614,6 +596,52 @@ predict_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant
                                         dfa_fma(acc[is][il], kv[u].hi, kv[u].lo, a.x, a.y);
                                         dfa_fma(acc[is][il], kv[u + 1].hi, kv[u + 1].lo, a.z, a.w);
                                     }
+                                }
+                        }
+                    }
+                }
+                // sigmas with far columns: each lane takes its own far columns
+                // in FP32 and queues the others, which the warp then runs
+                // through the double-float path one per lane per round, so
+                // the rounds are the longest queue, not the columns any lane needs
+#pragma unroll
+                for (int is = 0; is < OZ_NSP; ++is) {
+                    if (!((wfar >> is) & 1u)) continue;
+                    unsigned nf = 0;  // this lane's columns that are not far
+#pragma unroll
+                    for (int k = 0; k < OZP_SUB; ++k) {
+                        const float dh = sm.dist[et][k].x;
+                        const bool far = (dh - dfar) * chi[is] < -OZ_FAR;  // false while D_min = inf
+                        if (far) {
+                            const float kf = ex2_approx(__fmaf_rn(dh, chi[is], shh[is]) * 1.44269504088896341f);
+                            const int col = (int)col0 + k;
+#pragma unroll
+                            for (int il = 0; il < OZ_NLP; ++il)
+                                if (il < pp.nlam) {
+                                    const float4 a = cd.a2[is * OZ_NLP + il][col >> 1];
+                                    acc[is][il].c = __fmaf_rn(kf, (k & 1) ? a.z : a.x, acc[is][il].c);
+                                }
+                        } else {
+                            nf |= 1u << k;
+                        }
+                    }
+                    const df cs = df_make(chi[is], clo[is]);
+                    const float2 sv = sm.shift[is][et];  // (0, 0) for an unshifted row
+                    while (__any_sync(0xffffffffu, nf != 0)) {
+                        if (nf != 0) {
+                            const int k = __ffs(nf) - 1;
+                            nf &= nf - 1;
+                            const float2 dv = sm.dist[et][k];
+                            df x = df_mul(df_make(dv.x, dv.y), cs);
+                            if (wsh & (1u << is)) x = df_add(x, df_make(sv.x, sv.y));
+                            const df kv = df_exp_nonpos<false>(x, sm.exptab);
+                            const int col = (int)col0 + k;
+#pragma unroll
+                            for (int il = 0; il < OZ_NLP; ++il)
+                                if (il < pp.nlam) {
+                                    const float4 a = cd.a2[is * OZ_NLP + il][col >> 1];
+                                    if (k & 1) dfa_fma(acc[is][il], kv.hi, kv.lo, a.z, a.w);
+                                    else dfa_fma(acc[is][il], kv.hi, kv.lo, a.x, a.y);
                                 }
                         }
                     }
